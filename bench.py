@@ -1,0 +1,323 @@
+"""Benchmark of the peridynamic explicit step: bond updates per second.
+
+One step = one fused force + velocity-Verlet kernel of the whole lattice (PMB),
+or the dilatation pass plus the fused force + update kernel (LPS). A bond
+update is one directed bond processed in one step, all passes of that step.
+
+Default workload: 3D block 64^3 (h = 1/64 m, m = 3, 30,289,512 directed bonds),
+PMB with breaking at s_c = 1e-3, Gaussian velocity pulse and pre-notch,
+FP32-compensated bond arithmetic with FP64 integrator state. Its per-step
+working set (~45 MB) fits in the 129 MB L2, so L2 is flushed (a 512 MB write)
+before every timed step and each step is timed alone with CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload block64|lps128|plate50]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Multi-GPU: independent replicas (the step does not shard across GPUs here), one
+per rank; value = all ranks' bond updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1806_06917_gb300 import workloads as W  # noqa: E402
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# FP32 arithmetic of one bond as the kernels evaluate it (hand count; an FMA is
+# one operation; the 2 MUFU ops per bond are not included).
+FP32_OPS_PER_BOND = {"pmb3": 24, "pmb2": 18, "lps_dil": 19, "lps_force": 30}
+
+
+def workload(name):
+    if name == "block64":
+        wl = W.block3d_pulse(nside=64)
+        return wl, "block3d_64_pmb_break: 64^3 lattice, h=1/64 m, m=3, PMB s_c=1e-3, pulse + pre-notch"
+    if name == "lps128":
+        wl = W.block3d_lps(nside=128)
+        return wl, "block3d_128_lps: 128^3 lattice, h=1/128 m, m=3, LPS K=40 GPa mu=30 GPa"
+    if name == "plate50":
+        wl = W.plate2d(nside=50)
+        return wl, "plate2d_50_pmb: 50^2 lattice, h=0.02 m, m=3, PMB, collar velocities"
+    raise SystemExit("unknown workload " + name)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return None
+
+
+def make_sim(pd, wl, precision, stream):
+    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision)
+    sim = pd.pd_create(g, m, r)
+    pd.pd_build_neighbors(sim, stream)
+    if wl.notch is not None:
+        pd.pd_break_bonds(sim, wl.notch.axis, wl.notch.pos, np.asarray(wl.notch.lo), np.asarray(wl.notch.hi),
+                          stream)
+    return sim
+
+
+def time_steps(pd, torch, sim, wl, steps, warmup, stream, flush):
+    """Per-step CUDA-event durations (ms), L2 flushed before each timed step."""
+    pd.pd_set_state(sim, u=wl.u0, v=wl.v0, stream=stream)
+    if wl.bc_kind is not None and wl.bc_kind.any():
+        pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val, stream)
+    pd.pd_step_explicit(sim, warmup, stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        pd.pd_step_explicit(sim, 1, stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def cpu_baseline(wl, target_s=12.0, max_steps=50):
+    """The FP64 oracle (as it stands) on the host cores: a bounded number of explicit
+    steps of the same workload."""
+    from oracle import oracle as O
+    t0 = time.time()
+    bonds = O.neighbors(wl.grid)
+    if wl.notch is not None:
+        O.break_notch(wl.grid, bonds, wl.notch)
+    dt = wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
+    st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
+    st.run(dt, 1)                                    # computes f^0 and one step
+    setup = time.time() - t0
+    t1 = time.time()
+    st.run(dt, 1)
+    one = max(time.time() - t1, 1e-6)
+    n = int(max(1, min(max_steps, target_s / one)))
+    t2 = time.time()
+    st.run(dt, n)
+    el = time.time() - t2
+    return {"value": bonds.nbonds * n / el, "unit": "bond-updates/s", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": "%d explicit steps of the full workload (FP64 C oracle, OpenMP over points); "
+                      "setup %.1f s not timed" % (n, setup)}, bonds.nbonds
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, desc = workload(args.workload)
+    from oracle import oracle as O
+    bonds = O.neighbors(wl.grid)
+    if wl.notch is not None:
+        O.break_notch(wl.grid, bonds, wl.notch)
+    dt = wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
+    st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
+    st.run(dt, max(args.warmup, 1))
+    t0 = time.time()
+    st.run(dt, args.steps)
+    el = time.time() - t0
+    val = bonds.nbonds * args.steps / el
+    line = {"impl": "reference", "metric": "bond updates/s (explicit step)", "value": val,
+            "unit": "bond-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "bonds": bonds.nbonds},
+            "cpu_baseline": {"value": val, "unit": "bond-updates/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "%d explicit steps of the full workload after %d warm-up steps"
+                                       % (args.steps, max(args.warmup, 1))},
+            "e2e": {"value": val, "unit": "bond-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="block64", choices=["block64", "lps128", "plate50"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path and LPS side measurements")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1806_06917_gb300 import pd
+
+    wl, desc = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sim = make_sim(pd, wl, pd.PD_FP32C, stream)
+    nbonds = pd.pd_bond_count(sim)
+    key = "lps" if wl.mat.model == W.LPS else ("pmb3" if wl.grid.dim == 3 else "pmb2")
+    launches_per_step = 2 if key == "lps" else 1
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with Clocks(local) as clk:
+        t_wall = time.time()
+        durs = time_steps(pd, torch, sim, wl, args.steps, args.warmup, stream, flush)
+        t_wall = time.time() - t_wall
+    barrier()
+    ms = float(np.mean(durs))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nbonds / (ms * 1e-3)
+
+    # end to end through the public API: initial state from pinned host memory,
+    # the timed steps (graph-replayed), final state back to pinned host memory
+    u_h = torch.from_numpy(wl.u0).pin_memory()
+    v_h = torch.from_numpy(wl.v0).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    v_o = torch.empty_like(v_h).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    pd.pd_set_state(sim, u=u_h.numpy(), v=v_h.numpy(), stream=stream)
+    pd.pd_step_explicit(sim, args.steps, stream)
+    pd.pd_get_state(sim, u=u_o.numpy(), v=v_o.numpy(), stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": world * nbonds * args.steps / (e2e_ms * 1e-3), "unit": "bond-updates/s",
+           "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8 / args.steps,
+           "d2h_bytes_per_step": (u_o.numel() + v_o.numel()) * 8 / args.steps,
+           "note": "pd_set_state + pd_step_explicit(K) + pd_get_state with pinned host buffers, "
+                   "copies amortised over the K steps; L2 not flushed"}
+
+    # roofline of the dominant kernel: FP32 ALU (not HBM) bound
+    ops = FP32_OPS_PER_BOND[key] if key != "lps" else FP32_OPS_PER_BOND["lps_dil"] + FP32_OPS_PER_BOND["lps_force"]
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ops * nbonds / (ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP32 ops)",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz, one op per lane per clock",
+                "ops_per_bond": ops, "kernel": "pmb_fast<3,2,true>" if key == "pmb3" else key,
+                "launch_ms": ms / launches_per_step if key != "lps" else ms}
+    peaks = measured_peaks()
+    if peaks:
+        bytes_pt = 180.0 if key != "lps" else 250.0
+        roofline["hbm_frac_of_measured"] = (bytes_pt * wl.grid.npoints / (ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
+
+    line = {"metric": "bond updates/s (explicit step, FP32-compensated)", "value": value,
+            "unit": "bond-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bond arithmetic), f64 (integrator state)", "data": "synthetic",
+            "config": {"workload": desc, "bonds": nbonds, "points": wl.grid.npoints,
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas",
+                       "launches_per_step": launches_per_step},
+            "gpu_launches": args.steps * launches_per_step,
+            "roofline": roofline, "e2e": e2e}
+
+    if not args.no_extras and rank == 0:
+        # the plain all-FP64 GPU path on the same workload
+        sim64 = make_sim(pd, wl, pd.PD_FP64, stream)
+        d64 = time_steps(pd, torch, sim64, wl, max(3, min(args.steps, 10)), 3, stream, flush)
+        ms64 = float(np.mean(d64))
+        line["fp64_path"] = {"value": nbonds / (ms64 * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms64,
+                             "steps": len(d64), "ratio_fp32c_over_fp64": ms64 / ms}
+        sim64.close()
+        if args.workload == "block64":
+            wl2, desc2 = workload("lps128")
+            sim2 = make_sim(pd, wl2, pd.PD_FP32C, stream)
+            d2 = time_steps(pd, torch, sim2, wl2, 10, 3, stream, flush)
+            ms2 = float(np.mean(d2))
+            nb2 = pd.pd_bond_count(sim2)
+            ops2 = FP32_OPS_PER_BOND["lps_dil"] + FP32_OPS_PER_BOND["lps_force"]
+            line["lps128"] = {"workload": desc2, "value": nb2 / (ms2 * 1e-3), "unit": "bond-updates/s",
+                              "ms_per_step": ms2, "steps": len(d2), "launches_per_step": 2,
+                              "alu_frac": ops2 * nb2 / (ms2 * 1e-3) / 1e12 / peak}
+            sim2.close()
+
+    line["clocks"] = clk.summary()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(wl)
+        line["cpu_baseline"] = cb
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * pd.h -- C ABI of libpd, the GB300 (sm_103a) peridynamics hot path.
+ *
+ * The library evaluates the nonlocal internal force of peridynamics on a uniform
+ * lattice (the EMU nodal discretization of Sec. 3.1 of Diehl et al., "An
+ * asynchronous and task-based implementation of peridynamics utilizing HPX"):
+ *   - the bond-based prototype micro-elastic brittle (PMB) model with bond
+ *     breaking at a critical stretch (Eq. (3), Algorithm 1's loop structure);
+ *   - the state-based linear peridynamic solid (LPS): a dilatation pass, then a
+ *     force pass (Eq. (4), Algorithm 2);
+ *   - the explicit central-difference / velocity-Verlet update (Eqs. (7)-(10),
+ *     Algorithm 4);
+ *   - the tangent Jacobian-vector product and its adjoint, the matrix-free
+ *     form of the stiffness of Eq. (6) / Algorithm 3.
+ *
+ * Conventions for every call:
+ *   - Return value: PD_OK (0) or a negative PD_E* code; pd_last_error() gives
+ *     the message of the last failure on the calling thread. On failure no
+ *     output is written unless the call says otherwise, and the simulation keeps
+ *     its previous state.
+ *   - Points are in user order at this boundary: i = x + nx*(y + ny*z), reference
+ *     position X_i = origin + h*(x, y, z). Vectors are AoS (npoints, dim) FP64.
+ *     The library keeps its own (Morton, tile-major) order internally.
+ *   - Every array argument may be a host pointer or a device pointer of the
+ *     current device (the library copies with cudaMemcpyDefault). Host arrays
+ *     are read or written before the call returns only for calls marked
+ *     "synchronous"; for the others a host array must stay valid until the
+ *     stream has reached the call (as with cudaMemcpyAsync).
+ *   - Caller-owned arrays are borrowed for the duration of the call; the library
+ *     owns every buffer it allocates and frees them in pd_destroy().
+ *   - stream: a cudaStream_t passed as void*; NULL selects the simulation's own
+ *     stream. Work is ordered on that stream.
+ *   - A pd_sim is not thread-safe: calls on one simulation must not overlap.
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define PD_OK 0
+#define PD_EINVAL (-1)     /* bad argument or unsupported configuration */
+#define PD_ENOMEM (-2)     /* device or host allocation failed */
+#define PD_ECUDA (-3)      /* a CUDA runtime call failed */
+#define PD_ETIMEOUT (-4)   /* a bounded wait ran out */
+#define PD_EBUSY (-5)      /* the resource is in use */
+#define PD_ENOTREADY (-6)  /* result not available yet */
+#define PD_ESTATE (-7)     /* call out of order (e.g. force before neighbours) */
+
+/* ------------------------------------------------------------------- constants */
+#define PD_MODEL_PMB 0     /* bond-based prototype micro-elastic brittle */
+#define PD_MODEL_LPS 1     /* state-based linear peridynamic solid (3D only) */
+
+#define PD_FP32C 0         /* FP32 bond arithmetic on per-tile reference-frame
+                              displacements, FP64 integrator state */
+#define PD_FP64 1          /* all-FP64 bond arithmetic and state */
+
+#define PD_BC_FREE 0
+#define PD_BC_VELOCITY 1       /* prescribed velocity on this DOF */
+#define PD_BC_DISPLACEMENT 2   /* prescribed displacement, velocity held at 0 */
+
+#define PD_FORCE_UPDATE_BREAKING 1u   /* pd_force: break bonds with s > s_c */
+
+#define PD_JVP_MASK_DIRICHLET 1u      /* pd_jvp/pd_vjp: identity on prescribed-
+                                         displacement DOFs, zero coupling to them */
+
+/* ---------------------------------------------------------------- descriptions */
+
+/* Uniform lattice: npoints = n[0]*n[1]*n[2] (n[2] = 1 in 2D), spacing h,
+ * horizon delta = m*h. B_delta(X_i) = { X_j : j != i, |X_j - X_i| <= delta }
+ * (Sec. 3.1), decided on integer offsets: a^2 + b^2 + c^2 <= m^2. */
+typedef struct {
+    int32_t dim;        /* 2 or 3 */
+    int32_t n[3];       /* points per axis, each >= 1 */
+    int32_t m;          /* horizon factor, 1 <= m <= 24 */
+    int32_t reserved;   /* must be 0 */
+    double h;           /* lattice spacing (m), > 0 */
+    double origin[3];
+} pd_grid;
+
+/* Material. PMB micromodulus (the paper does not give it; literature values):
+ * 3D c = 18 K'/(pi delta^4) with K' = E/(3(1-2nu)), nu = 1/4; 2D plane stress
+ * c = 9E/(pi t delta^3) with nodal volume h^2 t. LPS uses K and mu
+ * (Algorithm 2) and is 3D only. Influence function omega = 1. */
+typedef struct {
+    int32_t model;      /* PD_MODEL_PMB or PD_MODEL_LPS */
+    int32_t vol_corr;   /* 1: partial volume V_ij = (delta + h/2 - |xi|)/h for
+                           |xi| > delta - h/2 (Remark of Sec. 3.1), else 1 */
+    double E;           /* Young's modulus (PMB), Pa */
+    double rho;         /* mass density, kg/m^3, > 0 */
+    double K;           /* bulk modulus (LPS), Pa */
+    double mu;          /* shear modulus (LPS), Pa */
+    double s_c;         /* critical stretch (PMB); 0 disables breaking */
+    double thickness;   /* 2D plate thickness t (m); ignored in 3D */
+} pd_material;
+
+/* Run parameters. */
+typedef struct {
+    double dt;          /* time step; 0 selects dt_factor * dt_crit with the
+                           Silling-Askari bound dt_crit = min_i sqrt(2 rho /
+                           sum_j c V_j V_ij / |xi_ij|) (PMB c of the same E for LPS) */
+    double dt_factor;   /* used when dt == 0; 0 means 0.5 */
+    int32_t precision;  /* PD_FP32C or PD_FP64 */
+    int32_t tile_log2;  /* points per tile = 2^tile_log2 (a Morton brick);
+                           0 selects the default (9 in 3D, 8 in 2D); 6..10 */
+} pd_run;
+
+typedef struct pd_sim pd_sim;
+
+/* ------------------------------------------------------------------- lifecycle */
+
+/* Validate the descriptions and allocate the simulation's device buffers on the
+ * current device. *out receives an opaque handle owned by the caller until
+ * pd_destroy(). Initial state: u = v = 0, all DOFs free, no body force.
+ * Errors: PD_EINVAL (bad description, LPS in 2D, LPS with s_c > 0),
+ * PD_ENOMEM, PD_ECUDA. Synchronous. */
+int pd_create(pd_sim **out, const pd_grid *grid, const pd_material *mat, const pd_run *run);
+
+/* Free every buffer, graph and stream of the simulation. NULL is accepted. */
+int pd_destroy(pd_sim *sim);
+
+/* Copy the message of the last failure on this thread into buf (NUL-terminated,
+ * truncated to len). Returns the length of the full message. */
+int pd_last_error(char *buf, size_t len);
+
+/* ------------------------------------------------------------------ neighbours */
+
+/* Build B_delta(X_i) for every point (Sec. 3.1; computed and stored once in the
+ * reference configuration, Sec. 4.2.1) on the device: a cell list with cell edge
+ * m h, a Morton permutation of the points, and a CSR bond list in Morton
+ * numbering with each row ascending. The CSR is then encoded as one stencil
+ * bit per (point, lattice offset) -- the bond-intact mask the force kernels
+ * read -- and, for LPS, the weighted volume m_i = sum_j |xi|^2 V_j V_ij of
+ * Algorithm 2's first loop. Also fixes dt when pd_run.dt was 0.
+ * Synchronous. Errors: PD_ENOMEM, PD_ECUDA. Calling it again rebuilds and
+ * resets every bond to intact. */
+int pd_build_neighbors(pd_sim *sim, void *stream);
+
+/* Number of directed bonds (CSR entries). Errors: PD_ESTATE before the build. */
+int pd_bond_count(const pd_sim *sim, int64_t *nbonds);
+
+/* Copy the CSR in Morton numbering: row_ptr[npoints+1] (int64), col[nbonds]
+ * (int32, Morton ranks, rows ascending) and perm[npoints] (int64, perm[rank] =
+ * user index). Any of the three may be NULL. Synchronous. */
+int pd_get_neighbors(pd_sim *sim, int64_t *row_ptr, int32_t *col, int64_t *perm, void *stream);
+
+/* One byte per CSR entry of pd_get_neighbors (1 = broken, 0 = intact).
+ * Synchronous. */
+int pd_get_broken(pd_sim *sim, uint8_t *broken, void *stream);
+
+/* Pre-notch: every bond whose segment crosses the planar rectangle
+ * { x[axis] = pos, lo[b] <= x[b] <= hi[b] for the other axes b } (lattice units,
+ * multiples of h from the origin) is marked broken. *nbroken (may be NULL)
+ * receives the number of directed bonds marked by this call. Synchronous. */
+int pd_break_bonds(pd_sim *sim, int axis, double pos, const double lo[3], const double hi[3],
+                   int64_t *nbroken, void *stream);
+
+/* -------------------------------------------------------------------- state */
+
+/* Set displacement u and/or velocity v (npoints x dim, FP64, user order) at the
+ * current time; a NULL pointer leaves that field unchanged. Initial conditions
+ * u0, v0 of Eqs. (1)-(2). Stream-ordered. */
+int pd_set_state(pd_sim *sim, const double *u, const double *v, void *stream);
+
+/* Read u and/or v (npoints x dim, FP64, user order) at the current integer time
+ * step. If the last step left the velocity at a half step, this evaluates the
+ * force at the current u to complete it (Eq. (9)); the trajectory is unchanged.
+ * Synchronous. */
+int pd_get_state(pd_sim *sim, double *u, double *v, void *stream);
+
+/* Boundary conditions on a collar Omega_c (Sec. 3; Sec. 5.2.2): kind and value
+ * per DOF (npoints x dim; uint8 PD_BC_*, FP64). PD_BC_VELOCITY holds v = value
+ * and advances u by dt*value; PD_BC_DISPLACEMENT holds u = value, v = 0.
+ * kind == NULL frees every DOF. Stream-ordered. */
+int pd_set_bc(pd_sim *sim, const uint8_t *kind, const double *value, void *stream);
+
+/* External force density b (npoints x dim, FP64, user order) of Eq. (3);
+ * NULL removes it. Stream-ordered. */
+int pd_set_body_force(pd_sim *sim, const double *b, void *stream);
+
+int pd_get_dt(const pd_sim *sim, double *dt);
+/* Set dt (> 0). Stream-ordered with respect to later steps. */
+int pd_set_dt(pd_sim *sim, double dt);
+/* Number of explicit steps taken so far. */
+int pd_get_step(const pd_sim *sim, int64_t *step);
+
+/* --------------------------------------------------------------------- force */
+
+/* One internal-force evaluation f_i = sum_{j in B(i)} f(eta, xi) V_j V_ij
+ * (PMB, Eq. (3)) or sum_j (T_i<xi> - T_j<-xi>) V_j V_ij (LPS, Eq. (4), after the
+ * dilatation pass of Algorithm 2) at displacement u (npoints x dim FP64, user
+ * order) or, if u == NULL, at the current state. f_out: npoints x dim FP64,
+ * user order, force per unit volume (N/m^3). With PD_FORCE_UPDATE_BREAKING a
+ * bond whose stretch exceeds s_c breaks for good before it contributes.
+ * Stream-ordered. */
+int pd_force(pd_sim *sim, const double *u, double *f_out, unsigned flags, void *stream);
+
+/* LPS dilatation theta_i = (3/m_i) sum_j |xi| e V_j V_ij (Algorithm 2, second
+ * loop) at u (or the current state if NULL), npoints FP64, user order.
+ * PD_EINVAL for PMB. Stream-ordered. */
+int pd_dilatation(pd_sim *sim, const double *u, double *theta_out, void *stream);
+
+/* ------------------------------------------------------------------ explicit */
+
+/* Advance nsteps >= 0 explicit steps, velocity-Verlet form of the central
+ * difference scheme (Eqs. (7)-(10), Algorithm 4): kick with f^k, drift,
+ * boundary conditions, force at the new u (bonds break here), kick. One fused
+ * force + update kernel per step (two for LPS), replayed as CUDA graphs.
+ * Stream-ordered. */
+int pd_step_explicit(pd_sim *sim, int64_t nsteps, void *stream);
+
+/* ------------------------------------------------------------------- tangent */
+
+/* Tangent Jacobian-vector product out = K w with K = df/du at u_lin (npoints x
+ * dim FP64, user order; NULL = current state), the matrix-free form of Eq. (6)
+ * and Algorithm 3 for the PMB model:
+ *   (K w)_i = sum_j D_ij (w_j - w_i) V_j V_ij,
+ *   D_ij = c [ n n^T / |xi| + s (I - n n^T) / |xi + eta| ],  n = (xi+eta)/|xi+eta|,
+ * over intact bonds. K is symmetric; -K is positive semi-definite near the
+ * reference configuration. With PD_JVP_MASK_DIRICHLET, prescribed-displacement
+ * DOFs give out = w and do not couple to the others. PD_EINVAL for LPS.
+ * Stream-ordered. */
+int pd_jvp(pd_sim *sim, const double *u_lin, const double *w, double *out,
+           unsigned flags, void *stream);
+
+/* Adjoint (vector-Jacobian) product out = K^T v, computed by its own kernel in
+ * the transposed gather form (K^T v)_i = sum_j D_ij (V_i v_j - V_j v_i) V_ij.
+ * Same arguments and errors as pd_jvp. */
+int pd_vjp(pd_sim *sim, const double *u_lin, const double *v, double *out,
+           unsigned flags, void *stream);
+
+/* -------------------------------------------------------------------- energy */
+
+/* Kinetic energy sum_i rho |v_i|^2 V_i / 2 and strain energy sum_i V_i W_i
+ * (PMB: W_i = 1/2 sum_j c s^2 |xi| / 2 V_j V_ij; LPS: W_i = K theta_i^2 / 2 +
+ * 15 mu / (2 m_i) sum_j (e^d)^2 V_j V_ij) at the current integer step, reduced
+ * in FP64 in a fixed order (bit-reproducible). Either pointer may be NULL.
+ * Synchronous. */
+int pd_energy(pd_sim *sim, double *kinetic, double *strain, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_H */

@@ -1,0 +1,894 @@
+// pd_api.cu -- the C ABI of libpd (include/pd.h): simulation lifecycle, the
+// per-simulation tables, host/device transfers in user order, graph-captured
+// explicit stepping, force, tangent and energy entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pd_tile.cuh"
+
+namespace pdk {
+
+// ------------------------------------------------------------ error plumbing
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PD_ENOMEM : PD_ECUDA;
+}
+
+// launchers defined in the kernel files
+int launch_pmb_args(const TileArgs &a, int precision, cudaStream_t st);
+int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st);
+int launch_jvp_args(const TileArgs &a, int precision, cudaStream_t st);
+int launch_energy_points(const TileArgs &a, int precision, double *kin, cudaStream_t st);
+int reduce_sum(const double *x, long long n, double scale, double *partial, double *out, cudaStream_t st);
+int reduce_blocks_for(long long n);
+size_t pmb_generic_smem(const Geom &g, int precision);
+size_t pmb_fast_smem(const Geom &g);
+size_t lps_generic_smem(const Geom &g, int precision, bool dil);
+size_t jvp_smem(const Geom &g, int precision);
+size_t energy_smem(const Geom &g, int precision);
+int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st);
+int dirichlet_mask(const Geom &g, const uint8_t *kind, double *const v[3], const double *const w[3], int copy,
+                   cudaStream_t st);
+
+}  // namespace pdk
+
+using namespace pdk;
+
+constexpr int GRAPH_CHUNK = 16;   // steps per captured graph (even: parity-preserving)
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+struct pd_sim {
+    pd_grid grid;
+    pd_material pmat;
+    pd_run run;
+    Geom g;
+    Material mat;
+    int precision = PD_FP32C;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool built = false;
+    double dt = 0.0, dt_crit = 0.0;
+    int64_t step = 0;
+    int v_is_half = 0;
+    int cur = 0;
+    bool use_body = false;
+    double c_dt = 0.0;          // micromodulus used by the stable-step bound
+
+    // tables
+    int4 *tile_org = nullptr;
+    int *tile_ref = nullptr, *tile_lut = nullptr;
+    int *user_of_slot = nullptr, *slot_of_user = nullptr, *rank_of_slot = nullptr, *slot_of_rank = nullptr;
+    int4 *stencil = nullptr;
+    double *stencil_r0 = nullptr;
+    int *stencil_lut = nullptr;
+    // CSR
+    BuildOut csr{nullptr, nullptr, 0};
+    // state
+    double *u[3] = {nullptr, nullptr, nullptr}, *v[3] = {nullptr, nullptr, nullptr};
+    float4 *hl[2] = {nullptr, nullptr};
+    double4_32a *d4[2] = {nullptr, nullptr};
+    float4 *lin_hl = nullptr;
+    double4_32a *lin_d4 = nullptr;
+    uint8_t *bc_kind = nullptr;
+    double *bc_val = nullptr, *body = nullptr;
+    uint32_t *mask = nullptr;
+    double *mtil = nullptr;
+    float *minv32 = nullptr, *theta32 = nullptr;
+    double *theta64 = nullptr;
+    double *f[3] = {nullptr, nullptr, nullptr}, *w[3] = {nullptr, nullptr, nullptr};
+    double *jv[3] = {nullptr, nullptr, nullptr}, *ulin[3] = {nullptr, nullptr, nullptr};
+    double *epoint = nullptr, *ekin = nullptr, *red = nullptr, *dout = nullptr;
+    double *io = nullptr;
+    int *d_err = nullptr;
+    unsigned long long *d_count = nullptr;
+    std::vector<void *> allocs;
+    // graphs: [start parity]
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+static int pd_alloc(pd_sim *s, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc");
+    }
+    s->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    return PD_OK;
+}
+
+#define ALLOC(ptr, bytes)                                                  \
+    do {                                                                   \
+        int rc_ = pd_alloc(s, (void **)&(ptr), (size_t)(bytes));           \
+        if (rc_ != PD_OK) return rc_;                                      \
+    } while (0)
+
+static cudaStream_t pick(pd_sim *s, void *stream) { return stream ? (cudaStream_t)stream : s->stream; }
+
+static void drop_graphs(pd_sim *s)
+{
+    for (int p = 0; p < 2; ++p)
+        if (s->graph[p]) {
+            cudaGraphExecDestroy(s->graph[p]);
+            s->graph[p] = nullptr;
+        }
+}
+
+static size_t max_smem(const Geom &g, int precision, int model)
+{
+    size_t m = jvp_smem(g, PD_FP64);
+    m = std::max(m, energy_smem(g, precision));
+    if (model == PD_MODEL_PMB)
+        m = std::max(m, precision == PD_FP64 ? pmb_generic_smem(g, precision) : pmb_fast_smem(g));
+    else m = std::max(m, lps_generic_smem(g, precision, false));
+    return m;
+}
+
+// ---------------------------------------------------------------- create
+
+static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
+{
+    if (!gr || !mt || !rn) { set_error("null description"); return PD_EINVAL; }
+    if (gr->dim != 2 && gr->dim != 3) { set_error("dim must be 2 or 3"); return PD_EINVAL; }
+    for (int a = 0; a < 3; ++a)
+        if (gr->n[a] < 1) { set_error("n[%d] must be >= 1", a); return PD_EINVAL; }
+    if (gr->dim == 2 && gr->n[2] != 1) { set_error("2D grids need n[2] == 1"); return PD_EINVAL; }
+    if (gr->m < 1 || gr->m > 24) { set_error("horizon factor m must be in [1, 24]"); return PD_EINVAL; }
+    if (!(gr->h > 0.0) || !isfinite(gr->h)) { set_error("h must be > 0"); return PD_EINVAL; }
+    if (gr->reserved != 0) { set_error("pd_grid.reserved must be 0"); return PD_EINVAL; }
+    if ((double)gr->n[0] * gr->n[1] * gr->n[2] > 1.0e9) { set_error("more than 1e9 points"); return PD_EINVAL; }
+    if (mt->model != PD_MODEL_PMB && mt->model != PD_MODEL_LPS) { set_error("unknown model"); return PD_EINVAL; }
+    if (!(mt->rho > 0.0)) { set_error("rho must be > 0"); return PD_EINVAL; }
+    if (mt->model == PD_MODEL_PMB && !(mt->E > 0.0)) { set_error("E must be > 0"); return PD_EINVAL; }
+    if (mt->model == PD_MODEL_LPS) {
+        if (gr->dim != 3) { set_error("LPS is 3D only"); return PD_EINVAL; }
+        if (!(mt->K > 0.0) || !(mt->mu > 0.0)) { set_error("LPS needs K > 0 and mu > 0"); return PD_EINVAL; }
+        if (mt->s_c != 0.0) { set_error("LPS has no bond breaking (s_c must be 0)"); return PD_EINVAL; }
+    }
+    if (mt->s_c < 0.0) { set_error("s_c must be >= 0"); return PD_EINVAL; }
+    if (gr->dim == 2 && !(mt->thickness > 0.0)) { set_error("2D needs thickness > 0"); return PD_EINVAL; }
+    if (rn->precision != PD_FP32C && rn->precision != PD_FP64) { set_error("unknown precision"); return PD_EINVAL; }
+    if (rn->tile_log2 != 0 && (rn->tile_log2 < 6 || rn->tile_log2 > 10)) {
+        set_error("tile_log2 must be 0 or in [6, 10]");
+        return PD_EINVAL;
+    }
+    if (rn->dt < 0.0 || rn->dt_factor < 0.0) { set_error("dt and dt_factor must be >= 0"); return PD_EINVAL; }
+    return PD_OK;
+}
+
+static int create_impl(pd_sim *s)
+{
+    const pd_grid &gr = s->grid;
+    Geom &g = s->g;
+    memset(&g, 0, sizeof(g));
+    g.dim = gr.dim;
+    g.m = gr.m;
+    g.nx = gr.n[0];
+    g.ny = gr.n[1];
+    g.nz = gr.dim == 3 ? gr.n[2] : 1;
+    g.h = gr.h;
+    g.L = s->run.tile_log2 ? s->run.tile_log2 : 9;
+    g.T = 1 << g.L;
+    int b[3];
+    brick_dims(g.dim, g.L, b);
+    g.bx = b[0];
+    g.by = b[1];
+    g.bz = b[2];
+    g.lbx = __builtin_ctz(b[0]);
+    g.lby = __builtin_ctz(b[1]);
+    g.lbz = __builtin_ctz(b[2]);
+    g.tgx = (g.nx + g.bx - 1) / g.bx;
+    g.tgy = (g.ny + g.by - 1) / g.by;
+    g.tgz = (g.nz + g.bz - 1) / g.bz;
+    g.npoints = g.nx * g.ny * g.nz;
+
+    // stencil: offsets 0 < |d|^2 <= m^2 ordered by (dz, dy, dx)
+    std::vector<int4> st;
+    std::vector<double> r0;
+    const int wdt = 2 * g.m + 1;
+    std::vector<int> lut((size_t)wdt * wdt * (g.dim == 3 ? wdt : 1), -1);
+    for (int dz = (g.dim == 3 ? -g.m : 0); dz <= (g.dim == 3 ? g.m : 0); ++dz)
+        for (int dy = -g.m; dy <= g.m; ++dy)
+            for (int dx = -g.m; dx <= g.m; ++dx) {
+                const int d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 == 0 || d2 > g.m * g.m) continue;
+                lut[(dx + g.m) + wdt * ((dy + g.m) + wdt * (g.dim == 3 ? dz + g.m : 0))] = (int)st.size();
+                st.push_back(make_int4(dx, dy, dz, d2));
+                r0.push_back(sqrt((double)d2));
+            }
+    g.S = (int)st.size();
+    g.W = (g.S + 31) / 32;
+    if (g.W > 64) { set_error("horizon stencil too large"); return PD_EINVAL; }
+
+    // tiles: bricks intersecting the grid, ordered by the Morton code of their origin
+    struct TileKey { uint64_t code; int tx, ty, tz; };
+    std::vector<TileKey> tiles;
+    tiles.reserve((size_t)g.tgx * g.tgy * g.tgz);
+    for (int tz = 0; tz < g.tgz; ++tz)
+        for (int ty = 0; ty < g.tgy; ++ty)
+            for (int tx = 0; tx < g.tgx; ++tx)
+                tiles.push_back({morton_encode(g.dim, tx * g.bx, ty * g.by, tz * g.bz), tx, ty, tz});
+    std::sort(tiles.begin(), tiles.end(), [](const TileKey &x, const TileKey &y) { return x.code < y.code; });
+    g.ntiles = (int)tiles.size();
+    const long long nslots = (long long)g.ntiles * g.T;
+    if (nslots >= (1LL << 31)) { set_error("lattice too large for 32-bit slots"); return PD_EINVAL; }
+    g.nslots = (int)nslots;
+    std::vector<int4> org(g.ntiles);
+    std::vector<int> ref(g.ntiles), tlut((size_t)g.tgx * g.tgy * g.tgz, -1);
+    for (int t = 0; t < g.ntiles; ++t) {
+        org[t] = make_int4(tiles[t].tx * g.bx, tiles[t].ty * g.by, tiles[t].tz * g.bz, 0);
+        ref[t] = t * g.T;   // the brick's origin corner is always inside the grid
+        tlut[tiles[t].tx + g.tgx * (tiles[t].ty + g.tgy * tiles[t].tz)] = t;
+    }
+
+    const size_t smem = max_smem(g, s->precision, s->pmat.model);
+    if (smem > SMEM_LIMIT) {
+        set_error("halo box needs %zu bytes of shared memory (> %zu); use a smaller tile_log2", smem, SMEM_LIMIT);
+        return PD_EINVAL;
+    }
+
+    // material constants
+    Material &mt = s->mat;
+    mt.model = s->pmat.model;
+    mt.vol_corr = s->pmat.vol_corr;
+    mt.E = s->pmat.E;
+    mt.rho = s->pmat.rho;
+    mt.K = s->pmat.K;
+    mt.mu = s->pmat.mu;
+    mt.s_c = s->pmat.s_c;
+    mt.thickness = s->pmat.thickness;
+    const double delta = g.m * g.h;
+    const double PI = 3.14159265358979323846;
+    auto pmb_c = [&](double E) {
+        if (g.dim == 3) {
+            const double Kp = E / (3.0 * (1.0 - 2.0 * 0.25));   // nu = 1/4
+            return 18.0 * Kp / (PI * delta * delta * delta * delta);
+        }
+        return 9.0 * E / (PI * mt.thickness * delta * delta * delta);
+    };
+    mt.V = g.dim == 3 ? g.h * g.h * g.h : g.h * g.h * mt.thickness;
+    mt.c = mt.model == PD_MODEL_PMB ? pmb_c(mt.E) : 0.0;
+    s->c_dt = mt.model == PD_MODEL_PMB ? mt.c : pmb_c(9.0 * mt.K * mt.mu / (3.0 * mt.K + mt.mu));
+
+    PD_CUDA(cudaGetDevice(&s->device));
+    PD_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+
+    const size_t NS = (size_t)g.nslots, NP = (size_t)g.npoints;
+    ALLOC(s->tile_org, sizeof(int4) * g.ntiles);
+    ALLOC(s->tile_ref, sizeof(int) * g.ntiles);
+    ALLOC(s->tile_lut, sizeof(int) * tlut.size());
+    ALLOC(s->user_of_slot, sizeof(int) * NS);
+    ALLOC(s->slot_of_user, sizeof(int) * NP);
+    ALLOC(s->rank_of_slot, sizeof(int) * NS);
+    ALLOC(s->slot_of_rank, sizeof(int) * NP);
+    ALLOC(s->stencil, sizeof(int4) * g.S);
+    ALLOC(s->stencil_r0, sizeof(double) * g.S);
+    ALLOC(s->stencil_lut, sizeof(int) * lut.size());
+    PD_CUDA(cudaMemcpy(s->tile_org, org.data(), sizeof(int4) * g.ntiles, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(s->tile_ref, ref.data(), sizeof(int) * g.ntiles, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(s->tile_lut, tlut.data(), sizeof(int) * tlut.size(), cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(s->stencil, st.data(), sizeof(int4) * g.S, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(s->stencil_r0, r0.data(), sizeof(double) * g.S, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(s->stencil_lut, lut.data(), sizeof(int) * lut.size(), cudaMemcpyHostToDevice));
+
+    for (int c = 0; c < 3; ++c) {
+        ALLOC(s->u[c], sizeof(double) * NS);
+        ALLOC(s->v[c], sizeof(double) * NS);
+        ALLOC(s->f[c], sizeof(double) * NS);
+        ALLOC(s->w[c], sizeof(double) * NS);
+        ALLOC(s->jv[c], sizeof(double) * NS);
+        ALLOC(s->ulin[c], sizeof(double) * NS);
+    }
+    if (s->precision == PD_FP64) {
+        ALLOC(s->d4[0], sizeof(double4_32a) * NS);
+        ALLOC(s->d4[1], sizeof(double4_32a) * NS);
+        ALLOC(s->lin_d4, sizeof(double4_32a) * NS);
+    } else {
+        ALLOC(s->hl[0], 2 * sizeof(float4) * NS);
+        ALLOC(s->hl[1], 2 * sizeof(float4) * NS);
+        ALLOC(s->lin_hl, 2 * sizeof(float4) * NS);
+    }
+    ALLOC(s->bc_kind, 3 * NS);
+    ALLOC(s->bc_val, 3 * sizeof(double) * NS);
+    ALLOC(s->mask, sizeof(uint32_t) * g.W * NS);
+    if (mt.model == PD_MODEL_LPS) {
+        ALLOC(s->mtil, sizeof(double) * NS);
+        ALLOC(s->minv32, sizeof(float) * NS);
+        ALLOC(s->theta32, sizeof(float) * NS);
+        ALLOC(s->theta64, sizeof(double) * NS);
+    }
+    ALLOC(s->epoint, sizeof(double) * NS);
+    ALLOC(s->ekin, sizeof(double) * NS);
+    ALLOC(s->red, sizeof(double) * reduce_blocks_for(NS));
+    ALLOC(s->dout, sizeof(double) * 8);
+    ALLOC(s->io, sizeof(double) * 3 * std::max(NP, NS));
+    ALLOC(s->d_err, sizeof(int));
+    ALLOC(s->d_count, sizeof(unsigned long long));
+    return PD_OK;
+}
+
+static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const double4_32a *src_d4)
+{
+    TileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = s->g;
+    a.tile_org = s->tile_org;
+    a.tile_ref = s->tile_ref;
+    a.tile_lut = s->tile_lut;
+    a.stencil = s->stencil;
+    a.stencil_r0 = s->stencil_r0;
+    a.src_hl = src_hl;
+    a.src_d4 = src_d4;
+    a.dst_hl = s->hl[s->cur ^ 1];
+    a.dst_d4 = s->d4[s->cur ^ 1];
+    a.mask = s->mask;
+    for (int c = 0; c < 3; ++c) {
+        a.u[c] = s->u[c];
+        a.v[c] = s->v[c];
+        a.f[c] = s->f[c];
+        a.w[c] = s->w[c];
+        a.jv[c] = s->jv[c];
+    }
+    a.bc_kind = s->bc_kind;
+    a.bc_val = s->bc_val;
+    a.body = s->body;
+    a.minv32 = s->minv32;
+    a.mtil = s->mtil;
+    a.theta32 = s->theta32;
+    a.theta64 = s->theta64;
+    a.epoint = s->epoint;
+    a.cV = s->mat.c * s->mat.V;
+    a.inv_rho = 1.0 / s->mat.rho;
+    a.dt = s->dt;
+    a.s_c = s->mat.s_c;
+    a.h = s->g.h;
+    a.inv_h = 1.0 / s->g.h;
+    a.A = 3.0 * s->mat.K - 5.0 * s->mat.mu;
+    a.B = 15.0 * s->mat.mu;
+    a.K = s->mat.K;
+    a.model = s->mat.model;
+    a.v_is_half = s->v_is_half;
+    a.update_breaking = s->mat.s_c > 0.0 ? 1 : 0;
+    a.mode = mode;
+    a.vol_corr = s->mat.vol_corr;
+    a.use_body = s->use_body ? 1 : 0;
+    a.adjoint = 0;
+    return a;
+}
+
+// Internal force at the staging buffer src (+ update per mode).
+static int run_force(pd_sim *s, int mode, const float4 *src_hl, const double4_32a *src_d4, int update_breaking,
+                     cudaStream_t st)
+{
+    TileArgs a = make_args(s, mode, src_hl, src_d4);
+    a.update_breaking = update_breaking && s->mat.s_c > 0.0;
+    if (s->mat.model == PD_MODEL_PMB) return launch_pmb_args(a, s->precision, st);
+    int rc = launch_lps_args(a, s->precision, 1, st);
+    if (rc != PD_OK) return rc;
+    return launch_lps_args(a, s->precision, 0, st);
+}
+
+// Complete a half-step velocity (Eq. (9)) with the force at the current u.
+static int finalize(pd_sim *s, cudaStream_t st)
+{
+    if (!s->v_is_half) return PD_OK;
+    int rc = run_force(s, MODE_FINALIZE, s->hl[s->cur], s->d4[s->cur], 1, st);
+    if (rc != PD_OK) return rc;
+    s->v_is_half = 0;
+    return PD_OK;
+}
+
+static int one_step(pd_sim *s, cudaStream_t st)
+{
+    int rc = run_force(s, MODE_STEP, s->hl[s->cur], s->d4[s->cur], 1, st);
+    if (rc != PD_OK) return rc;
+    s->cur ^= 1;
+    s->v_is_half = 1;
+    s->step += 1;
+    return PD_OK;
+}
+
+static int capture_graph(pd_sim *s, int parity)
+{
+    const int cur0 = s->cur;
+    const int64_t step0 = s->step;
+    s->cur = parity;
+    PD_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = PD_OK;
+    for (int k = 0; k < GRAPH_CHUNK && rc == PD_OK; ++k) rc = one_step(s, s->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+    s->cur = cur0;
+    s->step = step0;
+    if (rc != PD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&s->graph[parity], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return PD_OK;
+}
+
+static int upload_user(pd_sim *s, const void *src, size_t bytes, cudaStream_t st)
+{
+    PD_CUDA(cudaMemcpyAsync(s->io, src, bytes, cudaMemcpyDefault, st));
+    return PD_OK;
+}
+
+// Scatter a user-order (n x dim) FP64 vector into slot-order SoA arrays.
+static int user_to_slots(pd_sim *s, const double *user, double *const dst[3], cudaStream_t st)
+{
+    int rc = upload_user(s, user, sizeof(double) * s->g.npoints * s->g.dim, st);
+    if (rc != PD_OK) return rc;
+    Tables t = {};
+    t.slot_of_user = s->slot_of_user;
+    return scatter_user_to_slots(s->g, t, s->io, dst, 0.0, st);
+}
+
+static int slots_to_user(pd_sim *s, double *const src[3], double *user, cudaStream_t st)
+{
+    Tables t = {};
+    t.slot_of_user = s->slot_of_user;
+    int rc = gather_slots_to_user(s->g, t, src, s->io, st);
+    if (rc != PD_OK) return rc;
+    PD_CUDA(cudaMemcpyAsync(user, s->io, sizeof(double) * s->g.npoints * s->g.dim, cudaMemcpyDefault, st));
+    return PD_OK;
+}
+
+static int stage_lin(pd_sim *s, const double *u, const float4 **hl, const double4_32a **d4, cudaStream_t st)
+{
+    if (!u) {
+        *hl = s->hl[s->cur];
+        *d4 = s->d4[s->cur];
+        return PD_OK;
+    }
+    int rc = user_to_slots(s, u, s->ulin, st);
+    if (rc != PD_OK) return rc;
+    rc = pack_stage(s->g, s->ulin, s->lin_hl, s->lin_d4, st);
+    *hl = s->lin_hl;
+    *d4 = s->lin_d4;
+    return rc;
+}
+
+__global__ void k_scalar_gather(Geom g, const int *slot_of_user, const float *a32, const double *a64, double *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.npoints) return;
+    const int s = slot_of_user[i];
+    out[i] = a64 ? a64[s] : (double)a32[s];
+}
+
+__global__ void k_perm(Geom g, const int *slot_of_rank, const int *user_of_slot, long long *perm)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    perm[r] = user_of_slot[slot_of_rank[r]];
+}
+
+#define CHECK_SIM(s)                                                   \
+    do {                                                               \
+        if (!(s)) { set_error("null simulation"); return PD_EINVAL; }  \
+    } while (0)
+#define CHECK_BUILT(s)                                                          \
+    do {                                                                        \
+        CHECK_SIM(s);                                                           \
+        if (!(s)->built) { set_error("call pd_build_neighbors first"); return PD_ESTATE; } \
+    } while (0)
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+int pd_last_error(char *buf, size_t len)
+{
+    const int n = (int)strlen(g_err);
+    if (buf && len) {
+        strncpy(buf, g_err, len - 1);
+        buf[len - 1] = '\0';
+    }
+    return n;
+}
+
+int pd_create(pd_sim **out, const pd_grid *grid, const pd_material *mat, const pd_run *run)
+{
+    if (!out) { set_error("null out"); return PD_EINVAL; }
+    *out = nullptr;
+    int rc = validate(grid, mat, run);
+    if (rc != PD_OK) return rc;
+    pd_sim *s = new (std::nothrow) pd_sim();
+    if (!s) { set_error("host allocation failed"); return PD_ENOMEM; }
+    s->grid = *grid;
+    s->pmat = *mat;
+    s->run = *run;
+    s->precision = run->precision;
+    rc = create_impl(s);
+    if (rc != PD_OK) {
+        pd_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return PD_OK;
+}
+
+int pd_destroy(pd_sim *s)
+{
+    if (!s) return PD_OK;
+    drop_graphs(s);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (void *p : s->allocs) cudaFree(p);
+    cudaFree(s->csr.row_ptr);
+    cudaFree(s->csr.col);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    delete s;
+    return PD_OK;
+}
+
+int pd_build_neighbors(pd_sim *s, void *stream)
+{
+    CHECK_SIM(s);
+    cudaStream_t st = pick(s, stream);
+    drop_graphs(s);
+    cudaFree(s->csr.row_ptr);
+    cudaFree(s->csr.col);
+    s->csr = BuildOut{nullptr, nullptr, 0};
+    s->built = false;
+    Tables t = {};
+    t.tile_org = s->tile_org;
+    t.tile_ref = s->tile_ref;
+    t.tile_lut = s->tile_lut;
+    t.stencil = s->stencil;
+    t.stencil_lut = s->stencil_lut;
+    int rc = build_slots(s->g, t, s->user_of_slot, s->slot_of_user, s->rank_of_slot, s->slot_of_rank, st);
+    if (rc != PD_OK) return rc;
+    t.user_of_slot = s->user_of_slot;
+    t.slot_of_user = s->slot_of_user;
+    t.rank_of_slot = s->rank_of_slot;
+    t.slot_of_rank = s->slot_of_rank;
+    rc = build_csr(s->g, t, &s->csr, st);
+    if (rc != PD_OK) return rc;
+    rc = build_mask(s->g, t, s->csr, s->mask, s->d_err, st);
+    if (rc != PD_OK) return rc;
+    if (s->mat.model == PD_MODEL_LPS) {
+        rc = build_weighted_volume(s->g, s->mat, t, s->csr, s->mtil, s->minv32, st);
+        if (rc != PD_OK) return rc;
+    }
+    rc = build_dt_bound(s->g, s->mat, t, s->csr, s->dout, st);
+    if (rc != PD_OK) return rc;
+    double smax = 0.0;
+    PD_CUDA(cudaMemcpyAsync(&smax, s->dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PD_CUDA(cudaStreamSynchronize(st));
+    // sum_j c V V_ij / |xi| = (c V / h) sum_j V_ij / |d|
+    const double denom = s->c_dt * s->mat.V / s->g.h * smax;
+    s->dt_crit = denom > 0.0 ? sqrt(2.0 * s->mat.rho / denom) : 0.0;
+    if (s->run.dt > 0.0) s->dt = s->run.dt;
+    else s->dt = (s->run.dt_factor > 0.0 ? s->run.dt_factor : 0.5) * s->dt_crit;
+    if (!(s->dt > 0.0)) { set_error("time step could not be determined (no bonds?)"); return PD_EINVAL; }
+    rc = pack_stage(s->g, s->u, s->hl[s->cur], s->d4[s->cur], st);
+    if (rc != PD_OK) return rc;
+    PD_CUDA(cudaStreamSynchronize(st));
+    s->built = true;
+    return PD_OK;
+}
+
+int pd_bond_count(const pd_sim *s, int64_t *nb)
+{
+    CHECK_BUILT(s);
+    if (!nb) { set_error("null output"); return PD_EINVAL; }
+    *nb = s->csr.nbonds;
+    return PD_OK;
+}
+
+int pd_get_neighbors(pd_sim *s, int64_t *row_ptr, int32_t *col, int64_t *perm, void *stream)
+{
+    CHECK_BUILT(s);
+    cudaStream_t st = pick(s, stream);
+    if (row_ptr)
+        PD_CUDA(cudaMemcpyAsync(row_ptr, s->csr.row_ptr, sizeof(int64_t) * (s->g.npoints + 1), cudaMemcpyDefault, st));
+    if (col && s->csr.nbonds)
+        PD_CUDA(cudaMemcpyAsync(col, s->csr.col, sizeof(int32_t) * s->csr.nbonds, cudaMemcpyDefault, st));
+    if (perm) {
+        long long *tmp = reinterpret_cast<long long *>(s->io);
+        k_perm<<<(s->g.npoints + 255) / 256, 256, 0, st>>>(s->g, s->slot_of_rank, s->user_of_slot, tmp);
+        PD_CUDA(cudaGetLastError());
+        PD_CUDA(cudaMemcpyAsync(perm, tmp, sizeof(int64_t) * s->g.npoints, cudaMemcpyDefault, st));
+    }
+    PD_CUDA(cudaStreamSynchronize(st));
+    return PD_OK;
+}
+
+int pd_get_broken(pd_sim *s, uint8_t *broken, void *stream)
+{
+    CHECK_BUILT(s);
+    if (!broken) { set_error("null output"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    uint8_t *tmp = nullptr;
+    PD_CUDA(cudaMalloc(&tmp, s->csr.nbonds > 0 ? s->csr.nbonds : 1));
+    Tables t = {};
+    t.tile_org = s->tile_org;
+    t.slot_of_rank = s->slot_of_rank;
+    t.stencil_lut = s->stencil_lut;
+    int rc = csr_broken_flags(s->g, t, s->csr, s->mask, tmp, st);
+    if (rc == PD_OK && s->csr.nbonds) {
+        cudaError_t e = cudaMemcpyAsync(broken, tmp, s->csr.nbonds, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "broken copy");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (rc == PD_OK && e != cudaSuccess) rc = cuda_fail(e, "pd_get_broken");
+    return rc;
+}
+
+int pd_break_bonds(pd_sim *s, int axis, double pos, const double lo[3], const double hi[3], int64_t *nbroken,
+                   void *stream)
+{
+    CHECK_BUILT(s);
+    if (axis < 0 || axis >= s->g.dim || !lo || !hi) { set_error("bad notch description"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    Tables t = {};
+    t.tile_org = s->tile_org;
+    t.user_of_slot = s->user_of_slot;
+    t.stencil = s->stencil;
+    int rc = break_notch(s->g, t, s->mask, axis, pos, lo, hi, s->d_count, st);
+    if (rc != PD_OK) return rc;
+    unsigned long long cnt = 0;
+    PD_CUDA(cudaMemcpyAsync(&cnt, s->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    PD_CUDA(cudaStreamSynchronize(st));
+    if (nbroken) *nbroken = (int64_t)cnt;
+    return PD_OK;
+}
+
+int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
+{
+    CHECK_BUILT(s);
+    cudaStream_t st = pick(s, stream);
+    int rc = finalize(s, st);
+    if (rc != PD_OK) return rc;
+    if (u) {
+        rc = user_to_slots(s, u, s->u, st);
+        if (rc != PD_OK) return rc;
+        rc = pack_stage(s->g, s->u, s->hl[s->cur], s->d4[s->cur], st);
+        if (rc != PD_OK) return rc;
+    }
+    if (v) {
+        rc = user_to_slots(s, v, s->v, st);
+        if (rc != PD_OK) return rc;
+    }
+    return PD_OK;
+}
+
+int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
+{
+    CHECK_BUILT(s);
+    cudaStream_t st = pick(s, stream);
+    int rc = finalize(s, st);
+    if (rc != PD_OK) return rc;
+    if (u && (rc = slots_to_user(s, s->u, u, st)) != PD_OK) return rc;
+    if (v && (rc = slots_to_user(s, s->v, v, st)) != PD_OK) return rc;
+    PD_CUDA(cudaStreamSynchronize(st));
+    return PD_OK;
+}
+
+int pd_set_bc(pd_sim *s, const uint8_t *kind, const double *value, void *stream)
+{
+    CHECK_BUILT(s);
+    cudaStream_t st = pick(s, stream);
+    const size_t NS = s->g.nslots;
+    if (!kind) {
+        PD_CUDA(cudaMemsetAsync(s->bc_kind, 0, 3 * NS, st));
+        return PD_OK;
+    }
+    if (!value) { set_error("pd_set_bc needs values with kinds"); return PD_EINVAL; }
+    const size_t n = (size_t)s->g.npoints * s->g.dim;
+    PD_CUDA(cudaMemsetAsync(s->bc_kind, 0, 3 * NS, st));
+    PD_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
+    uint8_t *kbuf = reinterpret_cast<uint8_t *>(s->ekin);   // n bytes of scratch
+    PD_CUDA(cudaMemcpyAsync(kbuf, kind, n, cudaMemcpyDefault, st));
+    Tables t = {};
+    t.slot_of_user = s->slot_of_user;
+    int rc = scatter_kinds(s->g, t, kbuf, s->bc_kind, s->d_err, st);
+    if (rc != PD_OK) return rc;
+    double *vals[3] = {s->bc_val, s->bc_val + NS, s->bc_val + 2 * NS};
+    rc = user_to_slots(s, value, vals, st);
+    if (rc != PD_OK) return rc;
+    int herr = 0;
+    PD_CUDA(cudaMemcpyAsync(&herr, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PD_CUDA(cudaStreamSynchronize(st));
+    if (herr) {
+        PD_CUDA(cudaMemset(s->bc_kind, 0, 3 * NS));
+        set_error("unknown boundary-condition kind");
+        return PD_EINVAL;
+    }
+    return PD_OK;
+}
+
+int pd_set_body_force(pd_sim *s, const double *b, void *stream)
+{
+    CHECK_BUILT(s);
+    cudaStream_t st = pick(s, stream);
+    drop_graphs(s);
+    if (!b) {
+        s->use_body = false;
+        return PD_OK;
+    }
+    if (!s->body) ALLOC(s->body, 3 * sizeof(double) * s->g.nslots);
+    double *dst[3] = {s->body, s->body + s->g.nslots, s->body + 2 * (size_t)s->g.nslots};
+    int rc = user_to_slots(s, b, dst, st);
+    if (rc != PD_OK) return rc;
+    s->use_body = true;
+    return PD_OK;
+}
+
+int pd_get_dt(const pd_sim *s, double *dt)
+{
+    CHECK_BUILT(s);
+    if (!dt) { set_error("null output"); return PD_EINVAL; }
+    *dt = s->dt;
+    return PD_OK;
+}
+
+int pd_set_dt(pd_sim *s, double dt)
+{
+    CHECK_BUILT(s);
+    if (!(dt > 0.0)) { set_error("dt must be > 0"); return PD_EINVAL; }
+    if (s->v_is_half) {
+        int rc = finalize(s, s->stream);
+        if (rc != PD_OK) return rc;
+    }
+    s->dt = dt;
+    drop_graphs(s);
+    return PD_OK;
+}
+
+int pd_get_step(const pd_sim *s, int64_t *step)
+{
+    CHECK_SIM(s);
+    if (!step) { set_error("null output"); return PD_EINVAL; }
+    *step = s->step;
+    return PD_OK;
+}
+
+int pd_force(pd_sim *s, const double *u, double *f_out, unsigned flags, void *stream)
+{
+    CHECK_BUILT(s);
+    if (!f_out) { set_error("null output"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    const float4 *hl;
+    const double4_32a *d4;
+    int rc = stage_lin(s, u, &hl, &d4, st);
+    if (rc != PD_OK) return rc;
+    rc = run_force(s, MODE_FORCE, hl, d4, (flags & PD_FORCE_UPDATE_BREAKING) ? 1 : 0, st);
+    if (rc != PD_OK) return rc;
+    return slots_to_user(s, s->f, f_out, st);
+}
+
+int pd_dilatation(pd_sim *s, const double *u, double *theta_out, void *stream)
+{
+    CHECK_BUILT(s);
+    if (s->mat.model != PD_MODEL_LPS) { set_error("dilatation is defined for LPS only"); return PD_EINVAL; }
+    if (!theta_out) { set_error("null output"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    const float4 *hl;
+    const double4_32a *d4;
+    int rc = stage_lin(s, u, &hl, &d4, st);
+    if (rc != PD_OK) return rc;
+    TileArgs a = make_args(s, MODE_FORCE, hl, d4);
+    rc = launch_lps_args(a, s->precision, 1, st);
+    if (rc != PD_OK) return rc;
+    k_scalar_gather<<<(s->g.npoints + 255) / 256, 256, 0, st>>>(
+        s->g, s->slot_of_user, s->theta32, s->precision == PD_FP64 ? s->theta64 : nullptr, s->io);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaMemcpyAsync(theta_out, s->io, sizeof(double) * s->g.npoints, cudaMemcpyDefault, st));
+    return PD_OK;
+}
+
+int pd_step_explicit(pd_sim *s, int64_t nsteps, void *stream)
+{
+    CHECK_BUILT(s);
+    if (nsteps < 0) { set_error("nsteps must be >= 0"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    int rc = PD_OK;
+    if (nsteps > 0 && !s->v_is_half) {
+        rc = one_step(s, st);
+        if (rc != PD_OK) return rc;
+        --nsteps;
+    }
+    while (nsteps >= GRAPH_CHUNK) {
+        if (!s->graph[s->cur]) {
+            rc = capture_graph(s, s->cur);
+            if (rc != PD_OK) return rc;
+        }
+        PD_CUDA(cudaGraphLaunch(s->graph[s->cur], st));
+        s->step += GRAPH_CHUNK;   // GRAPH_CHUNK is even: parity unchanged
+        nsteps -= GRAPH_CHUNK;
+    }
+    while (nsteps-- > 0) {
+        rc = one_step(s, st);
+        if (rc != PD_OK) return rc;
+    }
+    return PD_OK;
+}
+
+static int tangent(pd_sim *s, const double *u_lin, const double *w, double *out, unsigned flags, int adjoint,
+                   void *stream)
+{
+    CHECK_BUILT(s);
+    if (s->mat.model != PD_MODEL_PMB) { set_error("the tangent is implemented for PMB only"); return PD_EINVAL; }
+    if (!w || !out) { set_error("null vector"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    const float4 *hl;
+    const double4_32a *d4;
+    int rc = stage_lin(s, u_lin, &hl, &d4, st);
+    if (rc != PD_OK) return rc;
+    rc = user_to_slots(s, w, s->f, st);      // unmasked copy kept in f
+    if (rc != PD_OK) return rc;
+    for (int c = 0; c < s->g.dim; ++c)
+        PD_CUDA(cudaMemcpyAsync(s->w[c], s->f[c], sizeof(double) * s->g.nslots, cudaMemcpyDeviceToDevice, st));
+    const bool mask = (flags & PD_JVP_MASK_DIRICHLET) != 0;
+    if (mask && (rc = dirichlet_mask(s->g, s->bc_kind, s->w, nullptr, 0, st)) != PD_OK) return rc;
+    TileArgs a = make_args(s, MODE_FORCE, hl, d4);
+    a.adjoint = adjoint;
+    rc = launch_jvp_args(a, s->precision, st);
+    if (rc != PD_OK) return rc;
+    if (mask) {
+        const double *src[3] = {s->f[0], s->f[1], s->f[2]};
+        if ((rc = dirichlet_mask(s->g, s->bc_kind, s->jv, src, 1, st)) != PD_OK) return rc;
+    }
+    return slots_to_user(s, s->jv, out, st);
+}
+
+int pd_jvp(pd_sim *s, const double *u_lin, const double *w, double *out, unsigned flags, void *stream)
+{
+    return tangent(s, u_lin, w, out, flags, 0, stream);
+}
+
+int pd_vjp(pd_sim *s, const double *u_lin, const double *v, double *out, unsigned flags, void *stream)
+{
+    return tangent(s, u_lin, v, out, flags, 1, stream);
+}
+
+int pd_energy(pd_sim *s, double *kinetic, double *strain, void *stream)
+{
+    CHECK_BUILT(s);
+    cudaStream_t st = pick(s, stream);
+    int rc = finalize(s, st);
+    if (rc != PD_OK) return rc;
+    TileArgs a = make_args(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur]);
+    if (s->mat.model == PD_MODEL_LPS && (rc = launch_lps_args(a, s->precision, 1, st)) != PD_OK) return rc;
+    if ((rc = launch_energy_points(a, s->precision, s->ekin, st)) != PD_OK) return rc;
+    if ((rc = reduce_sum(s->epoint, s->g.nslots, s->mat.V, s->red, s->dout, st)) != PD_OK) return rc;
+    if ((rc = reduce_sum(s->ekin, s->g.nslots, 0.5 * s->mat.rho * s->mat.V, s->red, s->dout + 1, st)) != PD_OK)
+        return rc;
+    double h[2];
+    PD_CUDA(cudaMemcpyAsync(h, s->dout, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PD_CUDA(cudaStreamSynchronize(st));
+    if (strain) *strain = h[0];
+    if (kinetic) *kinetic = h[1];
+    return PD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,715 @@
+// pd_build.cu -- neighbour build and the per-simulation tables (done once, in the
+// reference configuration, Sec. 4.2.1).
+//
+//   1. slots: tile-major Morton layout, user <-> slot maps, Morton ranks (scan);
+//   2. cell list with cell edge m h >= delta: counting sort of the points by cell;
+//   3. CSR: every point tests the points of the 3^d cells around it with the
+//      integer predicate a^2 + b^2 + c^2 <= m^2 (Sec. 3.1, points at exactly
+//      delta included); a warp per row collects its neighbours and sorts them
+//      (bitonic) so each row lists Morton ranks in ascending order;
+//   4. the CSR encoded as stencil bits per point (the bond-intact mask);
+//   5. LPS weighted volume m~_i = sum_j |d|^2 V_ij (Algorithm 2, first loop, in
+//      lattice units) and the stable-step sum of every point.
+// Atomics are used only for counts and for the order of points inside a cell;
+// the sorted CSR, the mask and every table are independent of that order.
+#include "pd_tile.cuh"
+
+namespace pdk {
+
+// ------------------------------------------------------------------ scan
+
+constexpr int SCAN_CHUNK = 1024;
+
+__global__ void k_scan_sums(const int *in, long long n, long long *bsum)
+{
+    __shared__ long long sh[256];
+    const long long lo = (long long)blockIdx.x * SCAN_CHUNK;
+    long long acc = 0;
+    for (int k = threadIdx.x; k < SCAN_CHUNK; k += blockDim.x)
+        if (lo + k < n) acc += in[lo + k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+}
+
+// Exclusive scan of the block sums in place (one block, sequential carry).
+__global__ void k_scan_offsets(long long *bsum, int nb, long long *total)
+{
+    __shared__ long long sh[256];
+    long long carry = 0;
+    for (int base = 0; base < nb; base += 256) {
+        const int i = base + threadIdx.x;
+        const long long v = i < nb ? bsum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 256; off <<= 1) {
+            long long t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+        const long long tot = sh[255];
+        __syncthreads();
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_apply(const int *in, long long n, const long long *boff, long long *out)
+{
+    __shared__ long long sh[256];
+    const long long lo = (long long)blockIdx.x * SCAN_CHUNK;
+    constexpr int PER = SCAN_CHUNK / 256;
+    long long v[PER];
+    long long acc = 0;
+    for (int k = 0; k < PER; ++k) {
+        const long long i = lo + threadIdx.x * PER + k;
+        v[k] = i < n ? in[i] : 0;
+        acc += v[k];
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        long long t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    long long run = boff[blockIdx.x] + sh[threadIdx.x] - acc;
+    for (int k = 0; k < PER; ++k) {
+        const long long i = lo + threadIdx.x * PER + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+}
+
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+static int exclusive_scan(const int *in, long long n, long long *out, cudaStream_t st)
+{
+    const int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    long long *bsum = nullptr;
+    PD_CUDA(cudaMalloc(&bsum, sizeof(long long) * (nb > 0 ? nb : 1)));
+    if (nb > 0) {
+        k_scan_sums<<<nb, 256, 0, st>>>(in, n, bsum);
+        k_scan_offsets<<<1, 256, 0, st>>>(bsum, nb, out + n);
+        k_scan_apply<<<nb, 256, 0, st>>>(in, n, bsum, out);
+    } else {
+        PD_CUDA(cudaMemsetAsync(out, 0, sizeof(long long), st));
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaStreamSynchronize(st);
+    cudaFree(bsum);
+    if (e != cudaSuccess) return cuda_fail(e, "exclusive_scan");
+    return PD_OK;
+}
+
+// ----------------------------------------------------------------- slots
+
+__device__ __forceinline__ void slot_coord(const Geom &g, const int4 *tile_org, int s, int c[3])
+{
+    const int tile = s >> g.L;
+    const int4 o = tile_org[tile];
+    int l[3];
+    morton_decode(g.dim, (uint64_t)(s & (g.T - 1)), l);
+    c[0] = o.x + l[0];
+    c[1] = o.y + l[1];
+    c[2] = o.z + l[2];
+}
+
+__global__ void k_slots(Geom g, const int4 *tile_org, int *user_of_slot, int *slot_of_user, int *active)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    int c[3];
+    slot_coord(g, tile_org, (int)s, c);
+    const bool in = c[0] < g.nx && c[1] < g.ny && c[2] < g.nz;
+    if (in) {
+        const int u = c[0] + g.nx * (c[1] + g.ny * c[2]);
+        user_of_slot[s] = u;
+        slot_of_user[u] = (int)s;
+    } else {
+        user_of_slot[s] = -1;
+    }
+    active[s] = in ? 1 : 0;
+}
+
+__global__ void k_ranks(Geom g, const int *active, const long long *scan, int *rank_of_slot, int *slot_of_rank)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    if (active[s]) {
+        const int r = (int)scan[s];
+        rank_of_slot[s] = r;
+        slot_of_rank[r] = (int)s;
+    } else {
+        rank_of_slot[s] = -1;
+    }
+}
+
+int build_slots(const Geom &g, const Tables &t, int *user_of_slot, int *slot_of_user, int *rank_of_slot,
+                int *slot_of_rank, cudaStream_t st)
+{
+    int *active = nullptr;
+    long long *scan = nullptr;
+    PD_CUDA(cudaMalloc(&active, sizeof(int) * (size_t)g.nslots));
+    PD_CUDA(cudaMalloc(&scan, sizeof(long long) * ((size_t)g.nslots + 1)));
+    const int nb = (g.nslots + 255) / 256;
+    k_slots<<<nb, 256, 0, st>>>(g, t.tile_org, user_of_slot, slot_of_user, active);
+    int rc = exclusive_scan(active, g.nslots, scan, st);
+    if (rc == PD_OK) {
+        k_ranks<<<nb, 256, 0, st>>>(g, active, scan, rank_of_slot, slot_of_rank);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "build_slots");
+    }
+    cudaFree(active);
+    cudaFree(scan);
+    return rc;
+}
+
+// ------------------------------------------------------------- cell list
+
+struct CellGrid {
+    int m, cx, cy, cz;
+};
+
+__global__ void k_rank_coords(Geom g, const int4 *tile_org, const int *slot_of_rank, int4 *crd)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    int c[3];
+    slot_coord(g, tile_org, slot_of_rank[r], c);
+    crd[r] = make_int4(c[0], c[1], c[2], 0);
+}
+
+__device__ __forceinline__ int cell_of(const CellGrid &cg, int4 c)
+{
+    return c.x / cg.m + cg.cx * (c.y / cg.m + cg.cy * (c.z / cg.m));
+}
+
+__global__ void k_cell_count(Geom g, CellGrid cg, const int4 *crd, int *cell_count)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    atomicAdd(&cell_count[cell_of(cg, crd[r])], 1);
+}
+
+__global__ void k_cell_fill(Geom g, CellGrid cg, const int4 *crd, const long long *cell_start, int *cursor,
+                            int *cell_pts)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    const int cell = cell_of(cg, crd[r]);
+    const int pos = atomicAdd(&cursor[cell], 1);
+    cell_pts[cell_start[cell] + pos] = (int)r;
+}
+
+__device__ __forceinline__ bool in_horizon(int4 a, int4 b, int m)
+{
+    const int dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    return dx * dx + dy * dy + dz * dz <= m * m;
+}
+
+__global__ void k_row_count(Geom g, CellGrid cg, const int4 *crd, const long long *cell_start,
+                            const int *cell_pts, int *row_count)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    const int4 c = crd[r];
+    const int ci = c.x / cg.m, cj = c.y / cg.m, ck = c.z / cg.m;
+    int cnt = 0;
+    for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                const int a = ci + di, b = cj + dj, e = ck + dk;
+                if (a < 0 || b < 0 || e < 0 || a >= cg.cx || b >= cg.cy || e >= cg.cz) continue;
+                const int cell = a + cg.cx * (b + cg.cy * e);
+                for (long long p = cell_start[cell]; p < cell_start[cell + 1]; ++p) {
+                    const int j = cell_pts[p];
+                    if (j != r && in_horizon(c, crd[j], g.m)) ++cnt;
+                }
+            }
+    row_count[r] = cnt;
+}
+
+constexpr int ROW_CAP = 2048;
+constexpr int FILL_WARPS = 4;
+
+// A warp per row: gather the row from the cell list, bitonic-sort it in shared
+// memory, write it out. err[0] is set if a row differs from its counted length.
+__global__ void __launch_bounds__(32 * FILL_WARPS) k_row_fill(Geom g, CellGrid cg, const int4 *crd,
+                                                              const long long *cell_start, const int *cell_pts,
+                                                              const int64_t *row_ptr, int *col, int *err)
+{
+    __shared__ int buf[FILL_WARPS][ROW_CAP];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const long long r = (long long)blockIdx.x * FILL_WARPS + warp;
+    if (r >= g.npoints) return;
+    int *b = buf[warp];
+    const int4 c = crd[r];
+    const int ci = c.x / cg.m, cj = c.y / cg.m, ck = c.z / cg.m;
+    int cnt = 0;
+    for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                const int a = ci + di, bb = cj + dj, e = ck + dk;
+                if (a < 0 || bb < 0 || e < 0 || a >= cg.cx || bb >= cg.cy || e >= cg.cz) continue;
+                const int cell = a + cg.cx * (bb + cg.cy * e);
+                const long long p0 = cell_start[cell], p1 = cell_start[cell + 1];
+                for (long long p = p0; p < p1; p += 32) {
+                    const long long q = p + lane;
+                    bool hit = false;
+                    int j = -1;
+                    if (q < p1) {
+                        j = cell_pts[q];
+                        hit = j != r && in_horizon(c, crd[j], g.m);
+                    }
+                    const unsigned ball = __ballot_sync(0xffffffffu, hit);
+                    const int pos = cnt + __popc(ball & ((1u << lane) - 1u));
+                    if (hit && pos < ROW_CAP) b[pos] = j;
+                    cnt += __popc(ball);
+                }
+            }
+    const long long base = row_ptr[r];
+    const int want = (int)(row_ptr[r + 1] - base);
+    if (cnt != want || cnt > ROW_CAP) {
+        if (lane == 0) atomicExch(err, 1);
+        return;
+    }
+    int N = 1;
+    while (N < cnt) N <<= 1;
+    for (int i = cnt + lane; i < N; i += 32) b[i] = 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < N; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const int x = b[i], y = b[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        b[i] = y;
+                        b[ixj] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < cnt; i += 32) col[base + i] = b[i];
+}
+
+int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
+{
+    CellGrid cg;
+    cg.m = g.m;
+    cg.cx = (g.nx + g.m - 1) / g.m;
+    cg.cy = (g.ny + g.m - 1) / g.m;
+    cg.cz = (g.nz + g.m - 1) / g.m;
+    const long long ncell = (long long)cg.cx * cg.cy * cg.cz;
+    const long long n = g.npoints;
+    int4 *crd = nullptr;
+    int *cell_count = nullptr, *cursor = nullptr, *cell_pts = nullptr, *row_count = nullptr, *err = nullptr;
+    long long *cell_start = nullptr;
+    int rc = PD_OK;
+    out->row_ptr = nullptr;
+    out->col = nullptr;
+    out->nbonds = 0;
+#define B_ALLOC(p, bytes)                                              \
+    do {                                                               \
+        if (cudaMalloc(&(p), (bytes)) != cudaSuccess) {                \
+            rc = PD_ENOMEM;                                            \
+            set_error("cudaMalloc of %lld bytes failed", (long long)(bytes)); \
+            goto done;                                                 \
+        }                                                              \
+    } while (0)
+    B_ALLOC(crd, sizeof(int4) * n);
+    B_ALLOC(cell_count, sizeof(int) * ncell);
+    B_ALLOC(cursor, sizeof(int) * ncell);
+    B_ALLOC(cell_start, sizeof(long long) * (ncell + 1));
+    B_ALLOC(cell_pts, sizeof(int) * n);
+    B_ALLOC(row_count, sizeof(int) * n);
+    B_ALLOC(err, sizeof(int));
+    B_ALLOC(out->row_ptr, sizeof(long long) * (n + 1));
+    {
+        const int nb = (int)((n + 255) / 256);
+        cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell, st);
+        cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st);
+        cudaMemsetAsync(err, 0, sizeof(int), st);
+        k_rank_coords<<<nb, 256, 0, st>>>(g, t.tile_org, t.slot_of_rank, crd);
+        k_cell_count<<<nb, 256, 0, st>>>(g, cg, crd, cell_count);
+        rc = exclusive_scan(cell_count, ncell, cell_start, st);
+        if (rc != PD_OK) goto done;
+        k_cell_fill<<<nb, 256, 0, st>>>(g, cg, crd, cell_start, cursor, cell_pts);
+        k_row_count<<<nb, 256, 0, st>>>(g, cg, crd, cell_start, cell_pts, row_count);
+        rc = exclusive_scan(row_count, n, (long long *)out->row_ptr, st);
+        if (rc != PD_OK) goto done;
+        long long nbonds = 0;
+        if (cudaMemcpy(&nbonds, out->row_ptr + n, sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "row_ptr readback");
+            goto done;
+        }
+        out->nbonds = nbonds;
+        B_ALLOC(out->col, sizeof(int) * (nbonds > 0 ? nbonds : 1));
+        const int nbw = (int)((n + FILL_WARPS - 1) / FILL_WARPS);
+        k_row_fill<<<nbw, 32 * FILL_WARPS, 0, st>>>(g, cg, crd, cell_start, cell_pts, out->row_ptr, out->col, err);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "neighbour rows");
+            goto done;
+        }
+        int herr = 0;
+        cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (herr) {
+            rc = PD_EINVAL;
+            set_error("neighbour row longer than %d entries or inconsistent", ROW_CAP);
+        }
+    }
+done:
+#undef B_ALLOC
+    cudaFree(crd);
+    cudaFree(cell_count);
+    cudaFree(cursor);
+    cudaFree(cell_start);
+    cudaFree(cell_pts);
+    cudaFree(row_count);
+    cudaFree(err);
+    if (rc != PD_OK) {
+        cudaFree(out->row_ptr);
+        cudaFree(out->col);
+        out->row_ptr = nullptr;
+        out->col = nullptr;
+    }
+    return rc;
+}
+
+// --------------------------------------------------------- stencil mask
+
+__device__ __forceinline__ int stencil_index(const Geom &g, const int *lut, int dx, int dy, int dz)
+{
+    const int w = 2 * g.m + 1;
+    if (dx < -g.m || dx > g.m || dy < -g.m || dy > g.m || dz < -g.m || dz > g.m) return -1;
+    return lut[(dx + g.m) + w * ((dy + g.m) + w * (g.dim == 3 ? dz + g.m : 0))];
+}
+
+constexpr int MAX_WORDS = 64;
+
+__global__ void k_mask(Geom g, const int4 *tile_org, const int *slot_of_rank, const int *stencil_lut,
+                       const int64_t *row_ptr, const int *col, uint32_t *mask, int *err)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    const int s = slot_of_rank[r];
+    int c[3];
+    slot_coord(g, tile_org, s, c);
+    uint32_t words[MAX_WORDS];
+    for (int w = 0; w < g.W; ++w) words[w] = 0u;
+    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        int cj[3];
+        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
+        const int k = stencil_index(g, stencil_lut, cj[0] - c[0], cj[1] - c[1], cj[2] - c[2]);
+        if (k < 0) {
+            atomicExch(err, 2);
+            continue;
+        }
+        words[k >> 5] |= 1u << (k & 31);
+    }
+    for (int w = 0; w < g.W; ++w) mask[(size_t)w * g.nslots + s] = words[w];
+}
+
+int build_mask(const Geom &g, const Tables &t, const BuildOut &csr, uint32_t *mask, int *d_err, cudaStream_t st)
+{
+    if (g.W > MAX_WORDS) {
+        set_error("stencil of %d offsets exceeds %d mask words", g.S, MAX_WORDS);
+        return PD_EINVAL;
+    }
+    PD_CUDA(cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (size_t)g.W * g.nslots, st));
+    PD_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    k_mask<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.tile_org, t.slot_of_rank, t.stencil_lut, csr.row_ptr,
+                                                    csr.col, mask, d_err);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaStreamSynchronize(st));
+    int herr = 0;
+    PD_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        set_error("a CSR entry lies outside the horizon stencil");
+        return PD_EINVAL;
+    }
+    return PD_OK;
+}
+
+// --------------------------------------------- weighted volume, step bound
+
+__device__ __forceinline__ double vol_factor_dev(int m, double r0, int vol_corr)
+{
+    return vol_corr ? vol_factor_lattice(m, r0) : 1.0;
+}
+
+__global__ void k_weighted_volume(Geom g, int vol_corr, const int4 *tile_org, const int *slot_of_rank,
+                                  const int64_t *row_ptr, const int *col, double *mtil, float *minv32)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    const int s = slot_of_rank[r];
+    int c[3];
+    slot_coord(g, tile_org, s, c);
+    double acc = 0.0;
+    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        int cj[3];
+        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
+        const double dx = cj[0] - c[0], dy = cj[1] - c[1], dz = cj[2] - c[2];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        acc += d2 * vol_factor_dev(g.m, sqrt(d2), vol_corr);
+    }
+    mtil[s] = acc;
+    minv32[s] = acc > 0.0 ? (float)(1.0 / acc) : 0.f;
+}
+
+int build_weighted_volume(const Geom &g, const Material &mat, const Tables &t, const BuildOut &csr, double *mtil,
+                          float *minv32, cudaStream_t st)
+{
+    k_weighted_volume<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, mat.vol_corr, t.tile_org, t.slot_of_rank,
+                                                              csr.row_ptr, csr.col, mtil, minv32);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// max_i sum_j V_ij / |d| (lattice units); positive doubles order like their bits.
+__global__ void k_dt_sum(Geom g, int vol_corr, const int4 *tile_org, const int *slot_of_rank,
+                         const int64_t *row_ptr, const int *col, unsigned long long *smax)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    int c[3];
+    slot_coord(g, tile_org, slot_of_rank[r], c);
+    double acc = 0.0;
+    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        int cj[3];
+        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
+        const double dx = cj[0] - c[0], dy = cj[1] - c[1], dz = cj[2] - c[2];
+        const double r0 = sqrt(dx * dx + dy * dy + dz * dz);
+        acc += vol_factor_dev(g.m, r0, vol_corr) / r0;
+    }
+    atomicMax(smax, (unsigned long long)__double_as_longlong(acc));
+}
+
+int build_dt_bound(const Geom &g, const Material &mat, const Tables &t, const BuildOut &csr, double *d_sum_max,
+                   cudaStream_t st)
+{
+    PD_CUDA(cudaMemsetAsync(d_sum_max, 0, sizeof(double), st));
+    k_dt_sum<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, mat.vol_corr, t.tile_org, t.slot_of_rank, csr.row_ptr,
+                                                      csr.col, reinterpret_cast<unsigned long long *>(d_sum_max));
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// ------------------------------------------------------- CSR bond state
+
+__global__ void k_csr_broken(Geom g, const int4 *tile_org, const int *slot_of_rank, const int *stencil_lut,
+                             const int64_t *row_ptr, const int *col, const uint32_t *mask, uint8_t *out)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.npoints) return;
+    const int s = slot_of_rank[r];
+    int c[3];
+    slot_coord(g, tile_org, s, c);
+    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+        int cj[3];
+        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
+        const int k = stencil_index(g, stencil_lut, cj[0] - c[0], cj[1] - c[1], cj[2] - c[2]);
+        if (k < 0) {
+            out[e] = 1;
+            continue;
+        }
+        const uint32_t word = mask[(size_t)(k >> 5) * g.nslots + s];
+        out[e] = ((word >> (k & 31)) & 1u) ? 0 : 1;
+    }
+}
+
+int csr_broken_flags(const Geom &g, const Tables &t, const BuildOut &csr, const uint32_t *mask, uint8_t *out,
+                     cudaStream_t st)
+{
+    k_csr_broken<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.tile_org, t.slot_of_rank, t.stencil_lut,
+                                                          csr.row_ptr, csr.col, mask, out);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// -------------------------------------------------------------- pre-notch
+
+struct NotchDesc {
+    int axis;
+    double pos;
+    double lo[3], hi[3];
+};
+
+// Segment X_i -> X_j crosses {x[axis] = pos} inside the rectangle. With
+// D = c_j[axis] - c_i[axis], the crossing point satisfies
+// P_b D = c_i[b] D + (pos - c_i[axis]) (c_j[b] - c_i[b]), exact in FP64 for
+// lattice coordinates and a half-integer pos; compare against lo D and hi D.
+__device__ __forceinline__ bool crosses(const NotchDesc &nd, int dim, const int ci[3], const int cj[3])
+{
+    const double si = __dadd_rn((double)ci[nd.axis], -nd.pos);
+    const double sj = __dadd_rn((double)cj[nd.axis], -nd.pos);
+    if (!((si < 0.0 && sj > 0.0) || (si > 0.0 && sj < 0.0))) return false;
+    const int D = cj[nd.axis] - ci[nd.axis];
+    const double ad = (double)(D < 0 ? -D : D);
+    const double sgn = D < 0 ? -1.0 : 1.0;
+    for (int b = 0; b < dim; ++b) {
+        if (b == nd.axis) continue;
+        const double pd = __dadd_rn(__dmul_rn((double)ci[b], (double)D),
+                                    __dmul_rn(__dadd_rn(nd.pos, -(double)ci[nd.axis]), (double)(cj[b] - ci[b])));
+        const double v = __dmul_rn(sgn, pd);
+        if (v < __dmul_rn(nd.lo[b], ad) || v > __dmul_rn(nd.hi[b], ad)) return false;
+    }
+    return true;
+}
+
+__global__ void k_notch(Geom g, const int4 *tile_org, const int *user_of_slot, const int4 *stencil, NotchDesc nd,
+                        uint32_t *mask, unsigned long long *count)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots || user_of_slot[s] < 0) return;
+    int c[3];
+    slot_coord(g, tile_org, (int)s, c);
+    unsigned long long local = 0;
+    for (int w = 0; w < g.W; ++w) {
+        uint32_t word = mask[(size_t)w * g.nslots + s];
+        const uint32_t orig = word;
+        const int nb = min(32, g.S - 32 * w);
+        for (int b = 0; b < nb; ++b) {
+            if (!((word >> b) & 1u)) continue;
+            const int4 d = stencil[32 * w + b];
+            const int cj[3] = {c[0] + d.x, c[1] + d.y, c[2] + d.z};
+            if (crosses(nd, g.dim, c, cj)) {
+                word &= ~(1u << b);
+                ++local;
+            }
+        }
+        if (word != orig) mask[(size_t)w * g.nslots + s] = word;
+    }
+    if (local) atomicAdd(count, local);
+}
+
+int break_notch(const Geom &g, const Tables &t, uint32_t *mask, int axis, double pos, const double lo[3],
+                const double hi[3], unsigned long long *d_count, cudaStream_t st)
+{
+    NotchDesc nd;
+    nd.axis = axis;
+    nd.pos = pos;
+    for (int b = 0; b < 3; ++b) {
+        nd.lo[b] = lo[b];
+        nd.hi[b] = hi[b];
+    }
+    PD_CUDA(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
+    k_notch<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, t.tile_org, t.user_of_slot, t.stencil, nd, mask, d_count);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// ---------------------------------------------------------- permutations
+
+__global__ void k_scatter(Geom g, const int *slot_of_user, const double *user, double *s0, double *s1, double *s2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.npoints) return;
+    const int s = slot_of_user[i];
+    double *dst[3] = {s0, s1, s2};
+    for (int c = 0; c < g.dim; ++c) dst[c][s] = user[i * g.dim + c];
+}
+
+__global__ void k_gather(Geom g, const int *slot_of_user, const double *s0, const double *s1, const double *s2,
+                         double *user)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.npoints) return;
+    const int s = slot_of_user[i];
+    const double *src[3] = {s0, s1, s2};
+    for (int c = 0; c < g.dim; ++c) user[i * g.dim + c] = src[c][s];
+}
+
+int scatter_user_to_slots(const Geom &g, const Tables &t, const double *user, double *const slot[3], double fill,
+                          cudaStream_t st)
+{
+    (void)fill;
+    k_scatter<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.slot_of_user, user, slot[0], slot[1], slot[2]);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int gather_slots_to_user(const Geom &g, const Tables &t, double *const slot[3], double *user, cudaStream_t st)
+{
+    k_gather<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.slot_of_user, slot[0], slot[1], slot[2], user);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+__global__ void k_scatter_kinds(Geom g, const int *slot_of_user, const uint8_t *user, uint8_t *kind, int *err)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.npoints) return;
+    const int s = slot_of_user[i];
+    for (int c = 0; c < g.dim; ++c) {
+        const uint8_t k = user[i * g.dim + c];
+        if (k > PD_BC_DISPLACEMENT) atomicExch(err, 1);
+        kind[(size_t)c * g.nslots + s] = k <= PD_BC_DISPLACEMENT ? k : 0;
+    }
+}
+
+int scatter_kinds(const Geom &g, const Tables &t, const uint8_t *user, uint8_t *kind, int *err, cudaStream_t st)
+{
+    k_scatter_kinds<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.slot_of_user, user, kind, err);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// Staging buffer from FP64 SoA displacements (FP32 hi/lo pairs or double4_32a).
+__global__ void k_pack_stage(Geom g, const double *u0, const double *u1, const double *u2, float4 *hl, double4_32a *d4)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const double x = u0[s], y = u1[s], z = g.dim == 3 ? u2[s] : 0.0;
+    if (d4) {
+        d4[s] = make_double4_32a(x, y, z, 0.0);
+    } else {
+        const float hx = (float)x, hy = (float)y, hz = (float)z;
+        hl[2 * s] = make_float4(hx, hy, hz, 0.f);
+        hl[2 * s + 1] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
+    }
+}
+
+int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st)
+{
+    k_pack_stage<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, u[0], u[1], u[2], hl, d4);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// Zero the prescribed-displacement components of a slot-order vector (JVP masking),
+// or copy them from src into dst (identity rows).
+__global__ void k_dirichlet(Geom g, const uint8_t *kind, double *v0, double *v1, double *v2, const double *w0,
+                            const double *w1, const double *w2, int copy)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    double *v[3] = {v0, v1, v2};
+    const double *w[3] = {w0, w1, w2};
+    for (int c = 0; c < g.dim; ++c)
+        if (kind[(size_t)c * g.nslots + s] == PD_BC_DISPLACEMENT) v[c][s] = copy ? w[c][s] : 0.0;
+}
+
+int dirichlet_mask(const Geom &g, const uint8_t *kind, double *const v[3], const double *const w[3], int copy,
+                   cudaStream_t st)
+{
+    k_dirichlet<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, kind, v[0], v[1], v[2], w ? w[0] : nullptr,
+                                                        w ? w[1] : nullptr, w ? w[2] : nullptr, copy);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+}  // namespace pdk

@@ -1,0 +1,294 @@
+"""Python binding of libpd (include/pd.h): the same entry points, argument
+marshalling only. Every computation runs in the CUDA library; importing this
+module raises if ``libpd.so`` has not been built.
+
+Array arguments may be numpy arrays (host memory) or torch CUDA tensors (device
+memory of the current device); both are passed to the library as raw pointers.
+The binding checks dtype, contiguity and size before each call so that the
+library never reads or writes outside the caller's buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpd.so")
+
+PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_EBUSY, PD_ENOTREADY, PD_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PD_MODEL_PMB, PD_MODEL_LPS = 0, 1
+PD_FP32C, PD_FP64 = 0, 1
+PD_BC_FREE, PD_BC_VELOCITY, PD_BC_DISPLACEMENT = 0, 1, 2
+PD_FORCE_UPDATE_BREAKING = 1
+PD_JVP_MASK_DIRICHLET = 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpd.so is not built (%s); run __graft_entry__.build() or "
+                      "python paper_1806_06917_gb300/build.py" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class pd_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("m", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("h", ctypes.c_double), ("origin", ctypes.c_double * 3)]
+
+
+class pd_material(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("vol_corr", ctypes.c_int32), ("E", ctypes.c_double),
+                ("rho", ctypes.c_double), ("K", ctypes.c_double), ("mu", ctypes.c_double),
+                ("s_c", ctypes.c_double), ("thickness", ctypes.c_double)]
+
+
+class pd_run(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dt_factor", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("tile_log2", ctypes.c_int32)]
+
+
+class PdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libpd error %d: %s" % (code, msg))
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "pd_create": [ctypes.POINTER(_P), ctypes.POINTER(pd_grid), ctypes.POINTER(pd_material), ctypes.POINTER(pd_run)],
+    "pd_destroy": [_P],
+    "pd_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+    "pd_build_neighbors": [_P, _P],
+    "pd_bond_count": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "pd_get_neighbors": [_P, _P, _P, _P, _P],
+    "pd_get_broken": [_P, _P, _P],
+    "pd_break_bonds": [_P, ctypes.c_int, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_int64), _P],
+    "pd_set_state": [_P, _P, _P, _P],
+    "pd_get_state": [_P, _P, _P, _P],
+    "pd_set_bc": [_P, _P, _P, _P],
+    "pd_set_body_force": [_P, _P, _P],
+    "pd_get_dt": [_P, ctypes.POINTER(ctypes.c_double)],
+    "pd_set_dt": [_P, ctypes.c_double],
+    "pd_get_step": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "pd_force": [_P, _P, _P, ctypes.c_uint, _P],
+    "pd_dilatation": [_P, _P, _P, _P],
+    "pd_step_explicit": [_P, ctypes.c_int64, _P],
+    "pd_jvp": [_P, _P, _P, _P, ctypes.c_uint, _P],
+    "pd_vjp": [_P, _P, _P, _P, ctypes.c_uint, _P],
+    "pd_energy": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int
+
+EXPORTS = tuple(_SIGS)
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    _lib.pd_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int) -> None:
+    if rc != PD_OK:
+        raise PdError(rc, last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return _P(stream.cuda_stream)
+    return _P(int(stream))
+
+
+def _buf(x, dtype, count, name, writable=False):
+    """Raw pointer of a numpy array or torch tensor with exactly `count` elements."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):          # torch tensor
+        import torch
+        tdt = {np.float64: torch.float64, np.uint8: torch.uint8, np.int64: torch.int64,
+               np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous() or x.numel() != count:
+            raise ValueError("%s: need a contiguous %s tensor of %d elements" % (name, tdt, count))
+        return _P(x.data_ptr())
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous or x.size != count:
+        raise ValueError("%s: need a C-contiguous numpy %s array of %d elements" % (name, np.dtype(dtype), count))
+    if writable and not x.flags.writeable:
+        raise ValueError("%s: array is read-only" % name)
+    return x.ctypes.data_as(_P)
+
+
+class Sim:
+    """Owner of one pd_sim handle; every method is the C call of the same name."""
+
+    def __init__(self, grid: pd_grid, mat: pd_material, run: pd_run):
+        h = _P()
+        _check(_lib.pd_create(ctypes.byref(h), ctypes.byref(grid), ctypes.byref(mat), ctypes.byref(run)))
+        self.h = h
+        self.grid, self.mat, self.run = grid, mat, run
+        self.dim = grid.dim
+        self.npoints = grid.n[0] * grid.n[1] * grid.n[2]
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.pd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nvec(self):
+        return self.npoints * self.dim
+
+
+def pd_create(grid: pd_grid, mat: pd_material, run: pd_run) -> Sim:
+    return Sim(grid, mat, run)
+
+
+def pd_destroy(sim: Sim) -> None:
+    sim.close()
+
+
+def pd_build_neighbors(sim: Sim, stream=None) -> None:
+    _check(_lib.pd_build_neighbors(sim.h, _stream(stream)))
+
+
+def pd_bond_count(sim: Sim) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.pd_bond_count(sim.h, ctypes.byref(v)))
+    return v.value
+
+
+def pd_get_neighbors(sim: Sim, row_ptr=None, col=None, perm=None, stream=None):
+    """CSR in Morton numbering and the Morton permutation (allocated if not given)."""
+    nb = pd_bond_count(sim)
+    row_ptr = np.empty(sim.npoints + 1, np.int64) if row_ptr is None else row_ptr
+    col = np.empty(nb, np.int32) if col is None else col
+    perm = np.empty(sim.npoints, np.int64) if perm is None else perm
+    _check(_lib.pd_get_neighbors(sim.h, _buf(row_ptr, np.int64, sim.npoints + 1, "row_ptr", True),
+                                 _buf(col, np.int32, nb, "col", True),
+                                 _buf(perm, np.int64, sim.npoints, "perm", True), _stream(stream)))
+    return row_ptr, col, perm
+
+
+def pd_get_broken(sim: Sim, out=None, stream=None):
+    nb = pd_bond_count(sim)
+    out = np.empty(nb, np.uint8) if out is None else out
+    _check(_lib.pd_get_broken(sim.h, _buf(out, np.uint8, nb, "broken", True), _stream(stream)))
+    return out
+
+
+def pd_break_bonds(sim: Sim, axis: int, pos: float, lo, hi, stream=None) -> int:
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    if lo.size != 3 or hi.size != 3:
+        raise ValueError("lo and hi need 3 entries")
+    n = ctypes.c_int64()
+    _check(_lib.pd_break_bonds(sim.h, int(axis), float(pos), _buf(lo, np.float64, 3, "lo"),
+                               _buf(hi, np.float64, 3, "hi"), ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def pd_set_state(sim: Sim, u=None, v=None, stream=None) -> None:
+    _check(_lib.pd_set_state(sim.h, _buf(u, np.float64, sim.nvec, "u"), _buf(v, np.float64, sim.nvec, "v"),
+                             _stream(stream)))
+
+
+def pd_get_state(sim: Sim, u=None, v=None, stream=None):
+    u = np.empty((sim.npoints, sim.dim)) if u is None else u
+    v = np.empty((sim.npoints, sim.dim)) if v is None else v
+    _check(_lib.pd_get_state(sim.h, _buf(u, np.float64, sim.nvec, "u", True),
+                             _buf(v, np.float64, sim.nvec, "v", True), _stream(stream)))
+    return u, v
+
+
+def pd_set_bc(sim: Sim, kind=None, value=None, stream=None) -> None:
+    _check(_lib.pd_set_bc(sim.h, _buf(kind, np.uint8, sim.nvec, "kind"),
+                          _buf(value, np.float64, sim.nvec, "value"), _stream(stream)))
+
+
+def pd_set_body_force(sim: Sim, b=None, stream=None) -> None:
+    _check(_lib.pd_set_body_force(sim.h, _buf(b, np.float64, sim.nvec, "b"), _stream(stream)))
+
+
+def pd_get_dt(sim: Sim) -> float:
+    v = ctypes.c_double()
+    _check(_lib.pd_get_dt(sim.h, ctypes.byref(v)))
+    return v.value
+
+
+def pd_set_dt(sim: Sim, dt: float) -> None:
+    _check(_lib.pd_set_dt(sim.h, float(dt)))
+
+
+def pd_get_step(sim: Sim) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.pd_get_step(sim.h, ctypes.byref(v)))
+    return v.value
+
+
+def pd_force(sim: Sim, u=None, f_out=None, flags: int = 0, stream=None):
+    f_out = np.empty((sim.npoints, sim.dim)) if f_out is None else f_out
+    _check(_lib.pd_force(sim.h, _buf(u, np.float64, sim.nvec, "u"),
+                         _buf(f_out, np.float64, sim.nvec, "f_out", True), int(flags), _stream(stream)))
+    return f_out
+
+
+def pd_dilatation(sim: Sim, u=None, theta_out=None, stream=None):
+    theta_out = np.empty(sim.npoints) if theta_out is None else theta_out
+    _check(_lib.pd_dilatation(sim.h, _buf(u, np.float64, sim.nvec, "u"),
+                              _buf(theta_out, np.float64, sim.npoints, "theta", True), _stream(stream)))
+    return theta_out
+
+
+def pd_step_explicit(sim: Sim, nsteps: int, stream=None) -> None:
+    _check(_lib.pd_step_explicit(sim.h, int(nsteps), _stream(stream)))
+
+
+def pd_jvp(sim: Sim, w, u_lin=None, out=None, flags: int = 0, stream=None):
+    out = np.empty((sim.npoints, sim.dim)) if out is None else out
+    _check(_lib.pd_jvp(sim.h, _buf(u_lin, np.float64, sim.nvec, "u_lin"), _buf(w, np.float64, sim.nvec, "w"),
+                       _buf(out, np.float64, sim.nvec, "out", True), int(flags), _stream(stream)))
+    return out
+
+
+def pd_vjp(sim: Sim, v, u_lin=None, out=None, flags: int = 0, stream=None):
+    out = np.empty((sim.npoints, sim.dim)) if out is None else out
+    _check(_lib.pd_vjp(sim.h, _buf(u_lin, np.float64, sim.nvec, "u_lin"), _buf(v, np.float64, sim.nvec, "v"),
+                       _buf(out, np.float64, sim.nvec, "out", True), int(flags), _stream(stream)))
+    return out
+
+
+def pd_energy(sim: Sim, stream=None):
+    k, s = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.pd_energy(sim.h, ctypes.byref(k), ctypes.byref(s), _stream(stream)))
+    return k.value, s.value
+
+
+# ------------------------------------------------------------ conveniences
+
+def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=0.5, tile_log2=0):
+    """pd_grid / pd_material / pd_run from the plain workload descriptions."""
+    g = pd_grid()
+    g.dim = workload_grid.dim
+    for a in range(3):
+        g.n[a] = workload_grid.n[a]
+        g.origin[a] = workload_grid.origin[a]
+    g.m = workload_grid.m
+    g.reserved = 0
+    g.h = workload_grid.h
+    m = pd_material()
+    m.model = workload_mat.model
+    m.vol_corr = workload_mat.vol_corr
+    m.E, m.rho, m.K, m.mu = workload_mat.E, workload_mat.rho, workload_mat.K, workload_mat.mu
+    m.s_c, m.thickness = workload_mat.s_c, workload_mat.thickness
+    r = pd_run()
+    r.dt, r.dt_factor, r.precision, r.tile_log2 = dt, dt_factor, precision, tile_log2
+    return g, m, r

@@ -1,0 +1,393 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bars: neighbour lists, permutation and bond states bit-exact; FP64 GPU path
+within round-off (1e-10 relative L2); FP32-compensated force within 1e-5
+relative L2; displacement within 1e-4 relative L2 after a full run; broken-bond
+sets equal except for bonds whose stretch lies within 1e-5 relative of s_c.
+Sizes span several tiles (8x8x8 bricks in 3D, 32x16 in 2D) and ragged edges.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1806_06917_gb300 import workloads as W
+from tests.helpers import gpu_csr_in_user_numbering, gpu_sim, oracle_pairs, oracle_setup, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL_FP32C = 1e-5
+U_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def pd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_06917_gb300 import pd as _pd
+    return _pd
+
+
+GRIDS = [
+    (2, (7, 5, 1), 2), (2, (13, 9, 1), 3), (2, (50, 50, 1), 3), (2, (70, 37, 1), 4),
+    (3, (9, 7, 8), 3), (3, (10, 9, 9), 4), (3, (20, 20, 20), 3), (3, (37, 29, 11), 3), (3, (17, 9, 26), 2),
+    (3, (1, 1, 1), 3), (2, (1, 3, 1), 1),
+]
+
+
+# ----------------------------------------------------------------- neighbours
+
+@pytest.mark.parametrize("dim,n,m", GRIDS)
+def test_neighbour_csr_and_morton_order_bit_exact(pd, dim, n, m):
+    grid = W.Grid(dim=dim, n=n, h=0.01, m=m)
+    mat = W.Material(model=W.PMB)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP32C, dt=1e-7)
+    rows_u, cols_u, _, (row_ptr, col, perm) = gpu_csr_in_user_numbering(pd, sim)
+    assert np.array_equal(perm, O.morton_perm(grid))
+    bonds = O.neighbors(grid, "brute" if grid.npoints <= 4000 else "cells")
+    r_o, c_o = oracle_pairs(bonds)
+    assert pd.pd_bond_count(sim) == bonds.nbonds
+    assert np.array_equal(rows_u, r_o) and np.array_equal(cols_u, c_o)
+    for r in range(min(grid.npoints, 2000)):                 # rows ascending in Morton numbering
+        seg = col[row_ptr[r]:row_ptr[r + 1]]
+        assert np.all(np.diff(seg) > 0)
+    assert not pd.pd_get_broken(sim).any()
+    sim.close()
+
+
+def test_notch_bond_states_bit_exact(pd):
+    wl = W.block3d_pulse(nside=20, steps=1)
+    sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C, notch=wl.notch)
+    bonds = oracle_setup(wl)
+    _, _, order, _ = gpu_csr_in_user_numbering(pd, sim)
+    brk = pd.pd_get_broken(sim)[order]
+    assert brk.sum() > 0
+    assert np.array_equal(brk, bonds.broken)
+    sim.close()
+
+
+# ------------------------------------------------------------------- forces
+
+def _u_random(grid, scale, seed, translate=0.0):
+    u = W.random_field(grid, scale * grid.h, seed)
+    return u + translate
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("dim,n,m", [(2, (50, 50, 1), 3), (2, (70, 37, 1), 4), (3, (20, 20, 20), 3),
+                                     (3, (37, 29, 11), 3), (3, (17, 9, 26), 2), (3, (12, 12, 12), 4)])
+def test_pmb_force_matches_oracle(pd, precision, dim, n, m):
+    grid = W.Grid(dim=dim, n=n, h=1.0 / 64, m=m)
+    mat = W.Material(model=W.PMB, E=72e9)
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim = gpu_sim(pd, grid, mat, prec)
+    bonds = O.neighbors(grid)
+    # strain ~1e-4 plus a rigid translation of 0.3 m, which FP32 alone could not resolve
+    u = _u_random(grid, 1e-4, seed=21, translate=0.3) + 1e-4 * grid.positions()
+    f_gpu = pd.pd_force(sim, u=u)
+    f_or = O.pmb_force(grid, mat, bonds, u)
+    tol = FORCE_TOL_FP32C if precision == "fp32c" else 1e-10
+    assert rel_l2(f_gpu, f_or) <= tol
+    # the current state path (no u argument) gives the same as passing u
+    pd.pd_set_state(sim, u=u)
+    assert np.array_equal(pd.pd_force(sim), f_gpu)
+    sim.close()
+
+
+@pytest.mark.parametrize("vol_corr", [0, 1])
+def test_pmb_partial_volume_matches_oracle(pd, vol_corr):
+    grid = W.Grid(dim=3, n=(19, 18, 17), h=0.01, m=3)
+    mat = W.Material(model=W.PMB, E=72e9, vol_corr=vol_corr)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP32C)
+    u = _u_random(grid, 3e-4, seed=3)
+    assert rel_l2(pd.pd_force(sim, u=u), O.pmb_force(grid, mat, O.neighbors(grid), u)) <= FORCE_TOL_FP32C
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_pmb_breaking_matches_oracle(pd, precision):
+    grid = W.Grid(dim=3, n=(18, 17, 16), h=0.01, m=3)
+    s_c = 1e-3
+    mat = W.Material(model=W.PMB, E=72e9, s_c=s_c)
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim = gpu_sim(pd, grid, mat, prec)
+    bonds = O.neighbors(grid)
+    # stretches spread around s_c
+    u = _u_random(grid, 1.2e-3, seed=9)
+    f_gpu = pd.pd_force(sim, u=u, flags=pd.PD_FORCE_UPDATE_BREAKING)
+    f_or = O.pmb_force(grid, mat, bonds, u, update_breaking=True)
+    _, _, order, _ = gpu_csr_in_user_numbering(pd, sim)
+    brk = pd.pd_get_broken(sim)[order].astype(bool)
+    ob = bonds.broken.astype(bool)
+    assert 0.05 < ob.mean() < 0.95
+    # stretch of every bond (oracle arithmetic) to locate the ones near s_c
+    X = grid.positions()
+    r, c = oracle_pairs(bonds)
+    xi = X[c] - X[r]
+    y = xi + (u[c] - u[r])
+    s = (np.linalg.norm(y, axis=1) - np.linalg.norm(xi, axis=1)) / np.linalg.norm(xi, axis=1)
+    near = np.abs(s - s_c) <= 1e-5 * s_c
+    assert np.array_equal(brk[~near], ob[~near])
+    if not near.any():
+        assert rel_l2(f_gpu, f_or) <= (FORCE_TOL_FP32C if precision == "fp32c" else 1e-10)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("n", [(20, 20, 20), (37, 29, 11)])
+def test_lps_dilatation_and_force_match_oracle(pd, precision, n):
+    grid = W.Grid(dim=3, n=n, h=1.0 / 128, m=3)
+    mat = W.Material(model=W.LPS, K=40e9, mu=30e9)
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim = gpu_sim(pd, grid, mat, prec)
+    bonds = O.neighbors(grid)
+    mv = O.weighted_volume(grid, mat, bonds)
+    u = (1e-4 / 3) * grid.positions() + _u_random(grid, 1e-5, seed=3, translate=0.2)
+    th_gpu = pd.pd_dilatation(sim, u=u)
+    th_or = O.dilatation(grid, mat, bonds, mv, u)
+    f_gpu = pd.pd_force(sim, u=u)
+    f_or = O.lps_force(grid, mat, bonds, mv, th_or, u)
+    tol = FORCE_TOL_FP32C if precision == "fp32c" else 1e-10
+    assert rel_l2(th_gpu, th_or) <= tol
+    assert rel_l2(f_gpu, f_or) <= tol
+    sim.close()
+
+
+# ---------------------------------------------------------------- explicit
+
+def _run_both(pd, wl, precision, steps, dt=None):
+    sim = gpu_sim(pd, wl.grid, wl.mat, precision, notch=wl.notch)
+    bonds = oracle_setup(wl)
+    dt_o = wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
+    assert abs(pd.pd_get_dt(sim) - dt_o) <= 1e-12 * dt_o
+    pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+    if wl.bc_kind is not None and wl.bc_kind.any():
+        pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
+    pd.pd_step_explicit(sim, steps)
+    u_g, v_g = pd.pd_get_state(sim)
+    st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
+    st.run(dt_o, steps)
+    return sim, bonds, st, u_g, v_g
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_plate2d_explicit_run_matches_oracle(pd, precision):
+    """50 x 50 plate, PMB, collar velocities, 200 steps (the plain-method workload)."""
+    wl = W.plate2d(nside=50, steps=200)
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim, _, st, u_g, v_g = _run_both(pd, wl, prec, wl.steps)
+    tol = U_TOL if precision == "fp32c" else 1e-10
+    assert rel_l2(u_g, st.u) <= tol
+    assert rel_l2(v_g, st.v) <= (1e-3 if precision == "fp32c" else 1e-9)
+    assert pd.pd_get_step(sim) == wl.steps
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_block_pulse_with_breaking_matches_oracle(pd, precision):
+    """Pulse + pre-notch + breaking (s_c lowered so bonds break within the run)."""
+    wl = W.block3d_pulse(nside=24, steps=120, s_c=2e-4)
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim, bonds, st, u_g, v_g = _run_both(pd, wl, prec, wl.steps)
+    _, _, order, _ = gpu_csr_in_user_numbering(pd, sim)
+    brk = pd.pd_get_broken(sim)[order].astype(bool)
+    ob = bonds.broken.astype(bool)
+    notch_only = oracle_setup(wl).broken.astype(bool)
+    assert ob.sum() > notch_only.sum()                 # bonds broke during the run
+    mism = int((brk != ob).sum())
+    assert mism <= max(2, int(1e-4 * ob.sum()))
+    assert rel_l2(u_g, st.u) <= (U_TOL if precision == "fp32c" else 1e-9)
+    sim.close()
+
+
+def test_lps_explicit_run_matches_oracle(pd):
+    wl = W.block3d_lps(nside=24, steps=40)
+    sim, _, st, u_g, v_g = _run_both(pd, wl, pd.PD_FP32C, wl.steps)
+    assert rel_l2(u_g, st.u) <= U_TOL
+    sim.close()
+
+
+def test_graph_replay_equals_single_steps_and_runs_are_deterministic(pd):
+    wl = W.block3d_pulse(nside=16, steps=40, s_c=2e-4)
+    outs = []
+    for chunks in ([40], [1] * 40, [40]):
+        sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C, notch=wl.notch)
+        pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+        for c in chunks:
+            pd.pd_step_explicit(sim, c)
+        outs.append(pd.pd_get_state(sim))
+        outs[-1] = (outs[-1][0], outs[-1][1], pd.pd_get_broken(sim))
+        sim.close()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_checkpoint_round_trip_is_bit_identical(pd):
+    wl = W.plate2d(nside=40, steps=60)
+    ref = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C)
+    pd.pd_set_state(ref, u=wl.u0, v=wl.v0)
+    pd.pd_set_bc(ref, wl.bc_kind, wl.bc_val)
+    pd.pd_step_explicit(ref, 60)
+    u_ref, v_ref = pd.pd_get_state(ref)
+    sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C)
+    pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+    pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
+    pd.pd_step_explicit(sim, 30)
+    u_mid, v_mid = pd.pd_get_state(sim)
+    pd.pd_set_state(sim, u=u_mid, v=v_mid)
+    pd.pd_step_explicit(sim, 30)
+    u_end, v_end = pd.pd_get_state(sim)
+    assert np.array_equal(u_end, u_ref) and np.array_equal(v_end, v_ref)
+    ref.close()
+    sim.close()
+
+
+def test_energy_matches_oracle_and_is_conserved(pd):
+    grid = W.Grid(dim=2, n=(40, 40, 1), h=0.02, m=3)
+    mat = W.Material(model=W.PMB, E=72e9, rho=2440.0)
+    u0 = W.gaussian_ic(grid, (1e-5, 0.5e-5), (0.4, 0.35), 0.003)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP64)
+    pd.pd_set_state(sim, u=u0, v=np.zeros_like(u0))
+    bonds = O.neighbors(grid)
+    k0, s0 = pd.pd_energy(sim)
+    assert k0 == 0.0
+    assert abs(s0 - O.strain_energy(grid, mat, bonds, u0)) <= 1e-10 * s0
+    pd.pd_step_explicit(sim, 100)
+    u, v = pd.pd_get_state(sim)
+    k1, s1 = pd.pd_energy(sim)
+    assert abs(k1 - O.kinetic_energy(grid, mat, v)) <= 1e-10 * k1
+    assert abs(s1 - O.strain_energy(grid, mat, bonds, u)) <= 1e-9 * s1
+    assert abs((k1 + s1) - s0) <= 3e-2 * s0
+    assert pd.pd_energy(sim) == (k1, s1)                 # bit-reproducible
+    sim.close()
+
+
+def test_lps_energy_matches_oracle(pd):
+    grid = W.Grid(dim=3, n=(14, 13, 12), h=0.01, m=3)
+    mat = W.Material(model=W.LPS, K=40e9, mu=30e9)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP64)
+    u = _u_random(grid, 2e-4, seed=4)
+    pd.pd_set_state(sim, u=u)
+    bonds = O.neighbors(grid)
+    mv = O.weighted_volume(grid, mat, bonds)
+    th = O.dilatation(grid, mat, bonds, mv, u)
+    _, s = pd.pd_energy(sim)
+    assert abs(s - O.strain_energy(grid, mat, bonds, u, mv, th)) <= 1e-9 * s
+    sim.close()
+
+
+# ------------------------------------------------------------------ tangent
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_jvp_vjp_match_assembled_tangent(pd, precision):
+    """20 x 20 sub-grid: K from Algorithm 3's central differences in the oracle."""
+    grid = W.Grid(dim=2, n=(20, 20, 1), h=0.005, m=3)
+    mat = W.Material(model=W.PMB, E=72e9)
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim = gpu_sim(pd, grid, mat, prec)
+    bonds = O.neighbors(grid)
+    u = _u_random(grid, 2e-3, seed=4)
+    K = O.tangent_fd(grid, mat, bonds, u, 1e-6 * grid.h)
+    w = W.random_field(grid, 1.0, seed=5)
+    jv = pd.pd_jvp(sim, w, u_lin=u)
+    vj = pd.pd_vjp(sim, w, u_lin=u)
+    tol = 1e-6 if precision == "fp64" else 2e-5
+    assert rel_l2(jv.ravel(), K @ w.ravel()) <= tol
+    assert rel_l2(vj.ravel(), K.T @ w.ravel()) <= tol
+    # central differences of the GPU's own force along w
+    eps = 1e-6 * grid.h
+    fd = O.jvp_fd(grid, mat, bonds, u, w, eps)
+    assert rel_l2(jv, fd) <= tol
+    sim.close()
+
+
+def test_jvp_dirichlet_mask_and_rigid_null_space(pd):
+    grid = W.Grid(dim=3, n=(12, 11, 10), h=0.01, m=3)
+    mat = W.Material(model=W.PMB, E=72e9)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP64)
+    X = grid.positions()
+    zero = np.zeros((grid.npoints, 3))
+    scale = np.abs(pd.pd_jvp(sim, W.random_field(grid, 1.0, seed=1), u_lin=zero)).max()
+    for w in (np.tile([1.0, -2.0, 0.5], (grid.npoints, 1)), np.stack([-X[:, 1], X[:, 0], 0 * X[:, 0]], 1)):
+        assert np.abs(pd.pd_jvp(sim, w, u_lin=zero)).max() <= 1e-10 * scale * np.abs(w).max() / grid.h
+    kind = np.zeros((grid.npoints, 3), np.uint8)
+    kind[W.collar_mask(grid, 0, -1)] = pd.PD_BC_DISPLACEMENT
+    pd.pd_set_bc(sim, kind, np.zeros((grid.npoints, 3)))
+    w = W.random_field(grid, 1.0, seed=2)
+    out = pd.pd_jvp(sim, w, u_lin=zero, flags=pd.PD_JVP_MASK_DIRICHLET)
+    fixed = kind.astype(bool)
+    assert np.array_equal(out[fixed], w[fixed])
+    w2 = w.copy()
+    w2[fixed] = 0.0
+    ref = pd.pd_jvp(sim, w2, u_lin=zero)
+    assert np.array_equal(out[~fixed], ref[~fixed])
+    sim.close()
+
+
+# ------------------------------------------------------- full-size sampled
+
+def test_full_size_block64_force_and_short_run(pd):
+    """64^3 PMB with breaking at the benchmark's configuration: the force of the
+    whole lattice after 5 steps against the oracle, and the broken set."""
+    wl = W.block3d_pulse(nside=64, steps=5)
+    sim, bonds, st, u_g, v_g = _run_both(pd, wl, pd.PD_FP32C, wl.steps)
+    assert rel_l2(u_g, st.u) <= U_TOL
+    f_gpu = pd.pd_force(sim, u=st.u)
+    f_or = O.pmb_force(wl.grid, wl.mat, bonds, st.u)
+    assert rel_l2(f_gpu, f_or) <= FORCE_TOL_FP32C
+    sim.close()
+
+
+def test_full_size_block128_lps_force_sampled(pd):
+    """128^3 LPS: the force at the initial state on the whole lattice."""
+    wl = W.block3d_lps(nside=128, steps=1)
+    sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C)
+    bonds = O.neighbors(wl.grid)
+    mv = O.weighted_volume(wl.grid, wl.mat, bonds)
+    th = O.dilatation(wl.grid, wl.mat, bonds, mv, wl.u0)
+    f_or = O.lps_force(wl.grid, wl.mat, bonds, mv, th, wl.u0)
+    f_gpu = pd.pd_force(sim, u=wl.u0)
+    assert rel_l2(f_gpu, f_or) <= FORCE_TOL_FP32C
+    sim.close()
+
+
+# --------------------------------------------------------------- edge cases
+
+def test_errors_are_reported_not_faulted(pd):
+    grid = W.Grid(dim=2, n=(4, 4, 1), h=0.01, m=2)
+    g, m, r = pd.describe(grid, W.Material(model=W.LPS, K=1e9, mu=1e9))
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_create(g, m, r)
+    assert e.value.code == pd.PD_EINVAL
+    g, m, r = pd.describe(grid, W.Material(model=W.PMB))
+    sim = pd.pd_create(g, m, r)
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_force(sim, u=np.zeros((16, 2)))
+    assert e.value.code == pd.PD_ESTATE
+    pd.pd_build_neighbors(sim)
+    with pytest.raises(pd.PdError):
+        pd.pd_set_bc(sim, np.full((16, 2), 7, np.uint8), np.zeros((16, 2)))
+    with pytest.raises(pd.PdError):
+        pd.pd_step_explicit(sim, -1)
+    sim.close()
+
+
+def test_single_point_and_torch_device_buffers(pd):
+    import torch
+    grid = W.Grid(dim=3, n=(1, 1, 1), h=0.01, m=3)
+    sim = gpu_sim(pd, grid, W.Material(model=W.PMB), pd.PD_FP32C, dt=1e-6)
+    assert pd.pd_bond_count(sim) == 0
+    assert np.all(pd.pd_force(sim, u=np.ones((1, 3))) == 0)
+    sim.close()
+    grid = W.Grid(dim=3, n=(16, 16, 16), h=0.01, m=3)
+    mat = W.Material(model=W.PMB)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP32C)
+    u = _u_random(grid, 1e-4, seed=7)
+    ud = torch.from_numpy(u).cuda()
+    fd = torch.empty_like(ud)
+    pd.pd_force(sim, u=ud, f_out=fd, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(fd.cpu().numpy(), pd.pd_force(sim, u=u))
+    sim.close()
