@@ -46,6 +46,9 @@ size_t energy_smem(const Geom &g, int precision);
 int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st);
 int dirichlet_mask(const Geom &g, const uint8_t *kind, double *const v[3], const double *const w[3], int copy,
                    cudaStream_t st);
+int unpack_pairs(const Geom &g, const float4 *in, double *const x[3], cudaStream_t st);
+int pack_dof_pairs(long long n, const double *in, float *out, cudaStream_t st);
+int pack_f4(const Geom &g, const double *in, float4 *out, cudaStream_t st);
 
 }  // namespace pdk
 
@@ -87,6 +90,9 @@ struct pd_sim {
     double4_32a *d4[2] = {nullptr, nullptr};
     float4 *lin_hl = nullptr;
     double4_32a *lin_d4 = nullptr;
+    float4 *vhl = nullptr;          // FP32C velocity, double-float pairs
+    float *bc32 = nullptr;          // FP32C boundary values, (hi, lo) per DOF
+    float4 *body32 = nullptr;       // FP32C body force
     uint8_t *bc_kind = nullptr;
     double *bc_val = nullptr, *body = nullptr;
     uint32_t *mask = nullptr;
@@ -137,7 +143,7 @@ static void drop_graphs(pd_sim *s)
 
 static size_t max_smem(const Geom &g, int precision, int model)
 {
-    size_t m = jvp_smem(g, PD_FP64);
+    size_t m = jvp_smem(g, precision);
     m = std::max(m, energy_smem(g, precision));
     if (model == PD_MODEL_PMB)
         m = std::max(m, precision == PD_FP64 ? pmb_generic_smem(g, precision) : pmb_fast_smem(g));
@@ -188,20 +194,22 @@ static int create_impl(pd_sim *s)
     g.ny = gr.n[1];
     g.nz = gr.dim == 3 ? gr.n[2] : 1;
     g.h = gr.h;
-    g.L = s->run.tile_log2 ? s->run.tile_log2 : 9;
-    g.T = 1 << g.L;
-    int b[3];
-    brick_dims(g.dim, g.L, b);
-    g.bx = b[0];
-    g.by = b[1];
-    g.bz = b[2];
-    g.lbx = __builtin_ctz(b[0]);
-    g.lby = __builtin_ctz(b[1]);
-    g.lbz = __builtin_ctz(b[2]);
-    g.tgx = (g.nx + g.bx - 1) / g.bx;
-    g.tgy = (g.ny + g.by - 1) / g.by;
-    g.tgz = (g.nz + g.bz - 1) / g.bz;
     g.npoints = g.nx * g.ny * g.nz;
+    auto set_tile = [&g](int L) {
+        g.L = L;
+        g.T = 1 << L;
+        int b[3];
+        brick_dims(g.dim, L, b);
+        g.bx = b[0];
+        g.by = b[1];
+        g.bz = b[2];
+        g.lbx = __builtin_ctz(b[0]);
+        g.lby = __builtin_ctz(b[1]);
+        g.lbz = __builtin_ctz(b[2]);
+        g.tgx = (g.nx + g.bx - 1) / g.bx;
+        g.tgy = (g.ny + g.by - 1) / g.by;
+        g.tgz = (g.nz + g.bz - 1) / g.bz;
+    };
 
     // stencil: offsets 0 < |d|^2 <= m^2 ordered by (dz, dy, dx)
     std::vector<int4> st;
@@ -220,6 +228,16 @@ static int create_impl(pd_sim *s)
     g.S = (int)st.size();
     g.W = (g.S + 31) / 32;
     if (g.W > 64) { set_error("horizon stencil too large"); return PD_EINVAL; }
+
+    // tile size: the requested one, or the largest brick (up to 2^9 points)
+    // whose halo box fits in shared memory for every kernel of this simulation
+    if (s->run.tile_log2) {
+        set_tile(s->run.tile_log2);
+    } else {
+        int L = 9;
+        set_tile(L);
+        while (L > 6 && max_smem(g, s->precision, s->pmat.model) > SMEM_LIMIT) set_tile(--L);
+    }
 
     // tiles: bricks intersecting the grid, ordered by the Morton code of their origin
     struct TileKey { uint64_t code; int tx, ty, tz; };
@@ -309,6 +327,8 @@ static int create_impl(pd_sim *s)
         ALLOC(s->hl[0], 2 * sizeof(float4) * NS);
         ALLOC(s->hl[1], 2 * sizeof(float4) * NS);
         ALLOC(s->lin_hl, 2 * sizeof(float4) * NS);
+        ALLOC(s->vhl, 2 * sizeof(float4) * NS);
+        ALLOC(s->bc32, 2 * 3 * sizeof(float) * NS);
     }
     ALLOC(s->bc_kind, 3 * NS);
     ALLOC(s->bc_val, 3 * sizeof(double) * NS);
@@ -375,6 +395,14 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.vol_corr = s->mat.vol_corr;
     a.use_body = s->use_body ? 1 : 0;
     a.adjoint = 0;
+    a.vhl = s->vhl;
+    a.bc32 = s->bc32;
+    a.body32 = s->body32;
+    a.fscale = s->mat.model == PD_MODEL_PMB ? s->mat.c * s->mat.V : 1.0 / s->g.h;
+    a.kF = (float)(0.5 * s->dt * a.fscale / s->mat.rho);
+    a.kB = (float)(0.5 * s->dt / s->mat.rho);
+    a.dt_h = (float)s->dt;
+    a.dt_l = (float)(s->dt - (double)a.dt_h);
     return a;
 }
 
@@ -677,8 +705,18 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     if (v) {
         rc = user_to_slots(s, v, s->v, st);
         if (rc != PD_OK) return rc;
+        if (s->precision == PD_FP32C && (rc = pack_stage(s->g, s->v, s->vhl, nullptr, st)) != PD_OK) return rc;
     }
     return PD_OK;
+}
+
+// FP32C keeps u and v as double-float pairs; refresh the FP64 SoA copies.
+static int unpack_state(pd_sim *s, cudaStream_t st)
+{
+    if (s->precision != PD_FP32C) return PD_OK;
+    int rc = unpack_pairs(s->g, s->hl[s->cur], s->u, st);
+    if (rc != PD_OK) return rc;
+    return unpack_pairs(s->g, s->vhl, s->v, st);
 }
 
 int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
@@ -687,6 +725,7 @@ int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
     cudaStream_t st = pick(s, stream);
     int rc = finalize(s, st);
     if (rc != PD_OK) return rc;
+    if ((rc = unpack_state(s, st)) != PD_OK) return rc;
     if (u && (rc = slots_to_user(s, s->u, u, st)) != PD_OK) return rc;
     if (v && (rc = slots_to_user(s, s->v, v, st)) != PD_OK) return rc;
     PD_CUDA(cudaStreamSynchronize(st));
@@ -715,6 +754,8 @@ int pd_set_bc(pd_sim *s, const uint8_t *kind, const double *value, void *stream)
     double *vals[3] = {s->bc_val, s->bc_val + NS, s->bc_val + 2 * NS};
     rc = user_to_slots(s, value, vals, st);
     if (rc != PD_OK) return rc;
+    if (s->precision == PD_FP32C && (rc = pack_dof_pairs(3 * (long long)NS, s->bc_val, s->bc32, st)) != PD_OK)
+        return rc;
     int herr = 0;
     PD_CUDA(cudaMemcpyAsync(&herr, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PD_CUDA(cudaStreamSynchronize(st));
@@ -739,6 +780,10 @@ int pd_set_body_force(pd_sim *s, const double *b, void *stream)
     double *dst[3] = {s->body, s->body + s->g.nslots, s->body + 2 * (size_t)s->g.nslots};
     int rc = user_to_slots(s, b, dst, st);
     if (rc != PD_OK) return rc;
+    if (s->precision == PD_FP32C) {
+        if (!s->body32) ALLOC(s->body32, sizeof(float4) * s->g.nslots);
+        if ((rc = pack_f4(s->g, s->body, s->body32, st)) != PD_OK) return rc;
+    }
     s->use_body = true;
     return PD_OK;
 }
@@ -877,6 +922,7 @@ int pd_energy(pd_sim *s, double *kinetic, double *strain, void *stream)
     cudaStream_t st = pick(s, stream);
     int rc = finalize(s, st);
     if (rc != PD_OK) return rc;
+    if ((rc = unpack_state(s, st)) != PD_OK) return rc;
     TileArgs a = make_args(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur]);
     if (s->mat.model == PD_MODEL_LPS && (rc = launch_lps_args(a, s->precision, 1, st)) != PD_OK) return rc;
     if ((rc = launch_energy_points(a, s->precision, s->ekin, st)) != PD_OK) return rc;

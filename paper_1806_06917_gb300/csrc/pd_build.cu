@@ -690,6 +690,58 @@ int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, c
     return PD_OK;
 }
 
+// Double-float pairs back to FP64 SoA: x = hi + lo.
+__global__ void k_unpack_pairs(Geom g, const float4 *in, double *x0, double *x1, double *x2)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const float4 hi = in[2 * s], lo = in[2 * s + 1];
+    x0[s] = (double)hi.x + (double)lo.x;
+    x1[s] = (double)hi.y + (double)lo.y;
+    if (g.dim == 3) x2[s] = (double)hi.z + (double)lo.z;
+}
+
+int unpack_pairs(const Geom &g, const float4 *in, double *const x[3], cudaStream_t st)
+{
+    k_unpack_pairs<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, in, x[0], x[1], x[2]);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// FP64 per-DOF values (component-major, 3 x nslots) to (hi, lo) float pairs.
+__global__ void k_pack_dof_pairs(long long n, const double *in, float *out)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double x = in[q];
+    const float h = (float)x;
+    out[2 * q] = h;
+    out[2 * q + 1] = (float)(x - (double)h);
+}
+
+int pack_dof_pairs(long long n, const double *in, float *out, cudaStream_t st)
+{
+    k_pack_dof_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, out);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// FP64 component-major per-DOF values to one float4 per slot.
+__global__ void k_pack_f4(Geom g, const double *in, float4 *out)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const size_t ns = g.nslots;
+    out[s] = make_float4((float)in[s], (float)in[ns + s], g.dim == 3 ? (float)in[2 * ns + s] : 0.f, 0.f);
+}
+
+int pack_f4(const Geom &g, const double *in, float4 *out, cudaStream_t st)
+{
+    k_pack_f4<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, in, out);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
 // Zero the prescribed-displacement components of a slot-order vector (JVP masking),
 // or copy them from src into dst (identity rows).
 __global__ void k_dirichlet(Geom g, const uint8_t *kind, double *v0, double *v1, double *v2, const double *w0,

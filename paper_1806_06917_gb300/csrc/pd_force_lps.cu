@@ -12,229 +12,212 @@
 // The weighted volume m~ is computed once at the neighbour build.
 #include <type_traits>
 
-#include "pd_tile.cuh"
+#include "pd_pair.cuh"
 
 namespace pdk {
 
-// Staging of the force pass: float4 (u~x, u~y, u~z, a_j) and float b_j.
-__device__ __forceinline__ void stage_box32_lps(float4 *box, float *boxb, int HX, int HY, int nbox,
-                                                int m, const TileArgs &a, const int4 &org,
-                                                const Ref32 &ref, float inv_h)
-{
-    for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
-        int bxl = b % HX, rest = b / HX;
-        int byl = rest % HY, bzl = rest / HY;
-        int x = org.x + bxl - m, y = org.y + byl - m, z = org.z + bzl - m;
-        int s = slot_at(a.g, a.tile_lut, x, y, z);
-        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-        float rb = 0.f;
-        if (s >= 0) {
-            float4 hi = __ldg(&a.src_hl[2 * s]);
-            float4 lo = __ldg(&a.src_hl[2 * s + 1]);
-            r.x = ((hi.x - ref.hx) + (lo.x - ref.lx)) * inv_h;
-            r.y = ((hi.y - ref.hy) + (lo.y - ref.ly)) * inv_h;
-            r.z = ((hi.z - ref.hz) + (lo.z - ref.lz)) * inv_h;
-            rb = __ldg(&a.minv32[s]);
-            r.w = a.theta32[s] * rb;
-        }
-        box[b] = r;
-        boxb[b] = rb;
-    }
-}
-
 // ------------------------------------------------------------------ fast path
 
-// FP32C, 3D, P points per thread, horizon at run time; rolled loop over a
-// shared-memory stencil table (dx, dy, dz, |d|) and (box offset, V_ij).
-__device__ __forceinline__ void build_tab(const TileArgs &a, int HX, int HY, float4 *tabA, int2 *tabB)
+// FP32C, 3D, thread = point pair (A, B) in f32x2 arithmetic (pd_pair.cuh);
+// rolled loop over a shared-memory table of pre-splatted stencil constants.
+// One 32-bond word of the dilatation sum (MASKED = false: every bond of the
+// warp's points exists and is intact, no per-bond mask operation).
+template <bool MASKED>
+__device__ __forceinline__ float2 lps_dil_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
+                                               float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1,
+                                               float2 acc)
 {
-    for (int k = threadIdx.x; k < a.g.S; k += blockDim.x) {
+PD_PRAGMA_UNROLL(PD_UNROLL)
+    for (int b = 0; b < nb; ++b) {
+        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
+        const int off = __float_as_int(tc.z);
+        const float4 r4 = P4[bi + off];
+        const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
+        const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
+        float2 qq = f2mul(yx, yx);
+        qq = f2fma(yy, yy, qq);
+        qq = f2fma(yz, yz, qq);
+        float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
+        num = f2fma(ey, f2add(yy, f2hi(ta)), num);
+        num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+        float2 e = f2div(num, f2add(f2mul(qq, f2rsqrt(qq)), f2hi(tb)));
+        if (MASKED) {
+            e.x = ((c0 >> b) & 1u) ? e.x : 0.f;
+            e.y = ((c1 >> b) & 1u) ? e.y : 0.f;
+        }
+        acc = f2fma(e, f2lo(tc), acc);
+    }
+    return acc;
+}
+
+// One 32-bond word of the LPS force sum.
+template <bool MASKED>
+__device__ __forceinline__ void lps_force_word(const float4 *tw, int nb, const float4 *P4, const float4 *PT,
+                                               const float2 *P2, int bi, float2 nux, float2 nuy, float2 nuz,
+                                               float2 ai, float2 bi_, uint32_t c0, uint32_t c1, float2 &Fx,
+                                               float2 &Fy, float2 &Fz)
+{
+PD_PRAGMA_UNROLL(PD_UNROLL)
+    for (int b = 0; b < nb; ++b) {
+        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
+        const int off = __float_as_int(tw[4 * b + 3].x);
+        const float4 r4 = P4[bi + off], t4 = PT[bi + off];
+        const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
+        const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
+        float2 qq = f2mul(yx, yx);
+        qq = f2fma(yy, yy, qq);
+        qq = f2fma(yz, yz, qq);
+        float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
+        num = f2fma(ey, f2add(yy, f2hi(ta)), num);
+        num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+        const float2 rs = f2rsqrt(qq);
+        const float2 e = f2div(num, f2add(f2mul(qq, rs), f2hi(tb)));
+        // (t_i + t_j) V_ij = A |d| V_ij (a_i + a_j) + B V_ij e (b_i + b_j)
+        float2 gg = f2mul(f2lo(tc), f2add(ai, f2lo(t4)));
+        gg = f2fma(f2mul(f2hi(tc), e), f2add(bi_, f2hi(t4)), gg);
+        float2 wgt = f2mul(gg, rs);
+        if (MASKED) {
+            wgt.x = ((c0 >> b) & 1u) ? wgt.x : 0.f;
+            wgt.y = ((c1 >> b) & 1u) ? wgt.y : 0.f;
+        }
+        Fx = f2fma(wgt, yx, Fx);
+        Fy = f2fma(wgt, yy, Fy);
+        Fz = f2fma(wgt, yz, Fz);
+    }
+}
+
+__global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs a)
+{
+    const Geom &g = a.g;
+    const PairBox pb = pair_box(g);
+    const int S = g.S;
+    extern __shared__ float4 smem4[];
+    float4 *P4 = smem4;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
+    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|V,|d|V,off,-}
+    const int tile = blockIdx.x;
+    const int4 org = __ldg(&a.tile_org[tile]);
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
         const int4 d = __ldg(&a.stencil[k]);
         const float r0 = (float)__ldg(&a.stencil_r0[k]);
-        tabA[k] = make_float4((float)d.x, (float)d.y, (float)d.z, r0);
-        const float vij = a.vol_corr ? (float)vol_factor_lattice(a.g.m, (double)r0) : 1.f;
-        tabB[k] = make_int2(d.x + HX * (d.y + HY * d.z), __float_as_int(vij));
+        const float vij = a.vol_corr ? (float)vol_factor_lattice(g.m, (double)r0) : 1.f;
+        tab[3 * k] = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
+        tab[3 * k + 1] = make_float4((float)d.z, (float)d.z, r0, r0);
+        tab[3 * k + 2] = make_float4(r0 * vij, r0 * vij, __int_as_float(d.x + pb.HX * (d.y + pb.HY * d.z)), 0.f);
     }
-}
-
-template <int P>
-__global__ void __launch_bounds__(256, 3) lps_dil_fast(const TileArgs a)
-{
-    const Geom &g = a.g;
-    const int m = g.m, S = g.S;
-    const int HX = g.bx + 2 * m, HY = g.by + 2 * m, HZ = g.bz + 2 * m;
-    const int nbox = HX * HY * HZ;
-    extern __shared__ float4 smem4[];
-    float4 *box = smem4;
-    float4 *tabA = box + nbox;
-    int2 *tabB = reinterpret_cast<int2 *>(tabA + S);
-    const int tile = blockIdx.x;
-    const int4 org = __ldg(&a.tile_org[tile]);
-    build_tab(a, HX, HY, tabA, tabB);
-    stage_box32(box, HX, HY, nbox, m, a, org, tile_ref32(a, tile), (float)a.inv_h);
+    stage_pairs(a, pb, org, tile, P4, P2);
     __syncthreads();
 
-    const int nthr = g.T / P;
+    const int nthr = g.T / 2;            // a multiple of blockDim
     for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
-        const int lx = t & (g.bx - 1), r1 = t >> g.lbx;
-        const int ly = r1 & (g.by - 1), lz0 = r1 >> g.lby;
-        int bi[P], slot[P];
-        bool act[P];
-        Pk<float, P> ux, uy, uz;
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const int lz = lz0 + p * (g.bz / P);
-            bi[p] = (lx + m) + HX * ((ly + m) + HY * (lz + m));
-            slot[p] = tile * g.T + brick_code(3, lx, ly, lz);
-            act[p] = org.x + lx < g.nx && org.y + ly < g.ny && org.z + lz < g.nz;
-            const float4 ui = box[bi[p]];
-            ux.v[p] = ui.x;
-            uy.v[p] = ui.y;
-            uz.v[p] = ui.z;
-        }
-        Pk<float, P> acc = splat<float, P>(0.f);
+        const PairPts q = pair_points(g, pb, org, tile, t);
+        const float4 ui4 = P4[q.bi];
+        const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4)), nuz = f2neg(P2[q.bi]);
+        float2 acc = make_float2(0.f, 0.f);
+        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
         for (int w = 0; w < g.W; ++w) {
-            uint32_t cur[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) cur[p] = act[p] ? a.mask[(size_t)w * g.nslots + slot[p]] : 0u;
-            const int nb = min(32, S - 32 * w);
-#pragma unroll 4
-            for (int b = 0; b < nb; ++b) {
-                const int k = 32 * w + b;
-                const float4 ta = tabA[k];
-                const int2 tb = tabB[k];
-                Pk<float, P> ex, ey, ez;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float4 rj = box[bi[p] + tb.x];
-                    ex.v[p] = rj.x;
-                    ey.v[p] = rj.y;
-                    ez.v[p] = rj.z;
-                }
-                ex = psub(ex, ux);
-                ey = psub(ey, uy);
-                ez = psub(ez, uz);
-                const Pk<float, P> yx = padds(ex, ta.x), yy = padds(ey, ta.y), yz = padds(ez, ta.z);
-                Pk<float, P> q = pmul(yx, yx);
-                q = pfma(yy, yy, q);
-                q = pfma(yz, yz, q);
-                Pk<float, P> num = pmul(ex, padds(yx, ta.x));
-                num = pfma(ey, padds(yy, ta.y), num);
-                num = pfma(ez, padds(yz, ta.z), num);
-                Pk<float, P> e = pdiv(num, padds(pmul(q, prsqrt(q)), ta.w));
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    e.v[p] = (cur[p] & 1u) ? e.v[p] : 0.f;
-                    cur[p] >>= 1;
-                }
-                acc = pfmas(e, ta.w * __int_as_float(tb.y), acc);
+            const uint32_t m0 = n0, m1 = n1;
+            if (w + 1 < g.W) {
+                const size_t mo = (size_t)(w + 1) * g.nslots;
+                n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
+                n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
             }
+            const int nb = min(32, S - 32 * w);
+            const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            const float4 *tw = tab + 3 * 32 * w;
+            if (__all_sync(0xffffffffu, m0 == full && m1 == full))
+                acc = lps_dil_word<false>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
+            else
+                acc = lps_dil_word<true>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
         }
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            if (act[p]) a.theta32[slot[p]] = 3.f * __ldg(&a.minv32[slot[p]]) * acc.v[p];
+        for (int p = 0; p < 2; ++p)
+            if (q.act[p]) a.theta32[q.slot[p]] = 3.f * __ldg(&a.minv32[q.slot[p]]) * (p ? acc.y : acc.x);
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(256, 3) lps_force_fast(const TileArgs a)
+__global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_force_fast(const TileArgs a)
 {
     const Geom &g = a.g;
-    const int m = g.m, S = g.S;
-    const int HX = g.bx + 2 * m, HY = g.by + 2 * m, HZ = g.bz + 2 * m;
-    const int nbox = HX * HY * HZ;
+    const PairBox pb = pair_box(g);
+    const int S = g.S;
     extern __shared__ float4 smem4[];
-    float4 *box = smem4;
-    float4 *tabA = box + nbox;
-    int2 *tabB = reinterpret_cast<int2 *>(tabA + S);
-    float *boxb = reinterpret_cast<float *>(tabB + S);
+    float4 *P4 = smem4;                                        // {xA, xB, yA, yB}
+    float4 *PT = P4 + pb.n;                                     // {aA, aB, bA, bB}: a = theta/m~, b = 1/m~
+    float2 *P2 = reinterpret_cast<float2 *>(PT + pb.n);        // {zA, zB}
+    float4 *tab = PT + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    build_tab(a, HX, HY, tabA, tabB);
-    stage_box32_lps(box, boxb, HX, HY, nbox, m, a, org, tile_ref32(a, tile), (float)a.inv_h);
-    __syncthreads();
-
     const float A = (float)a.A, B = (float)a.B;
-    const int nthr = g.T / P;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        const int4 d = __ldg(&a.stencil[k]);
+        const float r0 = (float)__ldg(&a.stencil_r0[k]);
+        const float vij = a.vol_corr ? (float)vol_factor_lattice(g.m, (double)r0) : 1.f;
+        tab[4 * k] = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
+        tab[4 * k + 1] = make_float4((float)d.z, (float)d.z, r0, r0);
+        tab[4 * k + 2] = make_float4(A * r0 * vij, A * r0 * vij, B * vij, B * vij);
+        tab[4 * k + 3] = make_float4(__int_as_float(d.x + pb.HX * (d.y + pb.HY * d.z)), 0.f, 0.f, 0.f);
+    }
+    {
+        const Ref32 ref = tile_ref32(a, tile);
+        const float inv_h = (float)a.inv_h;
+        for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
+            int cA[3], cB[3];
+            pair_coords(g, pb, org, b, cA, cB);
+            const int sA = slot_at(g, a.tile_lut, cA[0], cA[1], cA[2]);
+            const int sB = slot_at(g, a.tile_lut, cB[0], cB[1], cB[2]);
+            const float4 rA = stage_one(a, a.src_hl, sA, ref, inv_h);
+            const float4 rB = stage_one(a, a.src_hl, sB, ref, inv_h);
+            const float bA = sA >= 0 ? __ldg(&a.minv32[sA]) : 0.f, bB = sB >= 0 ? __ldg(&a.minv32[sB]) : 0.f;
+            const float aA = sA >= 0 ? a.theta32[sA] * bA : 0.f, aB = sB >= 0 ? a.theta32[sB] * bB : 0.f;
+            P4[b] = make_float4(rA.x, rB.x, rA.y, rB.y);
+            P2[b] = make_float2(rA.z, rB.z);
+            PT[b] = make_float4(aA, aB, bA, bB);
+        }
+    }
+    __syncthreads();
+
+    const int nthr = g.T / 2;            // a multiple of blockDim
     for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
-        const int lx = t & (g.bx - 1), r1 = t >> g.lbx;
-        const int ly = r1 & (g.by - 1), lz0 = r1 >> g.lby;
-        int bi[P], slot[P];
-        bool act[P];
-        Pk<float, P> ux, uy, uz, ai, bi_;
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const int lz = lz0 + p * (g.bz / P);
-            bi[p] = (lx + m) + HX * ((ly + m) + HY * (lz + m));
-            slot[p] = tile * g.T + brick_code(3, lx, ly, lz);
-            act[p] = org.x + lx < g.nx && org.y + ly < g.ny && org.z + lz < g.nz;
-            const float4 ui = box[bi[p]];
-            ux.v[p] = ui.x;
-            uy.v[p] = ui.y;
-            uz.v[p] = ui.z;
-            ai.v[p] = ui.w;
-            bi_.v[p] = boxb[bi[p]];
-        }
-        Pk<float, P> Fx = splat<float, P>(0.f), Fy = Fx, Fz = Fx;
+        const PairPts q = pair_points(g, pb, org, tile, t);
+        const float4 ui4 = P4[q.bi], ti4 = PT[q.bi];
+        const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4)), nuz = f2neg(P2[q.bi]);
+        const float2 ai = f2lo(ti4), bi = f2hi(ti4);
+        float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
+        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
         for (int w = 0; w < g.W; ++w) {
-            uint32_t cur[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) cur[p] = act[p] ? a.mask[(size_t)w * g.nslots + slot[p]] : 0u;
-            const int nb = min(32, S - 32 * w);
-#pragma unroll 4
-            for (int b = 0; b < nb; ++b) {
-                const int k = 32 * w + b;
-                const float4 ta = tabA[k];
-                const int2 tb = tabB[k];
-                Pk<float, P> ex, ey, ez, aj, bj;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float4 rj = box[bi[p] + tb.x];
-                    ex.v[p] = rj.x;
-                    ey.v[p] = rj.y;
-                    ez.v[p] = rj.z;
-                    aj.v[p] = rj.w;
-                    bj.v[p] = boxb[bi[p] + tb.x];
-                }
-                ex = psub(ex, ux);
-                ey = psub(ey, uy);
-                ez = psub(ez, uz);
-                const Pk<float, P> yx = padds(ex, ta.x), yy = padds(ey, ta.y), yz = padds(ez, ta.z);
-                Pk<float, P> q = pmul(yx, yx);
-                q = pfma(yy, yy, q);
-                q = pfma(yz, yz, q);
-                Pk<float, P> num = pmul(ex, padds(yx, ta.x));
-                num = pfma(ey, padds(yy, ta.y), num);
-                num = pfma(ez, padds(yz, ta.z), num);
-                const Pk<float, P> rs = prsqrt(q);
-                const Pk<float, P> e = pdiv(num, padds(pmul(q, rs), ta.w));
-                // t_i + t_j = A |d| (a_i + a_j) + B e (b_i + b_j)
-                Pk<float, P> gg = pmuls(padd(ai, aj), A * ta.w);
-                gg = pfma(pmuls(e, B), padd(bi_, bj), gg);
-                Pk<float, P> wgt = pmuls(pmul(gg, rs), __int_as_float(tb.y));
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    wgt.v[p] = (cur[p] & 1u) ? wgt.v[p] : 0.f;
-                    cur[p] >>= 1;
-                }
-                Fx = pfma(wgt, yx, Fx);
-                Fy = pfma(wgt, yy, Fy);
-                Fz = pfma(wgt, yz, Fz);
+            const uint32_t m0 = n0, m1 = n1;
+            if (w + 1 < g.W) {
+                const size_t mo = (size_t)(w + 1) * g.nslots;
+                n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
+                n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
             }
+            const int nb = min(32, S - 32 * w);
+            const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            const float4 *tw = tab + 4 * 32 * w;
+            if (__all_sync(0xffffffffu, m0 == full && m1 == full))
+                lps_force_word<false>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
+            else
+                lps_force_word<true>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
         }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            if (!act[p]) continue;
-            const double f[3] = {a.inv_h * (double)Fx.v[p], a.inv_h * (double)Fy.v[p], a.inv_h * (double)Fz.v[p]};
-            point_epilogue(a, slot[p], f, 3, false);
+        if (q.act[0]) {
+            const float F[3] = {Fx.x, Fy.x, Fz.x};
+            pair_epilogue(a, q.slot[0], F, 3);
+        }
+        if (q.act[1]) {
+            const float F[3] = {Fx.y, Fy.y, Fz.y};
+            pair_epilogue(a, q.slot[1], F, 3);
         }
     }
 }
 
 size_t lps_fast_smem(const Geom &g, bool dil)
 {
-    const size_t nbox = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz + 2 * g.m);
-    return nbox * (sizeof(float4) + (dil ? 0 : sizeof(float))) + (size_t)g.S * (sizeof(float4) + sizeof(int2));
+    const size_t n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
+    const size_t p2 = ((n + 1) / 2) * sizeof(float4);
+    if (dil) return n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
+    return 2 * n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
 }
 
 // ------------------------------------------------------------------ generic
@@ -300,28 +283,25 @@ __global__ void __launch_bounds__(256) lps_force_generic(const TileArgs a)
     R *boxb = reinterpret_cast<R *>(box + nbox);
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    if constexpr (sizeof(R) == 4) {
-        stage_box32_lps(reinterpret_cast<float4 *>(box), reinterpret_cast<float *>(boxb), HX, HY, nbox, m,
-                        a, org, tile_ref32(a, tile), (float)a.inv_h);
-    } else {
-        const double3 ref = tile_ref64(a, tile);
-        for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
-            int x, y, z;
-            box_coord(b, HX, HY, m, 3, org, x, y, z);
-            int s = slot_at(g, a.tile_lut, x, y, z);
-            double4_32a r = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-            double rb = 0.0;
-            if (s >= 0) {
-                double4_32a d = a.src_d4[s];
-                r.x = (d.x - ref.x) * a.inv_h;
-                r.y = (d.y - ref.y) * a.inv_h;
-                r.z = (d.z - ref.z) * a.inv_h;
-                rb = 1.0 / a.mtil[s];
-                r.w = a.theta64[s] * rb;
-            }
-            reinterpret_cast<double4_32a *>(box)[b] = r;
-            reinterpret_cast<double *>(boxb)[b] = rb;
+    {
+    const double3 ref = tile_ref64(a, tile);
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
+        int x, y, z;
+        box_coord(b, HX, HY, m, 3, org, x, y, z);
+        int s = slot_at(g, a.tile_lut, x, y, z);
+        double4_32a r = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        double rb = 0.0;
+        if (s >= 0) {
+            double4_32a d = a.src_d4[s];
+            r.x = (d.x - ref.x) * a.inv_h;
+            r.y = (d.y - ref.y) * a.inv_h;
+            r.z = (d.z - ref.z) * a.inv_h;
+            rb = 1.0 / a.mtil[s];
+            r.w = a.theta64[s] * rb;
         }
+        reinterpret_cast<double4_32a *>(box)[b] = r;
+        reinterpret_cast<double *>(boxb)[b] = rb;
+    }
     }
     __syncthreads();
     const R A = (R)a.A, B = (R)a.B;
@@ -376,7 +356,7 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
     const Geom &g = a.g;
     const size_t smem = lps_generic_smem(g, precision, dil);
     if (precision == PD_FP32C) {
-        auto k = dil ? lps_dil_fast<2> : lps_force_fast<2>;
+        auto k = dil ? lps_dil_fast : lps_force_fast;
         PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int threads = g.T / 2 < 256 ? g.T / 2 : 256;
         k<<<g.ntiles, threads, smem, st>>>(a);

@@ -10,139 +10,158 @@
 // sums its bonds sequentially in stencil order: no atomics, deterministic.
 #include <type_traits>
 
-#include "pd_tile.cuh"
+#include "pd_pair.cuh"
 
 namespace pdk {
 
 // ------------------------------------------------------------------ fast path
 
-// FP32C, P points per thread (P = 2: packed f32x2 arithmetic on the points
-// (lx, ly, lz) and (lx, ly, lz + bz/2) in 3D, (lx, ly) and (lx, ly + by/2) in
-// 2D), horizon and halo box at run time. The stencil lives in shared memory as
-// (dx, dy, dz, |d|) and (box offset, V_ij); the loop over it is rolled (partly
-// unrolled), which keeps the kernel near 50 registers.
-template <int DIM, int P, bool BRK>
-__global__ void __launch_bounds__(256, 3) pmb_fast(const TileArgs a)
+// FP32C. Thread t owns the point pair (A, B) of pd_pair.cuh and evaluates both
+// in f32x2 arithmetic; the stencil loop is rolled over a shared-memory table of
+// pre-splatted constants {dx, dx, dy, dy}, {dz, dz, R, R}, {C, C, off, s_c V_ij}
+// with R = |d| / V_ij and C = |d|^2 / V_ij, so that
+//   s V_ij = (2 d.eta + eta.eta) / (R |y| + C).
+//
+// One 32-bond word of the stencil at a time. MASKED = false is the path for
+// words whose bonds all exist and are intact for every point of the warp (the
+// common case: the warp then skips every per-bond mask operation); with
+// breaking on, it only reports whether some bond crossed s_c, and the warp then
+// redoes the word on the masked path, which breaks the bond before it counts.
+template <int DIM, bool MASKED, bool BRK>
+__device__ __forceinline__ bool pmb_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
+                                         float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1,
+                                         uint32_t &k0, uint32_t &k1, float2 &Fx, float2 &Fy, float2 &Fz)
+{
+    bool anybrk = false;
+PD_PRAGMA_UNROLL(PD_UNROLL)
+    for (int b = 0; b < nb; ++b) {
+        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
+        const int off = __float_as_int(tc.z);
+        const float4 r4 = P4[bi + off];
+        const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy);
+        const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta));
+        float2 qq = f2mul(yx, yx);
+        qq = f2fma(yy, yy, qq);
+        float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
+        num = f2fma(ey, f2add(yy, f2hi(ta)), num);
+        float2 yz = make_float2(0.f, 0.f);
+        if (DIM == 3) {
+            const float2 ez = f2add(P2[bi + off], nuz);
+            yz = f2add(ez, f2lo(tb));
+            qq = f2fma(yz, yz, qq);
+            num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+        }
+        const float2 rs = f2rsqrt(qq);
+        const float2 den = f2fma(f2mul(qq, rs), f2hi(tb), f2lo(tc));
+        const float2 sv = f2div(num, den);                 // s V_ij
+        float2 wgt = f2mul(sv, rs);
+        if (MASKED) {
+            const bool in0 = (c0 >> b) & 1u, in1 = (c1 >> b) & 1u;
+            bool ok0 = in0, ok1 = in1;
+            if (BRK) {
+                // s > s_c, tested as s V_ij > s_c V_ij (tc.w)
+                const bool b0 = in0 && sv.x > tc.w, b1 = in1 && sv.y > tc.w;
+                if (b0) k0 &= ~(1u << b);
+                if (b1) k1 &= ~(1u << b);
+                ok0 = in0 && !b0;
+                ok1 = in1 && !b1;
+            }
+            wgt.x = ok0 ? wgt.x : 0.f;
+            wgt.y = ok1 ? wgt.y : 0.f;
+        } else if (BRK) {
+            anybrk = anybrk || sv.x > tc.w || sv.y > tc.w;
+        }
+        Fx = f2fma(wgt, yx, Fx);
+        Fy = f2fma(wgt, yy, Fy);
+        if (DIM == 3) Fz = f2fma(wgt, yz, Fz);
+    }
+    return anybrk;
+}
+
+template <int DIM, bool BRK>
+__global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
 {
     const Geom &g = a.g;
-    const int m = g.m, S = g.S;
-    const int HX = g.bx + 2 * m, HY = g.by + 2 * m, HZ = DIM == 3 ? g.bz + 2 * m : 1;
-    const int nbox = HX * HY * HZ;
+    const PairBox pb = pair_box(g);
+    const int S = g.S;
     extern __shared__ float4 smem4[];
-    float4 *box = smem4;
-    float4 *tabA = box + nbox;                                  // dx, dy, dz, |d|
-    int2 *tabB = reinterpret_cast<int2 *>(tabA + S);            // box offset, V_ij bits
+    float4 *P4 = smem4;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
+    float4 *tab = P4 + pb.n + (DIM == 3 ? (pb.n + 1) / 2 : 0);      // 3 float4 per stencil entry
 
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
     for (int k = threadIdx.x; k < S; k += blockDim.x) {
         const int4 d = __ldg(&a.stencil[k]);
         const float r0 = (float)__ldg(&a.stencil_r0[k]);
-        tabA[k] = make_float4((float)d.x, (float)d.y, (float)d.z, r0);
-        const float vij = a.vol_corr ? (float)vol_factor_lattice(m, (double)r0) : 1.f;
-        tabB[k] = make_int2(d.x + HX * (d.y + HY * d.z), __float_as_int(vij));
+        const float vij = a.vol_corr ? (float)vol_factor_lattice(g.m, (double)r0) : 1.f;
+        const float R = r0 / vij, C = (float)d.w / vij;
+        tab[3 * k] = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
+        tab[3 * k + 1] = make_float4((float)d.z, (float)d.z, R, R);
+        tab[3 * k + 2] = make_float4(C, C, __int_as_float(d.x + pb.HX * (d.y + pb.HY * d.z)), (float)a.s_c * vij);
     }
-    stage_box32(box, HX, HY, nbox, m, a, org, tile_ref32(a, tile), (float)a.inv_h);
+    stage_pairs(a, pb, org, tile, P4, DIM == 3 ? P2 : nullptr);
     __syncthreads();
 
-    const int nthr = g.T / P;
-    const float s_c = (float)a.s_c;
+    const int nthr = g.T / 2;            // a multiple of blockDim: every lane runs every iteration
     for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
-        const int lx = t & (g.bx - 1);
-        const int r1 = t >> g.lbx;
-        int bi[P], slot[P];
-        bool act[P];
-        Pk<float, P> ux, uy, uz;
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            int ly, lz;
-            if (DIM == 3) {
-                ly = r1 & (g.by - 1);
-                lz = (r1 >> g.lby) + p * (g.bz / P);
-            } else {
-                ly = r1 + p * (g.by / P);
-                lz = 0;
-            }
-            bi[p] = (lx + m) + HX * ((ly + m) + HY * (DIM == 3 ? lz + m : 0));
-            slot[p] = tile * g.T + brick_code(DIM, lx, ly, lz);
-            act[p] = org.x + lx < g.nx && org.y + ly < g.ny && org.z + lz < g.nz;
-            const float4 ui = box[bi[p]];
-            ux.v[p] = ui.x;
-            uy.v[p] = ui.y;
-            uz.v[p] = ui.z;
-        }
-        Pk<float, P> Fx = splat<float, P>(0.f), Fy = Fx, Fz = Fx;
+        const PairPts q = pair_points(g, pb, org, tile, t);
+        const float4 ui4 = P4[q.bi];
+        const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4));
+        const float2 nuz = DIM == 3 ? f2neg(P2[q.bi]) : make_float2(0.f, 0.f);
+        float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
+        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
         for (int w = 0; w < g.W; ++w) {
-            uint32_t word[P], cur[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) word[p] = cur[p] = act[p] ? a.mask[(size_t)w * g.nslots + slot[p]] : 0u;
-            uint32_t keep[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) keep[p] = word[p];
-            const int nb = min(32, S - 32 * w);
-#pragma unroll 4
-            for (int b = 0; b < nb; ++b) {
-                const int k = 32 * w + b;
-                const float4 ta = tabA[k];
-                const int2 tb = tabB[k];
-                Pk<float, P> ex, ey, ez;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float4 rj = box[bi[p] + tb.x];
-                    ex.v[p] = rj.x;
-                    ey.v[p] = rj.y;
-                    ez.v[p] = rj.z;
-                }
-                ex = psub(ex, ux);
-                ey = psub(ey, uy);
-                ez = psub(ez, uz);
-                const Pk<float, P> yx = padds(ex, ta.x), yy = padds(ey, ta.y);
-                const Pk<float, P> yz = DIM == 3 ? padds(ez, ta.z) : ez;
-                Pk<float, P> q = pmul(yx, yx);
-                q = pfma(yy, yy, q);
-                if (DIM == 3) q = pfma(yz, yz, q);
-                // 2 d.eta + eta.eta = eta.(y + d)
-                Pk<float, P> num = pmul(ex, padds(yx, ta.x));
-                num = pfma(ey, padds(yy, ta.y), num);
-                if (DIM == 3) num = pfma(ez, padds(yz, ta.z), num);
-                const Pk<float, P> rs = prsqrt(q);
-                const Pk<float, P> den = pmuls(padds(pmul(q, rs), ta.w), ta.w);
-                const Pk<float, P> s = pdiv(num, den);
-                Pk<float, P> wgt = pmuls(pmul(s, rs), __int_as_float(tb.y));
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    bool intact = cur[p] & 1u;
-                    if (BRK) {
-                        const bool brk = intact && s.v[p] > s_c;
-                        if (brk) keep[p] &= ~(1u << b);
-                        intact = intact && !brk;
-                    }
-                    cur[p] >>= 1;
-                    wgt.v[p] = intact ? wgt.v[p] : 0.f;
-                }
-                Fx = pfma(wgt, yx, Fx);
-                Fy = pfma(wgt, yy, Fy);
-                if (DIM == 3) Fz = pfma(wgt, yz, Fz);
+            const uint32_t m0 = n0, m1 = n1;
+            if (w + 1 < g.W) {
+                const size_t mo = (size_t)(w + 1) * g.nslots;
+                n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
+                n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
             }
-            if (BRK) {
-#pragma unroll
-                for (int p = 0; p < P; ++p)
-                    if (act[p] && keep[p] != word[p]) a.mask[(size_t)w * g.nslots + slot[p]] = keep[p];
+            const int nb = min(32, S - 32 * w);
+            const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            const float4 *tw = tab + 3 * 32 * w;
+            uint32_t k0 = m0, k1 = m1;
+            bool masked = !__all_sync(0xffffffffu, m0 == full && m1 == full);
+            if (!masked) {
+                const float2 sx = Fx, sy = Fy, sz = Fz;
+                const bool brk = pmb_word<DIM, false, BRK>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, k0, k1,
+                                                           Fx, Fy, Fz);
+                if (BRK && __any_sync(0xffffffffu, brk)) {
+                    Fx = sx;
+                    Fy = sy;
+                    Fz = sz;
+                    masked = true;
+                }
+            }
+            if (masked) {
+                pmb_word<DIM, true, BRK>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, k0, k1, Fx, Fy, Fz);
+                if (BRK) {
+                    const size_t mo = (size_t)w * g.nslots;
+                    if (q.act[0] && k0 != m0) a.mask[mo + q.slot[0]] = k0;
+                    if (q.act[1] && k1 != m1) a.mask[mo + q.slot[1]] = k1;
+                }
             }
         }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            if (!act[p]) continue;
-            const double f[3] = {a.cV * (double)Fx.v[p], a.cV * (double)Fy.v[p], a.cV * (double)Fz.v[p]};
-            point_epilogue(a, slot[p], f, DIM, false);
+        if (q.act[0]) {
+            const float F[3] = {Fx.x, Fy.x, Fz.x};
+            pair_epilogue(a, q.slot[0], F, DIM);
+        }
+        if (q.act[1]) {
+            const float F[3] = {Fx.y, Fy.y, Fz.y};
+            pair_epilogue(a, q.slot[1], F, DIM);
         }
     }
 }
 
 size_t pmb_fast_smem(const Geom &g)
 {
-    const size_t nbox = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.dim == 3 ? g.bz + 2 * g.m : 1);
-    return nbox * sizeof(float4) + (size_t)g.S * (sizeof(float4) + sizeof(int2));
+    size_t n;
+    if (g.dim == 3) n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
+    else n = (size_t)(g.bx + 2 * g.m) * (g.by / 2 + 2 * g.m);
+    const size_t p2 = g.dim == 3 ? ((n + 1) / 2) * sizeof(float4) : 0;
+    return n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
 }
 
 // ------------------------------------------------------------------ generic
@@ -215,13 +234,13 @@ __global__ void __launch_bounds__(256) pmb_generic(const TileArgs a)
 
 // ---------------------------------------------------------------- dispatch
 
-template <int DIM, int P, bool BRK>
+template <int DIM, bool BRK>
 static int launch_fast(const TileArgs &a, cudaStream_t st)
 {
     const size_t smem = pmb_fast_smem(a.g);
-    PD_CUDA(cudaFuncSetAttribute(pmb_fast<DIM, P, BRK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int threads = a.g.T / P < 256 ? a.g.T / P : 256;
-    pmb_fast<DIM, P, BRK><<<a.g.ntiles, threads, smem, st>>>(a);
+    PD_CUDA(cudaFuncSetAttribute(pmb_fast<DIM, BRK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int threads = a.g.T / 2 < 256 ? a.g.T / 2 : 256;
+    pmb_fast<DIM, BRK><<<a.g.ntiles, threads, smem, st>>>(a);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -237,8 +256,8 @@ int launch_pmb_args(const TileArgs &a, int precision, cudaStream_t st)
     const Geom &g = a.g;
     const bool brk = a.update_breaking && a.s_c > 0.0;
     if (precision == PD_FP32C) {
-        if (g.dim == 3) return brk ? launch_fast<3, 2, true>(a, st) : launch_fast<3, 2, false>(a, st);
-        return brk ? launch_fast<2, 2, true>(a, st) : launch_fast<2, 2, false>(a, st);
+        if (g.dim == 3) return brk ? launch_fast<3, true>(a, st) : launch_fast<3, false>(a, st);
+        return brk ? launch_fast<2, true>(a, st) : launch_fast<2, false>(a, st);
     }
     const size_t smem = pmb_generic_smem(g, precision);
     PD_CUDA(cudaFuncSetAttribute(pmb_generic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

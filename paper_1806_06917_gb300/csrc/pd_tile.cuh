@@ -324,6 +324,12 @@ struct TileArgs {
     const double *w[3];         // tangent input (slot order)
     double *jv[3];              // tangent output
     double *epoint;             // per-point energy (slot order)
+    float4 *vhl;                // FP32C velocity as double-float pairs (2 float4 per slot)
+    const float *bc32;          // FP32C boundary values as (hi, lo) per DOF, component-major
+    const float4 *body32;       // FP32C body force per slot
+    float kF, kB;               // FP32C kick factors: dt/2 * fscale / rho and dt/2 / rho
+    float dt_h, dt_l;           // dt as a double-float pair
+    double fscale;              // force density = fscale * F (PMB: c V; LPS: 1/h)
     double cV;                  // c V (PMB)
     double inv_rho, dt, s_c, inv_h, h;
     double A, B;                // LPS 3K - 5 mu and 15 mu

@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libpd.so")
+# PD_LIBRARY may name another build of the same library (e.g. a variant for A/B timing)
+LIB_PATH = os.environ.get("PD_LIBRARY") or os.path.join(_HERE, "_build", "libpd.so")
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_EBUSY, PD_ENOTREADY, PD_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 PD_MODEL_PMB, PD_MODEL_LPS = 0, 1
@@ -95,11 +96,17 @@ def _check(rc: int) -> None:
         raise PdError(rc, last_error())
 
 
+CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy: the legacy default stream
+
+
 def _stream(stream):
+    """None selects the simulation's own stream. A torch stream object passes its
+    handle; torch's default stream has handle 0, which the C ABI would read as
+    "own stream", so it is passed as cudaStreamLegacy instead."""
     if stream is None:
         return None
     if hasattr(stream, "cuda_stream"):
-        return _P(stream.cuda_stream)
+        return _P(stream.cuda_stream or CUDA_STREAM_LEGACY)
     return _P(int(stream))
 
 

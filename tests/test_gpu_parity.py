@@ -187,7 +187,7 @@ def test_plate2d_explicit_run_matches_oracle(pd, precision):
 @pytest.mark.parametrize("precision", ["fp32c", "fp64"])
 def test_block_pulse_with_breaking_matches_oracle(pd, precision):
     """Pulse + pre-notch + breaking (s_c lowered so bonds break within the run)."""
-    wl = W.block3d_pulse(nside=24, steps=120, s_c=2e-4)
+    wl = W.block3d_pulse(nside=24, steps=120, s_c=5e-5)
     prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
     sim, bonds, st, u_g, v_g = _run_both(pd, wl, prec, wl.steps)
     _, _, order, _ = gpu_csr_in_user_numbering(pd, sim)
@@ -209,7 +209,7 @@ def test_lps_explicit_run_matches_oracle(pd):
 
 
 def test_graph_replay_equals_single_steps_and_runs_are_deterministic(pd):
-    wl = W.block3d_pulse(nside=16, steps=40, s_c=2e-4)
+    wl = W.block3d_pulse(nside=16, steps=40, s_c=5e-5)
     outs = []
     for chunks in ([40], [1] * 40, [40]):
         sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C, notch=wl.notch)
