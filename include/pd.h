@@ -57,7 +57,8 @@ extern "C" {
 #define PD_MODEL_LPS 1     /* state-based linear peridynamic solid (3D only) */
 
 #define PD_FP32C 0         /* FP32 bond arithmetic on per-tile reference-frame
-                              displacements, FP64 integrator state */
+                              displacements; integrator state u, v held as
+                              double-float (FP32 hi + lo, ~48-bit) */
 #define PD_FP64 1          /* all-FP64 bond arithmetic and state */
 
 #define PD_BC_FREE 0
@@ -107,7 +108,8 @@ typedef struct {
     double dt_factor;   /* used when dt == 0; 0 means 0.5 */
     int32_t precision;  /* PD_FP32C or PD_FP64 */
     int32_t tile_log2;  /* points per tile = 2^tile_log2 (a Morton brick);
-                           0 selects the default (9 in 3D, 8 in 2D); 6..10 */
+                           0 selects 9, or less when the halo box of a large
+                           horizon would not fit in shared memory; 6..10 */
 } pd_run;
 
 typedef struct pd_sim pd_sim;
