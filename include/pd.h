@@ -245,6 +245,31 @@ int pd_vjp(pd_sim *sim, const double *u_lin, const double *v, double *out,
  * Synchronous. */
 int pd_energy(pd_sim *sim, double *kinetic, double *strain, void *stream);
 
+/* ------------------------------------------------------------ no allocation */
+
+/* Largest n pd_sum_noalloc accepts: its scratch holds 1024 partial sums of
+ * 4096 values each. */
+#define PD_SUM_NOALLOC_MAX_VALUES 4194304
+
+/* out[0] = scale * (x[0] + ... + x[n-1]) in FP64, summed in the same fixed
+ * order as the reductions of pd_energy, by the same two kernels, but with the
+ * partial sums in a static device array of the library instead of a buffer
+ * allocated by pd_create. The paper has no counterpart: this entry point is for
+ * callers that may not allocate device memory at all, e.g. a host framework
+ * that owns every device allocation through its own pool or budget, or a loop
+ * where the implicit synchronisation of cudaMalloc/cudaFree is not allowed.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   x, out: device pointers of the current device (x may be NULL if n == 0).
+ *   n: 0 <= n <= PD_SUM_NOALLOC_MAX_VALUES, else PD_EINVAL with a message.
+ *   stream: cudaStream_t or NULL for the legacy default stream; stream-ordered.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress); make that first call before any stream capture. The
+ * array (8 KiB per device, held until the process exits) is shared by every
+ * call: each call overwrites every partial it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (different streams, no ordering)
+ * race on it and may return wrong sums. */
+int pd_sum_noalloc(const double *x, int64_t n, double scale, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ _SIGS = {
     "pd_jvp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_vjp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_energy": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
+    "pd_sum_noalloc": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -277,6 +278,24 @@ def pd_energy(sim: Sim, stream=None):
     k, s = ctypes.c_double(), ctypes.c_double()
     _check(_lib.pd_energy(sim.h, ctypes.byref(k), ctypes.byref(s), _stream(stream)))
     return k.value, s.value
+
+
+PD_SUM_NOALLOC_MAX_VALUES = 4194304
+
+
+def pd_sum_noalloc(x, scale=1.0, out=None, stream=None):
+    """scale * sum(x) in FP64 and fixed order, with no device allocation in the
+    library. x and out are CUDA tensors (float64); out has one element."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("x: need a contiguous float64 CUDA tensor")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise ValueError("out: need a float64 CUDA tensor with one element")
+    _check(_lib.pd_sum_noalloc(_P(x.data_ptr()) if x.numel() else None, int(x.numel()), float(scale),
+                               _P(out.data_ptr()), _stream(stream)))
+    return out
 
 
 # ------------------------------------------------------------ conveniences
