@@ -82,6 +82,10 @@ struct pd_sim {
     int4 *stencil = nullptr;
     double *stencil_r0 = nullptr;
     int *stencil_lut = nullptr;
+    float4 *tab_a = nullptr;        // FP32C stencil table: PMB, or LPS dilatation
+    float4 *tab_b = nullptr;        // FP32C stencil table: LPS force
+    int *tile_nbr = nullptr;        // [ntiles * 27]
+    int nbr_ok = 0;
     // CSR
     BuildOut csr{nullptr, nullptr, 0};
     // state
@@ -311,6 +315,60 @@ static int create_impl(pd_sim *s)
     PD_CUDA(cudaMemcpy(s->stencil_r0, r0.data(), sizeof(double) * g.S, cudaMemcpyHostToDevice));
     PD_CUDA(cudaMemcpy(s->stencil_lut, lut.data(), sizeof(int) * lut.size(), cudaMemcpyHostToDevice));
 
+    // FP32C stencil tables in the kernels' pre-splatted form; offsets index the
+    // paired halo box (x extent bx + 2m; y extent by + 2m in 3D, by/2 + 2m in 2D)
+    {
+        const int PHX = g.bx + 2 * g.m, PHY = g.dim == 3 ? g.by + 2 * g.m : g.by / 2 + 2 * g.m;
+        std::vector<float4> ta(4 * (size_t)g.S), tb(4 * (size_t)g.S);
+        const double A = 3.0 * mt.K - 5.0 * mt.mu, B = 15.0 * mt.mu;
+        for (int k = 0; k < g.S; ++k) {
+            const int4 d = st[k];
+            const double rr = r0[k], d2 = d.w;
+            const double vij = mt.vol_corr && rr > g.m - 0.5 ? (g.m + 0.5 - rr) : 1.0;
+            const int off = d.x + PHX * (d.y + PHY * d.z);
+            float offf;
+            memcpy(&offf, &off, sizeof(float));
+            const float4 dxy = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
+            ta[4 * k] = dxy;
+            tb[4 * k] = dxy;
+            // LPS force: {dz,dz,|d|,|d|} {A|d|V_ij x2, B V_ij x2} {|d|^2,|d|^2,offset,-}
+            tb[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
+            tb[4 * k + 2] = make_float4((float)(A * rr * vij), (float)(A * rr * vij), (float)(B * vij),
+                                        (float)(B * vij));
+            tb[4 * k + 3] = make_float4((float)d2, (float)d2, offf, 0.f);
+            if (mt.model == PD_MODEL_PMB) {
+                // {dz,dz,|d|^2,|d|^2} {|d|/V_ij x2, |d|^2/V_ij x2} {offset, s_c V_ij, -, -}
+                ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)d2, (float)d2);
+                ta[4 * k + 2] = make_float4((float)(rr / vij), (float)(rr / vij), (float)(d2 / vij), (float)(d2 / vij));
+                ta[4 * k + 3] = make_float4(offf, (float)(mt.s_c * vij), 0.f, 0.f);
+            } else {
+                // dilatation: {dz,dz,|d|,|d|} {|d|V_ij x2, |d|^2 x2} {offset,-,-,-}
+                ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
+                ta[4 * k + 2] = make_float4((float)(rr * vij), (float)(rr * vij), (float)d2, (float)d2);
+                ta[4 * k + 3] = make_float4(offf, 0.f, 0.f, 0.f);
+            }
+        }
+        ALLOC(s->tab_a, sizeof(float4) * ta.size());
+        ALLOC(s->tab_b, sizeof(float4) * tb.size());
+        PD_CUDA(cudaMemcpy(s->tab_a, ta.data(), sizeof(float4) * ta.size(), cudaMemcpyHostToDevice));
+        PD_CUDA(cudaMemcpy(s->tab_b, tb.data(), sizeof(float4) * tb.size(), cudaMemcpyHostToDevice));
+        // neighbour tiles (index (dx+1) + 3 (dy+1) + 9 (dz+1)); usable when the halo
+        // reaches at most one tile in every direction
+        std::vector<int> nbr(27 * (size_t)g.ntiles, -1);
+        for (int t = 0; t < g.ntiles; ++t)
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int x = tiles[t].tx + dx, y = tiles[t].ty + dy, z = tiles[t].tz + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= g.tgx || y >= g.tgy || z >= g.tgz) continue;
+                        nbr[27 * (size_t)t + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] =
+                            tlut[x + g.tgx * (y + g.tgy * z)];
+                    }
+        s->nbr_ok = g.m <= g.bx && g.m <= g.by && (g.dim == 2 || g.m <= g.bz);
+        ALLOC(s->tile_nbr, sizeof(int) * nbr.size());
+        PD_CUDA(cudaMemcpy(s->tile_nbr, nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice));
+    }
+
     for (int c = 0; c < 3; ++c) {
         ALLOC(s->u[c], sizeof(double) * NS);
         ALLOC(s->v[c], sizeof(double) * NS);
@@ -396,6 +454,10 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.use_body = s->use_body ? 1 : 0;
     a.adjoint = 0;
     a.vhl = s->vhl;
+    a.tab_a = s->tab_a;
+    a.tab_b = s->tab_b;
+    a.tile_nbr = s->tile_nbr;
+    a.nbr_ok = s->nbr_ok;
     a.bc32 = s->bc32;
     a.body32 = s->body32;
     a.fscale = s->mat.model == PD_MODEL_PMB ? s->mat.c * s->mat.V : 1.0 / s->g.h;

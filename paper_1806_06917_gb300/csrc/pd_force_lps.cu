@@ -29,18 +29,17 @@ __device__ __forceinline__ float2 lps_dil_word(const float4 *tw, int nb, const f
 {
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
-        const int off = __float_as_int(tc.z);
+        // table entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|V_ij,|d|V_ij,|d|^2,|d|^2} {offset,-,-,-}
+        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
+        const int off = __float_as_int(tw[4 * b + 3].x);
         const float4 r4 = P4[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
         const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
-        float2 qq = f2mul(yx, yx);
-        qq = f2fma(yy, yy, qq);
-        qq = f2fma(yz, yz, qq);
         float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
         num = f2fma(ey, f2add(yy, f2hi(ta)), num);
         num = f2fma(ez, f2add(yz, f2lo(tb)), num);
-        float2 e = f2div(num, f2add(f2mul(qq, f2rsqrt(qq)), f2hi(tb)));
+        const float2 qq = f2add(num, f2hi(tc));            // |y|^2 = |d|^2 + 2 d.e + e.e
+        float2 e = f2mul(num, f2rcp(f2add(f2sqrt(qq), f2hi(tb))));
         if (MASKED) {
             e.x = ((c0 >> b) & 1u) ? e.x : 0.f;
             e.y = ((c1 >> b) & 1u) ? e.y : 0.f;
@@ -59,19 +58,18 @@ __device__ __forceinline__ void lps_force_word(const float4 *tw, int nb, const f
 {
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
-        const int off = __float_as_int(tw[4 * b + 3].x);
+        // table entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {A|d|V_ij x2, B V_ij x2} {|d|^2,|d|^2,offset,-}
+        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2], td = tw[4 * b + 3];
+        const int off = __float_as_int(td.z);
         const float4 r4 = P4[bi + off], t4 = PT[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
         const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
-        float2 qq = f2mul(yx, yx);
-        qq = f2fma(yy, yy, qq);
-        qq = f2fma(yz, yz, qq);
         float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
         num = f2fma(ey, f2add(yy, f2hi(ta)), num);
         num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+        const float2 qq = f2add(num, f2lo(td));            // |y|^2 = |d|^2 + 2 d.e + e.e
         const float2 rs = f2rsqrt(qq);
-        const float2 e = f2div(num, f2add(f2mul(qq, rs), f2hi(tb)));
+        const float2 e = f2mul(num, f2rcp(f2add(f2mul(qq, rs), f2hi(tb))));
         // (t_i + t_j) V_ij = A |d| V_ij (a_i + a_j) + B V_ij e (b_i + b_j)
         float2 gg = f2mul(f2lo(tc), f2add(ai, f2lo(t4)));
         gg = f2fma(f2mul(f2hi(tc), e), f2add(bi_, f2hi(t4)), gg);
@@ -94,18 +92,14 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
     extern __shared__ float4 smem4[];
     float4 *P4 = smem4;
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
-    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|V,|d|V,off,-}
+    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
+    __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < S; k += blockDim.x) {
-        const int4 d = __ldg(&a.stencil[k]);
-        const float r0 = (float)__ldg(&a.stencil_r0[k]);
-        const float vij = a.vol_corr ? (float)vol_factor_lattice(g.m, (double)r0) : 1.f;
-        tab[3 * k] = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
-        tab[3 * k + 1] = make_float4((float)d.z, (float)d.z, r0, r0);
-        tab[3 * k + 2] = make_float4(r0 * vij, r0 * vij, __int_as_float(d.x + pb.HX * (d.y + pb.HY * d.z)), 0.f);
-    }
-    stage_pairs(a, pb, org, tile, P4, P2);
+    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    load_nbr(a, tile, s_nbr);
+    __syncthreads();
+    stage_pairs(a, pb, org, tile, s_nbr, P4, P2);
     __syncthreads();
 
     const int nthr = g.T / 2;            // a multiple of blockDim
@@ -125,7 +119,7 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
             }
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
-            const float4 *tw = tab + 3 * 32 * w;
+            const float4 *tw = tab + 4 * 32 * w;
             if (__all_sync(0xffffffffu, m0 == full && m1 == full))
                 acc = lps_dil_word<false>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
             else
@@ -146,26 +140,21 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_force_fast(const TileAr
     float4 *PT = P4 + pb.n;                                     // {aA, aB, bA, bB}: a = theta/m~, b = 1/m~
     float2 *P2 = reinterpret_cast<float2 *>(PT + pb.n);        // {zA, zB}
     float4 *tab = PT + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
+    __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    const float A = (float)a.A, B = (float)a.B;
-    for (int k = threadIdx.x; k < S; k += blockDim.x) {
-        const int4 d = __ldg(&a.stencil[k]);
-        const float r0 = (float)__ldg(&a.stencil_r0[k]);
-        const float vij = a.vol_corr ? (float)vol_factor_lattice(g.m, (double)r0) : 1.f;
-        tab[4 * k] = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
-        tab[4 * k + 1] = make_float4((float)d.z, (float)d.z, r0, r0);
-        tab[4 * k + 2] = make_float4(A * r0 * vij, A * r0 * vij, B * vij, B * vij);
-        tab[4 * k + 3] = make_float4(__int_as_float(d.x + pb.HX * (d.y + pb.HY * d.z)), 0.f, 0.f, 0.f);
-    }
+    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
+    load_nbr(a, tile, s_nbr);
+    __syncthreads();
     {
         const Ref32 ref = tile_ref32(a, tile);
         const float inv_h = (float)a.inv_h;
+#pragma unroll 2
         for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
             int cA[3], cB[3];
             pair_coords(g, pb, org, b, cA, cB);
-            const int sA = slot_at(g, a.tile_lut, cA[0], cA[1], cA[2]);
-            const int sB = slot_at(g, a.tile_lut, cB[0], cB[1], cB[2]);
+            const int sA = slot_of(a, s_nbr, org, cA);
+            const int sB = slot_of(a, s_nbr, org, cB);
             const float4 rA = stage_one(a, a.src_hl, sA, ref, inv_h);
             const float4 rB = stage_one(a, a.src_hl, sB, ref, inv_h);
             const float bA = sA >= 0 ? __ldg(&a.minv32[sA]) : 0.f, bB = sB >= 0 ? __ldg(&a.minv32[sB]) : 0.f;
@@ -201,14 +190,8 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_force_fast(const TileAr
             else
                 lps_force_word<true>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
         }
-        if (q.act[0]) {
-            const float F[3] = {Fx.x, Fy.x, Fz.x};
-            pair_epilogue(a, q.slot[0], F, 3);
-        }
-        if (q.act[1]) {
-            const float F[3] = {Fx.y, Fy.y, Fz.y};
-            pair_epilogue(a, q.slot[1], F, 3);
-        }
+        const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
+        pair_epilogue2(a, q, FA, FB, 3);
     }
 }
 
@@ -216,7 +199,7 @@ size_t lps_fast_smem(const Geom &g, bool dil)
 {
     const size_t n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
     const size_t p2 = ((n + 1) / 2) * sizeof(float4);
-    if (dil) return n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
+    if (dil) return n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
     return 2 * n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
 }
 

@@ -17,10 +17,13 @@ namespace pdk {
 // ------------------------------------------------------------------ fast path
 
 // FP32C. Thread t owns the point pair (A, B) of pd_pair.cuh and evaluates both
-// in f32x2 arithmetic; the stencil loop is rolled over a shared-memory table of
-// pre-splatted constants {dx, dx, dy, dy}, {dz, dz, R, R}, {C, C, off, s_c V_ij}
-// with R = |d| / V_ij and C = |d|^2 / V_ij, so that
-//   s V_ij = (2 d.eta + eta.eta) / (R |y| + C).
+// in f32x2 arithmetic; the stencil loop is rolled over a shared-memory copy of a
+// host-built table of pre-splatted constants, per entry
+//   {dx, dx, dy, dy}, {dz, dz, |d|^2, |d|^2}, {R, R, C, C}, {offset, s_c V_ij, -, -}
+// with R = |d| / V_ij and C = |d|^2 / V_ij. Per bond (lattice units, e = eta):
+//   num = e.(e + 2d) = 2 d.e + e.e,   q = |y|^2 = |d|^2 + num,   r = sqrt(q)
+//   w   = s V_ij / r = num / (R q + C r),   F += w y,
+// since s = num / (|d| (r + |d|)) and (R r + C) r = R q + C r.
 //
 // One 32-bond word of the stencil at a time. MASKED = false is the path for
 // words whose bonds all exist and are intact for every point of the warp (the
@@ -35,32 +38,30 @@ __device__ __forceinline__ bool pmb_word(const float4 *tw, int nb, const float4 
     bool anybrk = false;
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
-        const int off = __float_as_int(tc.z);
+        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2], td = tw[4 * b + 3];
+        const int off = __float_as_int(td.x);
         const float4 r4 = P4[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy);
         const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta));
-        float2 qq = f2mul(yx, yx);
-        qq = f2fma(yy, yy, qq);
         float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
         num = f2fma(ey, f2add(yy, f2hi(ta)), num);
         float2 yz = make_float2(0.f, 0.f);
         if (DIM == 3) {
             const float2 ez = f2add(P2[bi + off], nuz);
             yz = f2add(ez, f2lo(tb));
-            qq = f2fma(yz, yz, qq);
             num = f2fma(ez, f2add(yz, f2lo(tb)), num);
         }
-        const float2 rs = f2rsqrt(qq);
-        const float2 den = f2fma(f2mul(qq, rs), f2hi(tb), f2lo(tc));
-        const float2 sv = f2div(num, den);                 // s V_ij
-        float2 wgt = f2mul(sv, rs);
+        const float2 qq = f2add(num, f2hi(tb));
+        const float2 rr = f2sqrt(qq);
+        const float2 den = f2fma(qq, f2lo(tc), f2mul(rr, f2hi(tc)));
+        float2 wgt = f2mul(num, f2rcp(den));               // s V_ij / |y|
         if (MASKED) {
             const bool in0 = (c0 >> b) & 1u, in1 = (c1 >> b) & 1u;
             bool ok0 = in0, ok1 = in1;
             if (BRK) {
-                // s > s_c, tested as s V_ij > s_c V_ij (tc.w)
-                const bool b0 = in0 && sv.x > tc.w, b1 = in1 && sv.y > tc.w;
+                // s > s_c, tested as s V_ij = w |y| > s_c V_ij (td.y)
+                const float2 sv = f2mul(wgt, rr);
+                const bool b0 = in0 && sv.x > td.y, b1 = in1 && sv.y > td.y;
                 if (b0) k0 &= ~(1u << b);
                 if (b1) k1 &= ~(1u << b);
                 ok0 = in0 && !b0;
@@ -69,7 +70,8 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
             wgt.x = ok0 ? wgt.x : 0.f;
             wgt.y = ok1 ? wgt.y : 0.f;
         } else if (BRK) {
-            anybrk = anybrk || sv.x > tc.w || sv.y > tc.w;
+            const float2 sv = f2mul(wgt, rr);
+            anybrk = anybrk || sv.x > td.y || sv.y > td.y;
         }
         Fx = f2fma(wgt, yx, Fx);
         Fy = f2fma(wgt, yy, Fy);
@@ -87,20 +89,15 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
     extern __shared__ float4 smem4[];
     float4 *P4 = smem4;
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
-    float4 *tab = P4 + pb.n + (DIM == 3 ? (pb.n + 1) / 2 : 0);      // 3 float4 per stencil entry
+    float4 *tab = P4 + pb.n + (DIM == 3 ? (pb.n + 1) / 2 : 0);      // 4 float4 per stencil entry
 
+    __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < S; k += blockDim.x) {
-        const int4 d = __ldg(&a.stencil[k]);
-        const float r0 = (float)__ldg(&a.stencil_r0[k]);
-        const float vij = a.vol_corr ? (float)vol_factor_lattice(g.m, (double)r0) : 1.f;
-        const float R = r0 / vij, C = (float)d.w / vij;
-        tab[3 * k] = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
-        tab[3 * k + 1] = make_float4((float)d.z, (float)d.z, R, R);
-        tab[3 * k + 2] = make_float4(C, C, __int_as_float(d.x + pb.HX * (d.y + pb.HY * d.z)), (float)a.s_c * vij);
-    }
-    stage_pairs(a, pb, org, tile, P4, DIM == 3 ? P2 : nullptr);
+    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    load_nbr(a, tile, s_nbr);
+    __syncthreads();
+    stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr);
     __syncthreads();
 
     const int nthr = g.T / 2;            // a multiple of blockDim: every lane runs every iteration
@@ -121,7 +118,7 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
             }
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
-            const float4 *tw = tab + 3 * 32 * w;
+            const float4 *tw = tab + 4 * 32 * w;
             uint32_t k0 = m0, k1 = m1;
             bool masked = !__all_sync(0xffffffffu, m0 == full && m1 == full);
             if (!masked) {
@@ -144,14 +141,8 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
                 }
             }
         }
-        if (q.act[0]) {
-            const float F[3] = {Fx.x, Fy.x, Fz.x};
-            pair_epilogue(a, q.slot[0], F, DIM);
-        }
-        if (q.act[1]) {
-            const float F[3] = {Fx.y, Fy.y, Fz.y};
-            pair_epilogue(a, q.slot[1], F, DIM);
-        }
+        const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
+        pair_epilogue2(a, q, FA, FB, DIM);
     }
 }
 
@@ -161,7 +152,7 @@ size_t pmb_fast_smem(const Geom &g)
     if (g.dim == 3) n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
     else n = (size_t)(g.bx + 2 * g.m) * (g.by / 2 + 2 * g.m);
     const size_t p2 = g.dim == 3 ? ((n + 1) / 2) * sizeof(float4) : 0;
-    return n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
+    return n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
 }
 
 // ------------------------------------------------------------------ generic

@@ -51,11 +51,30 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c)
 }
 #endif
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 f2rsqrt(float2 q) { return make_float2(rsqrtf(q.x), rsqrtf(q.y)); }
-__device__ __forceinline__ float2 f2div(float2 a, float2 b)
+
+// Single special-function-unit approximations (PTX .approx.ftz forms).
+__device__ __forceinline__ float sfu_rsqrt(float x)
 {
-    return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
+__device__ __forceinline__ float sfu_sqrt(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 f2rsqrt(float2 q) { return make_float2(sfu_rsqrt(q.x), sfu_rsqrt(q.y)); }
+__device__ __forceinline__ float2 f2sqrt(float2 q) { return make_float2(sfu_sqrt(q.x), sfu_sqrt(q.y)); }
+__device__ __forceinline__ float2 f2rcp(float2 q) { return make_float2(sfu_rcp(q.x), sfu_rcp(q.y)); }
+__device__ __forceinline__ float2 f2div(float2 a, float2 b) { return f2mul(a, f2rcp(b)); }
 __device__ __forceinline__ float2 f2lo(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 f2hi(float4 v) { return make_float2(v.z, v.w); }
 
@@ -152,17 +171,43 @@ __device__ __forceinline__ void pair_coords(const Geom &g, const PairBox &pb, co
     }
 }
 
+// Load the tile's 3^d neighbour tiles (and, with them, the per-CTA tables) into
+// shared memory; call before __syncthreads.
+__device__ __forceinline__ void load_nbr(const TileArgs &a, int tile, int *s_nbr)
+{
+    if (a.nbr_ok)
+        for (int k = threadIdx.x; k < 27; k += blockDim.x) s_nbr[k] = __ldg(&a.tile_nbr[27 * tile + k]);
+}
+
+// Slot of (x, y, z) through the neighbour-tile table (no global lookup), or -1.
+__device__ __forceinline__ int slot_nbr(const Geom &g, const int *s_nbr, const int4 &org, int x, int y, int z)
+{
+    if ((unsigned)x >= (unsigned)g.nx || (unsigned)y >= (unsigned)g.ny || (unsigned)z >= (unsigned)g.nz)
+        return -1;
+    const int dtx = (x >> g.lbx) - (org.x >> g.lbx), dty = (y >> g.lby) - (org.y >> g.lby);
+    const int dtz = (z >> g.lbz) - (org.z >> g.lbz);
+    const int t = s_nbr[(dtx + 1) + 3 * (dty + 1) + 9 * (dtz + 1)];
+    return t * g.T + brick_code(g.dim, x & (g.bx - 1), y & (g.by - 1), z & (g.bz - 1));
+}
+
+__device__ __forceinline__ int slot_of(const TileArgs &a, const int *s_nbr, const int4 &org, const int c[3])
+{
+    return a.nbr_ok ? slot_nbr(a.g, s_nbr, org, c[0], c[1], c[2]) : slot_at(a.g, a.tile_lut, c[0], c[1], c[2]);
+}
+
 // Stage the paired box of displacements: P4[b] = {xA, xB, yA, yB}, P2[b] = {zA, zB}.
+// s_nbr must be loaded and visible (a __syncthreads after load_nbr).
 __device__ __forceinline__ void stage_pairs(const TileArgs &a, const PairBox &pb, const int4 &org, int tile,
-                                            float4 *P4, float2 *P2)
+                                            const int *s_nbr, float4 *P4, float2 *P2)
 {
     const Ref32 ref = tile_ref32(a, tile);
     const float inv_h = (float)a.inv_h;
+#pragma unroll 2
     for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
         int cA[3], cB[3];
         pair_coords(a.g, pb, org, b, cA, cB);
-        const float4 rA = stage_one(a, a.src_hl, slot_at(a.g, a.tile_lut, cA[0], cA[1], cA[2]), ref, inv_h);
-        const float4 rB = stage_one(a, a.src_hl, slot_at(a.g, a.tile_lut, cB[0], cB[1], cB[2]), ref, inv_h);
+        const float4 rA = stage_one(a, a.src_hl, slot_of(a, s_nbr, org, cA), ref, inv_h);
+        const float4 rB = stage_one(a, a.src_hl, slot_of(a, s_nbr, org, cB), ref, inv_h);
         P4[b] = make_float4(rA.x, rB.x, rA.y, rB.y);
         if (P2) P2[b] = make_float2(rA.z, rB.z);
     }
@@ -203,59 +248,72 @@ __device__ __forceinline__ PairPts pair_points(const Geom &g, const PairBox &pb,
 
 // ---------------------------------------------------------- update (FP32C)
 
-// Velocity-Verlet update of one point in double-float arithmetic from its
-// force F (FP32, in the kernel's units): the kick is kF * F (+ kB * b) with
-// kF = dt/2 * (force scale)/rho and kB = dt/2/rho. MODE_STEP applies the
+// Velocity-Verlet update of the thread's two points in double-float arithmetic
+// from their forces F (FP32, in the kernel's units): the kick is kF * F (+ kB * b)
+// with kF = dt/2 * (force scale)/rho and kB = dt/2/rho. MODE_STEP applies the
 // second half-kick of the previous step (if v holds a half step), the first
 // half-kick of this step, the drift u += dt v with boundary conditions, and
 // writes u to the next staging buffer; MODE_FINALIZE applies only the pending
-// half-kick; MODE_FORCE stores f = (force scale) * F in FP64.
-__device__ __forceinline__ void pair_epilogue(const TileArgs &a, int slot, const float F[3], int dim)
+// half-kick; MODE_FORCE stores f = (force scale) * F in FP64. Every load of both
+// points is issued before the arithmetic, so the two points share one memory
+// round trip.
+__device__ __forceinline__ void pair_epilogue2(const TileArgs &a, const PairPts &q, const float FA[3],
+                                               const float FB[3], int dim)
 {
     const int ns = a.g.nslots;
     if (a.mode == MODE_FORCE) {
-        for (int c = 0; c < dim; ++c) a.f[c][slot] = a.fscale * (double)F[c];
+        for (int p = 0; p < 2; ++p) {
+            if (!q.act[p]) continue;
+            const float *F = p ? FB : FA;
+            for (int c = 0; c < dim; ++c) a.f[c][q.slot[p]] = a.fscale * (double)F[c];
+        }
         return;
     }
-    const float4 vh4 = a.vhl[2 * slot], vl4 = a.vhl[2 * slot + 1];
-    DF v[3] = {{vh4.x, vl4.x}, {vh4.y, vl4.y}, {vh4.z, vl4.z}};
-    DF u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (a.use_body) bb = a.body32[slot];
-    const float bcomp[3] = {bb.x, bb.y, bb.z};
-    if (a.mode == MODE_STEP) {
-        const float4 uh4 = a.src_hl[2 * slot], ul4 = a.src_hl[2 * slot + 1];
-        u[0] = DF{uh4.x, ul4.x};
-        u[1] = DF{uh4.y, ul4.y};
-        u[2] = DF{uh4.z, ul4.z};
+    float4 vh[2], vl[2], uh[2], ul[2], bb[2];
+    int kind[2][3];
+    for (int p = 0; p < 2; ++p) {
+        const int s = q.act[p] ? q.slot[p] : q.slot[0];
+        vh[p] = a.vhl[2 * s];
+        vl[p] = a.vhl[2 * s + 1];
+        uh[p] = a.src_hl[2 * s];
+        ul[p] = a.src_hl[2 * s + 1];
+        bb[p] = a.use_body ? a.body32[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < 3; ++c) kind[p][c] = c < dim ? a.bc_kind[c * ns + s] : 0;
     }
-    for (int c = 0; c < dim; ++c) {
-        const float kick = fmaf(a.kF, F[c], a.kB * bcomp[c]);
-        const int kind = a.bc_kind[c * ns + slot];
-        if (a.v_is_half) v[c] = df_add_f(v[c], kick);
-        if (a.mode == MODE_STEP) {
-            v[c] = df_add_f(v[c], kick);
-            if (kind == PD_BC_VELOCITY) {
-                v[c] = DF{a.bc32[2 * (size_t)(c * ns + slot)], a.bc32[2 * (size_t)(c * ns + slot) + 1]};
-                u[c] = df_add(u[c], df_mul(DF{a.dt_h, a.dt_l}, v[c]));
-            } else if (kind == PD_BC_DISPLACEMENT) {
-                v[c] = DF{0.f, 0.f};
-                u[c] = DF{a.bc32[2 * (size_t)(c * ns + slot)], a.bc32[2 * (size_t)(c * ns + slot) + 1]};
+    for (int p = 0; p < 2; ++p) {
+        if (!q.act[p]) continue;
+        const int slot = q.slot[p];
+        const float *F = p ? FB : FA;
+        DF v[3] = {{vh[p].x, vl[p].x}, {vh[p].y, vl[p].y}, {vh[p].z, vl[p].z}};
+        DF u[3] = {{uh[p].x, ul[p].x}, {uh[p].y, ul[p].y}, {uh[p].z, ul[p].z}};
+        const float bcomp[3] = {bb[p].x, bb[p].y, bb[p].z};
+        for (int c = 0; c < dim; ++c) {
+            const float kick = fmaf(a.kF, F[c], a.kB * bcomp[c]);
+            const int kd = kind[p][c];
+            if (a.v_is_half) v[c] = df_add_f(v[c], kick);
+            const size_t bq = 2 * (size_t)(c * ns + slot);
+            if (a.mode == MODE_STEP) {
+                v[c] = df_add_f(v[c], kick);
+                if (kd == PD_BC_VELOCITY) {
+                    v[c] = DF{a.bc32[bq], a.bc32[bq + 1]};
+                    u[c] = df_add(u[c], df_mul(DF{a.dt_h, a.dt_l}, v[c]));
+                } else if (kd == PD_BC_DISPLACEMENT) {
+                    v[c] = DF{0.f, 0.f};
+                    u[c] = DF{a.bc32[bq], a.bc32[bq + 1]};
+                } else {
+                    u[c] = df_add(u[c], df_mul(DF{a.dt_h, a.dt_l}, v[c]));
+                }
             } else {
-                u[c] = df_add(u[c], df_mul(DF{a.dt_h, a.dt_l}, v[c]));
+                if (kd == PD_BC_VELOCITY) v[c] = DF{a.bc32[bq], a.bc32[bq + 1]};
+                else if (kd == PD_BC_DISPLACEMENT) v[c] = DF{0.f, 0.f};
             }
-        } else {
-            if (kind == PD_BC_VELOCITY)
-                v[c] = DF{a.bc32[2 * (size_t)(c * ns + slot)], a.bc32[2 * (size_t)(c * ns + slot) + 1]};
-            else if (kind == PD_BC_DISPLACEMENT)
-                v[c] = DF{0.f, 0.f};
         }
-    }
-    a.vhl[2 * slot] = make_float4(v[0].h, v[1].h, v[2].h, 0.f);
-    a.vhl[2 * slot + 1] = make_float4(v[0].l, v[1].l, v[2].l, 0.f);
-    if (a.mode == MODE_STEP) {
-        a.dst_hl[2 * slot] = make_float4(u[0].h, u[1].h, u[2].h, 0.f);
-        a.dst_hl[2 * slot + 1] = make_float4(u[0].l, u[1].l, u[2].l, 0.f);
+        a.vhl[2 * slot] = make_float4(v[0].h, v[1].h, v[2].h, 0.f);
+        a.vhl[2 * slot + 1] = make_float4(v[0].l, v[1].l, v[2].l, 0.f);
+        if (a.mode == MODE_STEP) {
+            a.dst_hl[2 * slot] = make_float4(u[0].h, u[1].h, u[2].h, 0.f);
+            a.dst_hl[2 * slot + 1] = make_float4(u[0].l, u[1].l, u[2].l, 0.f);
+        }
     }
 }
 
