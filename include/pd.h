@@ -109,7 +109,7 @@ typedef struct {
     int32_t precision;  /* PD_FP32C or PD_FP64 */
     int32_t tile_log2;  /* points per tile = 2^tile_log2 (a Morton brick);
                            0 selects 9, or less when the halo box of a large
-                           horizon would not fit in shared memory; 6..10 */
+                           horizon would not fit in shared memory; 6..9 */
 } pd_run;
 
 typedef struct pd_sim pd_sim;

@@ -179,8 +179,8 @@ static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
     if (mt->s_c < 0.0) { set_error("s_c must be >= 0"); return PD_EINVAL; }
     if (gr->dim == 2 && !(mt->thickness > 0.0)) { set_error("2D needs thickness > 0"); return PD_EINVAL; }
     if (rn->precision != PD_FP32C && rn->precision != PD_FP64) { set_error("unknown precision"); return PD_EINVAL; }
-    if (rn->tile_log2 != 0 && (rn->tile_log2 < 6 || rn->tile_log2 > 10)) {
-        set_error("tile_log2 must be 0 or in [6, 10]");
+    if (rn->tile_log2 != 0 && (rn->tile_log2 < 6 || rn->tile_log2 > 9)) {
+        set_error("tile_log2 must be 0 or in [6, 9]");
         return PD_EINVAL;
     }
     if (rn->dt < 0.0 || rn->dt_factor < 0.0) { set_error("dt and dt_factor must be >= 0"); return PD_EINVAL; }

@@ -130,7 +130,13 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
     }
 }
 
-__global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_force_fast(const TileArgs a)
+// The force pass needs 40 bytes of shared memory per point pair (u, and a, b of
+// both points), which allows only two CTAs per SM. To keep 32 warps per SM it
+// runs one thread per point (512 for a 2^9 tile): thread t of half h owns point
+// pair t and sums the stencil words of its half; the two partial forces are
+// added in a fixed order (half 0 + half 1) through shared memory before the
+// update.
+__global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
 {
     const Geom &g = a.g;
     const PairBox pb = pair_box(g);
@@ -166,18 +172,23 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_force_fast(const TileAr
     }
     __syncthreads();
 
-    const int nthr = g.T / 2;            // a multiple of blockDim
-    for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
-        const PairPts q = pair_points(g, pb, org, tile, t);
-        const float4 ui4 = P4[q.bi], ti4 = PT[q.bi];
-        const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4)), nuz = f2neg(P2[q.bi]);
-        const float2 ai = f2lo(ti4), bi = f2hi(ti4);
-        float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
-        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
-        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
-        for (int w = 0; w < g.W; ++w) {
+    const int np = g.T / 2;                                    // point pairs of the tile
+    const int half = threadIdx.x >= np;
+    const int t = threadIdx.x - half * np;
+    const int wsplit = (g.W + 1) / 2;
+    const int w0 = half ? wsplit : 0, w1 = half ? g.W : wsplit;
+    // blockDim == g.T: one pair per thread of each half
+    const PairPts q = pair_points(g, pb, org, tile, t);
+    const float4 ui4 = P4[q.bi], ti4 = PT[q.bi];
+    const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4)), nuz = f2neg(P2[q.bi]);
+    const float2 ai = f2lo(ti4), bi = f2hi(ti4);
+    float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
+    if (w0 < w1) {
+        uint32_t n0 = q.act[0] ? a.mask[(size_t)w0 * g.nslots + q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] ? a.mask[(size_t)w0 * g.nslots + q.slot[1]] : 0u;
+        for (int w = w0; w < w1; ++w) {
             const uint32_t m0 = n0, m1 = n1;
-            if (w + 1 < g.W) {
+            if (w + 1 < w1) {
                 const size_t mo = (size_t)(w + 1) * g.nslots;
                 n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
                 n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
@@ -190,6 +201,20 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_force_fast(const TileAr
             else
                 lps_force_word<true>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
         }
+    }
+    // combine the halves: half 1 publishes its partial force, half 0 adds it
+    __syncthreads();
+    float2 *ex = reinterpret_cast<float2 *>(smem4);            // reuses the staged box
+    if (half) {
+        ex[3 * t] = Fx;
+        ex[3 * t + 1] = Fy;
+        ex[3 * t + 2] = Fz;
+    }
+    __syncthreads();
+    if (!half) {
+        Fx = f2add(Fx, ex[3 * t]);
+        Fy = f2add(Fy, ex[3 * t + 1]);
+        Fz = f2add(Fz, ex[3 * t + 2]);
         const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
         pair_epilogue2(a, q, FA, FB, 3);
     }
@@ -341,7 +366,7 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
     if (precision == PD_FP32C) {
         auto k = dil ? lps_dil_fast : lps_force_fast;
         PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int threads = g.T / 2 < 256 ? g.T / 2 : 256;
+        const int threads = dil ? (g.T / 2 < 256 ? g.T / 2 : 256) : g.T;
         k<<<g.ntiles, threads, smem, st>>>(a);
     } else {
         auto k = dil ? lps_dil_generic<double> : lps_force_generic<double>;

@@ -391,3 +391,28 @@ def test_single_point_and_torch_device_buffers(pd):
     torch.cuda.synchronize()
     assert np.array_equal(fd.cpu().numpy(), pd.pd_force(sim, u=u))
     sim.close()
+
+
+@pytest.mark.parametrize("tile_log2,m", [(7, 3), (6, 2), (8, 4)])
+def test_lps_small_tiles_match_oracle(pd, tile_log2, m):
+    """Tiles other than 2^9 points (the FP32C force pass then runs 2^L threads)."""
+    grid = W.Grid(dim=3, n=(21, 18, 17), h=1.0 / 128, m=m)
+    mat = W.Material(model=W.LPS, K=40e9, mu=30e9)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP32C, tile_log2=tile_log2)
+    bonds = O.neighbors(grid)
+    mv = O.weighted_volume(grid, mat, bonds)
+    u = (1e-4 / 3) * grid.positions() + _u_random(grid, 1e-5, seed=5)
+    th = O.dilatation(grid, mat, bonds, mv, u)
+    assert rel_l2(pd.pd_force(sim, u=u), O.lps_force(grid, mat, bonds, mv, th, u)) <= FORCE_TOL_FP32C
+    sim.close()
+
+
+@pytest.mark.parametrize("tile_log2", [6, 7, 8])
+def test_pmb_small_tiles_match_oracle(pd, tile_log2):
+    grid = W.Grid(dim=3, n=(21, 18, 17), h=0.01, m=3)
+    mat = W.Material(model=W.PMB, E=72e9, s_c=1e-3)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP32C, tile_log2=tile_log2)
+    u = _u_random(grid, 3e-4, seed=6)
+    f = pd.pd_force(sim, u=u)
+    assert rel_l2(f, O.pmb_force(grid, mat, O.neighbors(grid), u)) <= FORCE_TOL_FP32C
+    sim.close()
