@@ -40,6 +40,48 @@ SM_MAX_MHZ = 2070.0
 # one operation; the 2 MUFU ops per bond are not included).
 FP32_OPS_PER_BOND = {"pmb3": 24, "pmb2": 18, "lps_dil": 19, "lps_force": 30}
 
+# Algorithmic bytes per point of one step, in the kernels' layout (u and v as
+# double-float pairs, 2 x float4 = 32 B each): u read 32, v read + written 64,
+# new u written 32, bond-mask words read (4 B x W: W = 4 in 3D, 1 in 2D at m = 3),
+# BC kinds 1 B per DOF. LPS: dilatation pass u 32 + masks 16 + 1/m~ 4 read,
+# theta 4 written (56); force pass u 32 + theta, 1/m~ 8 + masks 16 read, v 64,
+# new u 32, BC kinds 3 (155).
+BYTES_PER_POINT = {"pmb3": 147.0, "pmb2": 134.0, "lps": 211.0}
+CSR_BYTES_PER_BOND = {"pmb3": 4.25, "pmb2": 4.25, "lps": 8.0}
+KERNEL_LABEL = {
+    "pmb3": lambda wl: "pmb_fast<3, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
+    "pmb2": lambda wl: "pmb_fast<2, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
+    "lps": lambda wl: "lps_dil_fast + lps_force_fast (one step)",
+}
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step's
+# launches, from one `ncu --set full` capture of each workload's kernels (the
+# summaries under profiles/). A figure holds only while the kernel's sources and
+# build flags hash to the value recorded with it; otherwise traffic is null.
+_KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
+                  "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
+NCU_TRAFFIC = {
+    "pmb3": {"bytes": 21880064 + 0, "sha": "baf798de980efd6f",
+             "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
+             "profile": "profiles/pmb_fast_block3d_64.md"},
+    "lps": {"bytes": (109672704 + 6481664) + (195561472 + 97338112), "sha": "d741cb3a3b0e2293",
+            "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
+            "profile": "profiles/lps_block3d_128.md"},
+}
+
+
+def ncu_traffic(key):
+    """Bytes per step from the recorded ncu capture, or None if the kernel changed since."""
+    import hashlib
+    rec = NCU_TRAFFIC.get(key)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest()[:16] == rec["sha"] else None
+
 
 def workload(name):
     if name == "block64":
@@ -247,45 +289,62 @@ def main():
         ms = float(t.item())
     value = world * nbonds / (ms * 1e-3)
 
-    # end to end through the public API: initial state from pinned host memory,
-    # the timed steps (graph-replayed), final state back to pinned host memory
+    # end to end through the public API, host buffers every step: the state
+    # (u, v) in from pinned host memory, one explicit step, u back out to pinned
+    # host memory (pd_get_state is synchronous)
     u_h = torch.from_numpy(wl.u0).pin_memory()
     v_h = torch.from_numpy(wl.v0).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
-    v_o = torch.empty_like(v_h).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
+        pd.pd_step_explicit(sim, 1, stream)
+        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
     barrier()
     e0.record(stream)
-    pd.pd_set_state(sim, u=u_h.numpy(), v=v_h.numpy(), stream=stream)
-    pd.pd_step_explicit(sim, args.steps, stream)
-    pd.pd_get_state(sim, u=u_o.numpy(), v=v_o.numpy(), stream=stream)
+    for _ in range(args.steps):
+        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
+        pd.pd_step_explicit(sim, 1, stream)
+        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
     e2e = {"value": world * nbonds * args.steps / (e2e_ms * 1e-3), "unit": "bond-updates/s",
-           "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8 / args.steps,
-           "d2h_bytes_per_step": (u_o.numel() + v_o.numel()) * 8 / args.steps,
-           "note": "pd_set_state + pd_step_explicit(K) + pd_get_state with pinned host buffers, "
-                   "copies amortised over the K steps; L2 not flushed"}
+           "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8,
+           "d2h_bytes_per_step": u_o.numel() * 8,
+           "note": "per step: pd_set_state(u, v) from pinned host + pd_step_explicit(1) + pd_get_state(u) "
+                   "to pinned host; L2 not flushed"}
 
     # roofline of the dominant kernel: FP32 ALU (not HBM) bound
     ops = FP32_OPS_PER_BOND[key] if key != "lps" else FP32_OPS_PER_BOND["lps_dil"] + FP32_OPS_PER_BOND["lps_force"]
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     achieved = ops * nbonds / (ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP32 ops)",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": ncu_traffic(key),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz, one op per lane per clock",
-                "ops_per_bond": ops, "kernel": "pmb_fast<3,2,true>" if key == "pmb3" else key,
-                "launch_ms": ms / launches_per_step if key != "lps" else ms}
+                "ops_per_bond": ops, "kernel": KERNEL_LABEL[key](wl),
+                "launch_ms": ms / launches_per_step if key != "lps" else ms,
+                "traffic_note": "bytes per step (all launches of one step) from one ncu capture, "
+                                "cold L2; null when the kernel changed since"}
     peaks = measured_peaks()
     if peaks:
-        bytes_pt = 180.0 if key != "lps" else 250.0
+        # per-point bytes the fused step must move (the kernels read no neighbour
+        # list); and, for context, the bytes a CSR kernel would add (4 B of col
+        # per bond per pass plus the breaking bit)
+        bytes_pt, csr_b = BYTES_PER_POINT[key], CSR_BYTES_PER_BOND[key]
         roofline["hbm_frac_of_measured"] = (bytes_pt * wl.grid.npoints / (ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
+        roofline["hbm_frac_of_measured_csr_equivalent"] = (
+            (bytes_pt * wl.grid.npoints + csr_b * nbonds) / (ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
+        roofline["hbm_peak_gbs"] = peaks["hbm_gbs"]
 
     line = {"metric": "bond updates/s (explicit step, FP32-compensated)", "value": value,
             "unit": "bond-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (bond arithmetic), f64 (integrator state)", "data": "synthetic",
+            "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)", "data": "synthetic",
             "config": {"workload": desc, "bonds": nbonds, "points": wl.grid.npoints,
                        "l2": "flushed before every timed step (512 MB write, then a 256 MB read that writes the dirty lines back)", "parallelism": "replicas",
                        "launches_per_step": launches_per_step},

@@ -165,14 +165,15 @@ int pd_break_bonds(pd_sim *sim, int axis, double pos, const double lo[3], const 
 /* -------------------------------------------------------------------- state */
 
 /* Set displacement u and/or velocity v (npoints x dim, FP64, user order) at the
- * current time; a NULL pointer leaves that field unchanged. Initial conditions
- * u0, v0 of Eqs. (1)-(2). Stream-ordered. */
+ * current time; a NULL pointer leaves that field unchanged (a kept v that the
+ * last step left at a half step is first completed, as in pd_get_state).
+ * Initial conditions u0, v0 of Eqs. (1)-(2). Stream-ordered. */
 int pd_set_state(pd_sim *sim, const double *u, const double *v, void *stream);
 
 /* Read u and/or v (npoints x dim, FP64, user order) at the current integer time
- * step. If the last step left the velocity at a half step, this evaluates the
- * force at the current u to complete it (Eq. (9)); the trajectory is unchanged.
- * Synchronous. */
+ * step; a NULL pointer skips that field. If v is requested and the last step
+ * left the velocity at a half step, this evaluates the force at the current u
+ * to complete it (Eq. (9)); the trajectory is unchanged. Synchronous. */
 int pd_get_state(pd_sim *sim, double *u, double *v, void *stream);
 
 /* Boundary conditions on a collar Omega_c (Sec. 3; Sec. 5.2.2): kind and value

@@ -756,8 +756,10 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
 {
     CHECK_BUILT(s);
     cudaStream_t st = pick(s, stream);
-    int rc = finalize(s, st);
-    if (rc != PD_OK) return rc;
+    int rc = PD_OK;
+    // a kept v must first be completed to the integer step; a replaced one not
+    if (v) s->v_is_half = 0;
+    else if ((rc = finalize(s, st)) != PD_OK) return rc;
     if (u) {
         rc = user_to_slots(s, u, s->u, st);
         if (rc != PD_OK) return rc;
@@ -773,21 +775,23 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
 }
 
 // FP32C keeps u and v as double-float pairs; refresh the FP64 SoA copies.
-static int unpack_state(pd_sim *s, cudaStream_t st)
+static int unpack_state(pd_sim *s, cudaStream_t st, bool want_u = true, bool want_v = true)
 {
     if (s->precision != PD_FP32C) return PD_OK;
-    int rc = unpack_pairs(s->g, s->hl[s->cur], s->u, st);
-    if (rc != PD_OK) return rc;
-    return unpack_pairs(s->g, s->vhl, s->v, st);
+    int rc = PD_OK;
+    if (want_u && (rc = unpack_pairs(s->g, s->hl[s->cur], s->u, st)) != PD_OK) return rc;
+    if (want_v && (rc = unpack_pairs(s->g, s->vhl, s->v, st)) != PD_OK) return rc;
+    return PD_OK;
 }
 
 int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
 {
     CHECK_BUILT(s);
     cudaStream_t st = pick(s, stream);
-    int rc = finalize(s, st);
-    if (rc != PD_OK) return rc;
-    if ((rc = unpack_state(s, st)) != PD_OK) return rc;
+    int rc = PD_OK;
+    // u is always at the integer step; only v may need the completing half kick
+    if (v && (rc = finalize(s, st)) != PD_OK) return rc;
+    if ((rc = unpack_state(s, st, u != nullptr, v != nullptr)) != PD_OK) return rc;
     if (u && (rc = slots_to_user(s, s->u, u, st)) != PD_OK) return rc;
     if (v && (rc = slots_to_user(s, s->v, v, st)) != PD_OK) return rc;
     PD_CUDA(cudaStreamSynchronize(st));

@@ -209,9 +209,11 @@ def pd_set_state(sim: Sim, u=None, v=None, stream=None) -> None:
                              _stream(stream)))
 
 
-def pd_get_state(sim: Sim, u=None, v=None, stream=None):
+def pd_get_state(sim: Sim, u=None, v=None, stream=None, want_v: bool = True):
+    """(u, v) at the current step; want_v=False reads u alone (v is None)."""
     u = np.empty((sim.npoints, sim.dim)) if u is None else u
-    v = np.empty((sim.npoints, sim.dim)) if v is None else v
+    if v is None and want_v:
+        v = np.empty((sim.npoints, sim.dim))
     _check(_lib.pd_get_state(sim.h, _buf(u, np.float64, sim.nvec, "u", True),
                              _buf(v, np.float64, sim.nvec, "v", True), _stream(stream)))
     return u, v

@@ -244,6 +244,53 @@ def test_checkpoint_round_trip_is_bit_identical(pd):
     sim.close()
 
 
+def test_reading_u_alone_leaves_the_trajectory_unchanged(pd):
+    # a u-only read skips the completing half kick; steps after it, and the full
+    # read at the end, must be bit-identical to a run without intermediate reads
+    wl = W.block3d_pulse(nside=16, steps=30, s_c=5e-5)
+    outs = []
+    for read_every in (0, 1, 7):
+        sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C, notch=wl.notch)
+        pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+        us = []
+        for k in range(30):
+            pd.pd_step_explicit(sim, 1)
+            if read_every and k % read_every == 0:
+                u, v = pd.pd_get_state(sim, want_v=False)
+                assert v is None
+                us.append((k, u))
+        outs.append(pd.pd_get_state(sim))
+        outs[-1] = (outs[-1][0], outs[-1][1], pd.pd_get_broken(sim), us)
+        sim.close()
+    for o in outs[1:]:
+        for a, b in zip(outs[0][:3], o[:3]):
+            assert np.array_equal(a, b)
+    # the intermediate u reads agree between the two read patterns where both read
+    k1 = dict(outs[1][3])
+    for k, u in outs[2][3]:
+        assert np.array_equal(u, k1[k])
+
+
+def test_replacing_the_state_mid_run_equals_a_fresh_start(pd):
+    # pd_set_state(u, v) while v sits at a half step must discard that half step
+    wl = W.plate2d(nside=30, steps=20)
+    rng = np.random.default_rng(11)
+    u_x = wl.u0 + 1e-7 * rng.standard_normal(wl.u0.shape)
+    v_x = wl.v0 + 1e-3 * rng.standard_normal(wl.v0.shape)
+    a = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C)
+    pd.pd_set_state(a, u=wl.u0, v=wl.v0)
+    pd.pd_step_explicit(a, 13)
+    pd.pd_set_state(a, u=u_x, v=v_x)
+    pd.pd_step_explicit(a, 20)
+    b = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C)
+    pd.pd_set_state(b, u=u_x, v=v_x)
+    pd.pd_step_explicit(b, 20)
+    for x, y in zip(pd.pd_get_state(a), pd.pd_get_state(b)):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
 def test_energy_matches_oracle_and_is_conserved(pd):
     grid = W.Grid(dim=2, n=(40, 40, 1), h=0.02, m=3)
     mat = W.Material(model=W.PMB, E=72e9, rho=2440.0)
