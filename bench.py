@@ -185,6 +185,26 @@ def time_steps(pd, torch, sim, wl, steps, warmup, stream, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def time_build(pd, torch, wl, stream, reps=3):
+    """Wall time of pd_build_neighbors (CSR + bond mask + weighted volume + step
+    bound, with its allocations and host synchronisations), best of reps after
+    one untimed build."""
+    g, m, r = pd.describe(wl.grid, wl.mat, precision=pd.PD_FP32C)
+    sim = pd.pd_create(g, m, r)
+    pd.pd_build_neighbors(sim, stream)
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pd.pd_build_neighbors(sim, stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    nb = pd.pd_bond_count(sim)
+    sim.close()
+    return {"ms": best * 1e3, "bonds": nb, "bonds_per_s": nb / best}
+
+
 def cpu_baseline(wl, target_s=12.0, max_steps=50):
     """The FP64 oracle (as it stands) on the host cores: a bounded number of explicit
     steps of the same workload."""
@@ -369,6 +389,8 @@ def main():
             line["lps128"] = {"workload": desc2, "value": nb2 / (ms2 * 1e-3), "unit": "bond-updates/s",
                               "ms_per_step": ms2, "steps": len(d2), "launches_per_step": 2,
                               "alu_frac": ops2 * nb2 / (ms2 * 1e-3) / 1e12 / peak}
+            line["neighbour_build"] = {"block64": time_build(pd, torch, wl, stream),
+                                       "lps128": time_build(pd, torch, wl2, stream)}
             sim2.close()
 
     line["clocks"] = clk.summary()

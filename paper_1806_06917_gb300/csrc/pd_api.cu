@@ -653,21 +653,20 @@ int pd_build_neighbors(pd_sim *s, void *stream)
     t.tile_lut = s->tile_lut;
     t.stencil = s->stencil;
     t.stencil_lut = s->stencil_lut;
+    t.stencil_r0 = s->stencil_r0;
     int rc = build_slots(s->g, t, s->user_of_slot, s->slot_of_user, s->rank_of_slot, s->slot_of_rank, st);
     if (rc != PD_OK) return rc;
     t.user_of_slot = s->user_of_slot;
     t.slot_of_user = s->slot_of_user;
     t.rank_of_slot = s->rank_of_slot;
     t.slot_of_rank = s->slot_of_rank;
-    rc = build_csr(s->g, t, &s->csr, st);
-    if (rc != PD_OK) return rc;
-    rc = build_mask(s->g, t, s->csr, s->mask, s->d_err, st);
+    rc = build_csr(s->g, t, &s->csr, s->mask, st);
     if (rc != PD_OK) return rc;
     if (s->mat.model == PD_MODEL_LPS) {
-        rc = build_weighted_volume(s->g, s->mat, t, s->csr, s->mtil, s->minv32, st);
+        rc = build_weighted_volume(s->g, s->mat, t, s->mask, s->mtil, s->minv32, st);
         if (rc != PD_OK) return rc;
     }
-    rc = build_dt_bound(s->g, s->mat, t, s->csr, s->dout, st);
+    rc = build_dt_bound(s->g, s->mat, t, s->mask, s->dout, st);
     if (rc != PD_OK) return rc;
     double smax = 0.0;
     PD_CUDA(cudaMemcpyAsync(&smax, s->dout, sizeof(double), cudaMemcpyDeviceToHost, st));

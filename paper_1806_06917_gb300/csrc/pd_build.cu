@@ -5,11 +5,14 @@
 //   2. cell list with cell edge m h >= delta: counting sort of the points by cell;
 //   3. CSR: every point tests the points of the 3^d cells around it with the
 //      integer predicate a^2 + b^2 + c^2 <= m^2 (Sec. 3.1, points at exactly
-//      delta included); a warp per row collects its neighbours and sorts them
-//      (bitonic) so each row lists Morton ranks in ascending order;
-//   4. the CSR encoded as stencil bits per point (the bond-intact mask);
-//   5. LPS weighted volume m~_i = sum_j |d|^2 V_ij (Algorithm 2, first loop, in
-//      lattice units) and the stable-step sum of every point.
+//      delta included). A CTA per cell stages the candidates of its 3^d cells
+//      in shared memory once, sorts them by Morton rank (bitonic), and a warp
+//      per row of the cell scans them in that order, so each row comes out
+//      ascending; the same scan sets the row's stencil bits (the bond-intact
+//      mask);
+//   4. LPS weighted volume m~_i = sum_j |d|^2 V_ij (Algorithm 2, first loop, in
+//      lattice units) and the stable-step sum of every point, both summed over
+//      the point's mask bits in stencil order.
 // Atomics are used only for counts and for the order of points inside a cell;
 // the sorted CSR, the mask and every table are independent of that order.
 #include "pd_tile.cuh"
@@ -209,102 +212,174 @@ __global__ void k_cell_fill(Geom g, CellGrid cg, const int4 *crd, const long lon
     cell_pts[cell_start[cell] + pos] = (int)r;
 }
 
-__device__ __forceinline__ bool in_horizon(int4 a, int4 b, int m)
+// Candidates of a cell: the points of the 3^d cells around it, as (Morton rank,
+// lattice coordinates relative to the cell's origin packed in 3 x 8 bits; they
+// lie in [-m, 2m) with m <= 24).
+constexpr int CELL_THREADS = 256;
+constexpr int CELL_WARPS = CELL_THREADS / 32;
+constexpr int REL_BIAS = 64;
+
+__device__ __forceinline__ int pack_rel(int x, int y, int z)
 {
-    const int dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-    return dx * dx + dy * dy + dz * dz <= m * m;
+    return (x + REL_BIAS) | ((y + REL_BIAS) << 8) | ((z + REL_BIAS) << 16);
 }
 
-__global__ void k_row_count(Geom g, CellGrid cg, const int4 *crd, const long long *cell_start,
-                            const int *cell_pts, int *row_count)
+// Largest candidate count: a cell of edge m holds at most m^d lattice points.
+static long long cell_capacity(const Geom &g)
 {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= g.npoints) return;
-    const int4 c = crd[r];
-    const int ci = c.x / cg.m, cj = c.y / cg.m, ck = c.z / cg.m;
-    int cnt = 0;
-    for (int dk = -1; dk <= 1; ++dk)
-        for (int dj = -1; dj <= 1; ++dj)
-            for (int di = -1; di <= 1; ++di) {
-                const int a = ci + di, b = cj + dj, e = ck + dk;
-                if (a < 0 || b < 0 || e < 0 || a >= cg.cx || b >= cg.cy || e >= cg.cz) continue;
-                const int cell = a + cg.cx * (b + cg.cy * e);
-                for (long long p = cell_start[cell]; p < cell_start[cell + 1]; ++p) {
-                    const int j = cell_pts[p];
-                    if (j != r && in_horizon(c, crd[j], g.m)) ++cnt;
-                }
-            }
-    row_count[r] = cnt;
+    long long c = 1;
+    for (int d = 0; d < g.dim; ++d) c *= 3LL * g.m;
+    long long n = 1;
+    while (n < c) n <<= 1;
+    return n;
 }
 
-constexpr int ROW_CAP = 2048;
-constexpr int FILL_WARPS = 4;
-
-// A warp per row: gather the row from the cell list, bitonic-sort it in shared
-// memory, write it out. err[0] is set if a row differs from its counted length.
-__global__ void __launch_bounds__(32 * FILL_WARPS) k_row_fill(Geom g, CellGrid cg, const int4 *crd,
-                                                              const long long *cell_start, const int *cell_pts,
-                                                              const int64_t *row_ptr, int *col, int *err)
+static size_t cell_rows_smem(const Geom &g)
 {
-    __shared__ int buf[FILL_WARPS][ROW_CAP];
+    return (size_t)cell_capacity(g) * 2 * sizeof(int) + (size_t)CELL_WARPS * g.W * sizeof(uint32_t);
+}
+
+// FILL = false: row_count[i] for the rows of the cell (no sort needed).
+// FILL = true: col[row_ptr[i] ..] ascending, and the mask words of i's slot.
+// err: 1 = a row differs from its counted length, 3 = a cell above capacity.
+template <bool FILL>
+__global__ void __launch_bounds__(CELL_THREADS) k_cell_rows(Geom g, CellGrid cg, int ncap, const int4 *crd,
+                                                            const long long *cell_start, const int *cell_pts,
+                                                            const int *slot_of_rank, const int *stencil_lut,
+                                                            int *row_count, const int64_t *row_ptr, int *col,
+                                                            uint32_t *mask, int *err)
+{
+    extern __shared__ int csm[];
+    int *key = csm;
+    int *val = csm + ncap;
+    uint32_t *words = reinterpret_cast<uint32_t *>(csm + 2 * ncap);
+    __shared__ long long s_start[27];
+    __shared__ int s_off[28];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const long long r = (long long)blockIdx.x * FILL_WARPS + warp;
-    if (r >= g.npoints) return;
-    int *b = buf[warp];
-    const int4 c = crd[r];
-    const int ci = c.x / cg.m, cj = c.y / cg.m, ck = c.z / cg.m;
-    int cnt = 0;
-    for (int dk = -1; dk <= 1; ++dk)
-        for (int dj = -1; dj <= 1; ++dj)
-            for (int di = -1; di <= 1; ++di) {
-                const int a = ci + di, bb = cj + dj, e = ck + dk;
-                if (a < 0 || bb < 0 || e < 0 || a >= cg.cx || bb >= cg.cy || e >= cg.cz) continue;
-                const int cell = a + cg.cx * (bb + cg.cy * e);
-                const long long p0 = cell_start[cell], p1 = cell_start[cell + 1];
-                for (long long p = p0; p < p1; p += 32) {
-                    const long long q = p + lane;
-                    bool hit = false;
-                    int j = -1;
-                    if (q < p1) {
-                        j = cell_pts[q];
-                        hit = j != r && in_horizon(c, crd[j], g.m);
-                    }
-                    const unsigned ball = __ballot_sync(0xffffffffu, hit);
-                    const int pos = cnt + __popc(ball & ((1u << lane) - 1u));
-                    if (hit && pos < ROW_CAP) b[pos] = j;
-                    cnt += __popc(ball);
-                }
+    const int cell = blockIdx.x;
+    const int ca = cell % cg.cx, cb = (cell / cg.cx) % cg.cy, ce = cell / (cg.cx * cg.cy);
+    const int nc = g.dim == 3 ? 27 : 9, centre = g.dim == 3 ? 13 : 4;
+    if (warp == 0) {
+        int cnt = 0;
+        long long st0 = 0;
+        if (lane < nc) {
+            const int A = ca + lane % 3 - 1, B = cb + (lane / 3) % 3 - 1, E = ce + (g.dim == 3 ? lane / 9 - 1 : 0);
+            if (A >= 0 && B >= 0 && E >= 0 && A < cg.cx && B < cg.cy && E < cg.cz) {
+                const int c2 = A + cg.cx * (B + cg.cy * E);
+                st0 = cell_start[c2];
+                cnt = (int)(cell_start[c2 + 1] - st0);
             }
-    const long long base = row_ptr[r];
-    const int want = (int)(row_ptr[r + 1] - base);
-    if (cnt != want || cnt > ROW_CAP) {
-        if (lane == 0) atomicExch(err, 1);
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < nc) {
+            s_start[lane] = st0;
+            s_off[lane + 1] = incl;
+        }
+        if (lane == 0) s_off[0] = 0;
+    }
+    __syncthreads();
+    const int total = s_off[nc];
+    if (total > ncap) {
+        if (threadIdx.x == 0) atomicExch(err, 3);
         return;
     }
     int N = 1;
-    while (N < cnt) N <<= 1;
-    for (int i = cnt + lane; i < N; i += 32) b[i] = 0x7fffffff;
-    __syncwarp();
-    for (int k = 2; k <= N; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < N; i += 32) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const int x = b[i], y = b[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        b[i] = y;
-                        b[ixj] = x;
+    while (N < total) N <<= 1;
+    const int ox = ca * cg.m, oy = cb * cg.m, oz = ce * cg.m;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        if (q < total) {
+            int c = 0;
+            while (s_off[c + 1] <= q) ++c;
+            const int j = cell_pts[s_start[c] + (q - s_off[c])];
+            const int4 cj = crd[j];
+            key[q] = j;
+            val[q] = pack_rel(cj.x - ox, cj.y - oy, cj.z - oz);
+        } else {
+            key[q] = 0x7fffffff;
+            val[q] = 0;
+        }
+    }
+    __syncthreads();
+    if (FILL) {
+        // bitonic sort of (key, val) by key; keys are distinct ranks, pads last
+        for (int k = 2; k <= N; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                    const int i = 2 * t - (t & (j - 1));
+                    const int ixj = i + j;
+                    const int ki = key[i], kj = key[ixj];
+                    if ((ki > kj) == ((i & k) == 0)) {
+                        key[i] = kj;
+                        key[ixj] = ki;
+                        const int v = val[i];
+                        val[i] = val[ixj];
+                        val[ixj] = v;
                     }
                 }
+                __syncthreads();
             }
+    }
+    const int n0 = s_off[centre + 1] - s_off[centre];
+    const int mm = g.m * g.m, wdt = 2 * g.m + 1;
+    uint32_t *ww = words + warp * g.W;
+    for (int p = warp; p < n0; p += CELL_WARPS) {
+        const int i = cell_pts[s_start[centre] + p];
+        const int4 ci = crd[i];
+        const int rx = ci.x - ox, ry = ci.y - oy, rz = ci.z - oz;
+        long long base = 0;
+        int want = 0;
+        if (FILL) {
+            base = row_ptr[i];
+            want = (int)(row_ptr[i + 1] - base);
+            for (int w = lane; w < g.W; w += 32) ww[w] = 0u;
             __syncwarp();
         }
-    for (int i = lane; i < cnt; i += 32) col[base + i] = b[i];
+        int cnt = 0;
+        for (int q0 = 0; q0 < total; q0 += 32) {
+            const int q = q0 + lane;
+            bool hit = false;
+            int j = 0, dx = 0, dy = 0, dz = 0;
+            if (q < total) {
+                j = key[q];
+                const int v = val[q];
+                dx = (v & 0xff) - REL_BIAS - rx;
+                dy = ((v >> 8) & 0xff) - REL_BIAS - ry;
+                dz = ((v >> 16) & 0xff) - REL_BIAS - rz;
+                hit = j != i && dx * dx + dy * dy + dz * dz <= mm;
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, hit);
+            if (FILL && hit) {
+                const int pos = cnt + __popc(ball & ((1u << lane) - 1u));
+                if (pos < want) col[base + pos] = j;        // never false unless the count pass disagreed
+                const int k = stencil_lut[(dx + g.m) + wdt * ((dy + g.m) + wdt * (g.dim == 3 ? dz + g.m : 0))];
+                atomicOr(&ww[k >> 5], 1u << (k & 31));
+            }
+            cnt += __popc(ball);
+        }
+        if (!FILL) {
+            if (lane == 0) row_count[i] = cnt;
+        } else {
+            if (lane == 0 && cnt != want) atomicExch(err, 1);
+            __syncwarp();
+            const int sl = slot_of_rank[i];
+            for (int w = lane; w < g.W; w += 32) mask[(size_t)w * g.nslots + sl] = ww[w];
+            __syncwarp();
+        }
+    }
 }
 
-int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
+constexpr int MAX_WORDS = 64;
+
+int build_csr(const Geom &g, const Tables &t, BuildOut *out, uint32_t *mask, cudaStream_t st)
 {
+    if (g.W > MAX_WORDS) {
+        set_error("stencil of %d offsets exceeds %d mask words", g.S, MAX_WORDS);
+        return PD_EINVAL;
+    }
     CellGrid cg;
     cg.m = g.m;
     cg.cx = (g.nx + g.m - 1) / g.m;
@@ -312,6 +387,8 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
     cg.cz = (g.nz + g.m - 1) / g.m;
     const long long ncell = (long long)cg.cx * cg.cy * cg.cz;
     const long long n = g.npoints;
+    const int ncap = (int)cell_capacity(g);
+    const size_t smem = cell_rows_smem(g);
     int4 *crd = nullptr;
     int *cell_count = nullptr, *cursor = nullptr, *cell_pts = nullptr, *row_count = nullptr, *err = nullptr;
     long long *cell_start = nullptr;
@@ -319,6 +396,10 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
     out->row_ptr = nullptr;
     out->col = nullptr;
     out->nbonds = 0;
+    if (smem > 227 * 1024) {
+        set_error("neighbour build needs %zu bytes of shared memory per cell (m too large)", smem);
+        return PD_EINVAL;
+    }
 #define B_ALLOC(p, bytes)                                              \
     do {                                                               \
         if (cudaMalloc(&(p), (bytes)) != cudaSuccess) {                \
@@ -340,12 +421,17 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
         cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell, st);
         cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st);
         cudaMemsetAsync(err, 0, sizeof(int), st);
+        cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (size_t)g.W * g.nslots, st);
+        PD_CUDA(cudaFuncSetAttribute(k_cell_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(cudaFuncSetAttribute(k_cell_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_rank_coords<<<nb, 256, 0, st>>>(g, t.tile_org, t.slot_of_rank, crd);
         k_cell_count<<<nb, 256, 0, st>>>(g, cg, crd, cell_count);
         rc = exclusive_scan(cell_count, ncell, cell_start, st);
         if (rc != PD_OK) goto done;
         k_cell_fill<<<nb, 256, 0, st>>>(g, cg, crd, cell_start, cursor, cell_pts);
-        k_row_count<<<nb, 256, 0, st>>>(g, cg, crd, cell_start, cell_pts, row_count);
+        k_cell_rows<false><<<(unsigned)ncell, CELL_THREADS, smem, st>>>(
+            g, cg, ncap, crd, cell_start, cell_pts, t.slot_of_rank, t.stencil_lut, row_count, nullptr, nullptr,
+            nullptr, err);
         rc = exclusive_scan(row_count, n, (long long *)out->row_ptr, st);
         if (rc != PD_OK) goto done;
         long long nbonds = 0;
@@ -355,8 +441,9 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
         }
         out->nbonds = nbonds;
         B_ALLOC(out->col, sizeof(int) * (nbonds > 0 ? nbonds : 1));
-        const int nbw = (int)((n + FILL_WARPS - 1) / FILL_WARPS);
-        k_row_fill<<<nbw, 32 * FILL_WARPS, 0, st>>>(g, cg, crd, cell_start, cell_pts, out->row_ptr, out->col, err);
+        k_cell_rows<true><<<(unsigned)ncell, CELL_THREADS, smem, st>>>(
+            g, cg, ncap, crd, cell_start, cell_pts, t.slot_of_rank, t.stencil_lut, nullptr, out->row_ptr,
+            out->col, mask, err);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
@@ -367,7 +454,8 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st)
         cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
         if (herr) {
             rc = PD_EINVAL;
-            set_error("neighbour row longer than %d entries or inconsistent", ROW_CAP);
+            set_error(herr == 3 ? "a cell holds more points than the lattice allows"
+                                : "a neighbour row differs from its counted length");
         }
     }
 done:
@@ -397,113 +485,61 @@ __device__ __forceinline__ int stencil_index(const Geom &g, const int *lut, int 
     return lut[(dx + g.m) + w * ((dy + g.m) + w * (g.dim == 3 ? dz + g.m : 0))];
 }
 
-constexpr int MAX_WORDS = 64;
-
-__global__ void k_mask(Geom g, const int4 *tile_org, const int *slot_of_rank, const int *stencil_lut,
-                       const int64_t *row_ptr, const int *col, uint32_t *mask, int *err)
-{
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= g.npoints) return;
-    const int s = slot_of_rank[r];
-    int c[3];
-    slot_coord(g, tile_org, s, c);
-    uint32_t words[MAX_WORDS];
-    for (int w = 0; w < g.W; ++w) words[w] = 0u;
-    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-        int cj[3];
-        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
-        const int k = stencil_index(g, stencil_lut, cj[0] - c[0], cj[1] - c[1], cj[2] - c[2]);
-        if (k < 0) {
-            atomicExch(err, 2);
-            continue;
-        }
-        words[k >> 5] |= 1u << (k & 31);
-    }
-    for (int w = 0; w < g.W; ++w) mask[(size_t)w * g.nslots + s] = words[w];
-}
-
-int build_mask(const Geom &g, const Tables &t, const BuildOut &csr, uint32_t *mask, int *d_err, cudaStream_t st)
-{
-    if (g.W > MAX_WORDS) {
-        set_error("stencil of %d offsets exceeds %d mask words", g.S, MAX_WORDS);
-        return PD_EINVAL;
-    }
-    PD_CUDA(cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (size_t)g.W * g.nslots, st));
-    PD_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    k_mask<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.tile_org, t.slot_of_rank, t.stencil_lut, csr.row_ptr,
-                                                    csr.col, mask, d_err);
-    PD_CUDA(cudaGetLastError());
-    PD_CUDA(cudaStreamSynchronize(st));
-    int herr = 0;
-    PD_CUDA(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr) {
-        set_error("a CSR entry lies outside the horizon stencil");
-        return PD_EINVAL;
-    }
-    return PD_OK;
-}
-
 // --------------------------------------------- weighted volume, step bound
 
-__device__ __forceinline__ double vol_factor_dev(int m, double r0, int vol_corr)
+// Per-point sums over the intact stencil bits, in stencil order, of a per-entry
+// FP64 value built in shared memory from |d|: which = 0 gives the LPS weighted
+// volume sum_j |d|^2 V_ij, which = 1 the stable-step sum sum_j V_ij / |d|.
+__global__ void __launch_bounds__(256) k_stencil_sum(Geom g, int vol_corr, int which, const int *slot_of_rank,
+                                                     const int4 *stencil, const double *stencil_r0,
+                                                     const uint32_t *mask, double *mtil, float *minv32,
+                                                     unsigned long long *smax)
 {
-    return vol_corr ? vol_factor_lattice(m, r0) : 1.0;
-}
-
-__global__ void k_weighted_volume(Geom g, int vol_corr, const int4 *tile_org, const int *slot_of_rank,
-                                  const int64_t *row_ptr, const int *col, double *mtil, float *minv32)
-{
+    extern __shared__ double tabk[];
+    for (int k = threadIdx.x; k < g.S; k += blockDim.x) {
+        const double r0 = stencil_r0[k];
+        const double v = vol_corr ? vol_factor_lattice(g.m, r0) : 1.0;
+        tabk[k] = which == 0 ? (double)stencil[k].w * v : v / r0;     // .w = |d|^2, exact
+    }
+    __syncthreads();
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= g.npoints) return;
     const int s = slot_of_rank[r];
-    int c[3];
-    slot_coord(g, tile_org, s, c);
     double acc = 0.0;
-    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-        int cj[3];
-        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
-        const double dx = cj[0] - c[0], dy = cj[1] - c[1], dz = cj[2] - c[2];
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        acc += d2 * vol_factor_dev(g.m, sqrt(d2), vol_corr);
+    for (int w = 0; w < g.W; ++w) {
+        uint32_t word = mask[(size_t)w * g.nslots + s];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1u;
+            acc += tabk[32 * w + b];
+        }
     }
-    mtil[s] = acc;
-    minv32[s] = acc > 0.0 ? (float)(1.0 / acc) : 0.f;
+    if (which == 0) {
+        mtil[s] = acc;
+        minv32[s] = acc > 0.0 ? (float)(1.0 / acc) : 0.f;
+    } else {
+        // positive doubles order like their bit patterns
+        atomicMax(smax, (unsigned long long)__double_as_longlong(acc));
+    }
 }
 
-int build_weighted_volume(const Geom &g, const Material &mat, const Tables &t, const BuildOut &csr, double *mtil,
+int build_weighted_volume(const Geom &g, const Material &mat, const Tables &t, const uint32_t *mask, double *mtil,
                           float *minv32, cudaStream_t st)
 {
-    k_weighted_volume<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, mat.vol_corr, t.tile_org, t.slot_of_rank,
-                                                              csr.row_ptr, csr.col, mtil, minv32);
+    k_stencil_sum<<<(g.npoints + 255) / 256, 256, sizeof(double) * g.S, st>>>(
+        g, mat.vol_corr, 0, t.slot_of_rank, t.stencil, t.stencil_r0, mask, mtil, minv32, nullptr);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
 
-// max_i sum_j V_ij / |d| (lattice units); positive doubles order like their bits.
-__global__ void k_dt_sum(Geom g, int vol_corr, const int4 *tile_org, const int *slot_of_rank,
-                         const int64_t *row_ptr, const int *col, unsigned long long *smax)
-{
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= g.npoints) return;
-    int c[3];
-    slot_coord(g, tile_org, slot_of_rank[r], c);
-    double acc = 0.0;
-    for (long long e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-        int cj[3];
-        slot_coord(g, tile_org, slot_of_rank[col[e]], cj);
-        const double dx = cj[0] - c[0], dy = cj[1] - c[1], dz = cj[2] - c[2];
-        const double r0 = sqrt(dx * dx + dy * dy + dz * dz);
-        acc += vol_factor_dev(g.m, r0, vol_corr) / r0;
-    }
-    atomicMax(smax, (unsigned long long)__double_as_longlong(acc));
-}
-
-int build_dt_bound(const Geom &g, const Material &mat, const Tables &t, const BuildOut &csr, double *d_sum_max,
+// max_i sum_j V_ij / |d| (lattice units) over the intact bonds of the mask.
+int build_dt_bound(const Geom &g, const Material &mat, const Tables &t, const uint32_t *mask, double *d_sum_max,
                    cudaStream_t st)
 {
     PD_CUDA(cudaMemsetAsync(d_sum_max, 0, sizeof(double), st));
-    k_dt_sum<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, mat.vol_corr, t.tile_org, t.slot_of_rank, csr.row_ptr,
-                                                      csr.col, reinterpret_cast<unsigned long long *>(d_sum_max));
+    k_stencil_sum<<<(g.npoints + 255) / 256, 256, sizeof(double) * g.S, st>>>(
+        g, mat.vol_corr, 1, t.slot_of_rank, t.stencil, t.stencil_r0, mask, nullptr, nullptr,
+        reinterpret_cast<unsigned long long *>(d_sum_max));
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -577,6 +613,10 @@ __global__ void k_notch(Geom g, const int4 *tile_org, const int *user_of_slot, c
     if (s >= g.nslots || user_of_slot[s] < 0) return;
     int c[3];
     slot_coord(g, tile_org, (int)s, c);
+    // a bond spans at most m lattice units along the notch axis: points farther
+    // than that from the plane have no crossing bond
+    const double sd = __dadd_rn((double)c[nd.axis], -nd.pos);
+    if (sd > (double)g.m || sd < -(double)g.m) return;
     unsigned long long local = 0;
     for (int w = 0; w < g.W; ++w) {
         uint32_t word = mask[(size_t)w * g.nslots + s];

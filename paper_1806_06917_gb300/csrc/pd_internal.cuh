@@ -101,6 +101,7 @@ struct Tables {
     const int *slot_of_rank;    // [npoints]
     const int4 *stencil;        // [S] (dx, dy, dz, |d|^2)
     const int *stencil_lut;     // [(2m+1)^dim] offset -> stencil slot or -1
+    const double *stencil_r0;   // [S] |d| of each stencil entry
 };
 
 enum Mode { MODE_FORCE = 0, MODE_STEP = 1, MODE_FINALIZE = 2 };
@@ -115,12 +116,11 @@ struct BuildOut {
 };
 int build_slots(const Geom &g, const Tables &t, int *d_user_of_slot, int *d_slot_of_user,
                 int *d_rank_of_slot, int *d_slot_of_rank, cudaStream_t st);
-int build_csr(const Geom &g, const Tables &t, BuildOut *out, cudaStream_t st);
-int build_mask(const Geom &g, const Tables &t, const BuildOut &csr, uint32_t *mask,
-               int *d_err, cudaStream_t st);
+// CSR rows (ascending Morton ranks) and the bond-intact stencil mask of every slot.
+int build_csr(const Geom &g, const Tables &t, BuildOut *out, uint32_t *mask, cudaStream_t st);
 int build_weighted_volume(const Geom &g, const Material &mat, const Tables &t,
-                          const BuildOut &csr, double *mtil, float *minv32, cudaStream_t st);
-int build_dt_bound(const Geom &g, const Material &mat, const Tables &t, const BuildOut &csr,
+                          const uint32_t *mask, double *mtil, float *minv32, cudaStream_t st);
+int build_dt_bound(const Geom &g, const Material &mat, const Tables &t, const uint32_t *mask,
                    double *d_sum_max, cudaStream_t st);
 int csr_broken_flags(const Geom &g, const Tables &t, const BuildOut &csr, const uint32_t *mask,
                      uint8_t *out, cudaStream_t st);
