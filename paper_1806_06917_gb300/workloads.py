@@ -176,6 +176,56 @@ def block3d_lps(nside: int = 128, seed: int = 3, steps: int = 500, m: int = 3) -
                     u0=u0, v0=v0, bc_kind=kind, bc_val=val)
 
 
+@dataclasses.dataclass
+class StaticLoad:
+    """A quasi-static load path: the prescribed displacements bc_val (full load)
+    are applied in load_steps equal increments, s / load_steps for s = 1..load_steps."""
+    name: str
+    grid: Grid
+    mat: Material
+    bc_kind: np.ndarray          # (n, dim) uint8: BC_DISPLACEMENT or BC_FREE
+    bc_val: np.ndarray           # (n, dim) FP64 at full load
+    load_steps: int
+    strain: float
+    pin: Optional[int] = None    # point whose u_y is held at 0 (roller variant)
+
+
+def plate_static(nx: int = 200, ny: Optional[int] = None, load_steps: int = 10, strain: float = 1e-4,
+                 m: int = 3, variant: str = "clamped") -> StaticLoad:
+    """2D plate, h = 1/nx m, PMB without breaking, loaded by its x collars
+    (the m outermost columns on each side).
+
+    clamped: left collar u = 0 (both components); right collar u_x = strain * W
+             with W = (nx - 1) h, u_y free.
+    roller:  both collars carry the uniaxial-stress field u_x = strain * X, u_y
+             free, and the left-most point of row ny // 2 has u_y = 0; the
+             continuum solution is then u_x = strain X, u_y = -nu strain (Y - Y0)
+             with nu = 1/3 and Y0 the pinned point's Y.
+    """
+    ny = nx if ny is None else ny
+    h = 1.0 / nx
+    g = Grid(dim=2, n=(nx, ny, 1), h=h, m=m)
+    mat = Material(model=PMB, E=72e9, rho=2440.0, s_c=0.0, thickness=1.0)
+    kind = np.zeros((g.npoints, 2), dtype=np.uint8)
+    val = np.zeros((g.npoints, 2))
+    left, right = collar_mask(g, 0, -1), collar_mask(g, 0, +1)
+    X = g.positions()
+    pin = None
+    if variant == "clamped":
+        kind[left, :] = BC_DISPLACEMENT
+        kind[right, 0] = BC_DISPLACEMENT
+        val[right, 0] = strain * (nx - 1) * h
+    elif variant == "roller":
+        both = left | right
+        kind[both, 0] = BC_DISPLACEMENT
+        val[both, 0] = strain * X[both, 0]
+        pin = (ny // 2) * nx
+        kind[pin, 1] = BC_DISPLACEMENT
+    else:
+        raise ValueError("variant must be 'clamped' or 'roller'")
+    return StaticLoad("plate_static_%dx%d_%s" % (nx, ny, variant), g, mat, kind, val, load_steps, strain, pin)
+
+
 def gaussian_ic(grid: Grid, a: Tuple[float, ...], xc: Tuple[float, ...], beta: float) -> np.ndarray:
     """Gaussian displacement u0 = a * exp(-|X - xc|^2 / beta), the initial-condition
     shape of the paper's explicit convergence study (Sec. 5.2.2)."""
@@ -198,4 +248,5 @@ WORKLOADS: Dict[str, object] = {
     "plate2d_50_pmb": plate2d,
     "block3d_64_pmb_break": block3d_pulse,
     "block3d_128_lps": block3d_lps,
+    "plate_static_200_clamped": plate_static,
 }
