@@ -237,6 +237,51 @@ int pd_jvp(pd_sim *sim, const double *u_lin, const double *w, double *out,
 int pd_vjp(pd_sim *sim, const double *u_lin, const double *v, double *out,
            unsigned flags, void *stream);
 
+/* ------------------------------------------------------------------ implicit */
+
+/* Static equilibrium by matrix-free Newton-Krylov: the implicit scheme of Sec. 5
+ * (Newton on the residual, Eq. (6)) with the stiffness applied by the JVP kernel
+ * instead of being assembled by central differences (Algorithm 3). */
+
+#define PD_KRYLOV_GMRES 0    /* restarted GMRES(restart), CGS2 orthogonalisation */
+#define PD_KRYLOV_CG 1       /* conjugate gradients (the operator is SPD) */
+
+typedef struct {
+    int32_t krylov;           /* PD_KRYLOV_GMRES or PD_KRYLOV_CG */
+    int32_t restart;          /* GMRES restart length, 1..500 (50) */
+    int32_t max_linear_iters; /* per linear solve, >= 1 */
+    int32_t max_newton_iters; /* >= 1 */
+    double linear_rtol;       /* each solve: ||r - A du|| <= linear_rtol ||r|| */
+    double newton_rtol;       /* stop when ||r|| <= newton_rtol ||r_0|| + newton_atol */
+    double newton_atol;       /* N/m^3 */
+} pd_newton_opts;
+
+typedef struct {
+    int32_t newton_iters;     /* linear solves done */
+    int32_t linear_iters;     /* Krylov iterations, summed over the solves */
+    int32_t converged;        /* 1 if the Newton test was met */
+    int32_t linear_failures;  /* solves that stopped at max_linear_iters */
+    double res0;              /* ||r_0||: residual at the start, after the BCs (N/m^3) */
+    double res;               /* ||r|| at the last iterate */
+} pd_newton_stats;
+
+/* Solve f(u) + b = 0 (Eq. (3) with the inertia term dropped) for u on every DOF
+ * without PD_BC_DISPLACEMENT; those DOFs are set to their prescribed values
+ * first and stay there. r = f(u) + b on the free DOFs (0 on prescribed ones),
+ * ||.|| the Euclidean norm over free DOFs. Newton from the current u: solve
+ * A du = r, A = -K on free DOFs and the identity on prescribed ones (K = df/du
+ * of pd_jvp, so A is symmetric and positive definite once the prescribed DOFs
+ * remove the rigid modes), then u += du. The JVP is FP64 for PD_FP64 and FP32
+ * for PD_FP32C simulations (inexact Newton; the residual is FP64 in both). Bonds
+ * do not break during the solve. On return u is the last iterate and v = 0.
+ * PMB only (PD_EINVAL for LPS). opts == NULL takes the defaults in brackets and
+ * GMRES, 20000 linear iterations, 20 Newton iterations, linear_rtol 1e-8,
+ * newton_rtol 1e-8, newton_atol 0. Returns PD_OK whether or not the test was met
+ * (see stats->converged; stats may be NULL); PD_EINVAL if CG meets a
+ * non-positive curvature. Work buffers are allocated on the first call and
+ * kept until pd_destroy. Synchronous. */
+int pd_solve_static(pd_sim *sim, const pd_newton_opts *opts, pd_newton_stats *stats, void *stream);
+
 /* -------------------------------------------------------------------- energy */
 
 /* Kinetic energy sum_i rho |v_i|^2 V_i / 2 and strain energy sum_i V_i W_i

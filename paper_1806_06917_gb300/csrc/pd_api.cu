@@ -110,6 +110,10 @@ struct pd_sim {
     int *d_err = nullptr;
     unsigned long long *d_count = nullptr;
     std::vector<void *> allocs;
+    // Newton-Krylov work of pd_solve_static, allocated on first use
+    double *nk_basis = nullptr, *nk_tmp = nullptr, *nk_partial = nullptr, *nk_dsc = nullptr;
+    double *nk_r = nullptr, *nk_du = nullptr;
+    size_t nk_basis_n = 0, nk_partial_n = 0, nk_dsc_n = 0;
     // graphs: [start parity]
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
@@ -589,6 +593,80 @@ __global__ void k_perm(Geom g, const int *slot_of_rank, const int *user_of_slot,
         if (!(s)->built) { set_error("call pd_build_neighbors first"); return PD_ESTATE; } \
     } while (0)
 
+// ============================================================ Newton-Krylov
+
+// r = f + b on free DOFs of points, 0 elsewhere (component-major, c * nslots + s)
+__global__ void k_nk_residual(Geom g, const int *user_of_slot, const uint8_t *kind, const double *f0,
+                              const double *f1, const double *f2, const double *body, double *r)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const bool act = user_of_slot[s] >= 0;
+    const double *f[3] = {f0, f1, f2};
+    for (int c = 0; c < g.dim; ++c) {
+        const size_t e = (size_t)c * g.nslots + s;
+        r[e] = (act && kind[e] != PD_BC_DISPLACEMENT) ? f[c][s] + (body ? body[e] : 0.0) : 0.0;
+    }
+}
+
+// y = A x from y = K x: -y on free DOFs, x on prescribed ones, 0 off the lattice
+__global__ void k_nk_post(Geom g, const int *user_of_slot, const uint8_t *kind, const double *x, double *y)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const bool act = user_of_slot[s] >= 0;
+    for (int c = 0; c < g.dim; ++c) {
+        const size_t e = (size_t)c * g.nslots + s;
+        y[e] = !act ? 0.0 : (kind[e] == PD_BC_DISPLACEMENT ? x[e] : -y[e]);
+    }
+}
+
+// u = prescribed value on PD_BC_DISPLACEMENT DOFs; with du: u += du elsewhere
+__global__ void k_nk_update(Geom g, const uint8_t *kind, const double *val, const double *du, double *u0, double *u1,
+                            double *u2)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    double *u[3] = {u0, u1, u2};
+    for (int c = 0; c < g.dim; ++c) {
+        const size_t e = (size_t)c * g.nslots + s;
+        if (kind[e] == PD_BC_DISPLACEMENT) u[c][s] = val[e];
+        else if (du) u[c][s] += du[e];
+    }
+}
+
+static int nk_apply(void *ctx, const double *x, double *y, cudaStream_t st)
+{
+    pd_sim *s = static_cast<pd_sim *>(ctx);
+    const Geom &g = s->g;
+    TileArgs a = make_args(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur]);
+    for (int c = 0; c < g.dim; ++c) {
+        a.w[c] = x + (size_t)c * g.nslots;
+        a.jv[c] = y + (size_t)c * g.nslots;
+    }
+    int rc = launch_jvp_args(a, s->precision, st);
+    if (rc != PD_OK) return rc;
+    k_nk_post<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, s->user_of_slot, s->bc_kind, x, y);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+static int nk_reserve(double **p, size_t *have, size_t want)
+{
+    if (*p && *have >= want) return PD_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, sizeof(double) * (want ? want : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc of %zu doubles for the Newton-Krylov work failed", want);
+        return PD_ENOMEM;
+    }
+    *have = want;
+    return PD_OK;
+}
+
 // ==================================================================== C ABI
 
 extern "C" {
@@ -630,6 +708,7 @@ int pd_destroy(pd_sim *s)
     drop_graphs(s);
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (void *p : s->allocs) cudaFree(p);
+    for (double *p : {s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc, s->nk_r, s->nk_du}) cudaFree(p);
     cudaFree(s->csr.row_ptr);
     cudaFree(s->csr.col);
     if (s->stream) cudaStreamDestroy(s->stream);
@@ -979,6 +1058,78 @@ int pd_jvp(pd_sim *s, const double *u_lin, const double *w, double *out, unsigne
 int pd_vjp(pd_sim *s, const double *u_lin, const double *v, double *out, unsigned flags, void *stream)
 {
     return tangent(s, u_lin, v, out, flags, 1, stream);
+}
+
+int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stats, void *stream)
+{
+    CHECK_BUILT(s);
+    if (s->mat.model != PD_MODEL_PMB) { set_error("the static solve needs the PMB tangent"); return PD_EINVAL; }
+    pd_newton_opts o = {PD_KRYLOV_GMRES, 50, 20000, 20, 1e-8, 1e-8, 0.0};
+    if (opts) o = *opts;
+    if (o.krylov != PD_KRYLOV_GMRES && o.krylov != PD_KRYLOV_CG) { set_error("unknown Krylov method"); return PD_EINVAL; }
+    if (o.restart < 1 || o.restart > 500) { set_error("restart must be in [1, 500]"); return PD_EINVAL; }
+    if (o.max_linear_iters < 1 || o.max_newton_iters < 1) { set_error("iteration limits must be >= 1"); return PD_EINVAL; }
+    if (!(o.linear_rtol > 0.0) || !(o.newton_rtol >= 0.0) || !(o.newton_atol >= 0.0)) {
+        set_error("tolerances must be linear_rtol > 0, newton_rtol >= 0, newton_atol >= 0");
+        return PD_EINVAL;
+    }
+    cudaStream_t st = pick(s, stream);
+    const Geom &g = s->g;
+    const long long n = (long long)g.dim * g.nslots;
+    const int kdim = o.krylov == PD_KRYLOV_GMRES ? o.restart : 2;
+    size_t hr = 0, hd = 0;
+    int rc = PD_OK;
+    if ((rc = nk_reserve(&s->nk_basis, &s->nk_basis_n, (size_t)(kdim + 1) * n)) != PD_OK) return rc;
+    if ((rc = nk_reserve(&s->nk_partial, &s->nk_partial_n, krylov_partial_doubles(n, kdim + 1))) != PD_OK) return rc;
+    if ((rc = nk_reserve(&s->nk_dsc, &s->nk_dsc_n, (size_t)kdim + 2)) != PD_OK) return rc;
+    if (!s->nk_tmp) {
+        if ((rc = nk_reserve(&s->nk_tmp, &hr, (size_t)n)) != PD_OK) return rc;
+        if ((rc = nk_reserve(&s->nk_r, &hr, (size_t)n)) != PD_OK) return rc;
+        if ((rc = nk_reserve(&s->nk_du, &hd, (size_t)n)) != PD_OK) return rc;
+    }
+    KrylovWork wk{s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc};
+    KrylovOp op{nk_apply, s};
+    const unsigned nbs = (unsigned)((g.nslots + 255) / 256);
+
+    // the iterate lives in the FP64 slot arrays u; the prescribed values first
+    if ((rc = unpack_state(s, st, true, false)) != PD_OK) return rc;
+    k_nk_update<<<nbs, 256, 0, st>>>(g, s->bc_kind, s->bc_val, nullptr, s->u[0], s->u[1], s->u[2]);
+    PD_CUDA(cudaGetLastError());
+    pd_newton_stats ns = {0, 0, 0, 0, 0.0, 0.0};
+    for (int it = 0;; ++it) {
+        if ((rc = pack_stage(g, s->u, s->hl[s->cur], s->d4[s->cur], st)) != PD_OK) return rc;
+        if ((rc = run_force(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur], 0, st)) != PD_OK) return rc;
+        k_nk_residual<<<nbs, 256, 0, st>>>(g, s->user_of_slot, s->bc_kind, s->f[0], s->f[1], s->f[2],
+                                           s->use_body ? s->body : nullptr, s->nk_r);
+        PD_CUDA(cudaGetLastError());
+        double rn = 0.0;
+        if ((rc = krylov_norm(s->nk_r, n, wk, &rn, st)) != PD_OK) return rc;
+        if (it == 0) ns.res0 = rn;
+        ns.res = rn;
+        if (rn <= o.newton_rtol * ns.res0 + o.newton_atol) {
+            ns.converged = 1;
+            break;
+        }
+        if (it >= o.max_newton_iters) break;
+        KrylovStats ks = {0, 0, 0.0, 0.0};
+        rc = o.krylov == PD_KRYLOV_GMRES
+                 ? krylov_gmres(op, s->nk_r, s->nk_du, n, o.restart, o.max_linear_iters, o.linear_rtol, wk, &ks, st)
+                 : krylov_cg(op, s->nk_r, s->nk_du, n, o.max_linear_iters, o.linear_rtol, wk, &ks, st);
+        if (rc != PD_OK) return rc;
+        ns.newton_iters += 1;
+        ns.linear_iters += ks.iters;
+        ns.linear_failures += ks.converged ? 0 : 1;
+        k_nk_update<<<nbs, 256, 0, st>>>(g, s->bc_kind, s->bc_val, s->nk_du, s->u[0], s->u[1], s->u[2]);
+        PD_CUDA(cudaGetLastError());
+    }
+    // static state: v = 0 at an integer step
+    for (int c = 0; c < 3; ++c)
+        if (s->v[c]) PD_CUDA(cudaMemsetAsync(s->v[c], 0, sizeof(double) * g.nslots, st));
+    if (s->vhl) PD_CUDA(cudaMemsetAsync(s->vhl, 0, 2 * sizeof(float4) * g.nslots, st));
+    s->v_is_half = 0;
+    PD_CUDA(cudaStreamSynchronize(st));
+    if (stats) *stats = ns;
+    return PD_OK;
 }
 
 int pd_energy(pd_sim *s, double *kinetic, double *strain, void *stream)

@@ -128,6 +128,29 @@ int break_notch(const Geom &g, const Tables &t, uint32_t *mask, int axis, double
                 const double lo[3], const double hi[3], unsigned long long *d_count,
                 cudaStream_t st);
 
+// Krylov solvers (pd_krylov.cu). Vectors: n FP64 values on the device.
+struct KrylovOp {
+    int (*apply)(void *ctx, const double *x, double *y, cudaStream_t st);   // y = A x
+    void *ctx;
+};
+struct KrylovWork {
+    double *basis;      // GMRES: (restart + 1) * n; CG: 3 * n
+    double *tmp;        // n
+    double *partial;    // krylov_partial_doubles(n, restart)
+    double *dsc;        // restart + 2
+};
+struct KrylovStats {
+    int iters;
+    int converged;
+    double res0, res;   // ||b||, final ||b - A x|| (GMRES: at the last restart or the rotation estimate)
+};
+int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, int restart, int maxit,
+                 double rtol, KrylovWork &wk, KrylovStats *stats, cudaStream_t st);
+int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int maxit, double rtol,
+              KrylovWork &wk, KrylovStats *stats, cudaStream_t st);
+size_t krylov_partial_doubles(long long n, int kmax);
+int krylov_norm(const double *x, long long n, KrylovWork &wk, double *out, cudaStream_t st);
+
 // Permutations between user order (AoS n x dim) and slot order (SoA).
 int scatter_user_to_slots(const Geom &g, const Tables &t, const double *user, double *const slot[3],
                           double fill, cudaStream_t st);

@@ -24,6 +24,7 @@ PD_FP32C, PD_FP64 = 0, 1
 PD_BC_FREE, PD_BC_VELOCITY, PD_BC_DISPLACEMENT = 0, 1, 2
 PD_FORCE_UPDATE_BREAKING = 1
 PD_JVP_MASK_DIRICHLET = 1
+PD_KRYLOV_GMRES, PD_KRYLOV_CG = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpd.so is not built (%s); run __graft_entry__.build() or "
@@ -45,6 +46,17 @@ class pd_material(ctypes.Structure):
 class pd_run(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dt_factor", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("tile_log2", ctypes.c_int32)]
+
+
+class pd_newton_opts(ctypes.Structure):
+    _fields_ = [("krylov", ctypes.c_int32), ("restart", ctypes.c_int32), ("max_linear_iters", ctypes.c_int32),
+                ("max_newton_iters", ctypes.c_int32), ("linear_rtol", ctypes.c_double),
+                ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double)]
+
+
+class pd_newton_stats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int32), ("linear_iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("linear_failures", ctypes.c_int32), ("res0", ctypes.c_double), ("res", ctypes.c_double)]
 
 
 class PdError(RuntimeError):
@@ -76,6 +88,7 @@ _SIGS = {
     "pd_jvp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_vjp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_energy": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
+    "pd_solve_static": [_P, ctypes.POINTER(pd_newton_opts), ctypes.POINTER(pd_newton_stats), _P],
     "pd_sum_noalloc": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
 }
 for _name, _args in _SIGS.items():
@@ -274,6 +287,22 @@ def pd_vjp(sim: Sim, v, u_lin=None, out=None, flags: int = 0, stream=None):
     _check(_lib.pd_vjp(sim.h, _buf(u_lin, np.float64, sim.nvec, "u_lin"), _buf(v, np.float64, sim.nvec, "v"),
                        _buf(out, np.float64, sim.nvec, "out", True), int(flags), _stream(stream)))
     return out
+
+
+def newton_opts(krylov: int = PD_KRYLOV_GMRES, restart: int = 50, max_linear_iters: int = 20000,
+                max_newton_iters: int = 20, linear_rtol: float = 1e-8, newton_rtol: float = 1e-8,
+                newton_atol: float = 0.0) -> pd_newton_opts:
+    """pd_newton_opts with the library's defaults."""
+    return pd_newton_opts(krylov, restart, max_linear_iters, max_newton_iters, linear_rtol, newton_rtol,
+                          newton_atol)
+
+
+def pd_solve_static(sim: Sim, opts: pd_newton_opts | None = None, stream=None) -> dict:
+    """Newton-Krylov static equilibrium from the current state; returns the stats as a dict."""
+    st = pd_newton_stats()
+    _check(_lib.pd_solve_static(sim.h, ctypes.byref(opts) if opts is not None else None, ctypes.byref(st),
+                                _stream(stream)))
+    return {k: getattr(st, k) for k, _ in pd_newton_stats._fields_}
 
 
 def pd_energy(sim: Sim, stream=None):
