@@ -205,6 +205,64 @@ def time_build(pd, torch, wl, stream, reps=3):
     return {"ms": best * 1e3, "bonds": nb, "bonds_per_s": nb / best}
 
 
+def time_implicit(pd, torch, krylov, precision, nx=200):
+    """The 200 x 200 clamped plate (left collar u = 0, right collar u_x = 1e-4 W)
+    in 10 load steps, one pd_solve_static per step (matrix-free Newton-Krylov,
+    linear rtol 1e-8). Wall time of the whole load path and the iteration counts."""
+    L = W.plate_static(nx=nx, variant="clamped")
+    g, m, r = pd.describe(L.grid, L.mat, precision=precision)
+    sim = pd.pd_create(g, m, r)
+    pd.pd_build_neighbors(sim)
+    z = np.zeros((L.grid.npoints, 2))
+    pd.pd_set_state(sim, u=z, v=z)
+    fp64 = precision == pd.PD_FP64
+    opts = pd.newton_opts(krylov=krylov, restart=50, linear_rtol=1e-8, newton_rtol=1e-8 if fp64 else 1e-6,
+                          max_newton_iters=20 if fp64 else 8)
+    newton = lin = conv = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(1, L.load_steps + 1):
+        pd.pd_set_bc(sim, L.bc_kind, L.bc_val * s / L.load_steps)
+        st = pd.pd_solve_static(sim, opts)
+        newton += st["newton_iters"]
+        lin += st["linear_iters"]
+        conv += st["converged"]
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nb = pd.pd_bond_count(sim)
+    sim.close()
+    return {"sec": sec, "load_steps": L.load_steps, "converged_steps": conv, "newton_iters": newton,
+            "krylov_iters": lin, "ms_per_krylov_iter": 1e3 * sec / max(lin, 1),
+            "tangent_bond_applications_per_s": nb * lin / sec, "bonds": nb}
+
+
+def time_jvp(pd, torch, precision, nx=200, reps=20):
+    """One pd_jvp (user-order device tensors in and out, so the permutation
+    kernels are included) on the 200 x 200 plate at a random state; CUDA events."""
+    L = W.plate_static(nx=nx, variant="clamped")
+    g, m, r = pd.describe(L.grid, L.mat, precision=precision)
+    sim = pd.pd_create(g, m, r)
+    pd.pd_build_neighbors(sim)
+    rng = np.random.default_rng(4)
+    u = torch.tensor(rng.normal(0.0, 1e-4 * L.grid.h, (L.grid.npoints, 2)), device="cuda")
+    w = torch.tensor(rng.normal(size=(L.grid.npoints, 2)), device="cuda")
+    out = torch.empty_like(w)
+    pd.pd_set_state(sim, u=u)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        pd.pd_jvp(sim, w, out=out, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        pd.pd_jvp(sim, w, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nb = pd.pd_bond_count(sim)
+    sim.close()
+    return {"ms": ms, "bonds": nb, "bond_applications_per_s": nb / (ms * 1e-3)}
+
+
 def cpu_baseline(wl, target_s=12.0, max_steps=50):
     """The FP64 oracle (as it stands) on the host cores: a bounded number of explicit
     steps of the same workload."""
@@ -391,6 +449,13 @@ def main():
                               "alu_frac": ops2 * nb2 / (ms2 * 1e-3) / 1e12 / peak}
             line["neighbour_build"] = {"block64": time_build(pd, torch, wl, stream),
                                        "lps128": time_build(pd, torch, wl2, stream)}
+            line["jvp200"] = {"fp64": time_jvp(pd, torch, pd.PD_FP64), "fp32c": time_jvp(pd, torch, pd.PD_FP32C)}
+            line["implicit_plate200"] = {
+                "workload": "200x200 plate, h = 1/200 m, m = 3, PMB, left collar clamped, right collar "
+                            "u_x = 1e-4 W in 10 load steps; matrix-free Newton-Krylov",
+                "gmres50_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64),
+                "cg_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64),
+                "cg_fp32c": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP32C)}
             sim2.close()
 
     line["clocks"] = clk.summary()
