@@ -282,6 +282,76 @@ typedef struct {
  * kept until pd_destroy. Synchronous. */
 int pd_solve_static(pd_sim *sim, const pd_newton_opts *opts, pd_newton_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------- serving */
+
+/* A request server: independent simulations submitted at any time, run
+ * concurrently on one GPU and collected through tickets (the futures of the
+ * paper's task model, Sec. 2, applied to whole simulations). A worker thread of
+ * the library admits queued requests in submission order while their device
+ * memory (bond list, bond mask and per-point state, estimated before creation)
+ * fits the budget and fewer than max_active run; each admitted request gets its
+ * own simulation and stream and advances in quanta of quantum_steps explicit
+ * steps (graph-replayed), and a finished request frees its memory for the next
+ * in the queue between quanta (continuous batching). A request's result does
+ * not depend on what else runs: it equals the same simulation run alone with
+ * the tile size reported in pd_result. */
+
+typedef struct pd_server pd_server;
+
+typedef struct {
+    int64_t device_bytes;     /* admission budget; 0 = half the free device memory */
+    int32_t max_active;       /* simulations stepping at once, 1..256 (16) */
+    int32_t quantum_steps;    /* steps per scheduling quantum, >= 1 (64) */
+} pd_server_opts;
+
+typedef struct {
+    pd_grid grid;
+    pd_material material;
+    pd_run run;               /* run.tile_log2 = 0 lets the server choose */
+    int64_t nsteps;           /* explicit steps, >= 0 */
+    const double *u0, *v0;    /* host, npoints x dim, user order; NULL = 0; copied by pd_submit */
+    const uint8_t *bc_kind;   /* host, npoints x dim, or NULL (no collar); copied */
+    const double *bc_val;     /* host, with bc_kind; copied */
+    double *u_out, *v_out;    /* host, npoints x dim, caller-owned; written when the
+                                 request completes (NULL = not wanted); must stay
+                                 valid until the ticket is done or cancelled */
+} pd_request;
+
+#define PD_REQ_QUEUED 0
+#define PD_REQ_RUNNING 1
+#define PD_REQ_DONE 2
+#define PD_REQ_CANCELLED 3
+#define PD_REQ_FAILED 4
+
+typedef struct {
+    int32_t state;            /* PD_REQ_* */
+    int32_t error;            /* PD_OK, or the status that failed the request */
+    int32_t tile_log2;        /* tile size the request runs with (0 before admission) */
+    int32_t reserved;
+    int64_t steps_done;
+    int64_t bonds;            /* directed bonds (0 before admission) */
+    double submit_s, start_s, end_s;   /* server clock (s since pd_server_create); 0 if not yet */
+    char message[160];        /* error text of a failed request */
+} pd_result;
+
+/* Start a server on the current device (its worker thread uses that device). */
+int pd_server_create(pd_server **out, const pd_server_opts *opts);
+/* Cancel what is queued or running (running requests stop after their current
+ * quantum), join the worker, free everything. */
+int pd_server_destroy(pd_server *srv);
+/* Validate and copy a request and queue it; *ticket identifies it (> 0).
+ * PD_EINVAL for an invalid description or one whose memory estimate exceeds the
+ * budget on its own. */
+int pd_submit(pd_server *srv, const pd_request *req, uint64_t *ticket);
+/* Current state of a ticket, without blocking. PD_EINVAL for an unknown ticket. */
+int pd_poll(pd_server *srv, uint64_t ticket, pd_result *out);
+/* Block until the ticket is done, cancelled or failed, at most timeout_s
+ * seconds: PD_OK, or PD_ETIMEOUT with out holding the current state. */
+int pd_wait(pd_server *srv, uint64_t ticket, double timeout_s, pd_result *out);
+/* Cancel a queued or running request (a running one stops after its current
+ * quantum; its outputs are not written). PD_OK also if it had already ended. */
+int pd_cancel(pd_server *srv, uint64_t ticket);
+
 /* -------------------------------------------------------------------- energy */
 
 /* Kinetic energy sum_i rho |v_i|^2 V_i / 2 and strain energy sum_i V_i W_i

@@ -191,6 +191,12 @@ static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
     return PD_OK;
 }
 
+int pdk::validate_description(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
+{
+    if (!gr || !mt || !rn) { set_error("null description"); return PD_EINVAL; }
+    return validate(gr, mt, rn);
+}
+
 static int create_impl(pd_sim *s)
 {
     const pd_grid &gr = s->grid;

@@ -128,6 +128,9 @@ int break_notch(const Geom &g, const Tables &t, uint32_t *mask, int axis, double
                 const double lo[3], const double hi[3], unsigned long long *d_count,
                 cudaStream_t st);
 
+// Description checks of pd_create (pd_api.cu), for the request server.
+int validate_description(const pd_grid *gr, const pd_material *mt, const pd_run *rn);
+
 // Krylov solvers (pd_krylov.cu). Vectors: n FP64 values on the device.
 struct KrylovOp {
     int (*apply)(void *ctx, const double *x, double *y, cudaStream_t st);   // y = A x

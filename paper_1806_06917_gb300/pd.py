@@ -25,6 +25,7 @@ PD_BC_FREE, PD_BC_VELOCITY, PD_BC_DISPLACEMENT = 0, 1, 2
 PD_FORCE_UPDATE_BREAKING = 1
 PD_JVP_MASK_DIRICHLET = 1
 PD_KRYLOV_GMRES, PD_KRYLOV_CG = 0, 1
+PD_REQ_QUEUED, PD_REQ_RUNNING, PD_REQ_DONE, PD_REQ_CANCELLED, PD_REQ_FAILED = 0, 1, 2, 3, 4
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpd.so is not built (%s); run __graft_entry__.build() or "
@@ -59,6 +60,24 @@ class pd_newton_stats(ctypes.Structure):
                 ("linear_failures", ctypes.c_int32), ("res0", ctypes.c_double), ("res", ctypes.c_double)]
 
 
+class pd_server_opts(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("quantum_steps", ctypes.c_int32)]
+
+
+class pd_request(ctypes.Structure):
+    _fields_ = [("grid", pd_grid), ("material", pd_material), ("run", pd_run), ("nsteps", ctypes.c_int64),
+                ("u0", ctypes.c_void_p), ("v0", ctypes.c_void_p), ("bc_kind", ctypes.c_void_p),
+                ("bc_val", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("v_out", ctypes.c_void_p)]
+
+
+class pd_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("tile_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("steps_done", ctypes.c_int64), ("bonds", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("end_s", ctypes.c_double),
+                ("message", ctypes.c_char * 160)]
+
+
 class PdError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("libpd error %d: %s" % (code, msg))
@@ -89,6 +108,12 @@ _SIGS = {
     "pd_vjp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_energy": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
     "pd_solve_static": [_P, ctypes.POINTER(pd_newton_opts), ctypes.POINTER(pd_newton_stats), _P],
+    "pd_server_create": [ctypes.POINTER(_P), ctypes.POINTER(pd_server_opts)],
+    "pd_server_destroy": [_P],
+    "pd_submit": [_P, ctypes.POINTER(pd_request), ctypes.POINTER(ctypes.c_uint64)],
+    "pd_poll": [_P, ctypes.c_uint64, ctypes.POINTER(pd_result)],
+    "pd_wait": [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(pd_result)],
+    "pd_cancel": [_P, ctypes.c_uint64],
     "pd_sum_noalloc": [_P, ctypes.c_int64, ctypes.c_double, _P, _P],
 }
 for _name, _args in _SIGS.items():
@@ -303,6 +328,84 @@ def pd_solve_static(sim: Sim, opts: pd_newton_opts | None = None, stream=None) -
     _check(_lib.pd_solve_static(sim.h, ctypes.byref(opts) if opts is not None else None, ctypes.byref(st),
                                 _stream(stream)))
     return {k: getattr(st, k) for k, _ in pd_newton_stats._fields_}
+
+
+def _result(r: pd_result) -> dict:
+    d = {k: getattr(r, k) for k, _ in pd_result._fields_ if k not in ("reserved", "message")}
+    d["message"] = r.message.decode(errors="replace")
+    return d
+
+
+class Server:
+    """Owner of one pd_server handle. Requests keep their host arrays alive
+    until the ticket has ended (the library copies the inputs at submit and
+    writes the outputs at completion)."""
+
+    def __init__(self, device_bytes: int = 0, max_active: int = 16, quantum_steps: int = 64):
+        h = _P()
+        _check(_lib.pd_server_create(ctypes.byref(h), ctypes.byref(pd_server_opts(device_bytes, max_active,
+                                                                                  quantum_steps))))
+        self.h = h
+        self._keep = {}
+
+    def close(self) -> None:
+        if self.h:
+            _check(_lib.pd_server_destroy(self.h))
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_server_create(device_bytes: int = 0, max_active: int = 16, quantum_steps: int = 64) -> Server:
+    return Server(device_bytes, max_active, quantum_steps)
+
+
+def pd_server_destroy(srv: Server) -> None:
+    srv.close()
+
+
+def pd_submit(srv: Server, grid: pd_grid, mat: pd_material, run: pd_run, nsteps: int, u0=None, v0=None,
+              bc_kind=None, bc_val=None, u_out=None, v_out=None) -> int:
+    """Queue a request; host numpy arrays of npoints x dim (u_out / v_out are
+    written when it completes). Returns the ticket."""
+    npts = grid.n[0] * grid.n[1] * (grid.n[2] if grid.dim == 3 else 1)
+    nvec = npts * grid.dim
+    arrs = {"u0": (u0, np.float64, False), "v0": (v0, np.float64, False), "bc_kind": (bc_kind, np.uint8, False),
+            "bc_val": (bc_val, np.float64, False), "u_out": (u_out, np.float64, True),
+            "v_out": (v_out, np.float64, True)}
+    req = pd_request()
+    req.grid, req.material, req.run, req.nsteps = grid, mat, run, int(nsteps)
+    for name, (a, dt, wr) in arrs.items():
+        if a is not None and hasattr(a, "data_ptr"):
+            raise ValueError("%s: server requests take host numpy arrays" % name)
+        p = _buf(a, dt, nvec, name, wr)
+        setattr(req, name, p.value if p is not None else None)
+    t = ctypes.c_uint64()
+    _check(_lib.pd_submit(srv.h, ctypes.byref(req), ctypes.byref(t)))
+    srv._keep[t.value] = (u_out, v_out)
+    return t.value
+
+
+def pd_poll(srv: Server, ticket: int) -> dict:
+    r = pd_result()
+    _check(_lib.pd_poll(srv.h, int(ticket), ctypes.byref(r)))
+    return _result(r)
+
+
+def pd_wait(srv: Server, ticket: int, timeout_s: float = 60.0) -> dict:
+    """Block until the ticket ends (PdError with code PD_ETIMEOUT after timeout_s)."""
+    r = pd_result()
+    _check(_lib.pd_wait(srv.h, int(ticket), float(timeout_s), ctypes.byref(r)))
+    return _result(r)
+
+
+def pd_cancel(srv: Server, ticket: int) -> None:
+    _check(_lib.pd_cancel(srv.h, int(ticket)))
 
 
 def pd_energy(sim: Sim, stream=None):

@@ -226,6 +226,52 @@ def plate_static(nx: int = 200, ny: Optional[int] = None, load_steps: int = 10, 
     return StaticLoad("plate_static_%dx%d_%s" % (nx, ny, variant), g, mat, kind, val, load_steps, strain, pin)
 
 
+@dataclasses.dataclass
+class Request:
+    """One independent simulation of a serving mix."""
+    grid: Grid
+    mat: Material
+    steps: int
+    arrival: float               # seconds after the first arrival of the mix
+    u0: np.ndarray               # (n, dim) FP64
+    seed: int
+
+
+def serving_mix(count: int = 512, seed: int = 5, rate: float = 1.0, side_median: float = 40.0,
+                side_sigma: float = 0.5, side_lo: int = 20, side_hi: int = 96, steps_lo: int = 100,
+                steps_hi: int = 2000, m_choices: Tuple[int, ...] = (2, 3, 4)) -> list:
+    """Independent simulations for the request server, arriving as a Poisson
+    process of the given rate (requests/s).
+
+    Per request: model PMB or LPS with probability 1/2; dimension 2 or 3 with
+    probability 1/2, LPS always 3D (its coefficients are 3D); side per axis
+    round(exp(N(ln side_median, side_sigma^2))) clipped to [side_lo, side_hi];
+    h = 1/side_x m; m uniform in m_choices; steps uniform in [steps_lo, steps_hi];
+    u0 ~ N(0, (1e-4 h)^2) per component from the request's own seed, v0 = 0, no
+    collar, no breaking. E = 72 GPa, rho = 2440 kg/m^3; LPS K = 40 GPa, mu = 30 GPa.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    for k in range(count):
+        lps = rng.random() < 0.5
+        dim = 3 if (lps or rng.random() < 0.5) else 2
+        sides = [int(np.clip(round(float(np.exp(rng.normal(np.log(side_median), side_sigma)))), side_lo, side_hi))
+                 for _ in range(dim)]
+        n = (sides[0], sides[1], sides[2] if dim == 3 else 1)
+        m = int(rng.choice(m_choices))
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        g = Grid(dim=dim, n=n, h=1.0 / n[0], m=m)
+        mat = Material(model=LPS, E=72e9, rho=2440.0, K=40e9, mu=30e9) if lps else \
+            Material(model=PMB, E=72e9, rho=2440.0)
+        rs = int(rng.integers(0, 2 ** 31 - 1))
+        u0 = np.random.default_rng(rs).normal(0.0, 1e-4 * g.h, size=(g.npoints, dim))
+        if k > 0:
+            t += float(rng.exponential(1.0 / rate))
+        out.append(Request(grid=g, mat=mat, steps=steps, arrival=t, u0=u0, seed=rs))
+    return out
+
+
 def gaussian_ic(grid: Grid, a: Tuple[float, ...], xc: Tuple[float, ...], beta: float) -> np.ndarray:
     """Gaussian displacement u0 = a * exp(-|X - xc|^2 / beta), the initial-condition
     shape of the paper's explicit convergence study (Sec. 5.2.2)."""
@@ -249,4 +295,5 @@ WORKLOADS: Dict[str, object] = {
     "block3d_64_pmb_break": block3d_pulse,
     "block3d_128_lps": block3d_lps,
     "plate_static_200_clamped": plate_static,
+    "serving_mix_512": serving_mix,
 }
