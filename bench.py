@@ -263,6 +263,60 @@ def time_jvp(pd, torch, precision, nx=200, reps=20):
     return {"ms": ms, "bonds": nb, "bond_applications_per_s": nb / (ms * 1e-3)}
 
 
+def _submit_request(pd, srv, r):
+    g, m, run = pd.describe(r.grid, r.mat, precision=pd.PD_FP32C)
+    return pd.pd_submit(srv, g, m, run, r.steps, u0=r.u0)
+
+
+def run_serving(args, pd, torch):
+    """The request mix through the server: one-at-a-time capacity on a sample
+    (max_active = 1), then the whole mix arriving as a Poisson process at
+    args.load x that capacity, max_active concurrent simulations."""
+    mix = W.serving_mix(count=args.requests)
+    k = min(args.serial_sample, len(mix))
+    srv = pd.Server(max_active=1, quantum_steps=64)
+    _submit_request(pd, srv, mix[0])                       # warm-up (module load, first graph)
+    t0 = time.perf_counter()
+    sres = [pd.pd_wait(srv, _submit_request(pd, srv, r), timeout_s=600.0) for r in mix[:k]]
+    serial_s = time.perf_counter() - t0
+    srv.close()
+    serial_work = sum(x["bonds"] * r.steps for x, r in zip(sres, mix[:k]))
+    capacity = k / serial_s
+    rate = args.load * capacity
+    srv = pd.Server(max_active=args.max_active, quantum_steps=64)
+    with Clocks(0) as clk:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in mix:
+            delay = t0 + r.arrival / rate - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(_submit_request(pd, srv, r))
+        res = [pd.pd_wait(srv, t, timeout_s=3600.0) for t in tickets]
+    srv.close()
+    ok = all(x["state"] == pd.PD_REQ_DONE for x in res)
+    work = sum(x["bonds"] * r.steps for x, r in zip(res, mix))
+    makespan = max(x["end_s"] for x in res) - min(x["submit_s"] for x in res)
+    lat = np.array([x["end_s"] - x["submit_s"] for x in res])
+    line = {"metric": "aggregate bond updates/s (served request mix)", "value": work / makespan,
+            "unit": "bond-updates/s", "n_gpus": 1, "steps": len(mix), "warmup": 1,
+            "ms_per_step": 1e3 * makespan / len(mix), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)",
+            "data": "synthetic",
+            "config": {"workload": "serving_mix: %d requests (2D/3D, PMB/LPS, lognormal sides 20..96, "
+                                   "m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
+                                   "one-at-a-time capacity" % (len(mix), args.load),
+                       "max_active": args.max_active, "quantum_steps": 64, "l2": "not flushed (independent "
+                       "simulations stream through it)"},
+            "all_done": ok, "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
+            "offered_rate_per_s": rate, "bond_updates": work,
+            "serial": {"requests": k, "value": serial_work / serial_s, "unit": "bond-updates/s",
+                       "capacity_requests_per_s": capacity},
+            "gpu_launches": None, "roofline": None, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(wl, target_s=12.0, max_steps=50):
     """The FP64 oracle (as it stands) on the host cores: a bounded number of explicit
     steps of the same workload."""
@@ -322,7 +376,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="block64", choices=["block64", "lps128", "plate50"])
+    ap.add_argument("--workload", default="block64", choices=["block64", "lps128", "plate50", "serve"])
+    ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
+    ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
+    ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")
+    ap.add_argument("--serial-sample", type=int, default=24, help="serve: requests timed one at a time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path and LPS side measurements")
     args = ap.parse_args()
@@ -340,6 +398,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_1806_06917_gb300 import pd
+
+    if args.workload == "serve":
+        if rank == 0:
+            run_serving(args, pd, torch)
+        return
 
     wl, desc = workload(args.workload)
     stream = torch.cuda.current_stream()
