@@ -246,11 +246,19 @@ int pd_vjp(pd_sim *sim, const double *u_lin, const double *v, double *out,
 #define PD_KRYLOV_GMRES 0    /* restarted GMRES(restart), CGS2 orthogonalisation */
 #define PD_KRYLOV_CG 1       /* conjugate gradients (the operator is SPD) */
 
+#define PD_TANGENT_CACHED 0  /* D_ij of every bond evaluated once per Newton iteration
+                                and kept (3 or 6 values per bond in the simulation's
+                                precision plus the neighbour index); each product
+                                streams it */
+#define PD_TANGENT_JVP 1     /* the JVP kernel of pd_jvp for every product (no cache) */
+
 typedef struct {
     int32_t krylov;           /* PD_KRYLOV_GMRES or PD_KRYLOV_CG */
     int32_t restart;          /* GMRES restart length, 1..500 (50) */
     int32_t max_linear_iters; /* per linear solve, >= 1 */
     int32_t max_newton_iters; /* >= 1 */
+    int32_t tangent;          /* PD_TANGENT_CACHED or PD_TANGENT_JVP */
+    int32_t reserved;         /* 0 */
     double linear_rtol;       /* each solve: ||r - A du|| <= linear_rtol ||r|| */
     double newton_rtol;       /* stop when ||r|| <= newton_rtol ||r_0|| + newton_atol */
     double newton_atol;       /* N/m^3 */
@@ -275,8 +283,8 @@ typedef struct {
  * for PD_FP32C simulations (inexact Newton; the residual is FP64 in both). Bonds
  * do not break during the solve. On return u is the last iterate and v = 0.
  * PMB only (PD_EINVAL for LPS). opts == NULL takes the defaults in brackets and
- * GMRES, 20000 linear iterations, 20 Newton iterations, linear_rtol 1e-8,
- * newton_rtol 1e-8, newton_atol 0. Returns PD_OK whether or not the test was met
+ * GMRES, 20000 linear iterations, 20 Newton iterations, the cached tangent,
+ * linear_rtol 1e-8, newton_rtol 1e-8, newton_atol 0. Returns PD_OK whether or not the test was met
  * (see stats->converged; stats may be NULL); PD_EINVAL if CG meets a
  * non-positive curvature. Work buffers are allocated on the first call and
  * kept until pd_destroy. Synchronous. */

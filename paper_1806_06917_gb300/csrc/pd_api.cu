@@ -42,6 +42,12 @@ size_t pmb_generic_smem(const Geom &g, int precision);
 size_t pmb_fast_smem(const Geom &g);
 size_t lps_generic_smem(const Geom &g, int precision, bool dil);
 size_t jvp_smem(const Geom &g, int precision);
+// Per-bond tangent cache (pd_tangent.cu): prepare at a linearisation point,
+// then y = A w (A = -K on free DOFs, identity on prescribed ones) from the cache.
+size_t tangent_cache_bytes(const Geom &g, int precision);
+int launch_tangent_prepare(const TileArgs &a, int precision, void *cache, cudaStream_t st);
+int launch_tangent_apply(const Geom &g, int precision, const void *cache, const int *user_of_slot,
+                         const uint8_t *kind, const double *w, double *y, cudaStream_t st);
 size_t energy_smem(const Geom &g, int precision);
 int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st);
 int dirichlet_mask(const Geom &g, const uint8_t *kind, double *const v[3], const double *const w[3], int copy,
@@ -114,6 +120,8 @@ struct pd_sim {
     double *nk_basis = nullptr, *nk_tmp = nullptr, *nk_partial = nullptr, *nk_dsc = nullptr;
     double *nk_r = nullptr, *nk_du = nullptr;
     size_t nk_basis_n = 0, nk_partial_n = 0, nk_dsc_n = 0;
+    void *nk_tan = nullptr;         // per-bond tangent cache
+    size_t nk_tan_n = 0;
     // graphs: [start parity]
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
@@ -657,6 +665,13 @@ static int nk_apply(void *ctx, const double *x, double *y, cudaStream_t st)
     return PD_OK;
 }
 
+// The same operator from the per-bond tangent cache of the current iterate.
+static int nk_apply_cached(void *ctx, const double *x, double *y, cudaStream_t st)
+{
+    pd_sim *s = static_cast<pd_sim *>(ctx);
+    return launch_tangent_apply(s->g, s->precision, s->nk_tan, s->user_of_slot, s->bc_kind, x, y, st);
+}
+
 static int nk_reserve(double **p, size_t *have, size_t want)
 {
     if (*p && *have >= want) return PD_OK;
@@ -715,6 +730,7 @@ int pd_destroy(pd_sim *s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (void *p : s->allocs) cudaFree(p);
     for (double *p : {s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc, s->nk_r, s->nk_du}) cudaFree(p);
+    cudaFree(s->nk_tan);
     cudaFree(s->csr.row_ptr);
     cudaFree(s->csr.col);
     if (s->stream) cudaStreamDestroy(s->stream);
@@ -1070,11 +1086,13 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
 {
     CHECK_BUILT(s);
     if (s->mat.model != PD_MODEL_PMB) { set_error("the static solve needs the PMB tangent"); return PD_EINVAL; }
-    pd_newton_opts o = {PD_KRYLOV_GMRES, 50, 20000, 20, 1e-8, 1e-8, 0.0};
+    pd_newton_opts o = {PD_KRYLOV_GMRES, 50, 20000, 20, PD_TANGENT_CACHED, 0, 1e-8, 1e-8, 0.0};
     if (opts) o = *opts;
     if (o.krylov != PD_KRYLOV_GMRES && o.krylov != PD_KRYLOV_CG) { set_error("unknown Krylov method"); return PD_EINVAL; }
     if (o.restart < 1 || o.restart > 500) { set_error("restart must be in [1, 500]"); return PD_EINVAL; }
     if (o.max_linear_iters < 1 || o.max_newton_iters < 1) { set_error("iteration limits must be >= 1"); return PD_EINVAL; }
+    if (o.tangent != PD_TANGENT_CACHED && o.tangent != PD_TANGENT_JVP) { set_error("unknown tangent mode"); return PD_EINVAL; }
+    const bool cached = o.tangent == PD_TANGENT_CACHED;
     if (!(o.linear_rtol > 0.0) || !(o.newton_rtol >= 0.0) || !(o.newton_atol >= 0.0)) {
         set_error("tolerances must be linear_rtol > 0, newton_rtol >= 0, newton_atol >= 0");
         return PD_EINVAL;
@@ -1093,8 +1111,20 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
         if ((rc = nk_reserve(&s->nk_r, &hr, (size_t)n)) != PD_OK) return rc;
         if ((rc = nk_reserve(&s->nk_du, &hd, (size_t)n)) != PD_OK) return rc;
     }
+    const size_t tan_bytes = cached ? tangent_cache_bytes(g, s->precision) : 0;
+    if (s->nk_tan_n < tan_bytes) {
+        cudaFree(s->nk_tan);
+        s->nk_tan = nullptr;
+        s->nk_tan_n = 0;
+        if (cudaMalloc(&s->nk_tan, tan_bytes) != cudaSuccess) {
+            s->nk_tan = nullptr;
+            set_error("cudaMalloc of %zu bytes for the tangent cache failed", tan_bytes);
+            return PD_ENOMEM;
+        }
+        s->nk_tan_n = tan_bytes;
+    }
     KrylovWork wk{s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc};
-    KrylovOp op{nk_apply, s};
+    KrylovOp op{cached ? nk_apply_cached : nk_apply, s};
     const unsigned nbs = (unsigned)((g.nslots + 255) / 256);
 
     // the iterate lives in the FP64 slot arrays u; the prescribed values first
@@ -1117,6 +1147,11 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
             break;
         }
         if (it >= o.max_newton_iters) break;
+        // the tangent at this iterate, once for the whole linear solve
+        if (cached) {
+            TileArgs ta = make_args(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur]);
+            if ((rc = launch_tangent_prepare(ta, s->precision, s->nk_tan, st)) != PD_OK) return rc;
+        }
         KrylovStats ks = {0, 0, 0.0, 0.0};
         rc = o.krylov == PD_KRYLOV_GMRES
                  ? krylov_gmres(op, s->nk_r, s->nk_du, n, o.restart, o.max_linear_iters, o.linear_rtol, wk, &ks, st)

@@ -1,0 +1,167 @@
+// pd_tangent.cu -- the PMB tangent of Eq. (6) kept per bond for repeated
+// products inside one Newton iteration.
+//
+// With n = y/|y| and s the stretch, a bond contributes D_ij (w_j - w_i) to
+// (K w)_i with the symmetric d x d matrix
+//   D_ij = (c V / h) V_ij [ (1/|d| - s/r) n n^T + (s/r) I ]      (lattice units, r = |y|)
+// (the same algebra as the JVP kernel in pd_jvp.cu). tangent_prepare evaluates
+// D for every intact bond of a linearisation point u once (3 entries in 2D, 6 in
+// 3D, stored [k][entry][slot] so that a warp's accesses are coalesced) together
+// with the slot of the neighbour; a broken or missing bond stores D = 0 and its
+// own slot. tangent_apply then costs one coalesced read of D and one gather of
+// w_j per bond and a few FMAs: on GB300, whose FP64 rate is 1/64 of FP32, this
+// moves the FP64 tangent from the arithmetic pipe (rsqrt, divide, ~35 FP64 ops
+// per bond per product) to memory that stays in L2 across a Krylov solve.
+#include <type_traits>
+
+#include "pd_tile.cuh"
+
+namespace pdk {
+
+size_t jvp_smem(const Geom &g, int precision);
+
+template <class R>
+__global__ void __launch_bounds__(256) tangent_prepare(const TileArgs a, R *coef, int *nbr)
+{
+    using R4 = typename std::conditional<sizeof(R) == 4, float4, double4_32a>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geom &g = a.g;
+    const int m = g.m;
+    const int HX = g.bx + 2 * m, HY = g.by + 2 * m, HZ = g.dim == 3 ? g.bz + 2 * m : 1;
+    const int nbox = HX * HY * HZ;
+    R4 *box = reinterpret_cast<R4 *>(smem_raw);
+    const int tile = blockIdx.x;
+    const int4 org = __ldg(&a.tile_org[tile]);
+    if constexpr (sizeof(R) == 4)
+        stage_box32(reinterpret_cast<float4 *>(box), HX, HY, nbox, m, a, org, tile_ref32(a, tile), (float)a.inv_h);
+    else
+        stage_box64(reinterpret_cast<double4_32a *>(box), HX, HY, nbox, m, a, org, tile_ref64(a, tile), a.inv_h);
+    __syncthreads();
+
+    const size_t ns = g.nslots;
+    const int nc = g.dim == 3 ? 6 : 3;
+    const R sc = (R)(a.cV * a.inv_h);
+    for (int t = threadIdx.x; t < g.T; t += blockDim.x) {
+        const int slot = tile * g.T + t;
+        int l[3];
+        morton_decode(g.dim, (uint64_t)t, l);
+        const int x = org.x + l[0], y = org.y + l[1], z = org.z + l[2];
+        const bool act = x < g.nx && y < g.ny && z < g.nz;
+        const int bi = (l[0] + m) + HX * ((l[1] + m) + HY * (g.dim == 3 ? l[2] + m : 0));
+        const R4 ui = box[act ? bi : 0];
+        uint32_t word = 0;
+        for (int k = 0; k < g.S; ++k) {
+            if ((k & 31) == 0) word = act ? a.mask[(size_t)(k >> 5) * ns + slot] : 0u;
+            R D[6] = {0, 0, 0, 0, 0, 0};
+            int js = slot;
+            if ((word >> (k & 31)) & 1u) {
+                const int4 d = __ldg(&a.stencil[k]);
+                const R r0 = (R)__ldg(&a.stencil_r0[k]);
+                const R4 uj = box[bi + d.x + HX * (d.y + HY * d.z)];
+                const R ex = uj.x - ui.x, ey = uj.y - ui.y, ez = uj.z - ui.z;
+                const R yx = ex + (R)d.x, yy = ey + (R)d.y, yz = ez + (R)d.z;
+                const R q = yx * yx + yy * yy + yz * yz;
+                const R num = ex * ex + ey * ey + ez * ez + (R)2 * ((R)d.x * ex + (R)d.y * ey + (R)d.z * ez);
+                const R rs = prsqrt1(q);
+                const R s = pdiv1(num, r0 * (q * rs + r0));
+                const R vij = a.vol_corr ? (R)vol_factor_lattice(m, (double)r0) : (R)1;
+                const R al = sc * vij * ((R)1 / r0 - s * rs) * rs * rs;    // times y y^T
+                const R be = sc * vij * s * rs;                             // times I
+                D[0] = al * yx * yx + be;
+                D[1] = al * yx * yy;
+                D[2] = al * yy * yy + be;
+                if (g.dim == 3) {
+                    D[3] = al * yx * yz;
+                    D[4] = al * yy * yz;
+                    D[5] = al * yz * yz + be;
+                }
+                js = slot_at(g, a.tile_lut, x + d.x, y + d.y, z + d.z);
+            }
+            for (int c = 0; c < nc; ++c) coef[((size_t)k * nc + c) * ns + slot] = D[c];
+            nbr[(size_t)k * ns + slot] = js;
+        }
+    }
+}
+
+// y = A w with A = -K on free DOFs and the identity on prescribed ones (the
+// Newton operator of pd_solve_static); w, y component-major over slots.
+template <class R>
+__global__ void __launch_bounds__(256) tangent_apply(Geom g, const R *coef, const int *nbr, const int *user_of_slot,
+                                                     const uint8_t *kind, const double *w, double *y)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const size_t ns = g.nslots;
+    const int d = g.dim;
+    if (user_of_slot[s] < 0) {
+        for (int c = 0; c < d; ++c) y[c * ns + s] = 0.0;
+        return;
+    }
+    const int nc = d == 3 ? 6 : 3;
+    const double wi0 = w[s], wi1 = w[ns + s], wi2 = d == 3 ? w[2 * ns + s] : 0.0;
+    R a0 = 0, a1 = 0, a2 = 0;
+    for (int k = 0; k < g.S; ++k) {
+        const int j = __ldg(&nbr[(size_t)k * ns + s]);
+        const R *Dk = coef + (size_t)k * nc * ns + s;
+        const R d0 = (R)(w[j] - wi0), d1 = (R)(w[ns + j] - wi1);
+        if (d == 3) {
+            const R d2 = (R)(w[2 * ns + j] - wi2);
+            const R xx = __ldg(&Dk[0]), xy = __ldg(&Dk[ns]), yy = __ldg(&Dk[2 * ns]);
+            const R xz = __ldg(&Dk[3 * ns]), yz = __ldg(&Dk[4 * ns]), zz = __ldg(&Dk[5 * ns]);
+            a0 += xx * d0 + xy * d1 + xz * d2;
+            a1 += xy * d0 + yy * d1 + yz * d2;
+            a2 += xz * d0 + yz * d1 + zz * d2;
+        } else {
+            const R xx = __ldg(&Dk[0]), xy = __ldg(&Dk[ns]), yy = __ldg(&Dk[2 * ns]);
+            a0 += xx * d0 + xy * d1;
+            a1 += xy * d0 + yy * d1;
+        }
+    }
+    const R acc[3] = {a0, a1, a2};
+    for (int c = 0; c < d; ++c) {
+        const size_t e = (size_t)c * ns + s;
+        y[e] = kind[e] == PD_BC_DISPLACEMENT ? w[e] : -(double)acc[c];
+    }
+}
+
+size_t tangent_cache_bytes(const Geom &g, int precision)
+{
+    const size_t nc = g.dim == 3 ? 6 : 3;
+    const size_t r = precision == PD_FP64 ? sizeof(double) : sizeof(float);
+    return (size_t)g.S * g.nslots * (nc * r + sizeof(int));
+}
+
+int launch_tangent_prepare(const TileArgs &a, int precision, void *cache, cudaStream_t st)
+{
+    const Geom &g = a.g;
+    const size_t nc = g.dim == 3 ? 6 : 3;
+    const size_t r = precision == PD_FP64 ? sizeof(double) : sizeof(float);
+    int *nbr = reinterpret_cast<int *>(static_cast<char *>(cache) + (size_t)g.S * g.nslots * nc * r);
+    const size_t smem = jvp_smem(g, precision) / 2;      // the u box alone
+    if (precision == PD_FP64) {
+        PD_CUDA(cudaFuncSetAttribute(tangent_prepare<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tangent_prepare<double><<<g.ntiles, 256, smem, st>>>(a, static_cast<double *>(cache), nbr);
+    } else {
+        PD_CUDA(cudaFuncSetAttribute(tangent_prepare<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tangent_prepare<float><<<g.ntiles, 256, smem, st>>>(a, static_cast<float *>(cache), nbr);
+    }
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int launch_tangent_apply(const Geom &g, int precision, const void *cache, const int *user_of_slot,
+                         const uint8_t *kind, const double *w, double *y, cudaStream_t st)
+{
+    const size_t nc = g.dim == 3 ? 6 : 3;
+    const size_t r = precision == PD_FP64 ? sizeof(double) : sizeof(float);
+    const int *nbr = reinterpret_cast<const int *>(static_cast<const char *>(cache) + (size_t)g.S * g.nslots * nc * r);
+    const unsigned nb = (unsigned)((g.nslots + 255) / 256);
+    if (precision == PD_FP64)
+        tangent_apply<double><<<nb, 256, 0, st>>>(g, static_cast<const double *>(cache), nbr, user_of_slot, kind, w, y);
+    else
+        tangent_apply<float><<<nb, 256, 0, st>>>(g, static_cast<const float *>(cache), nbr, user_of_slot, kind, w, y);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+}  // namespace pdk

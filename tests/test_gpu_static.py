@@ -39,14 +39,16 @@ def _static_sim(pd, L, precision, scale=1.0):
 
 @pytest.mark.parametrize("variant,nx,ny", [("roller", 40, 20), ("clamped", 37, 22)])
 @pytest.mark.parametrize("krylov", ["gmres", "cg"])
-def test_fp64_static_solve_matches_oracle_newton(pd, variant, nx, ny, krylov):
+@pytest.mark.parametrize("tangent", ["cached", "jvp"])
+def test_fp64_static_solve_matches_oracle_newton(pd, variant, nx, ny, krylov, tangent):
     L = W.plate_static(nx=nx, ny=ny, strain=1e-4, variant=variant)
     g = L.grid
     u_o, _, ok = I.solve_static(g, L.mat, O.neighbors(g), np.zeros((g.npoints, 2)), L.bc_kind, L.bc_val)
     assert ok
     sim = _static_sim(pd, L, pd.PD_FP64)
     kr = pd.PD_KRYLOV_GMRES if krylov == "gmres" else pd.PD_KRYLOV_CG
-    st = pd.pd_solve_static(sim, pd.newton_opts(krylov=kr, linear_rtol=1e-12, newton_rtol=1e-12))
+    tg = pd.PD_TANGENT_CACHED if tangent == "cached" else pd.PD_TANGENT_JVP
+    st = pd.pd_solve_static(sim, pd.newton_opts(krylov=kr, linear_rtol=1e-12, newton_rtol=1e-12, tangent=tg))
     assert st["converged"] == 1 and st["linear_failures"] == 0
     u, v = pd.pd_get_state(sim)
     assert rel_l2(u, u_o) <= 1e-9
@@ -54,13 +56,15 @@ def test_fp64_static_solve_matches_oracle_newton(pd, variant, nx, ny, krylov):
     sim.close()
 
 
-def test_fp32c_static_solve_is_an_inexact_newton_to_the_same_root(pd):
+@pytest.mark.parametrize("tangent", ["cached", "jvp"])
+def test_fp32c_static_solve_is_an_inexact_newton_to_the_same_root(pd, tangent):
     L = W.plate_static(nx=40, ny=20, strain=1e-4, variant="roller")
     g = L.grid
     u_o, _, _ = I.solve_static(g, L.mat, O.neighbors(g), np.zeros((g.npoints, 2)), L.bc_kind, L.bc_val)
     sim = _static_sim(pd, L, pd.PD_FP32C)
+    tg = pd.PD_TANGENT_CACHED if tangent == "cached" else pd.PD_TANGENT_JVP
     st = pd.pd_solve_static(sim, pd.newton_opts(krylov=pd.PD_KRYLOV_CG, linear_rtol=1e-6, newton_rtol=1e-6,
-                                                max_newton_iters=12))
+                                                max_newton_iters=12, tangent=tg))
     assert st["converged"] == 1
     u, _ = pd.pd_get_state(sim)
     assert rel_l2(u, u_o) <= 1e-5
@@ -139,7 +143,7 @@ def test_static_solve_argument_errors(pd):
     L = W.plate_static(nx=20, ny=10, variant="clamped")
     sim = _static_sim(pd, L, pd.PD_FP64)
     for bad in (pd.newton_opts(krylov=7), pd.newton_opts(restart=0), pd.newton_opts(linear_rtol=0.0),
-                pd.newton_opts(max_newton_iters=0)):
+                pd.newton_opts(max_newton_iters=0), pd.newton_opts(tangent=5)):
         with pytest.raises(pd.PdError) as e:
             pd.pd_solve_static(sim, bad)
         assert e.value.code == pd.PD_EINVAL
