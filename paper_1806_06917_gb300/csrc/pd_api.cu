@@ -129,13 +129,14 @@ struct pd_sim {
 static int pd_alloc(pd_sim *s, void **p, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = lib_malloc(p, bytes, s->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
-        return cuda_fail(e, "cudaMalloc");
+        return cuda_fail(e, "device allocation");
     }
     s->allocs.push_back(*p);
-    e = cudaMemset(*p, 0, bytes);
+    e = cudaMemsetAsync(*p, 0, bytes, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);    // usable on every stream from here
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
     return PD_OK;
 }
@@ -672,16 +673,17 @@ static int nk_apply_cached(void *ctx, const double *x, double *y, cudaStream_t s
     return launch_tangent_apply(s->g, s->precision, s->nk_tan, s->user_of_slot, s->bc_kind, x, y, st);
 }
 
-static int nk_reserve(double **p, size_t *have, size_t want)
+static int nk_reserve(double **p, size_t *have, size_t want, cudaStream_t st)
 {
     if (*p && *have >= want) return PD_OK;
-    cudaFree(*p);
+    lib_free(*p, st);
     *p = nullptr;
     *have = 0;
-    cudaError_t e = cudaMalloc(p, sizeof(double) * (want ? want : 1));
+    cudaError_t e = lib_malloc(reinterpret_cast<void **>(p), sizeof(double) * (want ? want : 1), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         *p = nullptr;
-        set_error("cudaMalloc of %zu doubles for the Newton-Krylov work failed", want);
+        set_error("device allocation of %zu doubles for the Newton-Krylov work failed", want);
         return PD_ENOMEM;
     }
     *have = want;
@@ -728,11 +730,13 @@ int pd_destroy(pd_sim *s)
     if (!s) return PD_OK;
     drop_graphs(s);
     if (s->stream) cudaStreamSynchronize(s->stream);
-    for (void *p : s->allocs) cudaFree(p);
-    for (double *p : {s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc, s->nk_r, s->nk_du}) cudaFree(p);
-    cudaFree(s->nk_tan);
-    cudaFree(s->csr.row_ptr);
-    cudaFree(s->csr.col);
+    cudaStream_t fs = s->stream;     // stream-ordered release after the simulation's own work
+    for (void *p : s->allocs) lib_free(p, fs);
+    for (double *p : {s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc, s->nk_r, s->nk_du}) lib_free(p, fs);
+    lib_free(s->nk_tan, fs);
+    lib_free(s->csr.row_ptr, fs);
+    lib_free(s->csr.col, fs);
+    if (fs) cudaStreamSynchronize(fs);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
@@ -744,8 +748,9 @@ int pd_build_neighbors(pd_sim *s, void *stream)
     CHECK_SIM(s);
     cudaStream_t st = pick(s, stream);
     drop_graphs(s);
-    cudaFree(s->csr.row_ptr);
-    cudaFree(s->csr.col);
+    cudaStreamSynchronize(st);
+    lib_free(s->csr.row_ptr, st);
+    lib_free(s->csr.col, st);
     s->csr = BuildOut{nullptr, nullptr, 0};
     s->built = false;
     Tables t = {};
@@ -817,7 +822,7 @@ int pd_get_broken(pd_sim *s, uint8_t *broken, void *stream)
     if (!broken) { set_error("null output"); return PD_EINVAL; }
     cudaStream_t st = pick(s, stream);
     uint8_t *tmp = nullptr;
-    PD_CUDA(cudaMalloc(&tmp, s->csr.nbonds > 0 ? s->csr.nbonds : 1));
+    PD_CUDA(lib_malloc(reinterpret_cast<void **>(&tmp), s->csr.nbonds > 0 ? s->csr.nbonds : 1, st));
     Tables t = {};
     t.tile_org = s->tile_org;
     t.slot_of_rank = s->slot_of_rank;
@@ -828,7 +833,7 @@ int pd_get_broken(pd_sim *s, uint8_t *broken, void *stream)
         if (e != cudaSuccess) rc = cuda_fail(e, "broken copy");
     }
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(tmp);
+    lib_free(tmp, st);
     if (rc == PD_OK && e != cudaSuccess) rc = cuda_fail(e, "pd_get_broken");
     return rc;
 }
@@ -1103,22 +1108,22 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
     const int kdim = o.krylov == PD_KRYLOV_GMRES ? o.restart : 2;
     size_t hr = 0, hd = 0;
     int rc = PD_OK;
-    if ((rc = nk_reserve(&s->nk_basis, &s->nk_basis_n, (size_t)(kdim + 1) * n)) != PD_OK) return rc;
-    if ((rc = nk_reserve(&s->nk_partial, &s->nk_partial_n, krylov_partial_doubles(n, kdim + 1))) != PD_OK) return rc;
-    if ((rc = nk_reserve(&s->nk_dsc, &s->nk_dsc_n, (size_t)kdim + 2)) != PD_OK) return rc;
+    if ((rc = nk_reserve(&s->nk_basis, &s->nk_basis_n, (size_t)(kdim + 1) * n, st)) != PD_OK) return rc;
+    if ((rc = nk_reserve(&s->nk_partial, &s->nk_partial_n, krylov_partial_doubles(n, kdim + 1), st)) != PD_OK) return rc;
+    if ((rc = nk_reserve(&s->nk_dsc, &s->nk_dsc_n, (size_t)kdim + 2, st)) != PD_OK) return rc;
     if (!s->nk_tmp) {
-        if ((rc = nk_reserve(&s->nk_tmp, &hr, (size_t)n)) != PD_OK) return rc;
-        if ((rc = nk_reserve(&s->nk_r, &hr, (size_t)n)) != PD_OK) return rc;
-        if ((rc = nk_reserve(&s->nk_du, &hd, (size_t)n)) != PD_OK) return rc;
+        if ((rc = nk_reserve(&s->nk_tmp, &hr, (size_t)n, st)) != PD_OK) return rc;
+        if ((rc = nk_reserve(&s->nk_r, &hr, (size_t)n, st)) != PD_OK) return rc;
+        if ((rc = nk_reserve(&s->nk_du, &hd, (size_t)n, st)) != PD_OK) return rc;
     }
     const size_t tan_bytes = cached ? tangent_cache_bytes(g, s->precision) : 0;
     if (s->nk_tan_n < tan_bytes) {
-        cudaFree(s->nk_tan);
+        lib_free(s->nk_tan, st);
         s->nk_tan = nullptr;
         s->nk_tan_n = 0;
-        if (cudaMalloc(&s->nk_tan, tan_bytes) != cudaSuccess) {
+        if (lib_malloc(&s->nk_tan, tan_bytes, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
             s->nk_tan = nullptr;
-            set_error("cudaMalloc of %zu bytes for the tangent cache failed", tan_bytes);
+            set_error("device allocation of %zu bytes for the tangent cache failed", tan_bytes);
             return PD_ENOMEM;
         }
         s->nk_tan_n = tan_bytes;

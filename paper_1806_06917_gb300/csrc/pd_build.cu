@@ -96,7 +96,7 @@ static int exclusive_scan(const int *in, long long n, long long *out, cudaStream
 {
     const int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
     long long *bsum = nullptr;
-    PD_CUDA(cudaMalloc(&bsum, sizeof(long long) * (nb > 0 ? nb : 1)));
+    PD_CUDA(lib_malloc(reinterpret_cast<void **>(&bsum), sizeof(long long) * (nb > 0 ? nb : 1), st));
     if (nb > 0) {
         k_scan_sums<<<nb, 256, 0, st>>>(in, n, bsum);
         k_scan_offsets<<<1, 256, 0, st>>>(bsum, nb, out + n);
@@ -106,7 +106,7 @@ static int exclusive_scan(const int *in, long long n, long long *out, cudaStream
     }
     cudaError_t e = cudaGetLastError();
     cudaStreamSynchronize(st);
-    cudaFree(bsum);
+    lib_free(bsum, st);
     if (e != cudaSuccess) return cuda_fail(e, "exclusive_scan");
     return PD_OK;
 }
@@ -159,8 +159,8 @@ int build_slots(const Geom &g, const Tables &t, int *user_of_slot, int *slot_of_
 {
     int *active = nullptr;
     long long *scan = nullptr;
-    PD_CUDA(cudaMalloc(&active, sizeof(int) * (size_t)g.nslots));
-    PD_CUDA(cudaMalloc(&scan, sizeof(long long) * ((size_t)g.nslots + 1)));
+    PD_CUDA(lib_malloc(reinterpret_cast<void **>(&active), sizeof(int) * (size_t)g.nslots, st));
+    PD_CUDA(lib_malloc(reinterpret_cast<void **>(&scan), sizeof(long long) * ((size_t)g.nslots + 1), st));
     const int nb = (g.nslots + 255) / 256;
     k_slots<<<nb, 256, 0, st>>>(g, t.tile_org, user_of_slot, slot_of_user, active);
     int rc = exclusive_scan(active, g.nslots, scan, st);
@@ -170,8 +170,8 @@ int build_slots(const Geom &g, const Tables &t, int *user_of_slot, int *slot_of_
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "build_slots");
     }
-    cudaFree(active);
-    cudaFree(scan);
+    lib_free(active, st);
+    lib_free(scan, st);
     return rc;
 }
 
@@ -402,9 +402,9 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, uint32_t *mask, cud
     }
 #define B_ALLOC(p, bytes)                                              \
     do {                                                               \
-        if (cudaMalloc(&(p), (bytes)) != cudaSuccess) {                \
+        if (lib_malloc(reinterpret_cast<void **>(&(p)), (bytes), st) != cudaSuccess) { \
             rc = PD_ENOMEM;                                            \
-            set_error("cudaMalloc of %lld bytes failed", (long long)(bytes)); \
+            set_error("device allocation of %lld bytes failed", (long long)(bytes)); \
             goto done;                                                 \
         }                                                              \
     } while (0)
@@ -460,16 +460,17 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, uint32_t *mask, cud
     }
 done:
 #undef B_ALLOC
-    cudaFree(crd);
-    cudaFree(cell_count);
-    cudaFree(cursor);
-    cudaFree(cell_start);
-    cudaFree(cell_pts);
-    cudaFree(row_count);
-    cudaFree(err);
+    cudaStreamSynchronize(st);
+    lib_free(crd, st);
+    lib_free(cell_count, st);
+    lib_free(cursor, st);
+    lib_free(cell_start, st);
+    lib_free(cell_pts, st);
+    lib_free(row_count, st);
+    lib_free(err, st);
     if (rc != PD_OK) {
-        cudaFree(out->row_ptr);
-        cudaFree(out->col);
+        lib_free(out->row_ptr, st);
+        lib_free(out->col, st);
         out->row_ptr = nullptr;
         out->col = nullptr;
     }

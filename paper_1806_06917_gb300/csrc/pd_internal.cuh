@@ -128,6 +128,10 @@ int break_notch(const Geom &g, const Tables &t, uint32_t *mask, int axis, double
                 const double lo[3], const double hi[3], unsigned long long *d_count,
                 cudaStream_t st);
 
+// Library device memory (pd_mem.cu): a stream-ordered pool per device.
+cudaError_t lib_malloc(void **p, size_t bytes, cudaStream_t st);
+cudaError_t lib_free(void *p, cudaStream_t st);
+
 // Description checks of pd_create (pd_api.cu), for the request server.
 int validate_description(const pd_grid *gr, const pd_material *mt, const pd_run *rn);
 
