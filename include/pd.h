@@ -27,7 +27,9 @@
  *     "synchronous"; for the others a host array must stay valid until the
  *     stream has reached the call (as with cudaMemcpyAsync).
  *   - Caller-owned arrays are borrowed for the duration of the call; the library
- *     owns every buffer it allocates and frees them in pd_destroy().
+ *     owns every buffer it allocates and frees them in pd_destroy(). Library
+ *     buffers come from one stream-ordered memory pool per device that keeps
+ *     released memory for reuse (allocation never synchronises the device).
  *   - stream: a cudaStream_t passed as void*; NULL selects the simulation's own
  *     stream. Work is ordered on that stream.
  *   - A pd_sim is not thread-safe: calls on one simulation must not overlap.
@@ -123,7 +125,11 @@ typedef struct pd_sim pd_sim;
  * PD_ENOMEM, PD_ECUDA. Synchronous. */
 int pd_create(pd_sim **out, const pd_grid *grid, const pd_material *mat, const pd_run *run);
 
-/* Free every buffer, graph and stream of the simulation. NULL is accepted. */
+/* Free every buffer, graph and stream of the simulation. NULL is accepted.
+ * Waits for the simulation's own stream; work that uses the simulation on a
+ * stream the caller passed must have completed (the buffers return, ordered on
+ * the simulation's stream, to the library's device memory pool, which keeps
+ * them for reuse instead of synchronising the device). */
 int pd_destroy(pd_sim *sim);
 
 /* Copy the message of the last failure on this thread into buf (NUL-terminated,
