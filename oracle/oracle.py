@@ -46,7 +46,8 @@ class _OrGrid(ctypes.Structure):
 class _OrMaterial(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("vol_corr", ctypes.c_int32),
                 ("E", ctypes.c_double), ("rho", ctypes.c_double), ("K", ctypes.c_double),
-                ("mu", ctypes.c_double), ("s_c", ctypes.c_double), ("thickness", ctypes.c_double)]
+                ("mu", ctypes.c_double), ("s_c", ctypes.c_double), ("thickness", ctypes.c_double),
+                ("psi_c", ctypes.c_double), ("psi_beta", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -100,7 +101,7 @@ def _grid(g) -> _OrGrid:
 
 
 def _mat(m) -> _OrMaterial:
-    return _OrMaterial(m.model, m.vol_corr, m.E, m.rho, m.K, m.mu, m.s_c, m.thickness)
+    return _OrMaterial(m.model, m.vol_corr, m.E, m.rho, m.K, m.mu, m.s_c, m.thickness, m.psi_c, m.psi_beta)
 
 
 def _c(a, dtype):

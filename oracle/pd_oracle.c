@@ -10,6 +10,7 @@
  * implementation of peridynamics utilizing HPX"):
  *   - discrete neighbourhoods B_delta(X_i)              Sec. 3.1
  *   - bond-based force (PMB law, breaking)              Eq. (3), Algorithm 1
+ *   - bond-based NP law and its linearisation LP        Algorithm 1, Sec. 5.2.2
  *   - state-based LPS: weighted volume, dilatation,
  *     force (gather form and Algorithm 2's scatter)     Eq. (4), Algorithm 2
  *   - velocity-Verlet and central-difference updates    Eqs. (7)-(10), Algorithm 4
@@ -43,7 +44,15 @@
  *   - stable step bound (Silling-Askari 2005):
  *     dt_crit = min_i sqrt(2 rho / sum_j c V_j / |xi_ij|);
  *   - optional partial volume V_ij = (delta + h/2 - |xi|) / h for
- *     |xi| > delta - h/2, else 1.
+ *     |xi| > delta - h/2, else 1;
+ *   - NP / LP (Algorithm 1 and the 2D study of Sec. 5.2.2): bond strain
+ *     S = (eta . xi) / |xi|^2, direction xi/|xi| (reference configuration),
+ *     psi(r) = C (1 - exp(-beta r)), LP uses psi'(0) = C beta in place of
+ *     psi'(|xi| S^2) and psi(r) = C beta r; influence function J = 1 for
+ *     |xi| < delta and 0 otherwise (on integer offsets a^2 + b^2 + c^2 < m^2);
+ *     |B_delta(0)| is the ball measure pi delta^2 (2D) or 4 pi delta^3 / 3
+ *     (3D); stable-step bound with the bond stiffness 4 C beta / (delta |B|)
+ *     in place of the PMB micromodulus.
  */
 #include <math.h>
 #include <stdint.h>
@@ -63,12 +72,13 @@ typedef struct {
 } or_grid;
 
 typedef struct {
-    int32_t model;    /* 0 PMB, 1 LPS */
+    int32_t model;    /* 0 PMB, 1 LPS, 2 NP, 3 LP */
     int32_t vol_corr; /* partial-volume correction on/off */
     double E, rho, K, mu, s_c, thickness;
+    double psi_c, psi_beta;   /* NP / LP potential psi(r) = C (1 - exp(-beta r)) */
 } or_material;
 
-enum { OR_PMB = 0, OR_LPS = 1 };
+enum { OR_PMB = 0, OR_LPS = 1, OR_NP = 2, OR_LP = 3 };
 enum { OR_BC_FREE = 0, OR_BC_VELOCITY = 1, OR_BC_DISPLACEMENT = 2 };
 
 static const double OR_PI = 3.14159265358979323846;
@@ -120,6 +130,20 @@ double or_pmb_micromodulus(const or_grid *g, const or_material *mat)
         return 18.0 * Kb / (OR_PI * pow(delta, 4));
     }
     return 9.0 * mat->E / (OR_PI * mat->thickness * pow(delta, 3));
+}
+
+/* |B_delta(0)|: the measure of the horizon ball. */
+static double ball_measure(const or_grid *g)
+{
+    double delta = horizon(g);
+    return g->dim == 3 ? 4.0 * OR_PI * delta * delta * delta / 3.0 : OR_PI * delta * delta;
+}
+
+/* Bond stiffness of the NP / LP laws at zero strain, 4 C beta / (delta |B|):
+ * their force is this times S xi/|xi| V_j for small S. */
+static double np_stiffness(const or_grid *g, const or_material *mat)
+{
+    return 4.0 * mat->psi_c * mat->psi_beta / (horizon(g) * ball_measure(g));
 }
 
 /* Young's modulus implied by K and mu (used for the LPS stable-step bound). */
@@ -347,6 +371,50 @@ void or_pmb_force(const or_grid *g, const or_material *mat,
     }
 }
 
+/* ---------------------------------------------------------- NP / LP force */
+
+/* J(|xi|) of the NP / LP laws: 1 inside the open horizon ball, 0 on its
+ * boundary (Sec. 5.2.2), decided on the lattice offset of the bond. */
+static double np_influence(const or_grid *g, int64_t i, int64_t j)
+{
+    int64_t ci[3], cj[3];
+    lattice_coord(g, i, ci);
+    lattice_coord(g, j, cj);
+    int64_t a = cj[0] - ci[0], b = cj[1] - ci[1], c = cj[2] - ci[2];
+    return a * a + b * b + c * c < (int64_t)g->m * g->m ? 1.0 : 0.0;
+}
+
+/* Algorithm 1: for every i, over j in B_delta(X_i) in ascending order,
+ *   S = (u_j - u_i) . xi / |xi|^2,
+ *   f_i += 4 / (delta |B_delta(0)|) J(|xi|) psi'(|xi| S^2) S xi/|xi| V_j (V_ij),
+ * with psi'(r) = C beta exp(-beta r) (NP) or C beta (LP, linear). */
+void or_np_force(const or_grid *g, const or_material *mat,
+                 const int64_t *row_ptr, const int32_t *col, const uint8_t *broken,
+                 const double *u, double *f)
+{
+    int64_t n = npoints(g);
+    int d = g->dim;
+    double k0 = 4.0 / (horizon(g) * ball_measure(g)), V = nodal_volume(g, mat);
+    double C = mat->psi_c, beta = mat->psi_beta;
+    int linear = mat->model == OR_LP;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            if (broken && broken[k]) continue;
+            int64_t j = col[k];
+            double xi[3], eta[3];
+            bond_vectors(g, i, j, u, xi, eta);
+            double r0 = norm3(xi);
+            double S = (eta[0] * xi[0] + eta[1] * xi[1] + eta[2] * xi[2]) / (r0 * r0);
+            double dpsi = linear ? C * beta : C * beta * exp(-beta * r0 * S * S);
+            double w = k0 * np_influence(g, i, j) * dpsi * S * V * volume_factor(g, mat, r0) / r0;
+            for (int a = 0; a < 3; ++a) fi[a] += w * xi[a];
+        }
+        for (int a = 0; a < d; ++a) f[i * d + a] = fi[a];
+    }
+}
+
 /* ---------------------------------------------------------------- LPS model */
 
 /* Algorithm 2, first loop: weighted volume m_i = sum_j |xi|^2 V_j (omega = 1),
@@ -469,6 +537,8 @@ static void internal_force(const or_grid *g, const or_material *mat,
 {
     if (mat->model == OR_PMB) {
         or_pmb_force(g, mat, row_ptr, col, u, broken, update_breaking, f);
+    } else if (mat->model == OR_NP || mat->model == OR_LP) {
+        or_np_force(g, mat, row_ptr, col, broken, u, f);
     } else {
         or_lps_dilatation(g, mat, row_ptr, col, broken, mvol, u, theta);
         or_lps_force(g, mat, row_ptr, col, broken, mvol, theta, u, f);
@@ -507,6 +577,13 @@ double or_strain_energy(const or_grid *g, const or_material *mat,
             if (mat->model == OR_PMB) {
                 double s = (r - r0) / r0;
                 Wi += 0.5 * (0.5 * c * s * s * r0) * V * vf;
+            } else if (mat->model == OR_NP || mat->model == OR_LP) {
+                /* Algorithm 1: U_i += J psi(|xi| S^2) V_j / (delta |B_delta(0)|) */
+                double S = (eta[0] * xi[0] + eta[1] * xi[1] + eta[2] * xi[2]) / (r0 * r0);
+                double arg = r0 * S * S;
+                double psi = mat->model == OR_LP ? mat->psi_c * mat->psi_beta * arg
+                                                 : mat->psi_c * (1.0 - exp(-mat->psi_beta * arg));
+                Wi += np_influence(g, i, col[k]) * psi * V * vf / (horizon(g) * ball_measure(g));
             } else {
                 double ed = (r - r0) - theta[i] * r0 / 3.0;
                 Wi += 15.0 * mat->mu / (2.0 * mvol[i]) * ed * ed * V * vf;
@@ -535,14 +612,16 @@ double or_kinetic_energy(const or_grid *g, const or_material *mat, const double 
 /* --------------------------------------------------------------- time step */
 
 /* Stable step bound dt_crit = min_i sqrt(2 rho / sum_j c V_j V_ij / |xi_ij|).
- * For LPS the PMB micromodulus of the same Young's modulus is used. */
+ * For LPS the PMB micromodulus of the same Young's modulus is used; for NP / LP
+ * the bond stiffness 4 C beta / (delta |B|). */
 double or_stable_dt(const or_grid *g, const or_material *mat,
                     const int64_t *row_ptr, const int32_t *col)
 {
     int64_t n = npoints(g);
     or_material pm = *mat;
     if (mat->model == OR_LPS) pm.E = lps_young(mat);
-    double c = or_pmb_micromodulus(g, &pm), V = nodal_volume(g, mat);
+    double c = (mat->model == OR_NP || mat->model == OR_LP) ? np_stiffness(g, mat) : or_pmb_micromodulus(g, &pm);
+    double V = nodal_volume(g, mat);
     double best = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         double Xi[3], Xj[3], sum = 0.0;

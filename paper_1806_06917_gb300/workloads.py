@@ -23,6 +23,8 @@ import numpy as np
 
 PMB = 0   # bond-based prototype micro-elastic brittle model
 LPS = 1   # state-based linear peridynamic solid
+NP = 2    # bond-based nonlinear model of Algorithm 1 (potential psi, linearised bond strain)
+LP = 3    # its linearisation (psi'(0) in place of psi')
 
 BC_FREE = 0
 BC_VELOCITY = 1      # prescribed velocity on this degree of freedom
@@ -67,6 +69,8 @@ class Material:
     s_c: float = 0.0         # critical stretch; 0 disables breaking
     thickness: float = 1.0   # plate thickness in 2D (m)
     vol_corr: int = 0        # partial-volume correction of boundary-of-horizon cells
+    psi_c: float = 1.0       # NP / LP potential psi(r) = psi_c (1 - exp(-psi_beta r))
+    psi_beta: float = 1.0
 
 
 @dataclasses.dataclass
