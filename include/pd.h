@@ -57,6 +57,9 @@ extern "C" {
 /* ------------------------------------------------------------------- constants */
 #define PD_MODEL_PMB 0     /* bond-based prototype micro-elastic brittle */
 #define PD_MODEL_LPS 1     /* state-based linear peridynamic solid (3D only) */
+#define PD_MODEL_NP 2      /* bond-based nonlinear law of Algorithm 1 (linearised bond
+                              strain, potential psi(r) = C (1 - exp(-beta r))) */
+#define PD_MODEL_LP 3      /* its linearisation: psi'(0) = C beta in place of psi' */
 
 #define PD_FP32C 0         /* FP32 bond arithmetic on per-tile reference-frame
                               displacements; integrator state u, v held as
@@ -89,9 +92,13 @@ typedef struct {
 /* Material. PMB micromodulus (the paper does not give it; literature values):
  * 3D c = 18 K'/(pi delta^4) with K' = E/(3(1-2nu)), nu = 1/4; 2D plane stress
  * c = 9E/(pi t delta^3) with nodal volume h^2 t. LPS uses K and mu
- * (Algorithm 2) and is 3D only. Influence function omega = 1. */
+ * (Algorithm 2) and is 3D only. Influence function omega = 1. NP / LP
+ * (Algorithm 1; Sec. 5.2.2): S = eta . xi / |xi|^2, f_i = 4 / (delta |B_delta|)
+ * sum_j J psi'(|xi| S^2) S xi/|xi| V_j with |B_delta| the ball measure (pi
+ * delta^2 in 2D, 4 pi delta^3 / 3 in 3D), J = 1 for |xi| < delta and 0 on the
+ * horizon boundary; no bond breaking (s_c must be 0). */
 typedef struct {
-    int32_t model;      /* PD_MODEL_PMB or PD_MODEL_LPS */
+    int32_t model;      /* PD_MODEL_PMB, PD_MODEL_LPS, PD_MODEL_NP or PD_MODEL_LP */
     int32_t vol_corr;   /* 1: partial volume V_ij = (delta + h/2 - |xi|)/h for
                            |xi| > delta - h/2 (Remark of Sec. 3.1), else 1 */
     double E;           /* Young's modulus (PMB), Pa */
@@ -100,6 +107,8 @@ typedef struct {
     double mu;          /* shear modulus (LPS), Pa */
     double s_c;         /* critical stretch (PMB); 0 disables breaking */
     double thickness;   /* 2D plate thickness t (m); ignored in 3D */
+    double psi_c;       /* NP / LP potential scale C, > 0 for those models */
+    double psi_beta;    /* NP / LP potential rate beta, > 0 for those models */
 } pd_material;
 
 /* Run parameters. */

@@ -162,7 +162,7 @@ static size_t max_smem(const Geom &g, int precision, int model)
 {
     size_t m = jvp_smem(g, precision);
     m = std::max(m, energy_smem(g, precision));
-    if (model == PD_MODEL_PMB)
+    if (model != PD_MODEL_LPS)
         m = std::max(m, precision == PD_FP64 ? pmb_generic_smem(g, precision) : pmb_fast_smem(g));
     else m = std::max(m, lps_generic_smem(g, precision, false));
     return m;
@@ -181,7 +181,11 @@ static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
     if (!(gr->h > 0.0) || !isfinite(gr->h)) { set_error("h must be > 0"); return PD_EINVAL; }
     if (gr->reserved != 0) { set_error("pd_grid.reserved must be 0"); return PD_EINVAL; }
     if ((double)gr->n[0] * gr->n[1] * gr->n[2] > 1.0e9) { set_error("more than 1e9 points"); return PD_EINVAL; }
-    if (mt->model != PD_MODEL_PMB && mt->model != PD_MODEL_LPS) { set_error("unknown model"); return PD_EINVAL; }
+    if (mt->model < PD_MODEL_PMB || mt->model > PD_MODEL_LP) { set_error("unknown model"); return PD_EINVAL; }
+    if (mt->model == PD_MODEL_NP || mt->model == PD_MODEL_LP) {
+        if (!(mt->psi_c > 0.0) || !(mt->psi_beta > 0.0)) { set_error("NP / LP need psi_c > 0 and psi_beta > 0"); return PD_EINVAL; }
+        if (mt->s_c != 0.0) { set_error("NP / LP have no bond breaking (s_c must be 0)"); return PD_EINVAL; }
+    }
     if (!(mt->rho > 0.0)) { set_error("rho must be > 0"); return PD_EINVAL; }
     if (mt->model == PD_MODEL_PMB && !(mt->E > 0.0)) { set_error("E must be > 0"); return PD_EINVAL; }
     if (mt->model == PD_MODEL_LPS) {
@@ -299,6 +303,8 @@ static int create_impl(pd_sim *s)
     mt.mu = s->pmat.mu;
     mt.s_c = s->pmat.s_c;
     mt.thickness = s->pmat.thickness;
+    mt.psi_c = s->pmat.psi_c;
+    mt.psi_beta = s->pmat.psi_beta;
     const double delta = g.m * g.h;
     const double PI = 3.14159265358979323846;
     auto pmb_c = [&](double E) {
@@ -309,8 +315,11 @@ static int create_impl(pd_sim *s)
         return 9.0 * E / (PI * mt.thickness * delta * delta * delta);
     };
     mt.V = g.dim == 3 ? g.h * g.h * g.h : g.h * g.h * mt.thickness;
-    mt.c = mt.model == PD_MODEL_PMB ? pmb_c(mt.E) : 0.0;
-    s->c_dt = mt.model == PD_MODEL_PMB ? mt.c : pmb_c(9.0 * mt.K * mt.mu / (3.0 * mt.K + mt.mu));
+    const bool np_law = mt.model == PD_MODEL_NP || mt.model == PD_MODEL_LP;
+    // NP / LP: 4 C beta / (delta |B_delta(0)|), the bond stiffness at zero strain
+    const double ball = g.dim == 3 ? 4.0 * PI * delta * delta * delta / 3.0 : PI * delta * delta;
+    mt.c = mt.model == PD_MODEL_PMB ? pmb_c(mt.E) : np_law ? 4.0 * mt.psi_c * mt.psi_beta / (delta * ball) : 0.0;
+    s->c_dt = mt.model == PD_MODEL_LPS ? pmb_c(9.0 * mt.K * mt.mu / (3.0 * mt.K + mt.mu)) : mt.c;
 
     PD_CUDA(cudaGetDevice(&s->device));
     PD_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
@@ -355,7 +364,16 @@ static int create_impl(pd_sim *s)
             tb[4 * k + 2] = make_float4((float)(A * rr * vij), (float)(A * rr * vij), (float)(B * vij),
                                         (float)(B * vij));
             tb[4 * k + 3] = make_float4((float)d2, (float)d2, offf, 0.f);
-            if (mt.model == PD_MODEL_PMB) {
+            if (mt.model == PD_MODEL_NP || mt.model == PD_MODEL_LP) {
+                // {dz,dz,1/|d|^2,1/|d|^2} {a,a,t,t} {offset,-,-,-} with the bond weight
+                // t = J V_ij / |d| and the exponent a = -beta h |d| log2(e), so that
+                // psi'(|xi| S^2) / (C beta) = exp2(a S^2)
+                const double J = d2 < (double)g.m * g.m ? 1.0 : 0.0;
+                const double a_ex2 = -mt.psi_beta * g.h * rr / log(2.0);
+                ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)(1.0 / d2), (float)(1.0 / d2));
+                ta[4 * k + 2] = make_float4((float)a_ex2, (float)a_ex2, (float)(J * vij / rr), (float)(J * vij / rr));
+                ta[4 * k + 3] = make_float4(offf, 0.f, 0.f, 0.f);
+            } else if (mt.model == PD_MODEL_PMB) {
                 // {dz,dz,|d|^2,|d|^2} {|d|/V_ij x2, |d|^2/V_ij x2} {offset, s_c V_ij, -, -}
                 ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)d2, (float)d2);
                 ta[4 * k + 2] = make_float4((float)(rr / vij), (float)(rr / vij), (float)(d2 / vij), (float)(d2 / vij));
@@ -479,7 +497,8 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.nbr_ok = s->nbr_ok;
     a.bc32 = s->bc32;
     a.body32 = s->body32;
-    a.fscale = s->mat.model == PD_MODEL_PMB ? s->mat.c * s->mat.V : 1.0 / s->g.h;
+    a.fscale = s->mat.model == PD_MODEL_LPS ? 1.0 / s->g.h : s->mat.c * s->mat.V;
+    a.psi_beta = s->mat.psi_beta;
     a.kF = (float)(0.5 * s->dt * a.fscale / s->mat.rho);
     a.kB = (float)(0.5 * s->dt / s->mat.rho);
     a.dt_h = (float)s->dt;
@@ -493,7 +512,7 @@ static int run_force(pd_sim *s, int mode, const float4 *src_hl, const double4_32
 {
     TileArgs a = make_args(s, mode, src_hl, src_d4);
     a.update_breaking = update_breaking && s->mat.s_c > 0.0;
-    if (s->mat.model == PD_MODEL_PMB) return launch_pmb_args(a, s->precision, st);
+    if (s->mat.model != PD_MODEL_LPS) return launch_pmb_args(a, s->precision, st);   // bond-based laws
     int rc = launch_lps_args(a, s->precision, 1, st);
     if (rc != PD_OK) return rc;
     return launch_lps_args(a, s->precision, 0, st);

@@ -157,6 +157,88 @@ size_t pmb_fast_smem(const Geom &g)
 
 // ------------------------------------------------------------------ generic
 
+// ------------------------------------------------------------- NP / LP, FP32C
+
+// One 32-bond word of the NP / LP sum (Algorithm 1) for a point pair in f32x2:
+//   S = eta.d / |d|^2,  w = t S [exp2(a S^2) for NP],  F += w d,
+// table entry {dx,dx,dy,dy} {dz,dz,1/|d|^2 x2} {a,a,t,t} {offset,-,-,-} with
+// t = J V_ij / |d| and a = -beta h |d| / ln 2 (see pd_api.cu). The direction is
+// the reference bond d, so no square root or reciprocal is needed.
+template <int DIM, bool MASKED, bool LINEAR>
+__device__ __forceinline__ void np_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
+                                        float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1, float2 &Fx,
+                                        float2 &Fy, float2 &Fz)
+{
+PD_PRAGMA_UNROLL(PD_UNROLL)
+    for (int b = 0; b < nb; ++b) {
+        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
+        const int off = __float_as_int(tw[4 * b + 3].x);
+        const float4 r4 = P4[bi + off];
+        const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy);
+        float2 dot = f2mul(ex, f2lo(ta));
+        dot = f2fma(ey, f2hi(ta), dot);
+        if (DIM == 3) dot = f2fma(f2add(P2[bi + off], nuz), f2lo(tb), dot);
+        const float2 S = f2mul(dot, f2hi(tb));
+        float2 wgt = f2mul(S, f2hi(tc));
+        if (!LINEAR) wgt = f2mul(wgt, f2ex2(f2mul(f2lo(tc), f2mul(S, S))));
+        if (MASKED) {
+            wgt.x = ((c0 >> b) & 1u) ? wgt.x : 0.f;
+            wgt.y = ((c1 >> b) & 1u) ? wgt.y : 0.f;
+        }
+        Fx = f2fma(wgt, f2lo(ta), Fx);
+        Fy = f2fma(wgt, f2hi(ta), Fy);
+        if (DIM == 3) Fz = f2fma(wgt, f2lo(tb), Fz);
+    }
+}
+
+template <int DIM, bool LINEAR>
+__global__ void __launch_bounds__(256, PD_MINBLOCKS) np_fast(const TileArgs a)
+{
+    const Geom &g = a.g;
+    const PairBox pb = pair_box(g);
+    const int S = g.S;
+    extern __shared__ float4 smem4[];
+    float4 *P4 = smem4;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
+    float4 *tab = P4 + pb.n + (DIM == 3 ? (pb.n + 1) / 2 : 0);      // the layout of pmb_fast_smem
+    __shared__ int s_nbr[27];
+    const int tile = blockIdx.x;
+    const int4 org = __ldg(&a.tile_org[tile]);
+    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    load_nbr(a, tile, s_nbr);
+    __syncthreads();
+    stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr);
+    __syncthreads();
+
+    const int nthr = g.T / 2;            // a multiple of blockDim
+    for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
+        const PairPts q = pair_points(g, pb, org, tile, t);
+        const float4 ui4 = P4[q.bi];
+        const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4));
+        const float2 nuz = DIM == 3 ? f2neg(P2[q.bi]) : make_float2(0.f, 0.f);
+        float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
+        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
+        for (int w = 0; w < g.W; ++w) {
+            const uint32_t m0 = n0, m1 = n1;
+            if (w + 1 < g.W) {
+                const size_t mo = (size_t)(w + 1) * g.nslots;
+                n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
+                n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
+            }
+            const int nb = min(32, S - 32 * w);
+            const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            const float4 *tw = tab + 4 * 32 * w;
+            if (__all_sync(0xffffffffu, m0 == full && m1 == full))
+                np_word<DIM, false, LINEAR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, Fx, Fy, Fz);
+            else
+                np_word<DIM, true, LINEAR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, Fx, Fy, Fz);
+        }
+        const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
+        pair_epilogue2(a, q, FA, FB, DIM);
+    }
+}
+
 // Runtime stencil (any horizon), one point per thread. R = float (FP32C) or
 // double (FP64). Stencil entries come from a.stencil; box dims from a.g.m.
 template <class R>
@@ -181,6 +263,7 @@ __global__ void __launch_bounds__(256) pmb_generic(const TileArgs a)
     __syncthreads();
 
     const bool brk_on = a.update_breaking && a.s_c > 0.0;
+    const bool np_law = a.model == PD_MODEL_NP || a.model == PD_MODEL_LP;
     const R s_c = (R)a.s_c;
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) {
         const int lx = t % g.bx, ly = (t / g.bx) % g.by, lz = t / (g.bx * g.by);
@@ -199,6 +282,20 @@ __global__ void __launch_bounds__(256) pmb_generic(const TileArgs a)
                 const int4 d = __ldg(&a.stencil[32 * w + b]);
                 const R4 rj = box[bi + d.x + HX * (d.y + HY * d.z)];
                 const R ex = rj.x - ui.x, ey = rj.y - ui.y, ez = rj.z - ui.z;
+                if (np_law) {
+                    // NP / LP (Algorithm 1): S = eta.d / |d|^2 in lattice units,
+                    // f += J psi'(|xi| S^2)/(C beta) S d/|d| V_ij (times c V below)
+                    if (d.w >= m * m) continue;                            // J = 0 on the boundary
+                    const R r0 = (R)__ldg(&a.stencil_r0[32 * w + b]);
+                    const R S = ((R)d.x * ex + (R)d.y * ey + (R)d.z * ez) / (R)d.w;
+                    R wgt = S / r0;
+                    if (a.model == PD_MODEL_NP) wgt *= exp(-(R)a.psi_beta * (R)a.h * r0 * S * S);
+                    if (a.vol_corr) wgt *= (R)vol_factor_lattice(m, (double)r0);
+                    Fx += wgt * (R)d.x;
+                    Fy += wgt * (R)d.y;
+                    Fz += wgt * (R)d.z;
+                    continue;
+                }
                 const R yx = ex + (R)d.x, yy = ey + (R)d.y, yz = ez + (R)d.z;
                 const R q = yx * yx + yy * yy + yz * yz;
                 const R num = ex * ex + ey * ey + ez * ez +
@@ -242,10 +339,27 @@ size_t pmb_generic_smem(const Geom &g, int precision)
     return (size_t)HX * HY * HZ * (precision == PD_FP64 ? sizeof(double4_32a) : sizeof(float4));
 }
 
+template <int DIM, bool LINEAR>
+static int launch_np_fast(const TileArgs &a, cudaStream_t st)
+{
+    const size_t smem = pmb_fast_smem(a.g);
+    PD_CUDA(cudaFuncSetAttribute(np_fast<DIM, LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int threads = a.g.T / 2 < 256 ? a.g.T / 2 : 256;
+    np_fast<DIM, LINEAR><<<a.g.ntiles, threads, smem, st>>>(a);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// Every bond-based law: PMB, NP, LP.
 int launch_pmb_args(const TileArgs &a, int precision, cudaStream_t st)
 {
     const Geom &g = a.g;
     const bool brk = a.update_breaking && a.s_c > 0.0;
+    if (precision == PD_FP32C && (a.model == PD_MODEL_NP || a.model == PD_MODEL_LP)) {
+        const bool lin = a.model == PD_MODEL_LP;
+        if (g.dim == 3) return lin ? launch_np_fast<3, true>(a, st) : launch_np_fast<3, false>(a, st);
+        return lin ? launch_np_fast<2, true>(a, st) : launch_np_fast<2, false>(a, st);
+    }
     if (precision == PD_FP32C) {
         if (g.dim == 3) return brk ? launch_fast<3, true>(a, st) : launch_fast<3, false>(a, st);
         return brk ? launch_fast<2, true>(a, st) : launch_fast<2, false>(a, st);

@@ -86,7 +86,8 @@ struct Geom {
 struct Material {
     int model, vol_corr;
     double E, rho, K, mu, s_c, thickness;
-    double c;            // PMB micromodulus
+    double psi_c, psi_beta;   // NP / LP potential
+    double c;            // PMB micromodulus; NP / LP bond stiffness 4 C beta / (delta |B|)
     double V;            // nodal volume
 };
 

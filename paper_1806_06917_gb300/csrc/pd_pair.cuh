@@ -71,7 +71,15 @@ __device__ __forceinline__ float sfu_rcp(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float sfu_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float2 f2rsqrt(float2 q) { return make_float2(sfu_rsqrt(q.x), sfu_rsqrt(q.y)); }
+__device__ __forceinline__ float2 f2ex2(float2 q) { return make_float2(sfu_ex2(q.x), sfu_ex2(q.y)); }
 __device__ __forceinline__ float2 f2sqrt(float2 q) { return make_float2(sfu_sqrt(q.x), sfu_sqrt(q.y)); }
 __device__ __forceinline__ float2 f2rcp(float2 q) { return make_float2(sfu_rcp(q.x), sfu_rcp(q.y)); }
 __device__ __forceinline__ float2 f2div(float2 a, float2 b) { return f2mul(a, f2rcp(b)); }

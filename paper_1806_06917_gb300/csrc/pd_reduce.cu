@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) energy_generic(const TileArgs a)
         stage_box64(reinterpret_cast<double4_32a *>(box), HX, HY, nbox, m, a, org, tile_ref64(a, tile), a.inv_h);
     __syncthreads();
     const bool lps = a.model == PD_MODEL_LPS;
+    const bool np_law = a.model == PD_MODEL_NP || a.model == PD_MODEL_LP;
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) {
         const int lx = t % g.bx, ly = (t / g.bx) % g.by, lz = t / (g.bx * g.by);
         const int slot = tile * g.T + brick_code(g.dim, lx, ly, lz);
@@ -53,6 +54,16 @@ __global__ void __launch_bounds__(256) energy_generic(const TileArgs a)
                 const R r0 = (R)__ldg(&a.stencil_r0[32 * w + b]);
                 const R4 rj = box[bi + d.x + HX * (d.y + HY * d.z)];
                 const R ex = rj.x - ui.x, ey = rj.y - ui.y, ez = rj.z - ui.z;
+                if (np_law) {
+                    // Algorithm 1's energy: J psi(|xi| S^2) V_ij; with r = h |d| S^2,
+                    // NP: psi / (C beta) = (1 - exp(-beta r)) / beta, LP: psi / (C beta) = r
+                    if (d.w >= m * m) continue;
+                    const R S = ((R)d.x * ex + (R)d.y * ey + (R)d.z * ez) / (R)d.w;
+                    const R rr = (R)a.h * r0 * S * S;
+                    const R vij = a.vol_corr ? (R)vol_factor_lattice(m, (double)r0) : (R)1;
+                    acc += (a.model == PD_MODEL_NP ? -expm1(-(R)a.psi_beta * rr) / (R)a.psi_beta : rr) * vij;
+                    continue;
+                }
                 const R yx = ex + (R)d.x, yy = ey + (R)d.y, yz = ez + (R)d.z;
                 const R q = yx * yx + yy * yy + yz * yz;
                 const R num = ex * ex + ey * ey + ez * ez + (R)2 * ((R)d.x * ex + (R)d.y * ey + (R)d.z * ez);
@@ -71,6 +82,9 @@ __global__ void __launch_bounds__(256) energy_generic(const TileArgs a)
         if (lps) {
             const double mt = sizeof(R) == 4 ? 1.0 / (double)a.minv32[slot] : a.mtil[slot];
             W = 0.5 * a.K * (double)th * (double)th + 0.5 * a.B / mt * (double)acc;
+        } else if (np_law) {
+            // W_i = sum_j J psi V_j V_ij / (delta |B|) = (c V / 4) sum_j J (psi / (C beta)) V_ij
+            W = 0.25 * a.cV * (double)acc;
         } else {
             W = 0.25 * a.cV * a.h * (double)acc;
         }

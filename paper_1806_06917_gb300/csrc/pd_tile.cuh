@@ -321,6 +321,7 @@ struct TileArgs {
     const double *mtil;         // LPS m~ (FP64)
     float *theta32;
     double *theta64;
+    double psi_beta;            // NP / LP potential rate
     const double *w[3];         // tangent input (slot order)
     double *jv[3];              // tangent output
     double *epoint;             // per-point energy (slot order)

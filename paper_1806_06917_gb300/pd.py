@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("PD_LIBRARY") or os.path.join(_HERE, "_build", "libpd.so")
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_EBUSY, PD_ENOTREADY, PD_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-PD_MODEL_PMB, PD_MODEL_LPS = 0, 1
+PD_MODEL_PMB, PD_MODEL_LPS, PD_MODEL_NP, PD_MODEL_LP = 0, 1, 2, 3
 PD_FP32C, PD_FP64 = 0, 1
 PD_BC_FREE, PD_BC_VELOCITY, PD_BC_DISPLACEMENT = 0, 1, 2
 PD_FORCE_UPDATE_BREAKING = 1
@@ -42,7 +42,8 @@ class pd_grid(ctypes.Structure):
 class pd_material(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("vol_corr", ctypes.c_int32), ("E", ctypes.c_double),
                 ("rho", ctypes.c_double), ("K", ctypes.c_double), ("mu", ctypes.c_double),
-                ("s_c", ctypes.c_double), ("thickness", ctypes.c_double)]
+                ("s_c", ctypes.c_double), ("thickness", ctypes.c_double), ("psi_c", ctypes.c_double),
+                ("psi_beta", ctypes.c_double)]
 
 
 class pd_run(ctypes.Structure):
@@ -451,6 +452,8 @@ def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=
     m.vol_corr = workload_mat.vol_corr
     m.E, m.rho, m.K, m.mu = workload_mat.E, workload_mat.rho, workload_mat.K, workload_mat.mu
     m.s_c, m.thickness = workload_mat.s_c, workload_mat.thickness
+    m.psi_c = getattr(workload_mat, "psi_c", 1.0)
+    m.psi_beta = getattr(workload_mat, "psi_beta", 1.0)
     r = pd_run()
     r.dt, r.dt_factor, r.precision, r.tile_log2 = dt, dt_factor, precision, tile_log2
     return g, m, r
