@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -318,6 +319,69 @@ def run_serving(args, pd, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_convergence(args, pd, torch):
+    """Sec. 5.2.2's 2D study: NP and LP, IC 1 and IC 2, meshes h = delta/2,
+    delta/4, delta/8 on [-delta, 1 + delta]^2 with the collar held at 0, dt =
+    1e-5 to t = 2. Every 0.1 time units the rate
+      alpha = (log ||u_1 - u_2|| - log ||u_2 - u_3||) / log 2
+    with ||f||^2 = sum over the coarse nodes in [0, 1]^2 of |f|^2 h_1^2 (the
+    coarse nodes are nodes of the finer meshes: index 2i and 4i)."""
+    ks = (2, 4, 8)
+    steps_total = args.conv_steps
+    chunk = max(1, steps_total // 20)
+    out = {}
+    work = 0
+    t_all = time.perf_counter()
+    for model in (W.NP, W.LP):
+        for ic in (1, 2):
+            wls = [W.np_square(k=k, model=model, ic=ic) for k in ks]
+            sims = []
+            for wl in wls:
+                g, m, r = pd.describe(wl.grid, wl.mat, precision=pd.PD_FP32C, dt=wl.dt)
+                sim = pd.pd_create(g, m, r)
+                pd.pd_build_neighbors(sim)
+                pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+                pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
+                sims.append(sim)
+            n1 = wls[0].grid.n[0]
+            X1 = wls[0].grid.positions()
+            inside = np.all((X1 > -1e-9) & (X1 < 1.0 + 1e-9), axis=1)
+            h1 = wls[0].grid.h
+            rates, times = [], []
+            done = 0
+            while done < steps_total:
+                q = min(chunk, steps_total - done)
+                for sim in sims:
+                    pd.pd_step_explicit(sim, q)
+                done += q
+                us = []
+                for wl, sim, k in zip(wls, sims, ks):
+                    u, _ = pd.pd_get_state(sim, want_v=False)
+                    n = wl.grid.n[0]
+                    step = k // ks[0]
+                    U = u.reshape(n, n, 2)[::step, ::step].reshape(-1, 2)      # the coarse nodes
+                    us.append(U[inside])
+                e12 = math.sqrt(float(((us[0] - us[1]) ** 2).sum()) * h1 * h1)
+                e23 = math.sqrt(float(((us[1] - us[2]) ** 2).sum()) * h1 * h1)
+                times.append(done * wls[0].dt)
+                rates.append((math.log(e12) - math.log(e23)) / math.log(2.0) if e12 > 0 and e23 > 0 else None)
+            for sim, wl in zip(sims, wls):
+                work += pd.pd_bond_count(sim) * steps_total
+                sim.close()
+            out["%s_ic%d" % ("np" if model == W.NP else "lp", ic)] = {
+                "t": [round(t, 4) for t in times], "alpha": [None if a is None else round(a, 4) for a in rates]}
+    sec = time.perf_counter() - t_all
+    line = {"metric": "bond updates/s (2D NP/LP convergence study, 12 runs)", "value": work / sec,
+            "unit": "bond-updates/s", "n_gpus": 1, "steps": steps_total, "warmup": 0, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)", "data": "synthetic",
+            "config": {"workload": "Sec. 5.2.2: [0,1]^2, delta = 0.1, h = delta/2, delta/4, delta/8, "
+                                   "collar u = 0, dt = 1e-5, t in [0, %g]" % (steps_total * 1e-5),
+                       "l2": "not flushed"},
+            "seconds": sec, "alpha": out, "gpu_launches": None, "roofline": None}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(wl, target_s=12.0, max_steps=50):
     """The FP64 oracle (as it stands) on the host cores: a bounded number of explicit
     steps of the same workload."""
@@ -377,7 +441,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="block64", choices=["block64", "lps128", "plate50", "serve"])
+    ap.add_argument("--workload", default="block64",
+                    choices=["block64", "lps128", "plate50", "serve", "convergence"])
+    ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
     ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")
@@ -403,6 +469,10 @@ def main():
     if args.workload == "serve":
         if rank == 0:
             run_serving(args, pd, torch)
+        return
+    if args.workload == "convergence":
+        if rank == 0:
+            run_convergence(args, pd, torch)
         return
 
     wl, desc = workload(args.workload)
