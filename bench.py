@@ -62,10 +62,10 @@ KERNEL_LABEL = {
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
-    "pmb3": {"bytes": 21880064 + 0, "sha": "baf798de980efd6f",
+    "pmb3": {"bytes": 21880064 + 256, "sha": "431684c1e40529ae",
              "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
              "profile": "profiles/pmb_fast_block3d_64.md"},
-    "lps": {"bytes": (109672704 + 6481664) + (195561472 + 97338112), "sha": "d741cb3a3b0e2293",
+    "lps": {"bytes": (109638144 + 6081280) + (195538432 + 96884480), "sha": "eacfbe8eda1ec707",
             "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
             "profile": "profiles/lps_block3d_128.md"},
 }
