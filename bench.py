@@ -40,6 +40,12 @@ SM_MAX_MHZ = 2070.0
 # FP32 arithmetic of one bond as the kernels evaluate it (hand count; an FMA is
 # one operation; the 2 MUFU ops per bond are not included).
 FP32_OPS_PER_BOND = {"pmb3": 24, "pmb2": 18, "lps_dil": 19, "lps_force": 30}
+# FP64 path (pmb_generic<double>): the arithmetic of one bond as written, flops
+# with an FMA as 2 and rsqrt, divide as one each (their expansion into several
+# FP64 instructions is not counted): eta, y 6; |y|^2 5; numerator 10; rsqrt 1;
+# stretch 6; weight 1; force 6 (plus 2 for the partial-volume factor when on).
+FP64_OPS_PER_BOND = 35
+FP64_NOMINAL_TFLOPS = 1.25
 
 # Algorithmic bytes per point of one step, in the kernels' layout (u and v as
 # double-float pairs, 2 x float4 = 32 B each): u read 32, v read + written 64,
@@ -401,10 +407,22 @@ def cpu_baseline(wl, target_s=12.0, max_steps=50):
     t2 = time.time()
     st.run(dt, n)
     el = time.time() - t2
-    return {"value": bonds.nbonds * n / el, "unit": "bond-updates/s", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": "%d explicit steps of the full workload (FP64 C oracle, OpenMP over points); "
-                      "setup %.1f s not timed" % (n, setup)}, bonds.nbonds
+    out = {"value": bonds.nbonds * n / el, "unit": "bond-updates/s", "cores": O.num_threads(),
+           "kind": "oracle",
+           "sample": "%d explicit steps of the full workload (FP64 C oracle, OpenMP over points); "
+                     "setup %.1f s not timed" % (n, setup)}
+    # the same oracle on one thread, a few steps
+    threads = O.num_threads()
+    try:
+        O.set_num_threads(1)
+        t3 = time.time()
+        n1 = max(1, min(3, int(target_s / 4 / (one * threads))))
+        st.run(dt, n1)
+        el1 = time.time() - t3
+        out["single_thread"] = {"value": bonds.nbonds * n1 / el1, "steps": n1}
+    finally:
+        O.set_num_threads(threads)
+    return out, bonds.nbonds
 
 
 def run_reference(args):
@@ -569,7 +587,12 @@ def main():
         d64 = time_steps(pd, torch, sim64, wl, max(3, min(args.steps, 10)), 3, stream, flush)
         ms64 = float(np.mean(d64))
         line["fp64_path"] = {"value": nbonds / (ms64 * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms64,
-                             "steps": len(d64), "ratio_fp32c_over_fp64": ms64 / ms}
+                             "steps": len(d64), "ratio_fp32c_over_fp64": ms64 / ms,
+                             "fp64_ops_per_bond": FP64_OPS_PER_BOND,
+                             "fp64_tflops": FP64_OPS_PER_BOND * nbonds / (ms64 * 1e-3) / 1e12,
+                             "fp64_frac_of_nominal": FP64_OPS_PER_BOND * nbonds / (ms64 * 1e-3) / 1e12
+                             / FP64_NOMINAL_TFLOPS,
+                             "fp64_peak_source": "nominal GB300 FP64 rate (not measured on this pool)"}
         sim64.close()
         if args.workload == "block64":
             wl2, desc2 = workload("lps128")

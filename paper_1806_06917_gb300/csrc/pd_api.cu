@@ -78,6 +78,7 @@ struct pd_sim {
     int64_t step = 0;
     int v_is_half = 0;
     int cur = 0;
+    bool tangent_ok = true;     // the tangent's halo box fits at this tile size
     bool use_body = false;
     double c_dt = 0.0;          // micromodulus used by the stable-step bound
 
@@ -158,10 +159,12 @@ static void drop_graphs(pd_sim *s)
         }
 }
 
-static size_t max_smem(const Geom &g, int precision, int model)
+// Shared memory of the largest halo box any kernel of the simulation stages;
+// with_tangent includes the tangent (PMB only), which stages u and w.
+static size_t max_smem(const Geom &g, int precision, int model, bool with_tangent)
 {
-    size_t m = jvp_smem(g, precision);
-    m = std::max(m, energy_smem(g, precision));
+    size_t m = energy_smem(g, precision);
+    if (with_tangent) m = std::max(m, jvp_smem(g, precision));
     if (model != PD_MODEL_LPS)
         m = std::max(m, precision == PD_FP64 ? pmb_generic_smem(g, precision) : pmb_fast_smem(g));
     else m = std::max(m, lps_generic_smem(g, precision, false));
@@ -258,13 +261,25 @@ static int create_impl(pd_sim *s)
 
     // tile size: the requested one, or the largest brick (up to 2^9 points)
     // whose halo box fits in shared memory for every kernel of this simulation
+    // (the tangent's, if it fits at all: at wide horizons in FP64 its two boxes
+    // do not fit even in the smallest tile, and the tangent calls then refuse)
+    const int model = s->pmat.model;
+    bool tangent = model == PD_MODEL_PMB;
     if (s->run.tile_log2) {
         set_tile(s->run.tile_log2);
+        tangent = tangent && max_smem(g, s->precision, model, true) <= SMEM_LIMIT;
     } else {
         int L = 9;
         set_tile(L);
-        while (L > 6 && max_smem(g, s->precision, s->pmat.model) > SMEM_LIMIT) set_tile(--L);
+        while (L > 6 && max_smem(g, s->precision, model, tangent) > SMEM_LIMIT) set_tile(--L);
+        if (tangent && max_smem(g, s->precision, model, true) > SMEM_LIMIT) {
+            tangent = false;
+            L = 9;
+            set_tile(L);
+            while (L > 6 && max_smem(g, s->precision, model, false) > SMEM_LIMIT) set_tile(--L);
+        }
     }
+    s->tangent_ok = tangent;
 
     // tiles: bricks intersecting the grid, ordered by the Morton code of their origin
     struct TileKey { uint64_t code; int tx, ty, tz; };
@@ -287,7 +302,7 @@ static int create_impl(pd_sim *s)
         tlut[tiles[t].tx + g.tgx * (tiles[t].ty + g.tgy * tiles[t].tz)] = t;
     }
 
-    const size_t smem = max_smem(g, s->precision, s->pmat.model);
+    const size_t smem = max_smem(g, s->precision, s->pmat.model, false);
     if (smem > SMEM_LIMIT) {
         set_error("halo box needs %zu bytes of shared memory (> %zu); use a smaller tile_log2", smem, SMEM_LIMIT);
         return PD_EINVAL;
@@ -1073,6 +1088,10 @@ static int tangent(pd_sim *s, const double *u_lin, const double *w, double *out,
 {
     CHECK_BUILT(s);
     if (s->mat.model != PD_MODEL_PMB) { set_error("the tangent is implemented for PMB only"); return PD_EINVAL; }
+    if (!s->tangent_ok) {
+        set_error("the tangent's halo box does not fit in shared memory at this horizon and precision");
+        return PD_EINVAL;
+    }
     if (!w || !out) { set_error("null vector"); return PD_EINVAL; }
     cudaStream_t st = pick(s, stream);
     const float4 *hl;
@@ -1117,6 +1136,10 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
     if (o.max_linear_iters < 1 || o.max_newton_iters < 1) { set_error("iteration limits must be >= 1"); return PD_EINVAL; }
     if (o.tangent != PD_TANGENT_CACHED && o.tangent != PD_TANGENT_JVP) { set_error("unknown tangent mode"); return PD_EINVAL; }
     const bool cached = o.tangent == PD_TANGENT_CACHED;
+    if (!cached && !s->tangent_ok) {
+        set_error("the tangent's halo box does not fit in shared memory at this horizon and precision");
+        return PD_EINVAL;
+    }
     if (!(o.linear_rtol > 0.0) || !(o.newton_rtol >= 0.0) || !(o.newton_atol >= 0.0)) {
         set_error("tolerances must be linear_rtol > 0, newton_rtol >= 0, newton_atol >= 0");
         return PD_EINVAL;

@@ -138,6 +138,10 @@ int launch_tangent_prepare(const TileArgs &a, int precision, void *cache, cudaSt
     const size_t r = precision == PD_FP64 ? sizeof(double) : sizeof(float);
     int *nbr = reinterpret_cast<int *>(static_cast<char *>(cache) + (size_t)g.S * g.nslots * nc * r);
     const size_t smem = jvp_smem(g, precision) / 2;      // the u box alone
+    if (smem > 227 * 1024) {
+        set_error("the tangent cache's halo box (%zu bytes) does not fit in shared memory", smem);
+        return PD_EINVAL;
+    }
     if (precision == PD_FP64) {
         PD_CUDA(cudaFuncSetAttribute(tangent_prepare<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         tangent_prepare<double><<<g.ntiles, 256, smem, st>>>(a, static_cast<double *>(cache), nbr);

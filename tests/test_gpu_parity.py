@@ -463,3 +463,31 @@ def test_pmb_small_tiles_match_oracle(pd, tile_log2):
     f = pd.pd_force(sim, u=u)
     assert rel_l2(f, O.pmb_force(grid, mat, O.neighbors(grid), u)) <= FORCE_TOL_FP32C
     sim.close()
+
+
+LARGE_HORIZONS = [
+    (2, (60, 41, 1), 12, W.PMB), (2, (45, 38, 1), 8, W.NP), (3, (14, 13, 12), 6, W.PMB),
+    (3, (13, 12, 11), 5, W.LPS), (3, (12, 11, 10), 7, W.PMB),
+]
+
+
+@pytest.mark.parametrize("dim,n,m,model", LARGE_HORIZONS)
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_large_horizons_match_oracle(pd, dim, n, m, model, precision):
+    # wide stencils (up to 1436 offsets, 45 mask words): neighbour build, the
+    # automatic tile shrink of the shared-memory halo, and the force kernels
+    g = W.Grid(dim=dim, n=n, h=0.01, m=m)
+    mat = {W.PMB: W.Material(model=W.PMB), W.NP: W.Material(model=W.NP, rho=1.0, psi_beta=2.0),
+           W.LPS: W.Material(model=W.LPS, K=40e9, mu=30e9)}[model]
+    bonds = O.neighbors(g)
+    rng = np.random.default_rng(m)
+    u = rng.normal(0.0, 1e-3 * g.h, (g.npoints, dim))
+    if model == W.NP:
+        u = rng.normal(0.0, 0.2 * g.h, (g.npoints, dim))
+    prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
+    sim = gpu_sim(pd, g, mat, prec)
+    assert pd.pd_bond_count(sim) == bonds.nbonds
+    f_o, _ = O.internal_force(g, mat, bonds, u, O.weighted_volume(g, mat, bonds) if model == W.LPS else None)
+    f_g = pd.pd_force(sim, u=u)
+    assert rel_l2(f_g, f_o) <= (FORCE_TOL_FP32C if precision == "fp32c" else 1e-10)
+    sim.close()
