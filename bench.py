@@ -291,7 +291,7 @@ def run_serving(args, pd, torch):
     serial_work = sum(x["bonds"] * r.steps for x, r in zip(sres, mix[:k]))
     capacity = k / serial_s
     rate = args.load * capacity
-    srv = pd.Server(max_active=args.max_active, quantum_steps=64)
+    srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum)
     with Clocks(0) as clk:
         t0 = time.perf_counter()
         tickets = []
@@ -314,7 +314,7 @@ def run_serving(args, pd, torch):
             "config": {"workload": "serving_mix: %d requests (2D/3D, PMB/LPS, lognormal sides 20..96, "
                                    "m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
                                    "one-at-a-time capacity" % (len(mix), args.load),
-                       "max_active": args.max_active, "quantum_steps": 64, "l2": "not flushed (independent "
+                       "max_active": args.max_active, "quantum_steps": args.quantum, "l2": "not flushed (independent "
                        "simulations stream through it)"},
             "all_done": ok, "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
@@ -466,6 +466,7 @@ def main():
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
     ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")
     ap.add_argument("--serial-sample", type=int, default=24, help="serve: requests timed one at a time")
+    ap.add_argument("--quantum", type=int, default=64, help="serve: steps per scheduling quantum")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path and LPS side measurements")
     args = ap.parse_args()

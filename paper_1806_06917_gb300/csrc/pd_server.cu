@@ -6,9 +6,11 @@
 // whole simulations on one GPU.
 //
 // Threads: the caller's threads only touch the queue and the ticket records
-// (under one mutex); one worker thread owns every simulation, stream and event.
-// Every wait of the worker is bounded (event queries with short sleeps, timed
-// condition-variable waits).
+// (under one mutex). A setup thread builds each admitted simulation (tables,
+// neighbour build, initial state) while the worker thread keeps stepping the
+// running ones; from then on the worker owns the simulation, its stream and
+// event. Every wait of either thread is bounded (event queries with short
+// sleeps, timed condition-variable waits).
 #include <string.h>
 
 #include <chrono>
@@ -95,13 +97,18 @@ struct pd_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req *> queue;
+    std::deque<Req *> setup_q;      // admitted, waiting for the setup thread
+    std::vector<Req *> ready;       // set up, waiting for the worker
+    int in_setup = 0;               // admitted but not yet handed to the worker
+    std::condition_variable cv_setup;
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
-    std::thread worker;
+    std::thread worker, setup_worker;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void run();
+    void run_setup();
     int setup(Req *r);
     void teardown(Req *r);
     void finish(Req *r, int state, int error, const char *msg);   // caller holds mu
@@ -151,6 +158,42 @@ void pd_server::teardown(Req *r)
     r->inflight = 0;
 }
 
+void pd_server::run_setup()
+{
+    cudaSetDevice(device);
+    while (true) {
+        Req *r = nullptr;
+        bool cancel = false;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            while (setup_q.empty() && !stop) cv_setup.wait_for(lk, std::chrono::milliseconds(20));
+            if (setup_q.empty()) break;                     // stop with nothing left
+            r = setup_q.front();
+            setup_q.pop_front();
+            cancel = r->cancel || stop;
+        }
+        int rc = PD_OK;
+        char msg[160] = {0};
+        if (!cancel) {
+            rc = setup(r);
+            if (rc != PD_OK) pd_last_error(msg, sizeof(msg));
+        }
+        if (cancel || rc != PD_OK) teardown(r);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (cancel || rc != PD_OK) {
+                used -= r->est_bytes;
+                --in_setup;
+                if (cancel) finish(r, PD_REQ_CANCELLED, PD_OK, nullptr);
+                else finish(r, PD_REQ_FAILED, rc, msg);
+            } else {
+                ready.push_back(r);
+            }
+        }
+        cv_work.notify_all();
+    }
+}
+
 void pd_server::run()
 {
     cudaSetDevice(device);
@@ -159,8 +202,14 @@ void pd_server::run()
         std::vector<Req *> admitted;
         {
             std::unique_lock<std::mutex> lk(mu);
-            // admission in submission order; the head of the queue waits for memory
-            while (!queue.empty() && (int)active.size() + (int)admitted.size() < max_active) {
+            for (Req *r : ready) {
+                --in_setup;
+                active.push_back(r);
+            }
+            ready.clear();
+            // admission in submission order; the head of the queue waits for memory.
+            // Nothing is admitted once stopping (the setup thread may have exited).
+            while (!stop && !queue.empty() && (int)active.size() + in_setup < max_active) {
                 Req *r = queue.front();
                 if (r->cancel) {
                     queue.pop_front();
@@ -172,31 +221,21 @@ void pd_server::run()
                 used += r->est_bytes;
                 r->res.state = PD_REQ_RUNNING;
                 r->res.start_s = now();
+                setup_q.push_back(r);
+                ++in_setup;
                 admitted.push_back(r);
             }
-            if (stop && admitted.empty()) {
+            if (!admitted.empty()) cv_setup.notify_one();
+            if (stop) {
                 for (Req *r : queue) finish(r, PD_REQ_CANCELLED, PD_OK, nullptr);
                 queue.clear();
                 for (Req *r : active) r->cancel = true;
-                if (active.empty()) break;
+                if (active.empty() && in_setup == 0) break;
             }
-            if (active.empty() && admitted.empty()) {
+            if (active.empty()) {
                 cv_work.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
-        }
-        for (Req *r : admitted) {
-            const int rc = setup(r);
-            if (rc != PD_OK) {
-                char msg[160];
-                pd_last_error(msg, sizeof(msg));
-                teardown(r);
-                std::lock_guard<std::mutex> lk(mu);
-                used -= r->est_bytes;
-                finish(r, PD_REQ_FAILED, rc, msg);
-                continue;
-            }
-            active.push_back(r);
         }
         // issue the next quantum of every idle simulation
         for (Req *r : active) {
@@ -293,6 +332,7 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
     s->quantum = o.quantum_steps;
     s->t0 = Clock::now();
     pd_server *raw = s.get();
+    s->setup_worker = std::thread([raw] { raw->run_setup(); });
     s->worker = std::thread([raw] { raw->run(); });
     *out = s.release();
     return PD_OK;
@@ -306,7 +346,9 @@ int pd_server_destroy(pd_server *s)
         s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_setup.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    if (s->setup_worker.joinable()) s->setup_worker.join();
     delete s;
     return PD_OK;
 }
