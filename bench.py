@@ -153,6 +153,26 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------ several ranks
+# One process per GPU (torchrun). The explicit step does not shard: every rank
+# runs its own replica, and ranks meet only to take the slowest rank's time.
+# The request mix does shard: rank r serves requests r, r + N, r + 2N, ...
+
+
+def rank_reduce(torch, x: float, op: str, device: str) -> float:
+    """x reduced over the ranks (op "max" or "sum"); x itself on one rank."""
+    if not torch.distributed.is_initialized() or torch.distributed.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX if op == "max" else torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(items, rank: int, world: int):
+    """This rank's share of independent work units (round robin)."""
+    return items[rank::world]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -276,11 +296,13 @@ def _submit_request(pd, srv, r):
     return pd.pd_submit(srv, g, m, run, r.steps, u0=r.u0)
 
 
-def run_serving(args, pd, torch):
+def run_serving(args, pd, torch, rank=0, world=1):
     """The request mix through the server: one-at-a-time capacity on a sample
     (max_active = 1), then the whole mix arriving as a Poisson process at
-    args.load x that capacity, max_active concurrent simulations."""
-    mix = W.serving_mix(count=args.requests)
+    args.load x that capacity, max_active concurrent simulations. With N ranks
+    each serves its round-robin share of the mix (arrivals at N x the rate of
+    one rank's share), with no collective until the totals are combined."""
+    mix = shard(W.serving_mix(count=args.requests), rank, world)
     k = min(args.serial_sample, len(mix))
     srv = pd.Server(max_active=1, quantum_steps=64)
     _submit_request(pd, srv, mix[0])                       # warm-up (module load, first graph)
@@ -290,9 +312,11 @@ def run_serving(args, pd, torch):
     srv.close()
     serial_work = sum(x["bonds"] * r.steps for x, r in zip(sres, mix[:k]))
     capacity = k / serial_s
-    rate = args.load * capacity
+    # the shard holds every world-th arrival of the global process, so the global
+    # rate world x load x capacity offers each rank load x its own capacity
+    rate = world * args.load * capacity
     srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum)
-    with Clocks(0) as clk:
+    with Clocks(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         tickets = []
         for r in mix:
@@ -303,17 +327,26 @@ def run_serving(args, pd, torch):
         res = [pd.pd_wait(srv, t, timeout_s=3600.0) for t in tickets]
     srv.close()
     ok = all(x["state"] == pd.PD_REQ_DONE for x in res)
-    work = sum(x["bonds"] * r.steps for x, r in zip(res, mix))
-    makespan = max(x["end_s"] for x in res) - min(x["submit_s"] for x in res)
+    work = rank_reduce(torch, float(sum(x["bonds"] * r.steps for x, r in zip(res, mix))), "sum", "cuda")
+    makespan = rank_reduce(torch, max(x["end_s"] for x in res) - min(x["submit_s"] for x in res), "max", "cuda")
     lat = np.array([x["end_s"] - x["submit_s"] for x in res])
+    if world > 1:
+        parts = [None] * world
+        torch.distributed.all_gather_object(parts, lat.tolist())
+        lat = np.array([x for part in parts for x in part])
+        ok = bool(rank_reduce(torch, 1.0 if ok else 0.0, "sum", "cuda") == world)
+    if rank != 0:
+        return
     line = {"metric": "aggregate bond updates/s (served request mix)", "value": work / makespan,
-            "unit": "bond-updates/s", "n_gpus": 1, "steps": len(mix), "warmup": 1,
-            "ms_per_step": 1e3 * makespan / len(mix), "higher_is_better": True, "scaling": "weak",
+            "unit": "bond-updates/s", "n_gpus": world, "steps": len(lat), "warmup": 1,
+            "ms_per_step": 1e3 * makespan / len(lat), "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak",
             "vs_baseline": None, "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)",
             "data": "synthetic",
             "config": {"workload": "serving_mix: %d requests (2D/3D, PMB/LPS, lognormal sides 20..96, "
                                    "m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
-                                   "one-at-a-time capacity" % (len(mix), args.load),
+                                   "one-at-a-time capacity" % (args.requests, args.load),
+                       "parallelism": "requests sharded round robin over %d rank(s)" % world,
                        "max_active": args.max_active, "quantum_steps": args.quantum, "l2": "not flushed (independent "
                        "simulations stream through it)"},
             "all_done": ok, "latency_p50_s": float(np.percentile(lat, 50)),
@@ -486,8 +519,9 @@ def main():
     from paper_1806_06917_gb300 import pd
 
     if args.workload == "serve":
-        if rank == 0:
-            run_serving(args, pd, torch)
+        run_serving(args, pd, torch, rank, world)
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     if args.workload == "convergence":
         if rank == 0:
@@ -513,11 +547,7 @@ def main():
         durs = time_steps(pd, torch, sim, wl, args.steps, args.warmup, stream, flush)
         t_wall = time.time() - t_wall
     barrier()
-    ms = float(np.mean(durs))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_reduce(torch, float(np.mean(durs)), "max", "cuda")
     value = world * nbonds / (ms * 1e-3)
 
     # end to end through the public API, host buffers every step: the state
@@ -539,11 +569,7 @@ def main():
         pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = rank_reduce(torch, e0.elapsed_time(e1), "max", "cuda")
     e2e = {"value": world * nbonds * args.steps / (e2e_ms * 1e-3), "unit": "bond-updates/s",
            "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8,
            "d2h_bytes_per_step": u_o.numel() * 8,
