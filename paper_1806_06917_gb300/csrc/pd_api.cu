@@ -582,24 +582,58 @@ static int upload_user(pd_sim *s, const void *src, size_t bytes, cudaStream_t st
     return PD_OK;
 }
 
+// An address of the caller's array that the simulation's kernels can use in
+// place: device or managed memory of this device (no staging copy). Host
+// memory, pinned or not, goes through a copy into the library's staging buffer:
+// on GB300 the copy engine moves a pinned host array at the link's rate, and
+// kernels reading pinned host memory directly measured no faster.
+static void *direct_ptr(const pd_sim *s, const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();     // clear the error of an unknown pointer
+        return nullptr;
+    }
+    if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == s->device)
+        return at.devicePointer;
+    return nullptr;
+}
+
+// The user array as the kernels read it: in place when possible, else uploaded.
+static int user_source(pd_sim *s, const double *user, const double **src, cudaStream_t st)
+{
+    *src = static_cast<const double *>(direct_ptr(s, user));
+    if (*src) return PD_OK;
+    int rc = upload_user(s, user, sizeof(double) * s->g.npoints * s->g.dim, st);
+    *src = s->io;
+    return rc;
+}
+
 // Scatter a user-order (n x dim) FP64 vector into slot-order SoA arrays.
 static int user_to_slots(pd_sim *s, const double *user, double *const dst[3], cudaStream_t st)
 {
-    int rc = upload_user(s, user, sizeof(double) * s->g.npoints * s->g.dim, st);
+    const double *src = nullptr;
+    int rc = user_source(s, user, &src, st);
     if (rc != PD_OK) return rc;
     Tables t = {};
     t.slot_of_user = s->slot_of_user;
-    return scatter_user_to_slots(s->g, t, s->io, dst, 0.0, st);
+    return scatter_user_to_slots(s->g, t, src, dst, 0.0, st);
+}
+
+// Slot arrays (hl: double-float pairs instead) to the caller's array, written in
+// place when the kernels can reach it, else through the staging buffer.
+static int to_user(pd_sim *s, const float4 *hl, double *const src[3], double *user, cudaStream_t st)
+{
+    double *dst = static_cast<double *>(direct_ptr(s, user));
+    int rc = gather_unstage(s->g, s->slot_of_user, hl, src, dst ? dst : s->io, st);
+    if (rc != PD_OK) return rc;
+    if (!dst) PD_CUDA(cudaMemcpyAsync(user, s->io, sizeof(double) * s->g.npoints * s->g.dim, cudaMemcpyDefault, st));
+    return PD_OK;
 }
 
 static int slots_to_user(pd_sim *s, double *const src[3], double *user, cudaStream_t st)
 {
-    Tables t = {};
-    t.slot_of_user = s->slot_of_user;
-    int rc = gather_slots_to_user(s->g, t, src, s->io, st);
-    if (rc != PD_OK) return rc;
-    PD_CUDA(cudaMemcpyAsync(user, s->io, sizeof(double) * s->g.npoints * s->g.dim, cudaMemcpyDefault, st));
-    return PD_OK;
+    return to_user(s, nullptr, src, user, st);
 }
 
 static int stage_lin(pd_sim *s, const double *u, const float4 **hl, const double4_32a **d4, cudaStream_t st)
@@ -899,16 +933,21 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     // a kept v must first be completed to the integer step; a replaced one not
     if (v) s->v_is_half = 0;
     else if ((rc = finalize(s, st)) != PD_OK) return rc;
+    // one pass per field from the uploaded user array: FP32C writes the
+    // double-float pairs the kernels read (its FP64 arrays are a view refreshed
+    // on demand), FP64 writes its SoA arrays and the double4 staging
+    const bool f32c = s->precision == PD_FP32C;
+    const double *src = nullptr;
     if (u) {
-        rc = user_to_slots(s, u, s->u, st);
-        if (rc != PD_OK) return rc;
-        rc = pack_stage(s->g, s->u, s->hl[s->cur], s->d4[s->cur], st);
+        if ((rc = user_source(s, u, &src, st)) != PD_OK) return rc;
+        rc = scatter_stage(s->g, s->slot_of_user, src, f32c ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
+                           f32c ? nullptr : s->d4[s->cur], st);
         if (rc != PD_OK) return rc;
     }
     if (v) {
-        rc = user_to_slots(s, v, s->v, st);
+        if ((rc = user_source(s, v, &src, st)) != PD_OK) return rc;
+        rc = scatter_stage(s->g, s->slot_of_user, src, f32c ? nullptr : s->v, f32c ? s->vhl : nullptr, nullptr, st);
         if (rc != PD_OK) return rc;
-        if (s->precision == PD_FP32C && (rc = pack_stage(s->g, s->v, s->vhl, nullptr, st)) != PD_OK) return rc;
     }
     return PD_OK;
 }
@@ -930,9 +969,11 @@ int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
     int rc = PD_OK;
     // u is always at the integer step; only v may need the completing half kick
     if (v && (rc = finalize(s, st)) != PD_OK) return rc;
-    if ((rc = unpack_state(s, st, u != nullptr, v != nullptr)) != PD_OK) return rc;
-    if (u && (rc = slots_to_user(s, s->u, u, st)) != PD_OK) return rc;
-    if (v && (rc = slots_to_user(s, s->v, v, st)) != PD_OK) return rc;
+    // one pass per field into user order: from the double-float pairs (FP32C)
+    // or the FP64 arrays, then one copy to the caller
+    const bool f32c = s->precision == PD_FP32C;
+    if (u && (rc = to_user(s, f32c ? s->hl[s->cur] : nullptr, s->u, u, st)) != PD_OK) return rc;
+    if (v && (rc = to_user(s, f32c ? s->vhl : nullptr, s->v, v, st)) != PD_OK) return rc;
     PD_CUDA(cudaStreamSynchronize(st));
     return PD_OK;
 }

@@ -664,14 +664,72 @@ __global__ void k_scatter(Geom g, const int *slot_of_user, const double *user, d
     for (int c = 0; c < g.dim; ++c) dst[c][s] = user[i * g.dim + c];
 }
 
-__global__ void k_gather(Geom g, const int *slot_of_user, const double *s0, const double *s1, const double *s2,
-                         double *user)
+// User order (n x dim FP64, AoS) to the slot of each point in one pass: the
+// FP64 SoA arrays if given, and the staging form if given (FP32C double-float
+// pair hi = fl(x), lo = fl(x - hi); FP64 double4).
+__global__ void k_scatter_stage(Geom g, const int *slot_of_user, const double *user, double *s0, double *s1,
+                                double *s2, float4 *hl, double4_32a *d4)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.npoints) return;
     const int s = slot_of_user[i];
-    const double *src[3] = {s0, s1, s2};
-    for (int c = 0; c < g.dim; ++c) user[i * g.dim + c] = src[c][s];
+    const int d = g.dim;
+    const double x = user[i * d], y = user[i * d + 1], z = d == 3 ? user[i * d + 2] : 0.0;
+    if (s0) {
+        s0[s] = x;
+        s1[s] = y;
+        if (d == 3) s2[s] = z;
+    }
+    if (d4) d4[s] = make_double4_32a(x, y, z, 0.0);
+    if (hl) {
+        const float hx = (float)x, hy = (float)y, hz = (float)z;
+        hl[2 * s] = make_float4(hx, hy, hz, 0.f);
+        hl[2 * s + 1] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
+    }
+}
+
+// The reverse: user order from the double-float pair (hl) or the FP64 SoA arrays.
+__global__ void k_gather_unstage(Geom g, const int *slot_of_user, const float4 *hl, const double *s0,
+                                 const double *s1, const double *s2, double *user)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.npoints) return;
+    const int s = slot_of_user[i];
+    const int d = g.dim;
+    double x, y, z;
+    if (hl) {
+        const float4 hi = hl[2 * s], lo = hl[2 * s + 1];
+        x = (double)hi.x + (double)lo.x;
+        y = (double)hi.y + (double)lo.y;
+        z = (double)hi.z + (double)lo.z;
+    } else {
+        x = s0[s];
+        y = s1[s];
+        z = d == 3 ? s2[s] : 0.0;
+    }
+    user[i * d] = x;
+    user[i * d + 1] = y;
+    if (d == 3) user[i * d + 2] = z;
+}
+
+int scatter_stage(const Geom &g, const int *slot_of_user, const double *user, double *const slot[3], float4 *hl,
+                  double4_32a *d4, cudaStream_t st)
+{
+    k_scatter_stage<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, slot_of_user, user, slot ? slot[0] : nullptr,
+                                                             slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
+                                                             hl, d4);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int gather_unstage(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
+                   cudaStream_t st)
+{
+    k_gather_unstage<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, slot_of_user, hl, slot ? slot[0] : nullptr,
+                                                              slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
+                                                              user);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
 }
 
 int scatter_user_to_slots(const Geom &g, const Tables &t, const double *user, double *const slot[3], double fill,
@@ -679,13 +737,6 @@ int scatter_user_to_slots(const Geom &g, const Tables &t, const double *user, do
 {
     (void)fill;
     k_scatter<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.slot_of_user, user, slot[0], slot[1], slot[2]);
-    PD_CUDA(cudaGetLastError());
-    return PD_OK;
-}
-
-int gather_slots_to_user(const Geom &g, const Tables &t, double *const slot[3], double *user, cudaStream_t st)
-{
-    k_gather<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, t.slot_of_user, slot[0], slot[1], slot[2], user);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

@@ -159,12 +159,15 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
 size_t krylov_partial_doubles(long long n, int kmax);
 int krylov_norm(const double *x, long long n, KrylovWork &wk, double *out, cudaStream_t st);
 
+// User order to slots with the staging form in one pass, and back (pd_build.cu).
+int scatter_stage(const Geom &g, const int *slot_of_user, const double *user, double *const slot[3], float4 *hl,
+                  double4_32a *d4, cudaStream_t st);
+int gather_unstage(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
+                   cudaStream_t st);
+
 // Permutations between user order (AoS n x dim) and slot order (SoA).
 int scatter_user_to_slots(const Geom &g, const Tables &t, const double *user, double *const slot[3],
                           double fill, cudaStream_t st);
-int gather_slots_to_user(const Geom &g, const Tables &t, double *const slot[3], double *user,
-                         cudaStream_t st);
-
 // Boundary-condition kinds (n x dim bytes, user order) into component-major
 // slot order; err[0] is set if a kind is unknown.
 int scatter_kinds(const Geom &g, const Tables &t, const uint8_t *user, uint8_t *kind, int *err, cudaStream_t st);
