@@ -232,7 +232,7 @@ def time_build(pd, torch, wl, stream, reps=3):
     return {"ms": best * 1e3, "bonds": nb, "bonds_per_s": nb / best}
 
 
-def time_implicit(pd, torch, krylov, precision, nx=200, tangent=None):
+def time_implicit(pd, torch, krylov, precision, nx=200, tangent=None, precond=0):
     """The 200 x 200 clamped plate (left collar u = 0, right collar u_x = 1e-4 W)
     in 10 load steps, one pd_solve_static per step (matrix-free Newton-Krylov,
     linear rtol 1e-8). Wall time of the whole load path and the iteration counts."""
@@ -245,7 +245,7 @@ def time_implicit(pd, torch, krylov, precision, nx=200, tangent=None):
     fp64 = precision == pd.PD_FP64
     opts = pd.newton_opts(krylov=krylov, restart=50, linear_rtol=1e-8, newton_rtol=1e-8 if fp64 else 1e-6,
                           max_newton_iters=20 if fp64 else 8,
-                          tangent=pd.PD_TANGENT_CACHED if tangent is None else tangent)
+                          tangent=pd.PD_TANGENT_CACHED if tangent is None else tangent, precond=precond)
     newton = lin = conv = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -641,6 +641,10 @@ def main():
                 "gmres50_fp64_jvp_tangent": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64,
                                                           tangent=pd.PD_TANGENT_JVP),
                 "cg_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64),
+                "gmres50_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64,
+                                                           precond=pd.PD_PRECOND_BLOCK_JACOBI),
+                "pcg_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64,
+                                                       precond=pd.PD_PRECOND_BLOCK_JACOBI),
                 "cg_fp32c": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP32C)}
             sim2.close()
 

@@ -267,13 +267,18 @@ int pd_vjp(pd_sim *sim, const double *u_lin, const double *v, double *out,
                                 streams it */
 #define PD_TANGENT_JVP 1     /* the JVP kernel of pd_jvp for every product (no cache) */
 
+#define PD_PRECOND_NONE 0
+#define PD_PRECOND_BLOCK_JACOBI 1   /* M = the d x d diagonal blocks sum_j D_ij of A (from
+                                       the cached tangent; CG becomes PCG, GMRES is
+                                       right-preconditioned) */
+
 typedef struct {
     int32_t krylov;           /* PD_KRYLOV_GMRES or PD_KRYLOV_CG */
     int32_t restart;          /* GMRES restart length, 1..500 (50) */
     int32_t max_linear_iters; /* per linear solve, >= 1 */
     int32_t max_newton_iters; /* >= 1 */
     int32_t tangent;          /* PD_TANGENT_CACHED or PD_TANGENT_JVP */
-    int32_t reserved;         /* 0 */
+    int32_t precond;          /* PD_PRECOND_NONE or PD_PRECOND_BLOCK_JACOBI (cached tangent) */
     double linear_rtol;       /* each solve: ||r - A du|| <= linear_rtol ||r|| */
     double newton_rtol;       /* stop when ||r|| <= newton_rtol ||r_0|| + newton_atol */
     double newton_atol;       /* N/m^3 */
@@ -298,8 +303,8 @@ typedef struct {
  * for PD_FP32C simulations (inexact Newton; the residual is FP64 in both). Bonds
  * do not break during the solve. On return u is the last iterate and v = 0.
  * PMB only (PD_EINVAL for LPS). opts == NULL takes the defaults in brackets and
- * GMRES, 20000 linear iterations, 20 Newton iterations, the cached tangent,
- * linear_rtol 1e-8, newton_rtol 1e-8, newton_atol 0. Returns PD_OK whether or not the test was met
+ * GMRES, 20000 linear iterations, 20 Newton iterations, the cached tangent, no
+ * preconditioner, linear_rtol 1e-8, newton_rtol 1e-8, newton_atol 0. Returns PD_OK whether or not the test was met
  * (see stats->converged; stats may be NULL); PD_EINVAL if CG meets a
  * non-positive curvature. Work buffers are allocated on the first call and
  * kept until pd_destroy. Synchronous. */

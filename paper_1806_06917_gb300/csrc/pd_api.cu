@@ -48,6 +48,10 @@ size_t tangent_cache_bytes(const Geom &g, int precision);
 int launch_tangent_prepare(const TileArgs &a, int precision, void *cache, cudaStream_t st);
 int launch_tangent_apply(const Geom &g, int precision, const void *cache, const int *user_of_slot,
                          const uint8_t *kind, const double *w, double *y, cudaStream_t st);
+int launch_tangent_jacobi(const Geom &g, int precision, void *cache, const int *user_of_slot, const uint8_t *kind,
+                          cudaStream_t st);
+int launch_tangent_precond(const Geom &g, int precision, const void *cache, const double *r, double *z,
+                           cudaStream_t st);
 size_t energy_smem(const Geom &g, int precision);
 int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st);
 int dirichlet_mask(const Geom &g, const uint8_t *kind, double *const v[3], const double *const w[3], int copy,
@@ -119,7 +123,7 @@ struct pd_sim {
     std::vector<void *> allocs;
     // Newton-Krylov work of pd_solve_static, allocated on first use
     double *nk_basis = nullptr, *nk_tmp = nullptr, *nk_partial = nullptr, *nk_dsc = nullptr;
-    double *nk_r = nullptr, *nk_du = nullptr;
+    double *nk_r = nullptr, *nk_du = nullptr, *nk_aux = nullptr;
     size_t nk_basis_n = 0, nk_partial_n = 0, nk_dsc_n = 0;
     void *nk_tan = nullptr;         // per-bond tangent cache
     size_t nk_tan_n = 0;
@@ -741,6 +745,13 @@ static int nk_apply_cached(void *ctx, const double *x, double *y, cudaStream_t s
     return launch_tangent_apply(s->g, s->precision, s->nk_tan, s->user_of_slot, s->bc_kind, x, y, st);
 }
 
+// z = M^-1 r with the block-Jacobi blocks of the cached tangent.
+static int nk_precond(void *ctx, const double *r, double *z, cudaStream_t st)
+{
+    pd_sim *s = static_cast<pd_sim *>(ctx);
+    return launch_tangent_precond(s->g, s->precision, s->nk_tan, r, z, st);
+}
+
 static int nk_reserve(double **p, size_t *have, size_t want, cudaStream_t st)
 {
     if (*p && *have >= want) return PD_OK;
@@ -800,7 +811,7 @@ int pd_destroy(pd_sim *s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaStream_t fs = s->stream;     // stream-ordered release after the simulation's own work
     for (void *p : s->allocs) lib_free(p, fs);
-    for (double *p : {s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc, s->nk_r, s->nk_du}) lib_free(p, fs);
+    for (double *p : {s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc, s->nk_r, s->nk_du, s->nk_aux}) lib_free(p, fs);
     lib_free(s->nk_tan, fs);
     lib_free(s->csr.row_ptr, fs);
     lib_free(s->csr.col, fs);
@@ -1170,13 +1181,16 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
 {
     CHECK_BUILT(s);
     if (s->mat.model != PD_MODEL_PMB) { set_error("the static solve needs the PMB tangent"); return PD_EINVAL; }
-    pd_newton_opts o = {PD_KRYLOV_GMRES, 50, 20000, 20, PD_TANGENT_CACHED, 0, 1e-8, 1e-8, 0.0};
+    pd_newton_opts o = {PD_KRYLOV_GMRES, 50, 20000, 20, PD_TANGENT_CACHED, PD_PRECOND_NONE, 1e-8, 1e-8, 0.0};
     if (opts) o = *opts;
     if (o.krylov != PD_KRYLOV_GMRES && o.krylov != PD_KRYLOV_CG) { set_error("unknown Krylov method"); return PD_EINVAL; }
     if (o.restart < 1 || o.restart > 500) { set_error("restart must be in [1, 500]"); return PD_EINVAL; }
     if (o.max_linear_iters < 1 || o.max_newton_iters < 1) { set_error("iteration limits must be >= 1"); return PD_EINVAL; }
     if (o.tangent != PD_TANGENT_CACHED && o.tangent != PD_TANGENT_JVP) { set_error("unknown tangent mode"); return PD_EINVAL; }
     const bool cached = o.tangent == PD_TANGENT_CACHED;
+    if (o.precond != PD_PRECOND_NONE && o.precond != PD_PRECOND_BLOCK_JACOBI) { set_error("unknown preconditioner"); return PD_EINVAL; }
+    const bool jacobi = o.precond == PD_PRECOND_BLOCK_JACOBI;
+    if (jacobi && !cached) { set_error("the block-Jacobi preconditioner needs the cached tangent"); return PD_EINVAL; }
     if (!cached && !s->tangent_ok) {
         set_error("the tangent's halo box does not fit in shared memory at this horizon and precision");
         return PD_EINVAL;
@@ -1198,6 +1212,7 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
         if ((rc = nk_reserve(&s->nk_tmp, &hr, (size_t)n, st)) != PD_OK) return rc;
         if ((rc = nk_reserve(&s->nk_r, &hr, (size_t)n, st)) != PD_OK) return rc;
         if ((rc = nk_reserve(&s->nk_du, &hd, (size_t)n, st)) != PD_OK) return rc;
+        if ((rc = nk_reserve(&s->nk_aux, &hd, 2 * (size_t)n, st)) != PD_OK) return rc;
     }
     const size_t tan_bytes = cached ? tangent_cache_bytes(g, s->precision) : 0;
     if (s->nk_tan_n < tan_bytes) {
@@ -1211,8 +1226,8 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
         }
         s->nk_tan_n = tan_bytes;
     }
-    KrylovWork wk{s->nk_basis, s->nk_tmp, s->nk_partial, s->nk_dsc};
-    KrylovOp op{cached ? nk_apply_cached : nk_apply, s};
+    KrylovWork wk{s->nk_basis, s->nk_tmp, s->nk_aux, s->nk_partial, s->nk_dsc};
+    KrylovOp op{cached ? nk_apply_cached : nk_apply, s, jacobi ? nk_precond : nullptr};
     const unsigned nbs = (unsigned)((g.nslots + 255) / 256);
 
     // the iterate lives in the FP64 slot arrays u; the prescribed values first
@@ -1239,6 +1254,8 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
         if (cached) {
             TileArgs ta = make_args(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur]);
             if ((rc = launch_tangent_prepare(ta, s->precision, s->nk_tan, st)) != PD_OK) return rc;
+            if (jacobi && (rc = launch_tangent_jacobi(g, s->precision, s->nk_tan, s->user_of_slot, s->bc_kind, st)) != PD_OK)
+                return rc;
         }
         KrylovStats ks = {0, 0, 0.0, 0.0};
         rc = o.krylov == PD_KRYLOV_GMRES

@@ -140,10 +140,12 @@ int validate_description(const pd_grid *gr, const pd_material *mt, const pd_run 
 struct KrylovOp {
     int (*apply)(void *ctx, const double *x, double *y, cudaStream_t st);   // y = A x
     void *ctx;
+    int (*precond)(void *ctx, const double *r, double *z, cudaStream_t st); // z = M^-1 r, or null
 };
 struct KrylovWork {
     double *basis;      // GMRES: (restart + 1) * n; CG: 3 * n
     double *tmp;        // n
+    double *aux;        // 2 * n (preconditioned solves)
     double *partial;    // krylov_partial_doubles(n, restart)
     double *dsc;        // restart + 2
 };

@@ -149,7 +149,9 @@ static int norm2(KrylovCtx &c, const double *x, double *out)
 // ------------------------------------------------------------------ GMRES(m)
 
 // Restarted GMRES with classical Gram-Schmidt applied twice (CGS2) and Givens
-// rotations: solve A x = b from x = 0 until ||b - A x|| <= rtol ||b||.
+// rotations: solve A x = b from x = 0 until ||b - A x|| <= rtol ||b||. With a
+// preconditioner M it is right-preconditioned (Arnoldi on A M^-1, x += M^-1 V y),
+// so the residual it monitors is the one of A x = b.
 int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, int restart, int maxit, double rtol,
                  KrylovWork &wk, KrylovStats *stats, cudaStream_t st)
 {
@@ -157,6 +159,8 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
     const int m = restart;
     double *V = wk.basis;                    // (m + 1) vectors of n
     double *w = wk.tmp;
+    double *zt = wk.aux, *ty = wk.aux + n;   // M^-1 v_j; V y before M^-1
+    const bool pc = op.precond != nullptr;
     PD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     double bnorm = 0.0;
     int rc = norm2(c, b, &bnorm);
@@ -197,7 +201,12 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
         int k = 0;
         for (int j = 0; j < m && stats->iters < maxit; ++j) {
             double *vj1 = V + (long long)(j + 1) * n;
-            if ((rc = op.apply(op.ctx, V + (long long)j * n, vj1, st)) != PD_OK) return rc;
+            const double *src = V + (long long)j * n;
+            if (pc) {
+                if ((rc = op.precond(op.ctx, src, zt, st)) != PD_OK) return rc;
+                src = zt;
+            }
+            if ((rc = op.apply(op.ctx, src, vj1, st)) != PD_OK) return rc;
             // CGS2: h = V^T w, w -= V h; twice
             if ((rc = dots(c, V, n, j + 1, vj1, nullptr)) != PD_OK) return rc;
             if ((rc = lincomb_dev(c, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return rc;
@@ -237,25 +246,36 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
             const double d = H[i + (size_t)(m + 1) * i];
             y[i] = d != 0.0 ? t / d : 0.0;
         }
-        if (k > 0 && (rc = lincomb_host(c, x, 1.0, V, n, k, y.data())) != PD_OK) return rc;
+        if (k > 0 && !pc && (rc = lincomb_host(c, x, 1.0, V, n, k, y.data())) != PD_OK) return rc;
+        if (k > 0 && pc) {
+            // x += M^-1 (V y)
+            if ((rc = lincomb_host(c, ty, 0.0, V, n, k, y.data())) != PD_OK) return rc;
+            if ((rc = op.precond(op.ctx, ty, zt, st)) != PD_OK) return rc;
+            if ((rc = axpby(c, 1.0, zt, 1.0, x)) != PD_OK) return rc;
+        }
     }
 }
 
 // ------------------------------------------------------------------------ CG
 
 // Conjugate gradients for symmetric positive definite A: x = 0 start, stop when
-// ||b - A x|| <= rtol ||b|| (recursive residual) or after maxit iterations.
+// ||b - A x|| <= rtol ||b|| (recursive residual) or after maxit iterations. With
+// a symmetric positive definite preconditioner M it is PCG (p from z = M^-1 r).
 int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int maxit, double rtol, KrylovWork &wk,
               KrylovStats *stats, cudaStream_t st)
 {
     KrylovCtx c{n, st, wk.partial, wk.dsc, {}};
     double *r = wk.basis, *p = wk.basis + n, *q = wk.basis + 2 * n;
+    double *z = op.precond ? wk.aux : r;       // without M, z is r itself
     PD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     PD_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    PD_CUDA(cudaMemcpyAsync(p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    double rr = 0.0;
-    int rc = dots(c, r, 0, 1, r, &rr);
-    if (rc != PD_OK) return rc;
+    int rc = PD_OK;
+    if (op.precond && (rc = op.precond(op.ctx, r, z, st)) != PD_OK) return rc;
+    PD_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    double rr = 0.0, rz = 0.0;
+    if ((rc = dots(c, r, 0, 1, r, &rr)) != PD_OK) return rc;
+    rz = rr;
+    if (op.precond && (rc = dots(c, r, 0, 1, z, &rz)) != PD_OK) return rc;
     stats->res0 = sqrt(rr);
     stats->res = stats->res0;
     stats->iters = 0;
@@ -269,7 +289,7 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
             set_error("CG: the operator is not positive definite (p.Ap = %g)", pq);
             return PD_EINVAL;
         }
-        const double alpha = rr / pq;
+        const double alpha = rz / pq;
         if ((rc = axpby(c, alpha, p, 1.0, x)) != PD_OK) return rc;
         if ((rc = axpby(c, -alpha, q, 1.0, r)) != PD_OK) return rc;
         double rr1 = 0.0;
@@ -280,8 +300,13 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
             stats->converged = 1;
             break;
         }
-        if ((rc = axpby(c, 1.0, r, rr1 / rr, p)) != PD_OK) return rc;     // p = r + beta p
-        rr = rr1;
+        double rz1 = rr1;
+        if (op.precond) {
+            if ((rc = op.precond(op.ctx, r, z, st)) != PD_OK) return rc;
+            if ((rc = dots(c, r, 0, 1, z, &rz1)) != PD_OK) return rc;
+        }
+        if ((rc = axpby(c, 1.0, z, rz1 / rz, p)) != PD_OK) return rc;     // p = z + beta p
+        rz = rz1;
     }
     return PD_OK;
 }

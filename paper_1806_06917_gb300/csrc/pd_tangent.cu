@@ -124,11 +124,113 @@ __global__ void __launch_bounds__(256) tangent_apply(Geom g, const R *coef, cons
     }
 }
 
-size_t tangent_cache_bytes(const Geom &g, int precision)
+// Block-Jacobi preconditioner of A: the d x d diagonal block of point i is
+// A_ii = sum_j D_ij (from (K w)_i = sum_j D_ij (w_j - w_i) and A = -K); a
+// prescribed component gets an identity row and column, as A has. Its inverse is
+// stored per slot (3 or 6 FP64 values); slots without a point store I.
+template <class R>
+__global__ void tangent_jacobi_prepare(Geom g, const R *coef, const int *user_of_slot, const uint8_t *kind,
+                                       double *inv)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const size_t ns = g.nslots;
+    const int d = g.dim, nc = d == 3 ? 6 : 3;
+    double B[6] = {0, 0, 0, 0, 0, 0};     // xx xy yy xz yz zz
+    if (user_of_slot[s] >= 0)
+        for (int k = 0; k < g.S; ++k)
+            for (int c = 0; c < nc; ++c) B[c] += (double)coef[((size_t)k * nc + c) * ns + s];
+    else {
+        B[0] = B[2] = B[5] = 1.0;
+    }
+    // prescribed components: identity row and column
+    const int diag[3] = {0, 2, 5};
+    for (int c = 0; c < d; ++c) {
+        if (user_of_slot[s] < 0 || kind[(size_t)c * ns + s] != PD_BC_DISPLACEMENT) continue;
+        if (c == 0) { B[1] = 0.0; B[3] = 0.0; }
+        if (c == 1) { B[1] = 0.0; B[4] = 0.0; }
+        if (c == 2) { B[3] = 0.0; B[4] = 0.0; }
+        B[diag[c]] = 1.0;
+    }
+    double *o = inv;
+    if (d == 2) {
+        const double det = B[0] * B[2] - B[1] * B[1];
+        const double id = det != 0.0 ? 1.0 / det : 0.0;
+        o[s] = B[2] * id;
+        o[ns + s] = -B[1] * id;
+        o[2 * ns + s] = B[0] * id;
+    } else {
+        // symmetric 3 x 3 inverse by cofactors
+        const double a = B[0], b = B[1], c = B[3], e = B[2], f = B[4], i = B[5];
+        const double A0 = e * i - f * f, A1 = -(b * i - c * f), A2 = b * f - c * e;
+        const double det = a * A0 + b * A1 + c * A2;
+        const double id = det != 0.0 ? 1.0 / det : 0.0;
+        o[s] = A0 * id;                          // xx
+        o[ns + s] = A1 * id;                     // xy
+        o[2 * ns + s] = (a * i - c * c) * id;    // yy
+        o[3 * ns + s] = A2 * id;                 // xz
+        o[4 * ns + s] = -(a * f - b * c) * id;   // yz
+        o[5 * ns + s] = (a * e - b * b) * id;    // zz
+    }
+}
+
+// z = M^-1 r with the stored inverse blocks
+__global__ void tangent_jacobi_apply(Geom g, const double *inv, const double *r, double *z)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const size_t ns = g.nslots;
+    const double r0 = r[s], r1 = r[ns + s];
+    const double xx = inv[s], xy = inv[ns + s], yy = inv[2 * ns + s];
+    if (g.dim == 2) {
+        z[s] = xx * r0 + xy * r1;
+        z[ns + s] = xy * r0 + yy * r1;
+        return;
+    }
+    const double r2 = r[2 * ns + s];
+    const double xz = inv[3 * ns + s], yz = inv[4 * ns + s], zz = inv[5 * ns + s];
+    z[s] = xx * r0 + xy * r1 + xz * r2;
+    z[ns + s] = xy * r0 + yy * r1 + yz * r2;
+    z[2 * ns + s] = xz * r0 + yz * r1 + zz * r2;
+}
+
+// Cache layout: D [S][nc][nslots] (precision R), neighbour [S][nslots] int, and
+// the preconditioner's inverse blocks [nc][nslots] FP64 (8-byte aligned).
+static size_t cache_inv_offset(const Geom &g, int precision)
 {
     const size_t nc = g.dim == 3 ? 6 : 3;
     const size_t r = precision == PD_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)g.S * g.nslots * (nc * r + sizeof(int));
+    const size_t b = (size_t)g.S * g.nslots * (nc * r + sizeof(int));
+    return (b + 7) & ~(size_t)7;
+}
+
+size_t tangent_cache_bytes(const Geom &g, int precision)
+{
+    const size_t nc = g.dim == 3 ? 6 : 3;
+    return cache_inv_offset(g, precision) + nc * g.nslots * sizeof(double);
+}
+
+int launch_tangent_jacobi(const Geom &g, int precision, void *cache, const int *user_of_slot, const uint8_t *kind,
+                          cudaStream_t st)
+{
+    double *inv = reinterpret_cast<double *>(static_cast<char *>(cache) + cache_inv_offset(g, precision));
+    const unsigned nb = (unsigned)((g.nslots + 255) / 256);
+    if (precision == PD_FP64)
+        tangent_jacobi_prepare<double><<<nb, 256, 0, st>>>(g, static_cast<const double *>(cache), user_of_slot, kind, inv);
+    else
+        tangent_jacobi_prepare<float><<<nb, 256, 0, st>>>(g, static_cast<const float *>(cache), user_of_slot, kind, inv);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int launch_tangent_precond(const Geom &g, int precision, const void *cache, const double *r, double *z,
+                           cudaStream_t st)
+{
+    const double *inv =
+        reinterpret_cast<const double *>(static_cast<const char *>(cache) + cache_inv_offset(g, precision));
+    tangent_jacobi_apply<<<(unsigned)((g.nslots + 255) / 256), 256, 0, st>>>(g, inv, r, z);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
 }
 
 int launch_tangent_prepare(const TileArgs &a, int precision, void *cache, cudaStream_t st)

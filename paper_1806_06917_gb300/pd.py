@@ -26,6 +26,7 @@ PD_FORCE_UPDATE_BREAKING = 1
 PD_JVP_MASK_DIRICHLET = 1
 PD_KRYLOV_GMRES, PD_KRYLOV_CG = 0, 1
 PD_TANGENT_CACHED, PD_TANGENT_JVP = 0, 1
+PD_PRECOND_NONE, PD_PRECOND_BLOCK_JACOBI = 0, 1
 PD_REQ_QUEUED, PD_REQ_RUNNING, PD_REQ_DONE, PD_REQ_CANCELLED, PD_REQ_FAILED = 0, 1, 2, 3, 4
 
 if not os.path.exists(LIB_PATH):
@@ -53,7 +54,7 @@ class pd_run(ctypes.Structure):
 
 class pd_newton_opts(ctypes.Structure):
     _fields_ = [("krylov", ctypes.c_int32), ("restart", ctypes.c_int32), ("max_linear_iters", ctypes.c_int32),
-                ("max_newton_iters", ctypes.c_int32), ("tangent", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_newton_iters", ctypes.c_int32), ("tangent", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("linear_rtol", ctypes.c_double),
                 ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double)]
 
@@ -319,9 +320,10 @@ def pd_vjp(sim: Sim, v, u_lin=None, out=None, flags: int = 0, stream=None):
 
 def newton_opts(krylov: int = PD_KRYLOV_GMRES, restart: int = 50, max_linear_iters: int = 20000,
                 max_newton_iters: int = 20, linear_rtol: float = 1e-8, newton_rtol: float = 1e-8,
-                newton_atol: float = 0.0, tangent: int = PD_TANGENT_CACHED) -> pd_newton_opts:
+                newton_atol: float = 0.0, tangent: int = PD_TANGENT_CACHED,
+                precond: int = PD_PRECOND_NONE) -> pd_newton_opts:
     """pd_newton_opts with the library's defaults."""
-    return pd_newton_opts(krylov, restart, max_linear_iters, max_newton_iters, tangent, 0, linear_rtol,
+    return pd_newton_opts(krylov, restart, max_linear_iters, max_newton_iters, tangent, precond, linear_rtol,
                           newton_rtol, newton_atol)
 
 

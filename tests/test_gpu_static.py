@@ -56,6 +56,39 @@ def test_fp64_static_solve_matches_oracle_newton(pd, variant, nx, ny, krylov, ta
     sim.close()
 
 
+@pytest.mark.parametrize("krylov", ["gmres", "cg"])
+def test_block_jacobi_preconditioned_solves_match_oracle(pd, krylov):
+    # the lattice operator's diagonal blocks are nearly uniform (they change only
+    # near the free edges), so block-Jacobi is not expected to cut iterations
+    # here; it must give the same root and not cost many more iterations
+    L = W.plate_static(nx=60, ny=30, strain=1e-4, variant="roller")
+    g = L.grid
+    u_o, _, ok = I.solve_static(g, L.mat, O.neighbors(g), np.zeros((g.npoints, 2)), L.bc_kind, L.bc_val)
+    assert ok
+    kr = pd.PD_KRYLOV_GMRES if krylov == "gmres" else pd.PD_KRYLOV_CG
+    iters = {}
+    for pc in (pd.PD_PRECOND_NONE, pd.PD_PRECOND_BLOCK_JACOBI):
+        sim = _static_sim(pd, L, pd.PD_FP64)
+        st = pd.pd_solve_static(sim, pd.newton_opts(krylov=kr, linear_rtol=1e-12, newton_rtol=1e-12, precond=pc))
+        assert st["converged"] == 1 and st["linear_failures"] == 0
+        u, _ = pd.pd_get_state(sim)
+        assert rel_l2(u, u_o) <= 1e-9
+        iters[pc] = st["linear_iters"]
+        sim.close()
+    assert iters[pd.PD_PRECOND_BLOCK_JACOBI] <= 1.2 * iters[pd.PD_PRECOND_NONE]
+
+
+def test_block_jacobi_needs_the_cached_tangent(pd):
+    L = W.plate_static(nx=20, ny=10, variant="clamped")
+    sim = _static_sim(pd, L, pd.PD_FP64)
+    for bad in (pd.newton_opts(precond=pd.PD_PRECOND_BLOCK_JACOBI, tangent=pd.PD_TANGENT_JVP),
+                pd.newton_opts(precond=9)):
+        with pytest.raises(pd.PdError) as e:
+            pd.pd_solve_static(sim, bad)
+        assert e.value.code == pd.PD_EINVAL
+    sim.close()
+
+
 @pytest.mark.parametrize("tangent", ["cached", "jvp"])
 def test_fp32c_static_solve_is_an_inexact_newton_to_the_same_root(pd, tangent):
     L = W.plate_static(nx=40, ny=20, strain=1e-4, variant="roller")
