@@ -181,8 +181,8 @@ def measured_peaks():
     return None
 
 
-def make_sim(pd, wl, precision, stream):
-    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision)
+def make_sim(pd, wl, precision, stream, integrator=0):
+    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, integrator=integrator)
     sim = pd.pd_create(g, m, r)
     pd.pd_build_neighbors(sim, stream)
     if wl.notch is not None:
@@ -621,6 +621,13 @@ def main():
                              / FP64_NOMINAL_TFLOPS,
                              "fp64_peak_source": "nominal GB300 FP64 rate (not measured on this pool)"}
         sim64.close()
+        # the same step with the central-difference drift (Eq. (10))
+        simcd = make_sim(pd, wl, pd.PD_FP32C, stream, integrator=pd.PD_INTEGRATOR_CD)
+        dcd = time_steps(pd, torch, simcd, wl, max(3, min(args.steps, 10)), 3, stream, flush)
+        mscd = float(np.mean(dcd))
+        line["central_difference"] = {"value": nbonds / (mscd * 1e-3), "unit": "bond-updates/s",
+                                      "ms_per_step": mscd, "steps": len(dcd), "ratio_over_verlet": mscd / ms}
+        simcd.close()
         if args.workload == "block64":
             wl2, desc2 = workload("lps128")
             sim2 = make_sim(pd, wl2, pd.PD_FP32C, stream)

@@ -111,6 +111,20 @@ typedef struct {
     double psi_beta;    /* NP / LP potential rate beta, > 0 for those models */
 } pd_material;
 
+/* Explicit integrators (Sec. 4.2.4 and its flow chart). Both give the same
+ * trajectory in exact arithmetic; they round differently.
+ * VERLET: v^{k+1/2} = v^k + dt/2 a^k, u^{k+1} = u^k + dt v^{k+1/2},
+ *         v^{k+1} = v^{k+1/2} + dt/2 a^{k+1}          (Eqs. (7)-(9))
+ * CD:     u^{k+1} = 2 u^k - u^{k-1} + dt^2 a^k          (Eq. (10))
+ * with a = (f + b) / rho. CD starts, and restarts after pd_set_state,
+ * pd_set_dt, pd_solve_static or pd_build_neighbors, with one velocity-Verlet
+ * step (the Taylor start u^1 = u^0 + dt v^0 + dt^2/2 a^0). Under CD the library
+ * still advances v by the two half-kicks, so pd_get_state and pd_energy report
+ * the same velocity as under VERLET; a prescribed velocity advances u by dt
+ * times its value and a prescribed displacement sets u, as under VERLET. */
+#define PD_INTEGRATOR_VERLET 0
+#define PD_INTEGRATOR_CD     1
+
 /* Run parameters. */
 typedef struct {
     double dt;          /* time step; 0 selects dt_factor * dt_crit with the
@@ -121,6 +135,8 @@ typedef struct {
     int32_t tile_log2;  /* points per tile = 2^tile_log2 (a Morton brick);
                            0 selects 9, or less when the halo box of a large
                            horizon would not fit in shared memory; 6..9 */
+    int32_t integrator; /* PD_INTEGRATOR_VERLET (0) or PD_INTEGRATOR_CD */
+    int32_t reserved;   /* must be 0 */
 } pd_run;
 
 typedef struct pd_sim pd_sim;

@@ -81,6 +81,7 @@ struct pd_sim {
     double dt = 0.0, dt_crit = 0.0;
     int64_t step = 0;
     int v_is_half = 0;
+    bool u_prev_ok = false;     // the other staging buffer holds u^{k-1} of the same dt
     int cur = 0;
     bool tangent_ok = true;     // the tangent's halo box fits at this tile size
     bool use_body = false;
@@ -208,6 +209,11 @@ static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
         return PD_EINVAL;
     }
     if (rn->dt < 0.0 || rn->dt_factor < 0.0) { set_error("dt and dt_factor must be >= 0"); return PD_EINVAL; }
+    if (rn->integrator != PD_INTEGRATOR_VERLET && rn->integrator != PD_INTEGRATOR_CD) {
+        set_error("unknown integrator");
+        return PD_EINVAL;
+    }
+    if (rn->reserved != 0) { set_error("pd_run.reserved must be 0"); return PD_EINVAL; }
     return PD_OK;
 }
 
@@ -504,6 +510,7 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.K = s->mat.K;
     a.model = s->mat.model;
     a.v_is_half = s->v_is_half;
+    a.cd = s->run.integrator == PD_INTEGRATOR_CD && s->u_prev_ok ? 1 : 0;
     a.update_breaking = s->mat.s_c > 0.0 ? 1 : 0;
     a.mode = mode;
     a.vol_corr = s->mat.vol_corr;
@@ -553,6 +560,7 @@ static int one_step(pd_sim *s, cudaStream_t st)
     if (rc != PD_OK) return rc;
     s->cur ^= 1;
     s->v_is_half = 1;
+    s->u_prev_ok = true;
     s->step += 1;
     return PD_OK;
 }
@@ -865,6 +873,7 @@ int pd_build_neighbors(pd_sim *s, void *stream)
     rc = pack_stage(s->g, s->u, s->hl[s->cur], s->d4[s->cur], st);
     if (rc != PD_OK) return rc;
     PD_CUDA(cudaStreamSynchronize(st));
+    s->u_prev_ok = false;
     s->built = true;
     return PD_OK;
 }
@@ -944,6 +953,7 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     // a kept v must first be completed to the integer step; a replaced one not
     if (v) s->v_is_half = 0;
     else if ((rc = finalize(s, st)) != PD_OK) return rc;
+    s->u_prev_ok = false;       // a central-difference run restarts from the new state
     // one pass per field from the uploaded user array: FP32C writes the
     // double-float pairs the kernels read (its FP64 arrays are a view refreshed
     // on demand), FP64 writes its SoA arrays and the double4 staging
@@ -1062,6 +1072,7 @@ int pd_set_dt(pd_sim *s, double dt)
         if (rc != PD_OK) return rc;
     }
     s->dt = dt;
+    s->u_prev_ok = false;
     drop_graphs(s);
     return PD_OK;
 }
@@ -1114,7 +1125,10 @@ int pd_step_explicit(pd_sim *s, int64_t nsteps, void *stream)
     if (nsteps < 0) { set_error("nsteps must be >= 0"); return PD_EINVAL; }
     cudaStream_t st = pick(s, stream);
     int rc = PD_OK;
-    if (nsteps > 0 && !s->v_is_half) {
+    // the first step after a restart is a velocity-Verlet step; graphs hold
+    // steps that start from a half-step velocity (and, under central
+    // difference, a valid u^{k-1})
+    if (nsteps > 0 && (!s->v_is_half || !s->u_prev_ok)) {
         rc = one_step(s, st);
         if (rc != PD_OK) return rc;
         --nsteps;
@@ -1273,6 +1287,7 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
         if (s->v[c]) PD_CUDA(cudaMemsetAsync(s->v[c], 0, sizeof(double) * g.nslots, st));
     if (s->vhl) PD_CUDA(cudaMemsetAsync(s->vhl, 0, 2 * sizeof(float4) * g.nslots, st));
     s->v_is_half = 0;
+    s->u_prev_ok = false;
     PD_CUDA(cudaStreamSynchronize(st));
     if (stats) *stats = ns;
     return PD_OK;

@@ -262,7 +262,10 @@ __device__ __forceinline__ PairPts pair_points(const Geom &g, const PairBox &pb,
 // second half-kick of the previous step (if v holds a half step), the first
 // half-kick of this step, the drift u += dt v with boundary conditions, and
 // writes u to the next staging buffer; MODE_FINALIZE applies only the pending
-// half-kick; MODE_FORCE stores f = (force scale) * F in FP64. Every load of both
+// half-kick; MODE_FORCE stores f = (force scale) * F in FP64. With a.cd set the
+// drift of a free DOF is the central difference of Eq. (10) instead,
+// u^{k+1} = u^k + (u^k - u^{k-1}) + dt^2 a^k with dt^2 a^k = 2 dt kick, and
+// u^{k-1} read from the staging buffer it overwrites. Every other load of both
 // points is issued before the arithmetic, so the two points share one memory
 // round trip.
 __device__ __forceinline__ void pair_epilogue2(const TileArgs &a, const PairPts &q, const float FA[3],
@@ -279,6 +282,7 @@ __device__ __forceinline__ void pair_epilogue2(const TileArgs &a, const PairPts 
     }
     float4 vh[2], vl[2], uh[2], ul[2], bb[2];
     int kind[2][3];
+    const bool cd = a.mode == MODE_STEP && a.cd;
     for (int p = 0; p < 2; ++p) {
         const int s = q.act[p] ? q.slot[p] : q.slot[0];
         vh[p] = a.vhl[2 * s];
@@ -295,6 +299,13 @@ __device__ __forceinline__ void pair_epilogue2(const TileArgs &a, const PairPts 
         DF v[3] = {{vh[p].x, vl[p].x}, {vh[p].y, vl[p].y}, {vh[p].z, vl[p].z}};
         DF u[3] = {{uh[p].x, ul[p].x}, {uh[p].y, ul[p].y}, {uh[p].z, ul[p].z}};
         const float bcomp[3] = {bb[p].x, bb[p].y, bb[p].z};
+        DF up[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        if (cd) {   // -u^{k-1}, loaded here only under central difference
+            const float4 ph = a.dst_hl[2 * slot], pl = a.dst_hl[2 * slot + 1];
+            up[0] = DF{-ph.x, -pl.x};
+            up[1] = DF{-ph.y, -pl.y};
+            up[2] = DF{-ph.z, -pl.z};
+        }
         for (int c = 0; c < dim; ++c) {
             const float kick = fmaf(a.kF, F[c], a.kB * bcomp[c]);
             const int kd = kind[p][c];
@@ -308,6 +319,9 @@ __device__ __forceinline__ void pair_epilogue2(const TileArgs &a, const PairPts 
                 } else if (kd == PD_BC_DISPLACEMENT) {
                     v[c] = DF{0.f, 0.f};
                     u[c] = DF{a.bc32[bq], a.bc32[bq + 1]};
+                } else if (cd) {
+                    const DF du = df_add(u[c], up[c]);
+                    u[c] = df_add(u[c], df_add(du, df_mul(DF{a.dt_h, a.dt_l}, DF{2.f * kick, 0.f})));
                 } else {
                     u[c] = df_add(u[c], df_mul(DF{a.dt_h, a.dt_l}, v[c]));
                 }

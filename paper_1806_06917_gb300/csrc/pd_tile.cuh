@@ -341,6 +341,7 @@ struct TileArgs {
     double K;                   // LPS bulk modulus (energy)
     int model;                  // PD_MODEL_PMB or PD_MODEL_LPS
     int v_is_half, update_breaking, mode, vol_corr, use_body, adjoint;
+    int cd;                     // MODE_STEP: central-difference drift from u^{k-1} at dst
 };
 
 // --------------------------------------------------------------- staging
@@ -416,6 +417,9 @@ __device__ __forceinline__ void stage_box64(double4_32a *box, int HX, int HY, in
 // MODE_FORCE  store f.
 // a = (f + b) / rho. Eqs. (7)-(9): the second half-kick of step k-1 and the
 // first half-kick of step k use the same force f^k and run in the same kernel.
+// With a.cd set a free DOF drifts by the central difference of Eq. (10),
+// u^{k+1} = 2 u^k - u^{k-1} + dt^2 a^k, u^{k-1} read from the staging buffer
+// the step overwrites.
 __device__ __forceinline__ void point_epilogue(const TileArgs &a, int slot, const double f[3],
                                                int dim, bool fp64)
 {
@@ -444,6 +448,16 @@ __device__ __forceinline__ void point_epilogue(const TileArgs &a, int slot, cons
             } else if (kind == PD_BC_DISPLACEMENT) {
                 v = 0.0;
                 u = a.bc_val[c * ns + slot];
+            } else if (a.cd) {
+                double up;
+                if (fp64) {
+                    const double4_32a p = a.dst_d4[slot];
+                    up = c == 0 ? p.x : (c == 1 ? p.y : p.z);
+                } else {
+                    const float4 ph = a.dst_hl[2 * slot], pl = a.dst_hl[2 * slot + 1];
+                    up = c == 0 ? (double)ph.x + pl.x : (c == 1 ? (double)ph.y + pl.y : (double)ph.z + pl.z);
+                }
+                u = fma(a.dt * a.dt, acc, 2.0 * u - up);
             } else {
                 u = fma(a.dt, v, u);
             }

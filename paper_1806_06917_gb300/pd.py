@@ -27,6 +27,7 @@ PD_JVP_MASK_DIRICHLET = 1
 PD_KRYLOV_GMRES, PD_KRYLOV_CG = 0, 1
 PD_TANGENT_CACHED, PD_TANGENT_JVP = 0, 1
 PD_PRECOND_NONE, PD_PRECOND_BLOCK_JACOBI = 0, 1
+PD_INTEGRATOR_VERLET, PD_INTEGRATOR_CD = 0, 1
 PD_REQ_QUEUED, PD_REQ_RUNNING, PD_REQ_DONE, PD_REQ_CANCELLED, PD_REQ_FAILED = 0, 1, 2, 3, 4
 
 if not os.path.exists(LIB_PATH):
@@ -49,7 +50,7 @@ class pd_material(ctypes.Structure):
 
 class pd_run(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dt_factor", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("tile_log2", ctypes.c_int32)]
+                ("tile_log2", ctypes.c_int32), ("integrator", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pd_newton_opts(ctypes.Structure):
@@ -439,7 +440,8 @@ def pd_sum_noalloc(x, scale=1.0, out=None, stream=None):
 
 # ------------------------------------------------------------ conveniences
 
-def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=0.5, tile_log2=0):
+def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=0.5, tile_log2=0,
+             integrator=PD_INTEGRATOR_VERLET):
     """pd_grid / pd_material / pd_run from the plain workload descriptions."""
     g = pd_grid()
     g.dim = workload_grid.dim
@@ -458,4 +460,5 @@ def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=
     m.psi_beta = getattr(workload_mat, "psi_beta", 1.0)
     r = pd_run()
     r.dt, r.dt_factor, r.precision, r.tile_log2 = dt, dt_factor, precision, tile_log2
+    r.integrator, r.reserved = integrator, 0
     return g, m, r

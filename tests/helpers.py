@@ -13,8 +13,8 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def gpu_sim(pd, grid, mat, precision, dt=0.0, notch=None, tile_log2=0):
-    g, m, r = pd.describe(grid, mat, precision=precision, dt=dt, tile_log2=tile_log2)
+def gpu_sim(pd, grid, mat, precision, dt=0.0, notch=None, tile_log2=0, integrator=0):
+    g, m, r = pd.describe(grid, mat, precision=precision, dt=dt, tile_log2=tile_log2, integrator=integrator)
     sim = pd.pd_create(g, m, r)
     pd.pd_build_neighbors(sim)
     if notch is not None:

@@ -1,6 +1,7 @@
 """The C ABI from a plain C program (tests/c/abi_smoke.c): it compiles and links
 against libpd with only include/pd.h on any machine; on a GPU it runs and prints
 exactly what the same simulation gives through the Python binding."""
+import ctypes
 import os
 import shutil
 import subprocess
@@ -61,3 +62,31 @@ def test_c_client_matches_the_python_binding(tmp_path):
     n = g.npoints
     assert got["u"] == [uo[0, 0], uo[n // 2, 0], uo[n - 1, 1]]
     sim.close()
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the
+    C compiler gives the struct of the same name in include/pd.h."""
+    from paper_1806_06917_gb300 import pd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(pd, n) for n in ("pd_grid", "pd_material", "pd_run", "pd_newton_opts", "pd_newton_stats",
+                                        "pd_server_opts", "pd_request", "pd_result")]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pd.h"', "int main(void) {"]
+    want = []
+    for cls in structs:
+        name = cls.__name__
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (name, name))
+        want.append("%s %d" % (name, ctypes.sizeof(cls)))
+        for field, _ in cls._fields_:
+            lines.append('printf("%%s %%zu\\n", "%s.%s", offsetof(%s, %s));' % (name, field, name, field))
+            want.append("%s.%s %d" % (name, field, getattr(cls, field).offset))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                   check=True, capture_output=True)
+    got = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    assert [l for l in got if l] == want
