@@ -39,7 +39,9 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # FP32 arithmetic of one bond as the kernels evaluate it (hand count; an FMA is
 # one operation; the 2 MUFU ops per bond are not included).
-FP32_OPS_PER_BOND = {"pmb3": 24, "pmb2": 18, "lps_dil": 19, "lps_force": 30}
+# NP in 2D (np_fast): eta 2, S = eta.d/|d|^2 3, t S 1, a S^2 2, times exp 1,
+# force 2 (11, plus one MUFU ex2).
+FP32_OPS_PER_BOND = {"pmb3": 24, "pmb2": 18, "lps_dil": 19, "lps_force": 30, "np2": 11}
 # FP64 path (pmb_generic<double>): the arithmetic of one bond as written, flops
 # with an FMA as 2 and rsqrt, divide as one each (their expansion into several
 # FP64 instructions is not counted): eta, y 6; |y|^2 5; numerator 10; rsqrt 1;
@@ -49,16 +51,17 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 # Algorithmic bytes per point of one step, in the kernels' layout (u and v as
 # double-float pairs, 2 x float4 = 32 B each): u read 32, v read + written 64,
-# new u written 32, bond-mask words read (4 B x W: W = 4 in 3D, 1 in 2D at m = 3),
-# BC kinds 1 B per DOF. LPS: dilatation pass u 32 + masks 16 + 1/m~ 4 read,
-# theta 4 written (56); force pass u 32 + theta, 1/m~ 8 + masks 16 read, v 64,
-# new u 32, BC kinds 3 (155).
-BYTES_PER_POINT = {"pmb3": 147.0, "pmb2": 134.0, "lps": 211.0}
-CSR_BYTES_PER_BOND = {"pmb3": 4.25, "pmb2": 4.25, "lps": 8.0}
+# new u written 32, bond-mask words read (4 B x W: W = 4 in 3D, 1 in 2D at m = 3,
+# 40 in 2D at m = 20), BC kinds 1 B per DOF. LPS: dilatation pass u 32 + masks
+# 16 + 1/m~ 4 read, theta 4 written (56); force pass u 32 + theta, 1/m~ 8 +
+# masks 16 read, v 64, new u 32, BC kinds 3 (155).
+BYTES_PER_POINT = {"pmb3": 147.0, "pmb2": 134.0, "lps": 211.0, "np2": 128.0 + 4 * 40 + 2}
+CSR_BYTES_PER_BOND = {"pmb3": 4.25, "pmb2": 4.25, "lps": 8.0, "np2": 4.0}
 KERNEL_LABEL = {
     "pmb3": lambda wl: "pmb_fast<3, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
     "pmb2": lambda wl: "pmb_fast<2, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
     "lps": lambda wl: "lps_dil_fast + lps_force_fast (one step)",
+    "np2": lambda wl: "np_fast<2, false>",
 }
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step's
@@ -97,6 +100,11 @@ def workload(name):
     if name == "lps128":
         wl = W.block3d_lps(nside=128)
         return wl, "block3d_128_lps: 128^3 lattice, h=1/128 m, m=3, LPS K=40 GPa mu=30 GPa"
+    if name == "paper443":
+        wl = W.np_benchmark()
+        return wl, ("np_benchmark_443_m20: the explicit benchmark shape of Sec. 6.2, 443^2 lattice (196,249 "
+                    "nodes), h = 0.0025 m, delta = 0.05 m (m = 20), NP law (C = beta = rho = 1), IC 1 "
+                    "Gaussian, collar u = 0, dt = 1e-5")
     if name == "plate50":
         wl = W.plate2d(nside=50)
         return wl, "plate2d_50_pmb: 50^2 lattice, h=0.02 m, m=3, PMB, collar velocities"
@@ -182,7 +190,7 @@ def measured_peaks():
 
 
 def make_sim(pd, wl, precision, stream, integrator=0):
-    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, integrator=integrator)
+    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator)
     sim = pd.pd_create(g, m, r)
     pd.pd_build_neighbors(sim, stream)
     if wl.notch is not None:
@@ -429,7 +437,7 @@ def cpu_baseline(wl, target_s=12.0, max_steps=50):
     bonds = O.neighbors(wl.grid)
     if wl.notch is not None:
         O.break_notch(wl.grid, bonds, wl.notch)
-    dt = wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
+    dt = wl.dt if wl.dt > 0 else wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
     st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
     st.run(dt, 1)                                    # computes f^0 and one step
     setup = time.time() - t0
@@ -467,7 +475,7 @@ def run_reference(args):
     bonds = O.neighbors(wl.grid)
     if wl.notch is not None:
         O.break_notch(wl.grid, bonds, wl.notch)
-    dt = wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
+    dt = wl.dt if wl.dt > 0 else wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
     st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
     st.run(dt, max(args.warmup, 1))
     t0 = time.time()
@@ -493,7 +501,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="block64",
-                    choices=["block64", "lps128", "plate50", "serve", "convergence"])
+                    choices=["block64", "lps128", "plate50", "paper443", "serve", "convergence"])
     ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
@@ -533,7 +541,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sim = make_sim(pd, wl, pd.PD_FP32C, stream)
     nbonds = pd.pd_bond_count(sim)
-    key = "lps" if wl.mat.model == W.LPS else ("pmb3" if wl.grid.dim == 3 else "pmb2")
+    key = {W.LPS: "lps", W.NP: "np2"}.get(wl.mat.model, "pmb3" if wl.grid.dim == 3 else "pmb2")
     launches_per_step = 2 if key == "lps" else 1
 
     def barrier():

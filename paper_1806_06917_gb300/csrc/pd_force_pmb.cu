@@ -8,6 +8,7 @@
 //   f_i += c V V_ij s y / r                          (PMB pair force)
 // A bond breaks for good when s > s_c, tested before it contributes. Each point
 // sums its bonds sequentially in stencil order: no atomics, deterministic.
+#include <algorithm>
 #include <type_traits>
 
 #include "pd_pair.cuh"
@@ -80,8 +81,37 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
     return anybrk;
 }
 
-template <int DIM, bool BRK>
-__global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
+// Sum the a.split partial forces of a point pair (each part summed one
+// contiguous range of stencil words): parts 1.. park theirs in red, part 0 adds
+// them in part order (fixed: the result does not depend on timing). Every
+// thread of the block calls this once.
+__device__ __forceinline__ void pair_split_sum(const TileArgs &a, float2 *red, int npairs, int t, int part,
+                                               float2 &Fx, float2 &Fy, float2 &Fz)
+{
+    if (part > 0) {
+        float2 *r = red + 3 * ((part - 1) * npairs + t);
+        r[0] = Fx;
+        r[1] = Fy;
+        r[2] = Fz;
+    }
+    __syncthreads();
+    if (part == 0) {
+        for (int j = 1; j < a.split; ++j) {
+            const float2 *r = red + 3 * ((j - 1) * npairs + t);
+            Fx = f2add(Fx, r[0]);
+            Fy = f2add(Fy, r[1]);
+            Fz = f2add(Fz, r[2]);
+        }
+    }
+}
+
+// Launch: one CTA per tile, (tile points / 2) * a.split threads. Thread
+// (t, part) owns point pair t and the stencil words [part W / split,
+// (part + 1) W / split). SPLIT = true (a.split of 2 or 4) at wide horizons,
+// where one CTA's halo box and table fill the shared memory, so that more warps
+// run per SM; SPLIT = false is the one-thread-per-pair kernel.
+template <int DIM, bool BRK, bool SPLIT>
+__global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) pmb_fast(const TileArgs a)
 {
     const Geom &g = a.g;
     const PairBox pb = pair_box(g);
@@ -100,18 +130,22 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
     stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr);
     __syncthreads();
 
-    const int nthr = g.T / 2;            // a multiple of blockDim: every lane runs every iteration
-    for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
+    const int nthr = g.T / 2;            // point pairs: a multiple of 32, so a warp has one part
+    const int part = SPLIT ? threadIdx.x / nthr : 0;
+    const int w0 = SPLIT ? part * g.W / a.split : 0, w1 = SPLIT ? (part + 1) * g.W / a.split : g.W;
+    // one iteration per thread (T / 2 <= 256 = blockDim without the split)
+    for (int t = SPLIT ? threadIdx.x % nthr : threadIdx.x; t < nthr; t += SPLIT ? nthr : blockDim.x) {
         const PairPts q = pair_points(g, pb, org, tile, t);
         const float4 ui4 = P4[q.bi];
         const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4));
         const float2 nuz = DIM == 3 ? f2neg(P2[q.bi]) : make_float2(0.f, 0.f);
         float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
-        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
-        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
-        for (int w = 0; w < g.W; ++w) {
+        const size_t mo0 = (size_t)w0 * g.nslots;
+        uint32_t n0 = q.act[0] && (!SPLIT || w0 < w1) ? a.mask[mo0 + q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] && (!SPLIT || w0 < w1) ? a.mask[mo0 + q.slot[1]] : 0u;
+        for (int w = w0; w < w1; ++w) {
             const uint32_t m0 = n0, m1 = n1;
-            if (w + 1 < g.W) {
+            if (w + 1 < w1) {
                 const size_t mo = (size_t)(w + 1) * g.nslots;
                 n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
                 n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
@@ -141,8 +175,11 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) pmb_fast(const TileArgs a)
                 }
             }
         }
-        const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
-        pair_epilogue2(a, q, FA, FB, DIM);
+        if (SPLIT) pair_split_sum(a, reinterpret_cast<float2 *>(tab + 4 * S), nthr, t, part, Fx, Fy, Fz);
+        if (part == 0) {
+            const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
+            pair_epilogue2(a, q, FA, FB, DIM);
+        }
     }
 }
 
@@ -191,8 +228,8 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
     }
 }
 
-template <int DIM, bool LINEAR>
-__global__ void __launch_bounds__(256, PD_MINBLOCKS) np_fast(const TileArgs a)
+template <int DIM, bool LINEAR, bool SPLIT>
+__global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) np_fast(const TileArgs a)
 {
     const Geom &g = a.g;
     const PairBox pb = pair_box(g);
@@ -210,18 +247,22 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) np_fast(const TileArgs a)
     stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr);
     __syncthreads();
 
-    const int nthr = g.T / 2;            // a multiple of blockDim
-    for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
+    const int nthr = g.T / 2;            // point pairs; thread (t, part) as in pmb_fast
+    const int part = SPLIT ? threadIdx.x / nthr : 0;
+    const int w0 = SPLIT ? part * g.W / a.split : 0, w1 = SPLIT ? (part + 1) * g.W / a.split : g.W;
+    // one iteration per thread (T / 2 <= 256 = blockDim without the split)
+    for (int t = SPLIT ? threadIdx.x % nthr : threadIdx.x; t < nthr; t += SPLIT ? nthr : blockDim.x) {
         const PairPts q = pair_points(g, pb, org, tile, t);
         const float4 ui4 = P4[q.bi];
         const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4));
         const float2 nuz = DIM == 3 ? f2neg(P2[q.bi]) : make_float2(0.f, 0.f);
         float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
-        uint32_t n0 = q.act[0] ? a.mask[q.slot[0]] : 0u;
-        uint32_t n1 = q.act[1] ? a.mask[q.slot[1]] : 0u;
-        for (int w = 0; w < g.W; ++w) {
+        const size_t mo0 = (size_t)w0 * g.nslots;
+        uint32_t n0 = q.act[0] && (!SPLIT || w0 < w1) ? a.mask[mo0 + q.slot[0]] : 0u;
+        uint32_t n1 = q.act[1] && (!SPLIT || w0 < w1) ? a.mask[mo0 + q.slot[1]] : 0u;
+        for (int w = w0; w < w1; ++w) {
             const uint32_t m0 = n0, m1 = n1;
-            if (w + 1 < g.W) {
+            if (w + 1 < w1) {
                 const size_t mo = (size_t)(w + 1) * g.nslots;
                 n0 = q.act[0] ? a.mask[mo + q.slot[0]] : 0u;
                 n1 = q.act[1] ? a.mask[mo + q.slot[1]] : 0u;
@@ -234,8 +275,11 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) np_fast(const TileArgs a)
             else
                 np_word<DIM, true, LINEAR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, Fx, Fy, Fz);
         }
-        const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
-        pair_epilogue2(a, q, FA, FB, DIM);
+        if (SPLIT) pair_split_sum(a, reinterpret_cast<float2 *>(tab + 4 * S), nthr, t, part, Fx, Fy, Fz);
+        if (part == 0) {
+            const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
+            pair_epilogue2(a, q, FA, FB, DIM);
+        }
     }
 }
 
@@ -322,15 +366,51 @@ __global__ void __launch_bounds__(256) pmb_generic(const TileArgs a)
 
 // ---------------------------------------------------------------- dispatch
 
-template <int DIM, bool BRK>
-static int launch_fast(const TileArgs &a, cudaStream_t st)
+// Shared memory of pmb_fast / np_fast with the stencil split over `split`
+// threads per pair: the split-sum buffer (3 float2 per pair and extra part).
+static size_t split_smem(const Geom &g, int split)
 {
-    const size_t smem = pmb_fast_smem(a.g);
-    PD_CUDA(cudaFuncSetAttribute(pmb_fast<DIM, BRK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int threads = a.g.T / 2 < 256 ? a.g.T / 2 : 256;
-    pmb_fast<DIM, BRK><<<a.g.ntiles, threads, smem, st>>>(a);
+    return pmb_fast_smem(g) + (size_t)(split - 1) * (g.T / 2) * 3 * sizeof(float2);
+}
+
+// Threads per point pair: of 1, 2, 4 (at most the number of stencil words), the
+// smallest that reaches the most resident threads per SM, counting the
+// 1024-thread limit of 64 registers per thread and 228 KB of shared memory per
+// SM (1 KB of it reserved per CTA).
+static int choose_split(const Geom &g)
+{
+    const int nthr = g.T / 2;
+    int best = 1, best_threads = 0;
+    for (int split = 1; split <= 4 && split <= g.W; split *= 2) {
+        const size_t smem = split_smem(g, split);
+        if (smem > 227 * 1024) break;
+        const int by_smem = (int)((228 * 1024) / (smem + 1024));
+        const int ctas = std::min(by_smem, 1024 / (nthr * split));
+        if (nthr * split * ctas > best_threads) {
+            best = split;
+            best_threads = nthr * split * ctas;
+        }
+    }
+    return best;
+}
+
+template <int DIM, bool BRK, bool SPLIT>
+static int launch_fast_split(const TileArgs &a, cudaStream_t st)
+{
+    const size_t smem = split_smem(a.g, a.split);
+    PD_CUDA(cudaFuncSetAttribute(pmb_fast<DIM, BRK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    pmb_fast<DIM, BRK, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
+}
+
+template <int DIM, bool BRK>
+static int launch_fast(const TileArgs &a0, cudaStream_t st)
+{
+    TileArgs a = a0;
+    a.split = choose_split(a.g);
+    return a.split > 1 ? launch_fast_split<DIM, BRK, true>(a, st) : launch_fast_split<DIM, BRK, false>(a, st);
 }
 
 size_t pmb_generic_smem(const Geom &g, int precision)
@@ -339,15 +419,23 @@ size_t pmb_generic_smem(const Geom &g, int precision)
     return (size_t)HX * HY * HZ * (precision == PD_FP64 ? sizeof(double4_32a) : sizeof(float4));
 }
 
-template <int DIM, bool LINEAR>
-static int launch_np_fast(const TileArgs &a, cudaStream_t st)
+template <int DIM, bool LINEAR, bool SPLIT>
+static int launch_np_split(const TileArgs &a, cudaStream_t st)
 {
-    const size_t smem = pmb_fast_smem(a.g);
-    PD_CUDA(cudaFuncSetAttribute(np_fast<DIM, LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int threads = a.g.T / 2 < 256 ? a.g.T / 2 : 256;
-    np_fast<DIM, LINEAR><<<a.g.ntiles, threads, smem, st>>>(a);
+    const size_t smem = split_smem(a.g, a.split);
+    PD_CUDA(cudaFuncSetAttribute(np_fast<DIM, LINEAR, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    np_fast<DIM, LINEAR, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
+}
+
+template <int DIM, bool LINEAR>
+static int launch_np_fast(const TileArgs &a0, cudaStream_t st)
+{
+    TileArgs a = a0;
+    a.split = choose_split(a.g);
+    return a.split > 1 ? launch_np_split<DIM, LINEAR, true>(a, st) : launch_np_split<DIM, LINEAR, false>(a, st);
 }
 
 // Every bond-based law: PMB, NP, LP.

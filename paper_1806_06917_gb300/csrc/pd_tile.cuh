@@ -342,6 +342,7 @@ struct TileArgs {
     int model;                  // PD_MODEL_PMB or PD_MODEL_LPS
     int v_is_half, update_breaking, mode, vol_corr, use_body, adjoint;
     int cd;                     // MODE_STEP: central-difference drift from u^{k-1} at dst
+    int split;                  // fused bond kernels: threads per point pair (1, 2 or 4)
 };
 
 // --------------------------------------------------------------- staging

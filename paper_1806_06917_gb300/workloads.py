@@ -181,17 +181,19 @@ def block3d_lps(nside: int = 128, seed: int = 3, steps: int = 500, m: int = 3) -
                     u0=u0, v0=v0, bc_kind=kind, bc_val=val)
 
 
-def np_square(k: int = 2, model: int = NP, ic: int = 1, steps: int = 200000, delta: float = 0.1) -> Workload:
+def np_square(k: int = 2, model: int = NP, ic: int = 1, steps: int = 200000, delta: float = 0.1,
+              pad: int = 0) -> Workload:
     """The 2D explicit convergence study of Sec. 5.2.2: material domain
     [0, 1]^2, horizon delta = 0.1, h = delta / k (m = k), a lattice over
     [-delta, 1 + delta]^2 whose points outside [0, 1]^2 form the collar held at
     u = 0; rho = 1, psi(r) = 1 - exp(-r) (C = beta = 1), dt = 1e-5, time [0, 2]
     (200000 steps). Initial displacement a exp(-|X - x_c|^2 / beta), v0 = 0:
     IC 1: a = (0.001, 0), x_c = (0.5, 0.5), beta = 0.003;
-    IC 2: a = (0.0002, 0.0007), x_c = (0.25, 0.25), beta = 0.01."""
+    IC 2: a = (0.0002, 0.0007), x_c = (0.25, 0.25), beta = 0.01.
+    ``pad`` adds that many lattice layers outside the collar on every side."""
     h = delta / k
-    n = int(round((1.0 + 2.0 * delta) / h)) + 1
-    g = Grid(dim=2, n=(n, n, 1), h=h, m=k, origin=(-delta, -delta, 0.0))
+    n = int(round((1.0 + 2.0 * delta) / h)) + 1 + 2 * pad
+    g = Grid(dim=2, n=(n, n, 1), h=h, m=k, origin=(-delta - pad * h, -delta - pad * h, 0.0))
     mat = Material(model=model, E=0.0, rho=1.0, psi_c=1.0, psi_beta=1.0, thickness=1.0)
     a, xc, beta = ((0.001, 0.0), (0.5, 0.5), 0.003) if ic == 1 else ((0.0002, 0.0007), (0.25, 0.25), 0.01)
     u0 = gaussian_ic(g, a, xc, beta)
@@ -204,6 +206,15 @@ def np_square(k: int = 2, model: int = NP, ic: int = 1, steps: int = 200000, del
     val = np.zeros((g.npoints, 2))
     name = "np_square_k%d_%s_ic%d" % (k, "np" if model == NP else "lp", ic)
     return Workload(name, g, mat, steps, ic, dt=1e-5, u0=u0, v0=np.zeros_like(u0), bc_kind=kind, bc_val=val)
+
+
+def np_benchmark(steps: int = 100, model: int = NP) -> Workload:
+    """The explicit benchmark of Sec. 6.2: the setup of the 2D study (Sec. 5.2.2,
+    IC 1) with horizon delta = 0.05 m and m = 20 (h = 0.0025 m), 196,249 nodes
+    (443^2: the lattice over [-delta, 1 + delta]^2 plus one layer on each side)."""
+    wl = np_square(k=20, model=model, ic=1, steps=steps, delta=0.05, pad=1)
+    wl.name = "np_benchmark_443_m20_%s" % ("np" if model == NP else "lp")
+    return wl
 
 
 @dataclasses.dataclass

@@ -468,6 +468,7 @@ def test_pmb_small_tiles_match_oracle(pd, tile_log2):
 LARGE_HORIZONS = [
     (2, (60, 41, 1), 12, W.PMB), (2, (45, 38, 1), 8, W.NP), (3, (14, 13, 12), 6, W.PMB),
     (3, (13, 12, 11), 5, W.LPS), (3, (12, 11, 10), 7, W.PMB),
+    (2, (90, 77, 1), 20, W.NP), (2, (83, 70, 1), 20, W.PMB), (2, (75, 71, 1), 20, W.LP),
 ]
 
 
@@ -478,11 +479,12 @@ def test_large_horizons_match_oracle(pd, dim, n, m, model, precision):
     # automatic tile shrink of the shared-memory halo, and the force kernels
     g = W.Grid(dim=dim, n=n, h=0.01, m=m)
     mat = {W.PMB: W.Material(model=W.PMB), W.NP: W.Material(model=W.NP, rho=1.0, psi_beta=2.0),
+           W.LP: W.Material(model=W.LP, rho=1.0, psi_beta=2.0),
            W.LPS: W.Material(model=W.LPS, K=40e9, mu=30e9)}[model]
     bonds = O.neighbors(g)
     rng = np.random.default_rng(m)
     u = rng.normal(0.0, 1e-3 * g.h, (g.npoints, dim))
-    if model == W.NP:
+    if model in (W.NP, W.LP):
         u = rng.normal(0.0, 0.2 * g.h, (g.npoints, dim))
     prec = pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64
     sim = gpu_sim(pd, g, mat, prec)
@@ -490,4 +492,55 @@ def test_large_horizons_match_oracle(pd, dim, n, m, model, precision):
     f_o, _ = O.internal_force(g, mat, bonds, u, O.weighted_volume(g, mat, bonds) if model == W.LPS else None)
     f_g = pd.pd_force(sim, u=u)
     assert rel_l2(f_g, f_o) <= (FORCE_TOL_FP32C if precision == "fp32c" else 1e-10)
+    sim.close()
+
+
+def test_paper_benchmark_shape_full_size(pd):
+    """The explicit benchmark shape of Sec. 6.2 at full size (443^2 nodes, m = 20,
+    237,103,580 bonds, NP law, clamped collar): the force at u0 against the
+    oracle, then 3 steps, compared by the displacement increment u - u0."""
+    wl = W.np_benchmark(steps=3)
+    sim = gpu_sim(pd, wl.grid, wl.mat, pd.PD_FP32C, dt=wl.dt)
+    bonds = O.neighbors(wl.grid)
+    assert pd.pd_bond_count(sim) == bonds.nbonds == 237103580
+    f_o, _ = O.internal_force(wl.grid, wl.mat, bonds, wl.u0, None)
+    f_g = pd.pd_force(sim, u=wl.u0)
+    assert rel_l2(f_g, f_o) <= FORCE_TOL_FP32C
+    pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+    pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
+    pd.pd_step_explicit(sim, wl.steps)
+    u_g, _ = pd.pd_get_state(sim)
+    st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
+    st.run(wl.dt, wl.steps)
+    assert np.abs(st.u - wl.u0).max() > 0
+    assert rel_l2(u_g - wl.u0, st.u - wl.u0) <= U_TOL
+    sim.close()
+
+
+@pytest.mark.parametrize("m,amp", [(12, 0.3), (20, 0.2)])
+def test_wide_horizon_breaking_run_matches_oracle(pd, m, amp):
+    """A 2D run with bonds breaking at m = 12 and m = 20, where the fused kernel
+    splits each point pair's stencil words over 2 and 4 threads."""
+    g = W.Grid(dim=2, n=(70, 61, 1), h=0.01, m=m)
+    mat = W.Material(model=W.PMB, E=72e9, rho=2440.0, s_c=2e-5, thickness=1.0)
+    X = g.positions()
+    r2 = ((X - X.mean(axis=0)) ** 2).sum(axis=1)
+    v0 = np.zeros((g.npoints, 2))
+    v0[:, 0] = amp * np.exp(-r2 / (0.08 ** 2))       # 0.7 % / 0.2 % of the bonds break
+    u0 = np.zeros_like(v0)
+    sim = gpu_sim(pd, g, mat, pd.PD_FP32C)
+    bonds = O.neighbors(g)
+    pd.pd_set_state(sim, u=u0, v=v0)
+    steps = 40
+    pd.pd_step_explicit(sim, steps)
+    u_g, v_g = pd.pd_get_state(sim)
+    st = O.ExplicitState(g, mat, bonds, u0, v0, None, None)
+    st.run(pd.pd_get_dt(sim), steps)
+    _, _, order, _ = gpu_csr_in_user_numbering(pd, sim)
+    brk = pd.pd_get_broken(sim)[order].astype(bool)
+    ob = bonds.broken.astype(bool)
+    assert ob.sum() > 0
+    assert int((brk != ob).sum()) <= max(2, int(1e-4 * ob.sum()))
+    assert rel_l2(u_g, st.u) <= U_TOL
+    assert rel_l2(v_g, st.v) <= 1e-3
     sim.close()
