@@ -40,6 +40,7 @@ int reduce_sum(const double *x, long long n, double scale, double *partial, doub
 int reduce_blocks_for(long long n);
 size_t pmb_generic_smem(const Geom &g, int precision);
 size_t pmb_fast_smem(const Geom &g);
+size_t np_fast_smem(const Geom &g);
 size_t lps_generic_smem(const Geom &g, int precision, bool dil);
 size_t jvp_smem(const Geom &g, int precision);
 // Per-bond tangent cache (pd_tangent.cu): prepare at a linearisation point,
@@ -170,7 +171,9 @@ static size_t max_smem(const Geom &g, int precision, int model, bool with_tangen
 {
     size_t m = energy_smem(g, precision);
     if (with_tangent) m = std::max(m, jvp_smem(g, precision));
-    if (model != PD_MODEL_LPS)
+    if (model == PD_MODEL_NP || model == PD_MODEL_LP)
+        m = std::max(m, precision == PD_FP64 ? pmb_generic_smem(g, precision) : np_fast_smem(g));
+    else if (model != PD_MODEL_LPS)
         m = std::max(m, precision == PD_FP64 ? pmb_generic_smem(g, precision) : pmb_fast_smem(g));
     else m = std::max(m, lps_generic_smem(g, precision, false));
     return m;
@@ -382,7 +385,7 @@ static int create_impl(pd_sim *s)
             float offf;
             memcpy(&offf, &off, sizeof(float));
             const float4 dxy = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
-            ta[4 * k] = dxy;
+            if (!np_law) ta[4 * k] = dxy;
             tb[4 * k] = dxy;
             // LPS force: {dz,dz,|d|,|d|} {A|d|V_ij x2, B V_ij x2} {|d|^2,|d|^2,offset,-}
             tb[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
@@ -390,14 +393,23 @@ static int create_impl(pd_sim *s)
                                         (float)(B * vij));
             tb[4 * k + 3] = make_float4((float)d2, (float)d2, offf, 0.f);
             if (mt.model == PD_MODEL_NP || mt.model == PD_MODEL_LP) {
-                // {dz,dz,1/|d|^2,1/|d|^2} {a,a,t,t} {offset,-,-,-} with the bond weight
-                // t = J V_ij / |d| and the exponent a = -beta h |d| log2(e), so that
-                // psi'(|xi| S^2) / (C beta) = exp2(a S^2)
+                // compact entries (NP_TAB_WORDS float4 each, written over the first
+                // entries of the table): the bond weight t = J V_ij / |d| and the
+                // exponent a = -beta h |d| log2(e) (so that psi'(|xi| S^2) / (C beta)
+                // = exp2(a S^2)) folded with S = p / |d|^2, p = eta.d, into
+                // k = t / |d|^2 and a' = a / |d|^4:
+                //   2D {dx,dx,dy,dy} {k,k,a',offset}; 3D {dx,dx,dy,dy} {dz,dz,k,k} {a',offset,-,-}
                 const double J = d2 < (double)g.m * g.m ? 1.0 : 0.0;
-                const double a_ex2 = -mt.psi_beta * g.h * rr / log(2.0);
-                ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)(1.0 / d2), (float)(1.0 / d2));
-                ta[4 * k + 2] = make_float4((float)a_ex2, (float)a_ex2, (float)(J * vij / rr), (float)(J * vij / rr));
-                ta[4 * k + 3] = make_float4(offf, 0.f, 0.f, 0.f);
+                const float kk = (float)(J * vij / rr / d2);
+                const float ak = (float)(-mt.psi_beta * g.h * rr / log(2.0) / (d2 * d2));
+                const int E = NP_TAB_WORDS(g.dim);
+                ta[E * k] = dxy;
+                if (g.dim == 3) {
+                    ta[E * k + 1] = make_float4((float)d.z, (float)d.z, kk, kk);
+                    ta[E * k + 2] = make_float4(ak, offf, 0.f, 0.f);
+                } else {
+                    ta[E * k + 1] = make_float4(kk, kk, ak, offf);
+                }
             } else if (mt.model == PD_MODEL_PMB) {
                 // {dz,dz,|d|^2,|d|^2} {|d|/V_ij x2, |d|^2/V_ij x2} {offset, s_c V_ij, -, -}
                 ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)d2, (float)d2);

@@ -183,41 +183,60 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     }
 }
 
-size_t pmb_fast_smem(const Geom &g)
+// Paired halo box (float4 {x_A, x_B, y_A, y_B}, plus float2 {z_A, z_B} in 3D)
+// followed by the stencil table of `words` float4 per entry.
+static size_t fast_smem(const Geom &g, int words)
 {
     size_t n;
     if (g.dim == 3) n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
     else n = (size_t)(g.bx + 2 * g.m) * (g.by / 2 + 2 * g.m);
     const size_t p2 = g.dim == 3 ? ((n + 1) / 2) * sizeof(float4) : 0;
-    return n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
+    return n * sizeof(float4) + p2 + (size_t)g.S * words * sizeof(float4);
 }
+
+size_t pmb_fast_smem(const Geom &g) { return fast_smem(g, 4); }
+
+size_t np_fast_smem(const Geom &g) { return fast_smem(g, NP_TAB_WORDS(g.dim)); }
 
 // ------------------------------------------------------------------ generic
 
 // ------------------------------------------------------------- NP / LP, FP32C
 
-// One 32-bond word of the NP / LP sum (Algorithm 1) for a point pair in f32x2:
-//   S = eta.d / |d|^2,  w = t S [exp2(a S^2) for NP],  F += w d,
-// table entry {dx,dx,dy,dy} {dz,dz,1/|d|^2 x2} {a,a,t,t} {offset,-,-,-} with
-// t = J V_ij / |d| and a = -beta h |d| / ln 2 (see pd_api.cu). The direction is
-// the reference bond d, so no square root or reciprocal is needed.
+// One 32-bond word of the NP / LP sum (Algorithm 1) for a point pair in f32x2.
+// With S = eta.d / |d|^2 the bond term is t S [exp2(a S^2) for NP] d, t = J
+// V_ij / |d| and a = -beta h |d| / ln 2 (see pd_api.cu); written in p = eta.d:
+//   w = k p [exp2(a' p^2) for NP],  F += w d,   k = t / |d|^2,  a' = a / |d|^4.
+// The direction is the reference bond d, so no square root or reciprocal is
+// needed. Table entries of NP_TAB_WORDS(DIM) float4, the fewest shared-memory
+// wavefronts per bond (a broadcast 16-byte load costs two):
+//   2D: {dx,dx,dy,dy} {k,k,a',offset}
+//   3D: {dx,dx,dy,dy} {dz,dz,k,k} {a',offset,-,-}
 template <int DIM, bool MASKED, bool LINEAR>
 __device__ __forceinline__ void np_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
                                         float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1, float2 &Fx,
                                         float2 &Fy, float2 &Fz)
 {
+    constexpr int E = NP_TAB_WORDS(DIM);
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
-        const int off = __float_as_int(tw[4 * b + 3].x);
+        const float4 ta = tw[E * b], tb = tw[E * b + 1];
+        float ak;
+        int off;
+        if (DIM == 3) {
+            const float2 tc = reinterpret_cast<const float2 *>(tw + E * b + 2)[0];
+            ak = tc.x;
+            off = __float_as_int(tc.y);
+        } else {
+            ak = tb.z;
+            off = __float_as_int(tb.w);
+        }
         const float4 r4 = P4[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy);
         float2 dot = f2mul(ex, f2lo(ta));
         dot = f2fma(ey, f2hi(ta), dot);
         if (DIM == 3) dot = f2fma(f2add(P2[bi + off], nuz), f2lo(tb), dot);
-        const float2 S = f2mul(dot, f2hi(tb));
-        float2 wgt = f2mul(S, f2hi(tc));
-        if (!LINEAR) wgt = f2mul(wgt, f2ex2(f2mul(f2lo(tc), f2mul(S, S))));
+        float2 wgt = f2mul(dot, DIM == 3 ? f2hi(tb) : f2lo(tb));
+        if (!LINEAR) wgt = f2mul(wgt, f2ex2(f2mul(make_float2(ak, ak), f2mul(dot, dot))));
         if (MASKED) {
             wgt.x = ((c0 >> b) & 1u) ? wgt.x : 0.f;
             wgt.y = ((c1 >> b) & 1u) ? wgt.y : 0.f;
@@ -237,11 +256,12 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     extern __shared__ float4 smem4[];
     float4 *P4 = smem4;
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
-    float4 *tab = P4 + pb.n + (DIM == 3 ? (pb.n + 1) / 2 : 0);      // the layout of pmb_fast_smem
+    float4 *tab = P4 + pb.n + (DIM == 3 ? (pb.n + 1) / 2 : 0);      // the layout of np_fast_smem
+    constexpr int E = NP_TAB_WORDS(DIM);
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    for (int k = threadIdx.x; k < E * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr);
@@ -269,13 +289,13 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
             }
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
-            const float4 *tw = tab + 4 * 32 * w;
+            const float4 *tw = tab + E * 32 * w;
             if (__all_sync(0xffffffffu, m0 == full && m1 == full))
                 np_word<DIM, false, LINEAR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, Fx, Fy, Fz);
             else
                 np_word<DIM, true, LINEAR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, Fx, Fy, Fz);
         }
-        if (SPLIT) pair_split_sum(a, reinterpret_cast<float2 *>(tab + 4 * S), nthr, t, part, Fx, Fy, Fz);
+        if (SPLIT) pair_split_sum(a, reinterpret_cast<float2 *>(tab + E * S), nthr, t, part, Fx, Fy, Fz);
         if (part == 0) {
             const float FA[3] = {Fx.x, Fy.x, Fz.x}, FB[3] = {Fx.y, Fy.y, Fz.y};
             pair_epilogue2(a, q, FA, FB, DIM);
@@ -366,23 +386,23 @@ __global__ void __launch_bounds__(256) pmb_generic(const TileArgs a)
 
 // ---------------------------------------------------------------- dispatch
 
-// Shared memory of pmb_fast / np_fast with the stencil split over `split`
-// threads per pair: the split-sum buffer (3 float2 per pair and extra part).
-static size_t split_smem(const Geom &g, int split)
+// Shared memory of pmb_fast / np_fast (base) with the stencil split over
+// `split` threads per pair: the split-sum buffer (3 float2 per pair and extra part).
+static size_t split_smem(const Geom &g, size_t base, int split)
 {
-    return pmb_fast_smem(g) + (size_t)(split - 1) * (g.T / 2) * 3 * sizeof(float2);
+    return base + (size_t)(split - 1) * (g.T / 2) * 3 * sizeof(float2);
 }
 
 // Threads per point pair: of 1, 2, 4 (at most the number of stencil words), the
 // smallest that reaches the most resident threads per SM, counting the
 // 1024-thread limit of 64 registers per thread and 228 KB of shared memory per
 // SM (1 KB of it reserved per CTA).
-static int choose_split(const Geom &g)
+static int choose_split(const Geom &g, size_t base)
 {
     const int nthr = g.T / 2;
     int best = 1, best_threads = 0;
     for (int split = 1; split <= 4 && split <= g.W; split *= 2) {
-        const size_t smem = split_smem(g, split);
+        const size_t smem = split_smem(g, base, split);
         if (smem > 227 * 1024) break;
         const int by_smem = (int)((228 * 1024) / (smem + 1024));
         const int ctas = std::min(by_smem, 1024 / (nthr * split));
@@ -397,7 +417,7 @@ static int choose_split(const Geom &g)
 template <int DIM, bool BRK, bool SPLIT>
 static int launch_fast_split(const TileArgs &a, cudaStream_t st)
 {
-    const size_t smem = split_smem(a.g, a.split);
+    const size_t smem = split_smem(a.g, pmb_fast_smem(a.g), a.split);
     PD_CUDA(cudaFuncSetAttribute(pmb_fast<DIM, BRK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     pmb_fast<DIM, BRK, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a);
@@ -409,7 +429,7 @@ template <int DIM, bool BRK>
 static int launch_fast(const TileArgs &a0, cudaStream_t st)
 {
     TileArgs a = a0;
-    a.split = choose_split(a.g);
+    a.split = choose_split(a.g, pmb_fast_smem(a.g));
     return a.split > 1 ? launch_fast_split<DIM, BRK, true>(a, st) : launch_fast_split<DIM, BRK, false>(a, st);
 }
 
@@ -422,7 +442,7 @@ size_t pmb_generic_smem(const Geom &g, int precision)
 template <int DIM, bool LINEAR, bool SPLIT>
 static int launch_np_split(const TileArgs &a, cudaStream_t st)
 {
-    const size_t smem = split_smem(a.g, a.split);
+    const size_t smem = split_smem(a.g, np_fast_smem(a.g), a.split);
     PD_CUDA(cudaFuncSetAttribute(np_fast<DIM, LINEAR, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     np_fast<DIM, LINEAR, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a);
@@ -434,7 +454,7 @@ template <int DIM, bool LINEAR>
 static int launch_np_fast(const TileArgs &a0, cudaStream_t st)
 {
     TileArgs a = a0;
-    a.split = choose_split(a.g);
+    a.split = choose_split(a.g, np_fast_smem(a.g));
     return a.split > 1 ? launch_np_split<DIM, LINEAR, true>(a, st) : launch_np_split<DIM, LINEAR, false>(a, st);
 }
 

@@ -22,6 +22,10 @@
 
 #include "pd_internal.cuh"
 
+// float4 words per stencil entry of the FP32C NP / LP table (np_word in
+// pd_force_pmb.cu; built in pd_api.cu)
+#define NP_TAB_WORDS(dim) ((dim) == 3 ? 3 : 2)
+
 namespace pdk {
 
 // ----------------------------------------------------------- packed values
