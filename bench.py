@@ -646,6 +646,17 @@ def main():
             line["lps128"] = {"workload": desc2, "value": nb2 / (ms2 * 1e-3), "unit": "bond-updates/s",
                               "ms_per_step": ms2, "steps": len(d2), "launches_per_step": 2,
                               "alu_frac": ops2 * nb2 / (ms2 * 1e-3) / 1e12 / peak}
+            sim2.close()
+            # the explicit benchmark shape of Sec. 6.2 (443^2 nodes, m = 20, NP law)
+            wl3, desc3 = workload("paper443")
+            sim3 = make_sim(pd, wl3, pd.PD_FP32C, stream)
+            d3 = time_steps(pd, torch, sim3, wl3, 10, 3, stream, flush)
+            ms3 = float(np.mean(d3))
+            nb3 = pd.pd_bond_count(sim3)
+            line["paper443"] = {"workload": desc3, "value": nb3 / (ms3 * 1e-3), "unit": "bond-updates/s",
+                                "ms_per_step": ms3, "steps": len(d3), "launches_per_step": 1,
+                                "alu_frac": FP32_OPS_PER_BOND["np2"] * nb3 / (ms3 * 1e-3) / 1e12 / peak}
+            sim3.close()
             line["neighbour_build"] = {"block64": time_build(pd, torch, wl, stream),
                                        "lps128": time_build(pd, torch, wl2, stream)}
             line["jvp200"] = {"fp64": time_jvp(pd, torch, pd.PD_FP64), "fp32c": time_jvp(pd, torch, pd.PD_FP32C)}
@@ -661,7 +672,6 @@ def main():
                 "pcg_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64,
                                                        precond=pd.PD_PRECOND_BLOCK_JACOBI),
                 "cg_fp32c": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP32C)}
-            sim2.close()
 
     line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
