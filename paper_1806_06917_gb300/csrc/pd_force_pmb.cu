@@ -303,6 +303,117 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     }
 }
 
+// 2D wide horizons: each thread owns two point pairs, t and t + T/4 (by/4 box
+// rows apart, the constant offset dbi), so that every table entry read from
+// shared memory serves four points: per 32-lane step 2 broadcast table loads
+// and 2 gathers move 128 bonds, against 2 + 1 for 64 bonds with one pair. The
+// shared-memory data pipe bounds np_fast at m = 20; the arithmetic is np_word's.
+template <bool MASKED, bool LINEAR>
+__device__ __forceinline__ void np_word2(const float4 *tw, int nb, const float4 *P4, int bi, int dbi,
+                                         float2 nux0, float2 nuy0, float2 nux1, float2 nuy1, uint32_t c0,
+                                         uint32_t c1, uint32_t c2, uint32_t c3, float2 &Fx0, float2 &Fy0,
+                                         float2 &Fx1, float2 &Fy1)
+{
+PD_PRAGMA_UNROLL(PD_UNROLL)
+    for (int b = 0; b < nb; ++b) {
+        const float4 ta = tw[2 * b], tb = tw[2 * b + 1];
+        const int off = __float_as_int(tb.w);
+        const float4 r0 = P4[bi + off], r1 = P4[bi + dbi + off];
+        const float2 ex0 = f2add(f2lo(r0), nux0), ey0 = f2add(f2hi(r0), nuy0);
+        const float2 ex1 = f2add(f2lo(r1), nux1), ey1 = f2add(f2hi(r1), nuy1);
+        float2 dot0 = f2mul(ex0, f2lo(ta)), dot1 = f2mul(ex1, f2lo(ta));
+        dot0 = f2fma(ey0, f2hi(ta), dot0);
+        dot1 = f2fma(ey1, f2hi(ta), dot1);
+        float2 w0 = f2mul(dot0, f2lo(tb)), w1 = f2mul(dot1, f2lo(tb));
+        if (!LINEAR) {
+            const float2 ak = make_float2(tb.z, tb.z);
+            w0 = f2mul(w0, f2ex2(f2mul(ak, f2mul(dot0, dot0))));
+            w1 = f2mul(w1, f2ex2(f2mul(ak, f2mul(dot1, dot1))));
+        }
+        if (MASKED) {
+            w0.x = ((c0 >> b) & 1u) ? w0.x : 0.f;
+            w0.y = ((c1 >> b) & 1u) ? w0.y : 0.f;
+            w1.x = ((c2 >> b) & 1u) ? w1.x : 0.f;
+            w1.y = ((c3 >> b) & 1u) ? w1.y : 0.f;
+        }
+        Fx0 = f2fma(w0, f2lo(ta), Fx0);
+        Fy0 = f2fma(w0, f2hi(ta), Fy0);
+        Fx1 = f2fma(w1, f2lo(ta), Fx1);
+        Fy1 = f2fma(w1, f2hi(ta), Fy1);
+    }
+}
+
+// Launch: one CTA per tile, (tile points / 4) * a.split threads; thread (t, sub)
+// owns pairs t and t + T/4 and the sub-th of a.split ranges of stencil words.
+template <bool LINEAR>
+__global__ void __launch_bounds__(1024, 1) np_fast2(const TileArgs a)
+{
+    const Geom &g = a.g;
+    const PairBox pb = pair_box(g);
+    const int S = g.S;
+    extern __shared__ float4 smem4[];
+    float4 *P4 = smem4;
+    float4 *tab = P4 + pb.n;                  // the layout of np_fast_smem in 2D
+    constexpr int E = NP_TAB_WORDS(2);
+    __shared__ int s_nbr[27];
+    const int tile = blockIdx.x;
+    const int4 org = __ldg(&a.tile_org[tile]);
+    for (int k = threadIdx.x; k < E * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    load_nbr(a, tile, s_nbr);
+    __syncthreads();
+    stage_pairs(a, pb, org, tile, s_nbr, P4, nullptr);
+    __syncthreads();
+
+    const int npairs = g.T / 2, nthr = npairs / 2;     // nthr: a multiple of 32 (T >= 128)
+    const int sub = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int w0 = sub * g.W / a.split, w1 = (sub + 1) * g.W / a.split;
+    const PairPts q0 = pair_points(g, pb, org, tile, t), q1 = pair_points(g, pb, org, tile, t + nthr);
+    const int dbi = q1.bi - q0.bi;
+    float2 Fx0, Fy0, Fx1, Fy1;
+    {
+        const float4 u0 = P4[q0.bi], u1 = P4[q1.bi];
+        const float2 nux0 = f2neg(f2lo(u0)), nuy0 = f2neg(f2hi(u0));
+        const float2 nux1 = f2neg(f2lo(u1)), nuy1 = f2neg(f2hi(u1));
+        Fx0 = Fy0 = Fx1 = Fy1 = make_float2(0.f, 0.f);
+        const size_t mo0 = (size_t)w0 * g.nslots;
+        uint32_t n0 = q0.act[0] ? a.mask[mo0 + q0.slot[0]] : 0u;
+        uint32_t n1 = q0.act[1] ? a.mask[mo0 + q0.slot[1]] : 0u;
+        uint32_t n2 = q1.act[0] ? a.mask[mo0 + q1.slot[0]] : 0u;
+        uint32_t n3 = q1.act[1] ? a.mask[mo0 + q1.slot[1]] : 0u;
+        for (int w = w0; w < w1; ++w) {
+            const uint32_t m0 = n0, m1 = n1, m2 = n2, m3 = n3;
+            if (w + 1 < w1) {
+                const size_t mo = (size_t)(w + 1) * g.nslots;
+                n0 = q0.act[0] ? a.mask[mo + q0.slot[0]] : 0u;
+                n1 = q0.act[1] ? a.mask[mo + q0.slot[1]] : 0u;
+                n2 = q1.act[0] ? a.mask[mo + q1.slot[0]] : 0u;
+                n3 = q1.act[1] ? a.mask[mo + q1.slot[1]] : 0u;
+            }
+            const int nb = min(32, S - 32 * w);
+            const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            const float4 *tw = tab + E * 32 * w;
+            if (__all_sync(0xffffffffu, m0 == full && m1 == full && m2 == full && m3 == full))
+                np_word2<false, LINEAR>(tw, nb, P4, q0.bi, dbi, nux0, nuy0, nux1, nuy1, m0, m1, m2, m3, Fx0, Fy0,
+                                        Fx1, Fy1);
+            else
+                np_word2<true, LINEAR>(tw, nb, P4, q0.bi, dbi, nux0, nuy0, nux1, nuy1, m0, m1, m2, m3, Fx0, Fy0,
+                                       Fx1, Fy1);
+        }
+    }
+    float2 *red = reinterpret_cast<float2 *>(tab + E * S);
+    float2 Fz0 = make_float2(0.f, 0.f), Fz1 = Fz0;
+    if (a.split > 1) {
+        pair_split_sum(a, red, npairs, t, sub, Fx0, Fy0, Fz0);
+        pair_split_sum(a, red, npairs, t + nthr, sub, Fx1, Fy1, Fz1);
+    }
+    if (sub == 0) {
+        const float FA0[3] = {Fx0.x, Fy0.x, 0.f}, FB0[3] = {Fx0.y, Fy0.y, 0.f};
+        pair_epilogue2(a, q0, FA0, FB0, 2);
+        const float FA1[3] = {Fx1.x, Fy1.x, 0.f}, FB1[3] = {Fx1.y, Fy1.y, 0.f};
+        pair_epilogue2(a, q1, FA1, FB1, 2);
+    }
+}
+
 // Runtime stencil (any horizon), one point per thread. R = float (FP32C) or
 // double (FP64). Stencil entries come from a.stencil; box dims from a.g.m.
 template <class R>
@@ -397,9 +508,9 @@ static size_t split_smem(const Geom &g, size_t base, int split)
 // smallest that reaches the most resident threads per SM, counting the
 // 1024-thread limit of 64 registers per thread and 228 KB of shared memory per
 // SM (1 KB of it reserved per CTA).
-static int choose_split(const Geom &g, size_t base)
+static int choose_split(const Geom &g, size_t base, int pairs_per_thread = 1)
 {
-    const int nthr = g.T / 2;
+    const int nthr = g.T / 2 / pairs_per_thread;
     int best = 1, best_threads = 0;
     for (int split = 1; split <= 4 && split <= g.W; split *= 2) {
         const size_t smem = split_smem(g, base, split);
@@ -450,11 +561,26 @@ static int launch_np_split(const TileArgs &a, cudaStream_t st)
     return PD_OK;
 }
 
+template <bool LINEAR>
+static int launch_np_fast2(const TileArgs &a, cudaStream_t st)
+{
+    const size_t smem = split_smem(a.g, np_fast_smem(a.g), a.split);
+    PD_CUDA(cudaFuncSetAttribute(np_fast2<LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    np_fast2<LINEAR><<<a.g.ntiles, a.g.T / 4 * a.split, smem, st>>>(a);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
 template <int DIM, bool LINEAR>
 static int launch_np_fast(const TileArgs &a0, cudaStream_t st)
 {
     TileArgs a = a0;
     a.split = choose_split(a.g, np_fast_smem(a.g));
+    // 2D wide horizons (the one-pair kernel would split): two pairs per thread
+    if (DIM == 2 && a.split > 1 && a.g.T >= 128) {
+        a.split = choose_split(a.g, np_fast_smem(a.g), 2);
+        return launch_np_fast2<LINEAR>(a, st);
+    }
     return a.split > 1 ? launch_np_split<DIM, LINEAR, true>(a, st) : launch_np_split<DIM, LINEAR, false>(a, st);
 }
 
