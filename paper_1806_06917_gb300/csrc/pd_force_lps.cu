@@ -130,6 +130,127 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
     }
 }
 
+// Dilatation with two point pairs per thread: pairs t and t + T/4 (2 z-layers
+// apart in the box, the constant offset dbi), so every table entry read from
+// shared memory serves four points; the CTA's two thread halves sum the two
+// halves of the stencil words, added in a fixed order (half 0 + half 1). The
+// one-pair kernel is bound by the L1 / shared-memory pipe (ncu: 92 % of its
+// throughput, 14 wavefronts per 64 bonds, 7 of them table broadcasts); this
+// form moves 19 per 128.
+template <bool MASKED>
+__device__ __forceinline__ void lps_dil_word2(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
+                                              int dbi, float2 nux0, float2 nuy0, float2 nuz0, float2 nux1,
+                                              float2 nuy1, float2 nuz1, uint32_t c0, uint32_t c1, uint32_t c2,
+                                              uint32_t c3, float2 &acc0, float2 &acc1)
+{
+PD_PRAGMA_UNROLL(PD_UNROLL)
+    for (int b = 0; b < nb; ++b) {
+        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
+        const int off = __float_as_int(tw[4 * b + 3].x);
+        const float4 r0 = P4[bi + off], r1 = P4[bi + dbi + off];
+        const float2 z0 = P2[bi + off], z1 = P2[bi + dbi + off];
+        float2 e0, e1;
+        {
+            const float2 ex = f2add(f2lo(r0), nux0), ey = f2add(f2hi(r0), nuy0), ez = f2add(z0, nuz0);
+            const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
+            float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
+            num = f2fma(ey, f2add(yy, f2hi(ta)), num);
+            num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+            e0 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2hi(tc))), f2hi(tb))));
+        }
+        {
+            const float2 ex = f2add(f2lo(r1), nux1), ey = f2add(f2hi(r1), nuy1), ez = f2add(z1, nuz1);
+            const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
+            float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
+            num = f2fma(ey, f2add(yy, f2hi(ta)), num);
+            num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+            e1 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2hi(tc))), f2hi(tb))));
+        }
+        if (MASKED) {
+            e0.x = ((c0 >> b) & 1u) ? e0.x : 0.f;
+            e0.y = ((c1 >> b) & 1u) ? e0.y : 0.f;
+            e1.x = ((c2 >> b) & 1u) ? e1.x : 0.f;
+            e1.y = ((c3 >> b) & 1u) ? e1.y : 0.f;
+        }
+        acc0 = f2fma(e0, f2lo(tc), acc0);
+        acc1 = f2fma(e1, f2lo(tc), acc1);
+    }
+}
+
+// Launch: one CTA per tile, T/2 threads (tiles of at least 2^7 points and two
+// stencil words).
+__global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArgs a)
+{
+    const Geom &g = a.g;
+    const PairBox pb = pair_box(g);
+    const int S = g.S;
+    extern __shared__ float4 smem4[];
+    float4 *P4 = smem4;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
+    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
+    __shared__ int s_nbr[27];
+    const int tile = blockIdx.x;
+    const int4 org = __ldg(&a.tile_org[tile]);
+    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    load_nbr(a, tile, s_nbr);
+    __syncthreads();
+    stage_pairs(a, pb, org, tile, s_nbr, P4, P2);
+    __syncthreads();
+
+    const int nthr = g.T / 4;                                  // a multiple of 32
+    const int half = threadIdx.x >= nthr, t = threadIdx.x - half * nthr;
+    const int wsplit = (g.W + 1) / 2;
+    const int w0 = half ? wsplit : 0, w1 = half ? g.W : wsplit;
+    const PairPts q0 = pair_points(g, pb, org, tile, t), q1 = pair_points(g, pb, org, tile, t + nthr);
+    const int dbi = q1.bi - q0.bi;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    {
+        const float4 u0 = P4[q0.bi], u1 = P4[q1.bi];
+        const float2 nux0 = f2neg(f2lo(u0)), nuy0 = f2neg(f2hi(u0)), nuz0 = f2neg(P2[q0.bi]);
+        const float2 nux1 = f2neg(f2lo(u1)), nuy1 = f2neg(f2hi(u1)), nuz1 = f2neg(P2[q1.bi]);
+        const size_t mo0 = (size_t)w0 * g.nslots;
+        uint32_t n0 = q0.act[0] && w0 < w1 ? a.mask[mo0 + q0.slot[0]] : 0u;
+        uint32_t n1 = q0.act[1] && w0 < w1 ? a.mask[mo0 + q0.slot[1]] : 0u;
+        uint32_t n2 = q1.act[0] && w0 < w1 ? a.mask[mo0 + q1.slot[0]] : 0u;
+        uint32_t n3 = q1.act[1] && w0 < w1 ? a.mask[mo0 + q1.slot[1]] : 0u;
+        for (int w = w0; w < w1; ++w) {
+            const uint32_t m0 = n0, m1 = n1, m2 = n2, m3 = n3;
+            if (w + 1 < w1) {
+                const size_t mo = (size_t)(w + 1) * g.nslots;
+                n0 = q0.act[0] ? a.mask[mo + q0.slot[0]] : 0u;
+                n1 = q0.act[1] ? a.mask[mo + q0.slot[1]] : 0u;
+                n2 = q1.act[0] ? a.mask[mo + q1.slot[0]] : 0u;
+                n3 = q1.act[1] ? a.mask[mo + q1.slot[1]] : 0u;
+            }
+            const int nb = min(32, S - 32 * w);
+            const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            const float4 *tw = tab + 4 * 32 * w;
+            if (__all_sync(0xffffffffu, m0 == full && m1 == full && m2 == full && m3 == full))
+                lps_dil_word2<false>(tw, nb, P4, P2, q0.bi, dbi, nux0, nuy0, nuz0, nux1, nuy1, nuz1, m0, m1, m2,
+                                     m3, acc0, acc1);
+            else
+                lps_dil_word2<true>(tw, nb, P4, P2, q0.bi, dbi, nux0, nuy0, nuz0, nux1, nuy1, nuz1, m0, m1, m2,
+                                    m3, acc0, acc1);
+        }
+    }
+    // combine the halves: half 1 publishes, half 0 adds and writes theta
+    __syncthreads();
+    float2 *ex = reinterpret_cast<float2 *>(smem4);            // reuses the staged box
+    if (half) {
+        ex[2 * t] = acc0;
+        ex[2 * t + 1] = acc1;
+    }
+    __syncthreads();
+    if (!half) {
+        acc0 = f2add(acc0, ex[2 * t]);
+        acc1 = f2add(acc1, ex[2 * t + 1]);
+        for (int p = 0; p < 2; ++p) {
+            if (q0.act[p]) a.theta32[q0.slot[p]] = 3.f * __ldg(&a.minv32[q0.slot[p]]) * (p ? acc0.y : acc0.x);
+            if (q1.act[p]) a.theta32[q1.slot[p]] = 3.f * __ldg(&a.minv32[q1.slot[p]]) * (p ? acc1.y : acc1.x);
+        }
+    }
+}
+
 // The force pass needs 40 bytes of shared memory per point pair (u, and a, b of
 // both points), which allows only two CTAs per SM. To keep 32 warps per SM it
 // runs one thread per point (512 for a 2^9 tile): thread t of half h owns point
@@ -364,7 +485,9 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
     const Geom &g = a.g;
     const size_t smem = lps_generic_smem(g, precision, dil);
     if (precision == PD_FP32C) {
-        auto k = dil ? lps_dil_fast : lps_force_fast;
+        // dilatation: two pairs per thread from 2^7-point tiles and two stencil words on
+        const bool dil2 = dil && g.T >= 128 && g.W >= 2;
+        auto k = dil ? (dil2 ? lps_dil_fast2 : lps_dil_fast) : lps_force_fast;
         PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int threads = dil ? (g.T / 2 < 256 ? g.T / 2 : 256) : g.T;
         k<<<g.ntiles, threads, smem, st>>>(a);
