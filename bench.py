@@ -61,7 +61,7 @@ KERNEL_LABEL = {
     "pmb3": lambda wl: "pmb_fast<3, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
     "pmb2": lambda wl: "pmb_fast<2, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
     "lps": lambda wl: "lps_dil_fast + lps_force_fast (one step)",
-    "np2": lambda wl: "np_fast<2, false>",
+    "np2": lambda wl: "np_fast2<false> (two point pairs per thread)",
 }
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step's
@@ -71,12 +71,15 @@ KERNEL_LABEL = {
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
-    "pmb3": {"bytes": 21880064 + 256, "sha": "431684c1e40529ae",
+    "pmb3": {"bytes": 21886720 + 512, "sha": "ffa0ad2942e0c313",
              "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
              "profile": "profiles/pmb_fast_block3d_64.md"},
-    "lps": {"bytes": (109638144 + 6081280) + (195538432 + 96884480), "sha": "eacfbe8eda1ec707",
+    "lps": {"bytes": (109677568 + 5741568) + (195601664 + 96896256), "sha": "913600bd9740b191",
             "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
             "profile": "profiles/lps_block3d_128.md"},
+    "np2": {"bytes": 45660672 + 98560, "sha": "ffa0ad2942e0c313",
+            "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
+            "profile": "profiles/np_fast2_paper443.md"},
 }
 
 
