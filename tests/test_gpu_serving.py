@@ -21,14 +21,15 @@ def pd():
     return _pd
 
 
-def _submit(pd, srv, r, u_out=None, v_out=None, precision=None, tile_log2=0):
+def _submit(pd, srv, r, u_out=None, v_out=None, precision=None, tile_log2=0, integrator=0):
     g, m, run = pd.describe(r.grid, r.mat, precision=pd.PD_FP32C if precision is None else precision,
-                            tile_log2=tile_log2)
+                            tile_log2=tile_log2, integrator=integrator)
     return pd.pd_submit(srv, g, m, run, r.steps, u0=r.u0, v0=np.zeros_like(r.u0), u_out=u_out, v_out=v_out)
 
 
-def _alone(pd, r, tile_log2, precision=None):
-    sim = gpu_sim(pd, r.grid, r.mat, pd.PD_FP32C if precision is None else precision, tile_log2=tile_log2)
+def _alone(pd, r, tile_log2, precision=None, integrator=0):
+    sim = gpu_sim(pd, r.grid, r.mat, pd.PD_FP32C if precision is None else precision, tile_log2=tile_log2,
+                  integrator=integrator)
     pd.pd_set_state(sim, u=r.u0, v=np.zeros_like(r.u0))
     pd.pd_step_explicit(sim, r.steps)
     u, v = pd.pd_get_state(sim)
@@ -55,6 +56,20 @@ def test_served_results_equal_the_same_runs_alone(pd):
         assert 0.0 < res["submit_s"] <= res["start_s"] <= res["end_s"]
         ua, va = _alone(pd, r, res["tile_log2"])
         assert np.array_equal(u, ua) and np.array_equal(v, va)
+
+
+def test_central_difference_requests_equal_the_same_runs_alone(pd):
+    # the CD state (u^{k-1} in the other staging buffer) carries across quanta
+    mix = _small_mix(4, 23)
+    srv = pd.Server(max_active=2, quantum_steps=9)
+    outs = [np.full(r.u0.shape, np.nan) for r in mix]
+    tickets = [_submit(pd, srv, r, u_out=o, integrator=pd.PD_INTEGRATOR_CD) for r, o in zip(mix, outs)]
+    results = [pd.pd_wait(srv, t, timeout_s=120.0) for t in tickets]
+    srv.close()
+    for r, res, u in zip(mix, results, outs):
+        assert res["state"] == pd.PD_REQ_DONE, res
+        ua, _ = _alone(pd, r, res["tile_log2"], integrator=pd.PD_INTEGRATOR_CD)
+        assert np.array_equal(u, ua)
 
 
 def test_fp64_requests_are_served_too(pd):
