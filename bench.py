@@ -632,6 +632,26 @@ def main():
                              / FP64_NOMINAL_TFLOPS,
                              "fp64_peak_source": "nominal GB300 FP64 rate (not measured on this pool)"}
         sim64.close()
+        # accuracy of the FP32-compensated path against the all-FP64 GPU path: the
+        # same workload from its initial state, the same number of steps
+        acc_steps = 200
+        acc = []
+        for prec in (pd.PD_FP32C, pd.PD_FP64):
+            sa = make_sim(pd, wl, prec, stream)
+            pd.pd_set_state(sa, u=wl.u0, v=wl.v0, stream=stream)
+            if wl.bc_kind is not None and wl.bc_kind.any():
+                pd.pd_set_bc(sa, wl.bc_kind, wl.bc_val, stream)
+            pd.pd_step_explicit(sa, acc_steps, stream)
+            ua, va = pd.pd_get_state(sa, stream=stream)
+            acc.append((ua, va, pd.pd_get_broken(sa, stream=stream)))
+            sa.close()
+        (u32, v32, k32), (u64, v64, k64) = acc
+        line["fp32c_vs_fp64"] = {
+            "steps": acc_steps,
+            "u_rel_l2": float(np.linalg.norm(u32 - u64) / max(np.linalg.norm(u64), 1e-300)),
+            "v_rel_l2": float(np.linalg.norm(v32 - v64) / max(np.linalg.norm(v64), 1e-300)),
+            "broken_fp32c": int(k32.sum()), "broken_fp64": int(k64.sum()),
+            "broken_differ": int((k32 != k64).sum())}
         # the same step with the central-difference drift (Eq. (10))
         simcd = make_sim(pd, wl, pd.PD_FP32C, stream, integrator=pd.PD_INTEGRATOR_CD)
         dcd = time_steps(pd, torch, simcd, wl, max(3, min(args.steps, 10)), 3, stream, flush)
