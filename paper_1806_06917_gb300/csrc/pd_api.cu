@@ -973,13 +973,13 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     const double *src = nullptr;
     if (u) {
         if ((rc = user_source(s, u, &src, st)) != PD_OK) return rc;
-        rc = scatter_stage(s->g, s->slot_of_user, src, f32c ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
+        rc = scatter_stage(s->g, s->user_of_slot, src, f32c ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
                            f32c ? nullptr : s->d4[s->cur], st);
         if (rc != PD_OK) return rc;
     }
     if (v) {
         if ((rc = user_source(s, v, &src, st)) != PD_OK) return rc;
-        rc = scatter_stage(s->g, s->slot_of_user, src, f32c ? nullptr : s->v, f32c ? s->vhl : nullptr, nullptr, st);
+        rc = scatter_stage(s->g, s->user_of_slot, src, f32c ? nullptr : s->v, f32c ? s->vhl : nullptr, nullptr, st);
         if (rc != PD_OK) return rc;
     }
     return PD_OK;

@@ -666,15 +666,23 @@ __global__ void k_scatter(Geom g, const int *slot_of_user, const double *user, d
 
 // User order (n x dim FP64, AoS) to the slot of each point in one pass: the
 // FP64 SoA arrays if given, and the staging form if given (FP32C double-float
-// pair hi = fl(x), lo = fl(x - hi); FP64 double4).
-__global__ void k_scatter_stage(Geom g, const int *slot_of_user, const double *user, double *s0, double *s1,
+// pair hi = fl(x), lo = fl(x - hi); FP64 double4). One thread per slot, so the
+// slot-order writes are coalesced and the user array is read in runs of
+// x-consecutive points (a Morton-ordered warp covers 4 x 4 x 2 points); slots
+// off the lattice get zeros.
+__global__ void k_scatter_stage(Geom g, const int *user_of_slot, const double *user, double *s0, double *s1,
                                 double *s2, float4 *hl, double4_32a *d4)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.npoints) return;
-    const int s = slot_of_user[i];
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const long long i = user_of_slot[s];
     const int d = g.dim;
-    const double x = user[i * d], y = user[i * d + 1], z = d == 3 ? user[i * d + 2] : 0.0;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (i >= 0) {
+        x = user[i * d];
+        y = user[i * d + 1];
+        if (d == 3) z = user[i * d + 2];
+    }
     if (s0) {
         s0[s] = x;
         s1[s] = y;
@@ -712,10 +720,10 @@ __global__ void k_gather_unstage(Geom g, const int *slot_of_user, const float4 *
     if (d == 3) user[i * d + 2] = z;
 }
 
-int scatter_stage(const Geom &g, const int *slot_of_user, const double *user, double *const slot[3], float4 *hl,
+int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, double *const slot[3], float4 *hl,
                   double4_32a *d4, cudaStream_t st)
 {
-    k_scatter_stage<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, slot_of_user, user, slot ? slot[0] : nullptr,
+    k_scatter_stage<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, user_of_slot, user, slot ? slot[0] : nullptr,
                                                              slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
                                                              hl, d4);
     PD_CUDA(cudaGetLastError());

@@ -162,7 +162,7 @@ size_t krylov_partial_doubles(long long n, int kmax);
 int krylov_norm(const double *x, long long n, KrylovWork &wk, double *out, cudaStream_t st);
 
 // User order to slots with the staging form in one pass, and back (pd_build.cu).
-int scatter_stage(const Geom &g, const int *slot_of_user, const double *user, double *const slot[3], float4 *hl,
+int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, double *const slot[3], float4 *hl,
                   double4_32a *d4, cudaStream_t st);
 int gather_unstage(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
                    cudaStream_t st);
