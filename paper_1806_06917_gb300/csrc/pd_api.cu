@@ -375,8 +375,7 @@ static int create_impl(pd_sim *s)
     // paired halo box (x extent bx + 2m; y extent by + 2m in 3D, by/2 + 2m in 2D)
     {
         const int PHX = g.bx + 2 * g.m, PHY = g.dim == 3 ? g.by + 2 * g.m : g.by / 2 + 2 * g.m;
-        std::vector<float4> ta(4 * (size_t)g.S), tb(4 * (size_t)g.S);
-        const double A = 3.0 * mt.K - 5.0 * mt.mu, B = 15.0 * mt.mu;
+        std::vector<float4> ta(4 * (size_t)g.S), tb(3 * (size_t)g.S);
         for (int k = 0; k < g.S; ++k) {
             const int4 d = st[k];
             const double rr = r0[k], d2 = d.w;
@@ -386,12 +385,11 @@ static int create_impl(pd_sim *s)
             memcpy(&offf, &off, sizeof(float));
             const float4 dxy = make_float4((float)d.x, (float)d.x, (float)d.y, (float)d.y);
             if (!np_law) ta[4 * k] = dxy;
-            tb[4 * k] = dxy;
-            // LPS force: {dz,dz,|d|,|d|} {A|d|V_ij x2, B V_ij x2} {|d|^2,|d|^2,offset,-}
-            tb[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
-            tb[4 * k + 2] = make_float4((float)(A * rr * vij), (float)(A * rr * vij), (float)(B * vij),
-                                        (float)(B * vij));
-            tb[4 * k + 3] = make_float4((float)d2, (float)d2, offf, 0.f);
+            // LPS force, 3 float4 per entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|^2,|d|^2,offset,V_ij}
+            // (the moduli 3K - 5mu and 15mu go with the staged theta / m~ and 1 / m~)
+            tb[3 * k] = dxy;
+            tb[3 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
+            tb[3 * k + 2] = make_float4((float)d2, (float)d2, offf, (float)vij);
             if (mt.model == PD_MODEL_NP || mt.model == PD_MODEL_LP) {
                 // compact entries (NP_TAB_WORDS float4 each, written over the first
                 // entries of the table): the bond weight t = J V_ij / |d| and the

@@ -49,8 +49,11 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
     return acc;
 }
 
-// One 32-bond word of the LPS force sum.
-template <bool MASKED>
+// One 32-bond word of the LPS force sum. The staged a = (3K - 5mu) theta / m~ and
+// b = 15 mu / m~ carry the moduli, so the bond weight is
+//   (t_i + t_j) V_ij / |y| = (|d| (a_i + a_j) + e (b_i + b_j)) V_ij / |y|
+// (VOLCORR = false: V_ij = 1, no multiply).
+template <bool MASKED, bool VOLCORR>
 __device__ __forceinline__ void lps_force_word(const float4 *tw, int nb, const float4 *P4, const float4 *PT,
                                                const float2 *P2, int bi, float2 nux, float2 nuy, float2 nuz,
                                                float2 ai, float2 bi_, uint32_t c0, uint32_t c1, float2 &Fx,
@@ -58,8 +61,8 @@ __device__ __forceinline__ void lps_force_word(const float4 *tw, int nb, const f
 {
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        // table entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {A|d|V_ij x2, B V_ij x2} {|d|^2,|d|^2,offset,-}
-        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2], td = tw[4 * b + 3];
+        // table entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|^2,|d|^2,offset,V_ij}
+        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], td = tw[3 * b + 2];
         const int off = __float_as_int(td.z);
         const float4 r4 = P4[bi + off], t4 = PT[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
@@ -70,9 +73,9 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
         const float2 qq = f2add(num, f2lo(td));            // |y|^2 = |d|^2 + 2 d.e + e.e
         const float2 rs = f2rsqrt(qq);
         const float2 e = f2mul(num, f2rcp(f2add(f2mul(qq, rs), f2hi(tb))));
-        // (t_i + t_j) V_ij = A |d| V_ij (a_i + a_j) + B V_ij e (b_i + b_j)
-        float2 gg = f2mul(f2lo(tc), f2add(ai, f2lo(t4)));
-        gg = f2fma(f2mul(f2hi(tc), e), f2add(bi_, f2hi(t4)), gg);
+        float2 gg = f2mul(f2hi(tb), f2add(ai, f2lo(t4)));
+        gg = f2fma(e, f2add(bi_, f2hi(t4)), gg);
+        if (VOLCORR) gg = f2mul(gg, make_float2(td.w, td.w));
         float2 wgt = f2mul(gg, rs);
         if (MASKED) {
             wgt.x = ((c0 >> b) & 1u) ? wgt.x : 0.f;
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArg
 // pair t and sums the stencil words of its half; the two partial forces are
 // added in a fixed order (half 0 + half 1) through shared memory before the
 // update.
+template <bool VOLCORR>
 __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
 {
     const Geom &g = a.g;
@@ -266,16 +270,17 @@ __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
     float4 *P4 = smem4;                                        // {xA, xB, yA, yB}
     float4 *PT = P4 + pb.n;                                     // {aA, aB, bA, bB}: a = theta/m~, b = 1/m~
     float2 *P2 = reinterpret_cast<float2 *>(PT + pb.n);        // {zA, zB}
-    float4 *tab = PT + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
+    float4 *tab = PT + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
+    for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     {
         const Ref32 ref = tile_ref32(a, tile);
         const float inv_h = (float)a.inv_h;
+        const float kA = (float)a.A, kB = (float)a.B;           // 3K - 5mu, 15mu
 #pragma unroll 2
         for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
             int cA[3], cB[3];
@@ -284,11 +289,11 @@ __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
             const int sB = slot_of(a, s_nbr, org, cB);
             const float4 rA = stage_one(a, a.src_hl, sA, ref, inv_h);
             const float4 rB = stage_one(a, a.src_hl, sB, ref, inv_h);
-            const float bA = sA >= 0 ? __ldg(&a.minv32[sA]) : 0.f, bB = sB >= 0 ? __ldg(&a.minv32[sB]) : 0.f;
-            const float aA = sA >= 0 ? a.theta32[sA] * bA : 0.f, aB = sB >= 0 ? a.theta32[sB] * bB : 0.f;
+            const float mA = sA >= 0 ? __ldg(&a.minv32[sA]) : 0.f, mB = sB >= 0 ? __ldg(&a.minv32[sB]) : 0.f;
+            const float aA = sA >= 0 ? kA * (a.theta32[sA] * mA) : 0.f, aB = sB >= 0 ? kA * (a.theta32[sB] * mB) : 0.f;
             P4[b] = make_float4(rA.x, rB.x, rA.y, rB.y);
             P2[b] = make_float2(rA.z, rB.z);
-            PT[b] = make_float4(aA, aB, bA, bB);
+            PT[b] = make_float4(aA, aB, kB * mA, kB * mB);
         }
     }
     __syncthreads();
@@ -316,11 +321,11 @@ __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
             }
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
-            const float4 *tw = tab + 4 * 32 * w;
+            const float4 *tw = tab + 3 * 32 * w;
             if (__all_sync(0xffffffffu, m0 == full && m1 == full))
-                lps_force_word<false>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
+                lps_force_word<false, VOLCORR>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
             else
-                lps_force_word<true>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
+                lps_force_word<true, VOLCORR>(tw, nb, P4, PT, P2, q.bi, nux, nuy, nuz, ai, bi, m0, m1, Fx, Fy, Fz);
         }
     }
     // combine the halves: half 1 publishes its partial force, half 0 adds it
@@ -346,7 +351,7 @@ size_t lps_fast_smem(const Geom &g, bool dil)
     const size_t n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
     const size_t p2 = ((n + 1) / 2) * sizeof(float4);
     if (dil) return n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
-    return 2 * n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
+    return 2 * n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
 }
 
 // ------------------------------------------------------------------ generic
@@ -487,7 +492,7 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
     if (precision == PD_FP32C) {
         // dilatation: two pairs per thread from 2^7-point tiles and two stencil words on
         const bool dil2 = dil && g.T >= 128 && g.W >= 2;
-        auto k = dil ? (dil2 ? lps_dil_fast2 : lps_dil_fast) : lps_force_fast;
+        auto k = dil ? (dil2 ? lps_dil_fast2 : lps_dil_fast) : (a.vol_corr ? lps_force_fast<true> : lps_force_fast<false>);
         PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int threads = dil ? (g.T / 2 < 256 ? g.T / 2 : 256) : g.T;
         k<<<g.ntiles, threads, smem, st>>>(a);

@@ -333,7 +333,7 @@ struct TileArgs {
     const float *bc32;          // FP32C boundary values as (hi, lo) per DOF, component-major
     const float4 *body32;       // FP32C body force per slot
     const float4 *tab_a;        // FP32C stencil table of the PMB or dilatation kernel (3 float4 / entry)
-    const float4 *tab_b;        // FP32C stencil table of the LPS force kernel (4 float4 / entry)
+    const float4 *tab_b;        // FP32C stencil table of the LPS force kernel (3 float4 / entry)
     const int *tile_nbr;        // [ntiles * 27] the 3^d neighbour tiles of each tile (or -1)
     int nbr_ok;                 // halo within one tile in every direction: tile_nbr is usable
     float kF, kB;               // FP32C kick factors: dt/2 * fscale / rho and dt/2 / rho

@@ -154,6 +154,22 @@ def test_lps_dilatation_and_force_match_oracle(pd, precision, n):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_lps_partial_volume_matches_oracle(pd, precision):
+    # V_ij enters the weighted volume, the dilatation and the force pass
+    grid = W.Grid(dim=3, n=(21, 19, 18), h=1.0 / 128, m=3)
+    mat = W.Material(model=W.LPS, K=40e9, mu=30e9, vol_corr=1)
+    sim = gpu_sim(pd, grid, mat, pd.PD_FP32C if precision == "fp32c" else pd.PD_FP64)
+    bonds = O.neighbors(grid)
+    mv = O.weighted_volume(grid, mat, bonds)
+    u = (1e-4 / 3) * grid.positions() + _u_random(grid, 1e-5, seed=4, translate=0.1)
+    th_or = O.dilatation(grid, mat, bonds, mv, u)
+    tol = FORCE_TOL_FP32C if precision == "fp32c" else 1e-10
+    assert rel_l2(pd.pd_dilatation(sim, u=u), th_or) <= tol
+    assert rel_l2(pd.pd_force(sim, u=u), O.lps_force(grid, mat, bonds, mv, th_or, u)) <= tol
+    sim.close()
+
+
 # ---------------------------------------------------------------- explicit
 
 def _run_both(pd, wl, precision, steps, dt=None):
