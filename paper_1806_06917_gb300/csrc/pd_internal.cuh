@@ -142,12 +142,15 @@ struct KrylovOp {
     void *ctx;
     int (*precond)(void *ctx, const double *r, double *z, cudaStream_t st); // z = M^-1 r, or null
 };
+// Device scalars a Krylov solve needs at least (dot results and CG's state).
+constexpr size_t KRYLOV_DSC_MIN = 16;
 struct KrylovWork {
     double *basis;      // GMRES: (restart + 1) * n; CG: 3 * n
     double *tmp;        // n
     double *aux;        // 2 * n (preconditioned solves)
     double *partial;    // krylov_partial_doubles(n, restart)
-    double *dsc;        // restart + 2
+    double *dsc;        // max(restart + 2, KRYLOV_DSC_MIN)
+    cudaStream_t cap;   // a stream for graph capture (CG), or null
 };
 struct KrylovStats {
     int iters;

@@ -5,11 +5,12 @@
 // Vectors are FP64, component-major over slots: v[c * nslots + s], c < dim;
 // slots without a point hold 0 and every operation keeps them 0. All sums are
 // deterministic: a fixed block partition, a fixed in-block tree, and a fixed
-// final tree over the block partials. The few scalars of a Krylov iteration
-// (the Hessenberg column, the Givens rotations, CG's alpha and beta) are FP64
-// host arithmetic on values read back from the device.
+// final tree over the block partials. GMRES's few scalars per iteration (the
+// Hessenberg column, the Givens rotations) are FP64 host arithmetic on values
+// read back from the device; CG keeps alpha and beta on the device.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "pd_tile.cuh"
@@ -258,6 +259,69 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
 
 // ------------------------------------------------------------------------ CG
 
+// CG's scalars live on the device, after the dot results in dsc[0..]: the host
+// enqueues CG_CHUNK iterations at a time and reads back once per chunk, instead
+// of waiting for p.Ap and r.r in every iteration. An iteration that finds the
+// residual below the target sets DONE; the later iterations of the chunk then
+// change neither x nor r (alpha = 0, p kept), so x is the iterate at which the
+// host loop would have stopped.
+enum { CG_RZ = 8, CG_ALPHA, CG_BETA, CG_RR, CG_TARGET, CG_DONE, CG_ITERS, CG_BAD };
+static_assert(CG_BAD < (int)KRYLOV_DSC_MIN, "CG scalars exceed the device scalar block");
+constexpr int CG_CHUNK = 32;
+
+// after dsc[0] = p.Ap: alpha = (r.z) / (p.Ap), or a non-positive curvature flag
+__global__ void k_cg_alpha(double *s)
+{
+    if (s[CG_DONE] != 0.0) {
+        s[CG_ALPHA] = 0.0;
+        return;
+    }
+    const double pq = s[0];
+    if (!(pq > 0.0)) {
+        s[CG_BAD] = pq == pq ? pq : -1.0;     // the offending p.Ap (NaN reported as -1)
+        s[CG_DONE] = 1.0;
+        s[CG_ALPHA] = 0.0;
+        return;
+    }
+    s[CG_ALPHA] = s[CG_RZ] / pq;
+}
+
+// y = (sign alpha) x + y, alpha from the device
+__global__ void k_cg_axpy(const double *s, double sign, const double *x, double *y, long long n)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    y[e] = (sign * s[CG_ALPHA]) * x[e] + 1.0 * y[e];
+}
+
+// after dsc[0] = r.r: count the iteration, test ||r|| <= target
+__global__ void k_cg_check(double *s)
+{
+    if (s[CG_DONE] != 0.0) return;
+    const double rr1 = s[0];
+    s[CG_ITERS] += 1.0;
+    s[CG_RR] = rr1;
+    if (sqrt(rr1) <= s[CG_TARGET]) s[CG_DONE] = 1.0;
+}
+
+// beta = (r.z)_new / (r.z)_old with (r.z)_new in dsc[0] (PCG) or r.r (CG)
+__global__ void k_cg_beta(double *s, int precond)
+{
+    if (s[CG_DONE] != 0.0) return;
+    const double rz1 = precond ? s[0] : s[CG_RR];
+    s[CG_BETA] = rz1 / s[CG_RZ];
+    s[CG_RZ] = rz1;
+}
+
+// p = z + beta p, unless done
+__global__ void k_cg_p(const double *s, const double *z, double *p, long long n)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n || s[CG_DONE] != 0.0) return;
+    const double beta = s[CG_BETA];
+    p[e] = 1.0 * z[e] + (beta == 0.0 ? 0.0 : beta * p[e]);
+}
+
 // Conjugate gradients for symmetric positive definite A: x = 0 start, stop when
 // ||b - A x|| <= rtol ||b|| (recursive residual) or after maxit iterations. With
 // a symmetric positive definite preconditioner M it is PCG (p from z = M^-1 r).
@@ -267,6 +331,7 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
     KrylovCtx c{n, st, wk.partial, wk.dsc, {}};
     double *r = wk.basis, *p = wk.basis + n, *q = wk.basis + 2 * n;
     double *z = op.precond ? wk.aux : r;       // without M, z is r itself
+    const unsigned nbk = (unsigned)((n + 255) / 256);
     PD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     PD_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     int rc = PD_OK;
@@ -280,34 +345,84 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
     stats->res = stats->res0;
     stats->iters = 0;
     stats->converged = rr == 0.0;
-    const double target = rtol * stats->res0;
-    while (!stats->converged && stats->iters < maxit) {
-        if ((rc = op.apply(op.ctx, p, q, st)) != PD_OK) return rc;
-        double pq = 0.0;
-        if ((rc = dots(c, p, 0, 1, q, &pq)) != PD_OK) return rc;
-        if (!(pq > 0.0)) {
-            set_error("CG: the operator is not positive definite (p.Ap = %g)", pq);
+    if (stats->converged) return PD_OK;
+    double init[CG_BAD + 1] = {0.0};
+    init[CG_RZ] = rz;
+    init[CG_RR] = rr;
+    init[CG_TARGET] = rtol * stats->res0;
+    PD_CUDA(cudaMemcpyAsync(c.dsc, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    // one iteration, enqueued on stream s (no host synchronisation)
+    auto iteration = [&](cudaStream_t s) -> int {
+        KrylovCtx cs{n, s, wk.partial, wk.dsc, {}};
+        int e = op.apply(op.ctx, p, q, s);
+        if (e == PD_OK) e = dots(cs, p, 0, 1, q, nullptr);
+        if (e != PD_OK) return e;
+        k_cg_alpha<<<1, 1, 0, s>>>(cs.dsc);
+        k_cg_axpy<<<nbk, 256, 0, s>>>(cs.dsc, 1.0, p, x, n);
+        k_cg_axpy<<<nbk, 256, 0, s>>>(cs.dsc, -1.0, q, r, n);
+        if ((e = dots(cs, r, 0, 1, r, nullptr)) != PD_OK) return e;
+        k_cg_check<<<1, 1, 0, s>>>(cs.dsc);
+        if (op.precond) {
+            if ((e = op.precond(op.ctx, r, z, s)) != PD_OK) return e;
+            if ((e = dots(cs, r, 0, 1, z, nullptr)) != PD_OK) return e;
+        }
+        k_cg_beta<<<1, 1, 0, s>>>(cs.dsc, op.precond ? 1 : 0);
+        k_cg_p<<<nbk, 256, 0, s>>>(cs.dsc, z, p, n);
+        PD_CUDA(cudaGetLastError());
+        return PD_OK;
+    };
+    // a full chunk as one CUDA graph (its launch gaps, not its kernels, dominate at
+    // small n); if the capture does not succeed the chunks are launched one by one
+    cudaGraphExec_t exec = nullptr;
+    if (wk.cap && maxit >= CG_CHUNK) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(wk.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int crc = PD_OK;
+            for (int k = 0; k < CG_CHUNK && crc == PD_OK; ++k) crc = iteration(wk.cap);
+            const cudaError_t e = cudaStreamEndCapture(wk.cap, &graph);
+            if (crc != PD_OK || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+                exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();
+    }
+    int launched = 0;
+    double back[CG_BAD + 1];
+    while (launched < maxit) {
+        const int chunk = std::min(CG_CHUNK, maxit - launched);
+        if (exec && chunk == CG_CHUNK) {
+            const cudaError_t e = cudaGraphLaunch(exec, st);
+            if (e != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(e, "cudaGraphLaunch (CG chunk)");
+            }
+        } else {
+            for (int k = 0; k < chunk; ++k)
+                if ((rc = iteration(st)) != PD_OK) {
+                    if (exec) cudaGraphExecDestroy(exec);
+                    return rc;
+                }
+        }
+        launched += chunk;
+        cudaError_t e = cudaMemcpyAsync(back, c.dsc, sizeof(back), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            if (exec) cudaGraphExecDestroy(exec);
+            return cuda_fail(e, "CG scalars");
+        }
+        stats->iters = (int)back[CG_ITERS];
+        stats->res = sqrt(back[CG_RR]);
+        if (back[CG_BAD] != 0.0) {
+            if (exec) cudaGraphExecDestroy(exec);
+            set_error("CG: the operator is not positive definite (p.Ap = %g)", back[CG_BAD]);
             return PD_EINVAL;
         }
-        const double alpha = rz / pq;
-        if ((rc = axpby(c, alpha, p, 1.0, x)) != PD_OK) return rc;
-        if ((rc = axpby(c, -alpha, q, 1.0, r)) != PD_OK) return rc;
-        double rr1 = 0.0;
-        if ((rc = dots(c, r, 0, 1, r, &rr1)) != PD_OK) return rc;
-        ++stats->iters;
-        stats->res = sqrt(rr1);
-        if (stats->res <= target) {
+        if (back[CG_DONE] != 0.0) {
             stats->converged = 1;
             break;
         }
-        double rz1 = rr1;
-        if (op.precond) {
-            if ((rc = op.precond(op.ctx, r, z, st)) != PD_OK) return rc;
-            if ((rc = dots(c, r, 0, 1, z, &rz1)) != PD_OK) return rc;
-        }
-        if ((rc = axpby(c, 1.0, z, rz1 / rz, p)) != PD_OK) return rc;     // p = z + beta p
-        rz = rz1;
     }
+    if (exec) cudaGraphExecDestroy(exec);
     return PD_OK;
 }
 
