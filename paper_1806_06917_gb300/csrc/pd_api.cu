@@ -1231,7 +1231,8 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
     int rc = PD_OK;
     if ((rc = nk_reserve(&s->nk_basis, &s->nk_basis_n, (size_t)(kdim + 1) * n, st)) != PD_OK) return rc;
     if ((rc = nk_reserve(&s->nk_partial, &s->nk_partial_n, krylov_partial_doubles(n, kdim + 1), st)) != PD_OK) return rc;
-    if ((rc = nk_reserve(&s->nk_dsc, &s->nk_dsc_n, std::max<size_t>((size_t)kdim + 2, KRYLOV_DSC_MIN), st)) != PD_OK)
+    if ((rc = nk_reserve(&s->nk_dsc, &s->nk_dsc_n,
+                         krylov_dsc_doubles(o.krylov == PD_KRYLOV_GMRES ? o.restart : 0), st)) != PD_OK)
         return rc;
     if (!s->nk_tmp) {
         if ((rc = nk_reserve(&s->nk_tmp, &hr, (size_t)n, st)) != PD_OK) return rc;

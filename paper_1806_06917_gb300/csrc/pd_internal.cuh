@@ -149,7 +149,7 @@ struct KrylovWork {
     double *tmp;        // n
     double *aux;        // 2 * n (preconditioned solves)
     double *partial;    // krylov_partial_doubles(n, restart)
-    double *dsc;        // max(restart + 2, KRYLOV_DSC_MIN)
+    double *dsc;        // krylov_dsc_doubles(...)
     cudaStream_t cap;   // a stream for graph capture (CG), or null
 };
 struct KrylovStats {
@@ -162,6 +162,8 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
 int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int maxit, double rtol,
               KrylovWork &wk, KrylovStats *stats, cudaStream_t st);
 size_t krylov_partial_doubles(long long n, int kmax);
+// Device scalars (KrylovWork::dsc) a solve needs: GMRES(restart) or, with 0, CG.
+size_t krylov_dsc_doubles(int krylov_gmres_restart);
 int krylov_norm(const double *x, long long n, KrylovWork &wk, double *out, cudaStream_t st);
 
 // User order to slots with the staging form in one pass, and back (pd_build.cu).

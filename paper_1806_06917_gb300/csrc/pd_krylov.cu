@@ -38,29 +38,22 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return t;
 }
 
-// partial[i * nb + b] = sum over block b of V_i . w, for i < k (V_i = V + i * ldv).
-__global__ void __launch_bounds__(KT) k_mdot(const double *V, long long ldv, int k, const double *w, long long n,
+// partial[i * nb + b] = sum over block b of V_i . w (V_i = V + i * ldv); grid
+// (nb, k): block (b, i) sums chunk b of vector i, so all k products run at once.
+__global__ void __launch_bounds__(KT) k_mdot(const double *V, long long ldv, const double *w, long long n,
                                              double *partial)
 {
     __shared__ double red[KT / 32];
     const long long base = (long long)blockIdx.x * KCHUNK + threadIdx.x;
-    double wq[KPER];
+    const double *vi = V + (long long)blockIdx.y * ldv;
+    double acc = 0.0;
 #pragma unroll
     for (int q = 0; q < KPER; ++q) {
         const long long e = base + (long long)q * KT;
-        wq[q] = e < n ? w[e] : 0.0;
+        if (e < n) acc = fma(vi[e], w[e], acc);
     }
-    for (int i = 0; i < k; ++i) {
-        const double *vi = V + (long long)i * ldv;
-        double acc = 0.0;
-#pragma unroll
-        for (int q = 0; q < KPER; ++q) {
-            const long long e = base + (long long)q * KT;
-            if (e < n) acc = fma(vi[e], wq[q], acc);
-        }
-        const double t = block_sum(acc, red);
-        if (threadIdx.x == 0) partial[(long long)i * gridDim.x + blockIdx.x] = t;
-    }
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // out[i] = sum_b partial[i * nb + b], one block per i, fixed order.
@@ -106,7 +99,7 @@ struct KrylovCtx {
 static int dots(KrylovCtx &c, const double *V, long long ldv, int k, const double *w, double *host_out)
 {
     const int nb = kblocks(c.n);
-    k_mdot<<<nb, KT, 0, c.st>>>(V, ldv, k, w, c.n, c.partial);
+    k_mdot<<<dim3(nb, k), KT, 0, c.st>>>(V, ldv, w, c.n, c.partial);
     k_partial_sum<<<k, KT, 0, c.st>>>(c.partial, nb, c.dsc);
     PD_CUDA(cudaGetLastError());
     if (host_out) {
@@ -131,13 +124,6 @@ static int lincomb_dev(KrylovCtx &c, double *y, double alpha, const double *V, l
     return PD_OK;
 }
 
-static int lincomb_host(KrylovCtx &c, double *y, double alpha, const double *V, long long ldv, int k,
-                        const double *coef)
-{
-    PD_CUDA(cudaMemcpyAsync(c.dsc, coef, sizeof(double) * k, cudaMemcpyHostToDevice, c.st));
-    return lincomb_dev(c, y, alpha, V, ldv, k, 1.0);
-}
-
 static int norm2(KrylovCtx &c, const double *x, double *out)
 {
     double d = 0.0;
@@ -149,6 +135,96 @@ static int norm2(KrylovCtx &c, const double *x, double *out)
 
 // ------------------------------------------------------------------ GMRES(m)
 
+// Device layout of GMRES's small arrays in dsc (m = restart): the dot results
+// [0, m+1), the Hessenberg matrix H (column-major, (m+1) x m), the rotations cs
+// and sn, the rotated right-hand side g (m+1), the solution y of the small
+// triangular system (m), and the scalars. The host enqueues GM_CHUNK Arnoldi
+// steps at a time and reads back once per chunk; a step after the one that
+// met the target (or broke down) changes nothing that the update of x uses.
+struct GmLayout {
+    int m, H, cs, sn, g, y, sc;
+    __host__ __device__ explicit GmLayout(int m_)
+        : m(m_), H(m_ + 1), cs(H + (m_ + 1) * m_), sn(cs + m_), g(sn + m_), y(g + m_ + 1), sc(y + m_)
+    {
+    }
+    __host__ __device__ int size() const { return sc + 8; }
+};
+enum { GM_TARGET = 0, GM_DONE, GM_K, GM_RES, GM_INVH, GM_ITERS };
+constexpr int GM_CHUNK = 8;
+
+size_t krylov_dsc_doubles(int krylov_gmres_restart)
+{
+    const size_t g = krylov_gmres_restart > 0 ? (size_t)GmLayout(krylov_gmres_restart).size() : 0;
+    return std::max(g, KRYLOV_DSC_MIN);
+}
+
+// H[0:j+1, j] = dsc[0:j+1] (first Gram-Schmidt pass) or += (second pass)
+__global__ void k_gm_hcol(double *d, int m, int j, int add)
+{
+    const GmLayout L(m);
+    if (d[L.sc + GM_DONE] != 0.0) return;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double *h = d + L.H + i + (m + 1) * j;
+        *h = add ? *h + d[i] : d[i];
+    }
+}
+
+// After dsc[0] = |w|^2: H[j+1, j] = |w|, the previous rotations and a new one on
+// column j, g rotated, the residual estimate |g[j+1]|, the scale 1/|w| for w.
+__global__ void k_gm_step(double *d, int m, int j)
+{
+    const GmLayout L(m);
+    double *sc = d + L.sc;
+    if (sc[GM_DONE] != 0.0) {
+        sc[GM_INVH] = 0.0;
+        return;
+    }
+    const double hn = sqrt(d[0]);
+    double *hj = d + L.H + (m + 1) * j;
+    double *cs = d + L.cs, *sn = d + L.sn, *g = d + L.g;
+    hj[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * hj[i] + sn[i] * hj[i + 1];
+        hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
+        hj[i] = t;
+    }
+    const double den = hypot(hj[j], hj[j + 1]);
+    cs[j] = den > 0.0 ? hj[j] / den : 1.0;
+    sn[j] = den > 0.0 ? hj[j + 1] / den : 0.0;
+    hj[j] = den;
+    hj[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    sc[GM_K] = j + 1;
+    sc[GM_ITERS] += 1.0;
+    sc[GM_RES] = fabs(g[j + 1]);
+    sc[GM_INVH] = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (sc[GM_RES] <= sc[GM_TARGET] || hn == 0.0) sc[GM_DONE] = 1.0;
+}
+
+// y = H(0:k, 0:k)^-1 g(0:k), back substitution
+__global__ void k_gm_solve(double *d, int m)
+{
+    const GmLayout L(m);
+    const int k = (int)d[L.sc + GM_K];
+    const double *H = d + L.H, *g = d + L.g;
+    double *y = d + L.y;
+    for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int l = i + 1; l < k; ++l) t -= H[i + (m + 1) * l] * y[l];
+        const double dd = H[i + (m + 1) * i];
+        y[i] = dd != 0.0 ? t / dd : 0.0;
+    }
+}
+
+// y *= d[idx]
+__global__ void k_scale_dev(const double *d, int idx, double *y, long long n)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    y[e] = d[idx] * y[e];
+}
+
 // Restarted GMRES with classical Gram-Schmidt applied twice (CGS2) and Givens
 // rotations: solve A x = b from x = 0 until ||b - A x|| <= rtol ||b||. With a
 // preconditioner M it is right-preconditioned (Arnoldi on A M^-1, x += M^-1 V y),
@@ -158,10 +234,12 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
 {
     KrylovCtx c{n, st, wk.partial, wk.dsc, {}};
     const int m = restart;
+    const GmLayout L(m);
     double *V = wk.basis;                    // (m + 1) vectors of n
     double *w = wk.tmp;
     double *zt = wk.aux, *ty = wk.aux + n;   // M^-1 v_j; V y before M^-1
     const bool pc = op.precond != nullptr;
+    const unsigned nbk = (unsigned)((n + 255) / 256);
     PD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     double bnorm = 0.0;
     int rc = norm2(c, b, &bnorm);
@@ -175,7 +253,60 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
         return PD_OK;
     }
     const double target = rtol * bnorm;
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hcol(m + 2);
+    // one Arnoldi step j of the cycle, enqueued on stream s without a host synchronisation
+    auto arnoldi = [&](int j, cudaStream_t s) -> int {
+        KrylovCtx cs{n, s, wk.partial, wk.dsc, {}};
+        double *vj1 = V + (long long)(j + 1) * n;
+        const double *src = V + (long long)j * n;
+        int e = PD_OK;
+        if (pc) {
+            if ((e = op.precond(op.ctx, src, zt, s)) != PD_OK) return e;
+            src = zt;
+        }
+        if ((e = op.apply(op.ctx, src, vj1, s)) != PD_OK) return e;
+        for (int pass = 0; pass < 2; ++pass) {          // CGS2: h = V^T w, w -= V h; twice
+            if ((e = dots(cs, V, n, j + 1, vj1, nullptr)) != PD_OK) return e;
+            k_gm_hcol<<<1, 64, 0, s>>>(cs.dsc, m, j, pass);
+            if ((e = lincomb_dev(cs, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return e;
+        }
+        if ((e = dots(cs, vj1, 0, 1, vj1, nullptr)) != PD_OK) return e;
+        k_gm_step<<<1, 1, 0, s>>>(cs.dsc, m, j);
+        k_scale_dev<<<nbk, 256, 0, s>>>(cs.dsc, L.sc + GM_INVH, vj1, n);
+        PD_CUDA(cudaGetLastError());
+        return PD_OK;
+    };
+    // The chunk of steps [j0, j0 + GM_CHUNK) as a CUDA graph, captured on first use
+    // (launch gaps dominate at small n); null if the capture does not succeed, and
+    // the chunk is then launched step by step.
+    struct Graphs {
+        std::vector<cudaGraphExec_t> g;
+        ~Graphs()
+        {
+            for (cudaGraphExec_t e : g)
+                if (e) cudaGraphExecDestroy(e);
+        }
+    } graphs;
+    graphs.g.assign((m + GM_CHUNK - 1) / GM_CHUNK, nullptr);
+    std::vector<char> tried(graphs.g.size(), 0);
+    auto chunk_graph = [&](int j0) -> cudaGraphExec_t {
+        const int ci = j0 / GM_CHUNK;
+        if (!wk.cap || tried[ci]) return graphs.g[ci];
+        tried[ci] = 1;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(wk.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int crc = PD_OK;
+            for (int j = j0; j < std::min(m, j0 + GM_CHUNK) && crc == PD_OK; ++j) crc = arnoldi(j, wk.cap);
+            const cudaError_t e = cudaStreamEndCapture(wk.cap, &graph);
+            if (crc != PD_OK || e != cudaSuccess || !graph ||
+                cudaGraphInstantiate(&graphs.g[ci], graph, 0) != cudaSuccess)
+                graphs.g[ci] = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();
+        return graphs.g[ci];
+    };
+    std::vector<double> init(L.size(), 0.0);
+    double back[8];
     bool first = true;
     while (true) {
         // r = b - A x  (x = 0 on the first cycle)
@@ -197,62 +328,40 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
         }
         if (stats->iters >= maxit) return PD_OK;
         if ((rc = axpby(c, 0.0, V, 1.0 / beta, V)) != PD_OK) return rc;   // V_0 = r / beta
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
+        std::fill(init.begin(), init.end(), 0.0);
+        init[L.g] = beta;
+        init[L.sc + GM_TARGET] = target;
+        PD_CUDA(cudaMemcpyAsync(c.dsc, init.data(), sizeof(double) * init.size(), cudaMemcpyHostToDevice, st));
+        const int steps = std::min(m, maxit - stats->iters);
         int k = 0;
-        for (int j = 0; j < m && stats->iters < maxit; ++j) {
-            double *vj1 = V + (long long)(j + 1) * n;
-            const double *src = V + (long long)j * n;
-            if (pc) {
-                if ((rc = op.precond(op.ctx, src, zt, st)) != PD_OK) return rc;
-                src = zt;
+        bool done = false;
+        for (int j0 = 0; j0 < steps && !done; j0 += GM_CHUNK) {
+            const int j1 = std::min(steps, j0 + GM_CHUNK);
+            cudaGraphExec_t ge = j1 == std::min(m, j0 + GM_CHUNK) ? chunk_graph(j0) : nullptr;
+            if (ge) {
+                PD_CUDA(cudaGraphLaunch(ge, st));
+            } else {
+                for (int j = j0; j < j1; ++j)
+                    if ((rc = arnoldi(j, st)) != PD_OK) return rc;
             }
-            if ((rc = op.apply(op.ctx, src, vj1, st)) != PD_OK) return rc;
-            // CGS2: h = V^T w, w -= V h; twice
-            if ((rc = dots(c, V, n, j + 1, vj1, nullptr)) != PD_OK) return rc;
-            if ((rc = lincomb_dev(c, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return rc;
-            PD_CUDA(cudaMemcpyAsync(hcol.data(), c.dsc, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
-            if ((rc = dots(c, V, n, j + 1, vj1, nullptr)) != PD_OK) return rc;
-            if ((rc = lincomb_dev(c, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return rc;
-            std::vector<double> h2(j + 1);
-            PD_CUDA(cudaMemcpyAsync(h2.data(), c.dsc, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
-            double hn = 0.0;
-            if ((rc = norm2(c, vj1, &hn)) != PD_OK) return rc;     // synchronises the stream
-            for (int i = 0; i <= j; ++i) H[i + (size_t)(m + 1) * j] = hcol[i] + h2[i];
-            H[j + 1 + (size_t)(m + 1) * j] = hn;
-            if (hn > 0.0 && (rc = axpby(c, 0.0, vj1, 1.0 / hn, vj1)) != PD_OK) return rc;
-            // apply the previous rotations to column j, then a new one
-            double *hj = &H[(size_t)(m + 1) * j];
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * hj[i] + sn[i] * hj[i + 1];
-                hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
-                hj[i] = t;
-            }
-            const double den = hypot(hj[j], hj[j + 1]);
-            cs[j] = den > 0.0 ? hj[j] / den : 1.0;
-            sn[j] = den > 0.0 ? hj[j + 1] / den : 0.0;
-            hj[j] = den;
-            hj[j + 1] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            ++stats->iters;
-            k = j + 1;
-            stats->res = fabs(g[j + 1]);
-            if (stats->res <= target || hn == 0.0) break;
+            PD_CUDA(cudaMemcpyAsync(back, c.dsc + L.sc, sizeof(back), cudaMemcpyDeviceToHost, st));
+            PD_CUDA(cudaStreamSynchronize(st));
+            done = back[GM_DONE] != 0.0;
+            k = (int)back[GM_K];
         }
+        stats->iters += (int)back[GM_ITERS];
+        stats->res = back[GM_RES];
         // y = H(0:k, 0:k)^-1 g(0:k); x += V(:, 0:k) y
-        for (int i = k - 1; i >= 0; --i) {
-            double t = g[i];
-            for (int l = i + 1; l < k; ++l) t -= H[i + (size_t)(m + 1) * l] * y[l];
-            const double d = H[i + (size_t)(m + 1) * i];
-            y[i] = d != 0.0 ? t / d : 0.0;
-        }
-        if (k > 0 && !pc && (rc = lincomb_host(c, x, 1.0, V, n, k, y.data())) != PD_OK) return rc;
-        if (k > 0 && pc) {
-            // x += M^-1 (V y)
-            if ((rc = lincomb_host(c, ty, 0.0, V, n, k, y.data())) != PD_OK) return rc;
-            if ((rc = op.precond(op.ctx, ty, zt, st)) != PD_OK) return rc;
-            if ((rc = axpby(c, 1.0, zt, 1.0, x)) != PD_OK) return rc;
+        if (k > 0) {
+            k_gm_solve<<<1, 1, 0, st>>>(c.dsc, m);
+            if (!pc) {
+                k_lincomb<<<nbk, 256, 0, st>>>(x, 1.0, V, n, k, c.dsc + L.y, 1.0, n);
+            } else {
+                k_lincomb<<<nbk, 256, 0, st>>>(ty, 0.0, V, n, k, c.dsc + L.y, 1.0, n);
+                if ((rc = op.precond(op.ctx, ty, zt, st)) != PD_OK) return rc;
+                if ((rc = axpby(c, 1.0, zt, 1.0, x)) != PD_OK) return rc;
+            }
+            PD_CUDA(cudaGetLastError());
         }
     }
 }
