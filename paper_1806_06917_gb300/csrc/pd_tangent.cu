@@ -84,43 +84,64 @@ __global__ void __launch_bounds__(256) tangent_prepare(const TileArgs a, R *coef
 }
 
 // y = A w with A = -K on free DOFs and the identity on prescribed ones (the
-// Newton operator of pd_solve_static); w, y component-major over slots.
+// Newton operator of pd_solve_static); w, y component-major over slots. A block
+// of 8 warps covers TA_SLOTS = 32 slots: warp k of the block takes every
+// TA_PARTS-th stencil entry from k, so a warp's loads of D and nbr cover 32
+// consecutive slots and the 8 warps share the slots' sums (the small grids of an implicit solve would otherwise run one warp per
+// 32 slots, a few warps per SM, each waiting on its gathers in turn). The parts
+// are added in part order through shared memory.
+constexpr int TA_PARTS = 8;
+constexpr int TA_SLOTS = 256 / TA_PARTS;
+
 template <class R>
 __global__ void __launch_bounds__(256) tangent_apply(Geom g, const R *coef, const int *nbr, const int *user_of_slot,
                                                      const uint8_t *kind, const double *w, double *y)
 {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.nslots) return;
+    __shared__ R part[TA_PARTS][3][TA_SLOTS];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int grp = warp / TA_PARTS, sub = warp % TA_PARTS;
+    const int ls = grp * 32 + lane;                        // slot within the block
+    const long long s = (long long)blockIdx.x * TA_SLOTS + ls;
     const size_t ns = g.nslots;
     const int d = g.dim;
-    if (user_of_slot[s] < 0) {
+    const bool act = s < g.nslots && user_of_slot[s] >= 0;
+    R a0 = 0, a1 = 0, a2 = 0;
+    if (act) {
+        const int nc = d == 3 ? 6 : 3;
+        const double wi0 = w[s], wi1 = w[ns + s], wi2 = d == 3 ? w[2 * ns + s] : 0.0;
+#pragma unroll 2
+        for (int k = sub; k < g.S; k += TA_PARTS) {
+            const int j = __ldg(&nbr[(size_t)k * ns + s]);
+            const R *Dk = coef + (size_t)k * nc * ns + s;
+            const R d0 = (R)(w[j] - wi0), d1 = (R)(w[ns + j] - wi1);
+            if (d == 3) {
+                const R d2 = (R)(w[2 * ns + j] - wi2);
+                const R xx = __ldg(&Dk[0]), xy = __ldg(&Dk[ns]), yy = __ldg(&Dk[2 * ns]);
+                const R xz = __ldg(&Dk[3 * ns]), yz = __ldg(&Dk[4 * ns]), zz = __ldg(&Dk[5 * ns]);
+                a0 += xx * d0 + xy * d1 + xz * d2;
+                a1 += xy * d0 + yy * d1 + yz * d2;
+                a2 += xz * d0 + yz * d1 + zz * d2;
+            } else {
+                const R xx = __ldg(&Dk[0]), xy = __ldg(&Dk[ns]), yy = __ldg(&Dk[2 * ns]);
+                a0 += xx * d0 + xy * d1;
+                a1 += xy * d0 + yy * d1;
+            }
+        }
+    }
+    part[sub][0][ls] = a0;
+    part[sub][1][ls] = a1;
+    part[sub][2][ls] = a2;
+    __syncthreads();
+    if (sub != 0 || s >= g.nslots) return;
+    if (!act) {
         for (int c = 0; c < d; ++c) y[c * ns + s] = 0.0;
         return;
     }
-    const int nc = d == 3 ? 6 : 3;
-    const double wi0 = w[s], wi1 = w[ns + s], wi2 = d == 3 ? w[2 * ns + s] : 0.0;
-    R a0 = 0, a1 = 0, a2 = 0;
-    for (int k = 0; k < g.S; ++k) {
-        const int j = __ldg(&nbr[(size_t)k * ns + s]);
-        const R *Dk = coef + (size_t)k * nc * ns + s;
-        const R d0 = (R)(w[j] - wi0), d1 = (R)(w[ns + j] - wi1);
-        if (d == 3) {
-            const R d2 = (R)(w[2 * ns + j] - wi2);
-            const R xx = __ldg(&Dk[0]), xy = __ldg(&Dk[ns]), yy = __ldg(&Dk[2 * ns]);
-            const R xz = __ldg(&Dk[3 * ns]), yz = __ldg(&Dk[4 * ns]), zz = __ldg(&Dk[5 * ns]);
-            a0 += xx * d0 + xy * d1 + xz * d2;
-            a1 += xy * d0 + yy * d1 + yz * d2;
-            a2 += xz * d0 + yz * d1 + zz * d2;
-        } else {
-            const R xx = __ldg(&Dk[0]), xy = __ldg(&Dk[ns]), yy = __ldg(&Dk[2 * ns]);
-            a0 += xx * d0 + xy * d1;
-            a1 += xy * d0 + yy * d1;
-        }
-    }
-    const R acc[3] = {a0, a1, a2};
     for (int c = 0; c < d; ++c) {
+        R acc = part[0][c][ls];
+        for (int p = 1; p < TA_PARTS; ++p) acc += part[p][c][ls];
         const size_t e = (size_t)c * ns + s;
-        y[e] = kind[e] == PD_BC_DISPLACEMENT ? w[e] : -(double)acc[c];
+        y[e] = kind[e] == PD_BC_DISPLACEMENT ? w[e] : -(double)acc;
     }
 }
 
@@ -261,7 +282,7 @@ int launch_tangent_apply(const Geom &g, int precision, const void *cache, const 
     const size_t nc = g.dim == 3 ? 6 : 3;
     const size_t r = precision == PD_FP64 ? sizeof(double) : sizeof(float);
     const int *nbr = reinterpret_cast<const int *>(static_cast<const char *>(cache) + (size_t)g.S * g.nslots * nc * r);
-    const unsigned nb = (unsigned)((g.nslots + 255) / 256);
+    const unsigned nb = (unsigned)((g.nslots + TA_SLOTS - 1) / TA_SLOTS);
     if (precision == PD_FP64)
         tangent_apply<double><<<nb, 256, 0, st>>>(g, static_cast<const double *>(cache), nbr, user_of_slot, kind, w, y);
     else
