@@ -74,6 +74,7 @@ __global__ void k_lincomb(double *y, double alpha, const double *V, long long ld
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     double acc = alpha == 0.0 ? 0.0 : alpha * y[e];
+#pragma unroll 8
     for (int i = 0; i < k; ++i) acc = fma(csign * coef[i], V[(long long)i * ldv + e], acc);
     y[e] = acc;
 }
@@ -171,28 +172,41 @@ __global__ void k_gm_hcol(double *d, int m, int j, int add)
 
 // After dsc[0] = |w|^2: H[j+1, j] = |w|, the previous rotations and a new one on
 // column j, g rotated, the residual estimate |g[j+1]|, the scale 1/|w| for w.
+// The block stages column j and the rotations in shared memory (3 (m + 1)
+// doubles, dynamic) so that the sequential rotation loop of thread 0 does not
+// wait on global loads.
 __global__ void k_gm_step(double *d, int m, int j)
 {
+    extern __shared__ double gs[];
     const GmLayout L(m);
     double *sc = d + L.sc;
     if (sc[GM_DONE] != 0.0) {
-        sc[GM_INVH] = 0.0;
+        if (threadIdx.x == 0) sc[GM_INVH] = 0.0;
         return;
     }
-    const double hn = sqrt(d[0]);
     double *hj = d + L.H + (m + 1) * j;
-    double *cs = d + L.cs, *sn = d + L.sn, *g = d + L.g;
-    hj[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * hj[i] + sn[i] * hj[i + 1];
-        hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
-        hj[i] = t;
+    double *hs = gs, *css = gs + (m + 1), *sns = gs + 2 * (m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = hj[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        css[i] = d[L.cs + i];
+        sns[i] = d[L.sn + i];
     }
-    const double den = hypot(hj[j], hj[j + 1]);
-    cs[j] = den > 0.0 ? hj[j] / den : 1.0;
-    sn[j] = den > 0.0 ? hj[j + 1] / den : 0.0;
-    hj[j] = den;
-    hj[j + 1] = 0.0;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double hn = sqrt(d[0]);
+    double *cs = d + L.cs, *sn = d + L.sn, *g = d + L.g;
+    hs[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = css[i] * hs[i] + sns[i] * hs[i + 1];
+        hs[i + 1] = -sns[i] * hs[i] + css[i] * hs[i + 1];
+        hs[i] = t;
+    }
+    const double den = hypot(hs[j], hs[j + 1]);
+    cs[j] = den > 0.0 ? hs[j] / den : 1.0;
+    sn[j] = den > 0.0 ? hs[j + 1] / den : 0.0;
+    hs[j] = den;
+    hs[j + 1] = 0.0;
+    for (int i = 0; i <= j + 1; ++i) hj[i] = hs[i];
     g[j + 1] = -sn[j] * g[j];
     g[j] = cs[j] * g[j];
     sc[GM_K] = j + 1;
@@ -270,7 +284,7 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
             if ((e = lincomb_dev(cs, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return e;
         }
         if ((e = dots(cs, vj1, 0, 1, vj1, nullptr)) != PD_OK) return e;
-        k_gm_step<<<1, 1, 0, s>>>(cs.dsc, m, j);
+        k_gm_step<<<1, 64, 3 * (m + 1) * sizeof(double), s>>>(cs.dsc, m, j);
         k_scale_dev<<<nbk, 256, 0, s>>>(cs.dsc, L.sc + GM_INVH, vj1, n);
         PD_CUDA(cudaGetLastError());
         return PD_OK;
