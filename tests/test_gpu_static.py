@@ -56,6 +56,38 @@ def test_fp64_static_solve_matches_oracle_newton(pd, variant, nx, ny, krylov, ta
     sim.close()
 
 
+@pytest.mark.parametrize("restart", [3, 13, 50])
+def test_gmres_restarts_off_the_chunk_size_match_oracle(pd, restart):
+    # the device-side Arnoldi runs in chunks of 8 steps: restart lengths below,
+    # between and above that, with several restart cycles per solve
+    L = W.plate_static(nx=31, ny=17, strain=1e-4, variant="clamped")
+    g = L.grid
+    u_o, _, ok = I.solve_static(g, L.mat, O.neighbors(g), np.zeros((g.npoints, 2)), L.bc_kind, L.bc_val)
+    assert ok
+    sim = _static_sim(pd, L, pd.PD_FP64)
+    st = pd.pd_solve_static(sim, pd.newton_opts(krylov=pd.PD_KRYLOV_GMRES, restart=restart, max_linear_iters=20000,
+                                                linear_rtol=1e-12, newton_rtol=1e-12))
+    assert st["converged"] == 1 and st["linear_failures"] == 0
+    u, _ = pd.pd_get_state(sim)
+    assert rel_l2(u, u_o) <= 1e-9
+    sim.close()
+
+
+@pytest.mark.parametrize("krylov,limit", [("gmres", 37), ("cg", 45)])
+def test_linear_iteration_limits_are_exact(pd, krylov, limit):
+    # a limit that ends inside a chunk of device-side iterations: each Newton
+    # step's linear solve stops after exactly `limit` iterations
+    L = W.plate_static(nx=40, ny=20, strain=1e-4, variant="clamped")
+    sim = _static_sim(pd, L, pd.PD_FP64)
+    kr = pd.PD_KRYLOV_GMRES if krylov == "gmres" else pd.PD_KRYLOV_CG
+    st = pd.pd_solve_static(sim, pd.newton_opts(krylov=kr, restart=50, max_linear_iters=limit, max_newton_iters=2,
+                                                linear_rtol=1e-14, newton_rtol=1e-14))
+    assert st["newton_iters"] == 2
+    assert st["linear_iters"] == 2 * limit and st["linear_failures"] == 2
+    assert st["converged"] == 0
+    sim.close()
+
+
 @pytest.mark.parametrize("krylov", ["gmres", "cg"])
 def test_block_jacobi_preconditioned_solves_match_oracle(pd, krylov):
     # the lattice operator's diagonal blocks are nearly uniform (they change only
