@@ -598,6 +598,9 @@ def main():
                 "launch_ms": ms / launches_per_step if key != "lps" else ms,
                 "traffic_note": "bytes per step (all launches of one step) from one ncu capture, "
                                 "cold L2; null when the kernel changed since"}
+    if roofline["traffic"] is not None:
+        # the captured DRAM bytes per step over this run's step time
+        roofline["traffic_gbs"] = roofline["traffic"] / (ms * 1e-3) / 1e9
     peaks = measured_peaks()
     if peaks:
         # per-point bytes the fused step must move (the kernels read no neighbour
