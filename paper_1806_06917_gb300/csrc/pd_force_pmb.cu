@@ -124,10 +124,25 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    // the table (at most two float4 per thread here) is loaded into registers
+    // before the staging and stored after it, so its load latency overlaps the
+    // staging's instead of preceding it
+    const bool tab2 = 4 * S <= 2 * (int)blockDim.x;
+    const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
+    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+    if (tab2) {
+        if (k0 < 4 * S) t0 = __ldg(&a.tab_a[k0]);
+        if (k1 < 4 * S) t1 = __ldg(&a.tab_a[k1]);
+    } else {
+        for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    }
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr);
+    if (tab2) {
+        if (k0 < 4 * S) tab[k0] = t0;
+        if (k1 < 4 * S) tab[k1] = t1;
+    }
     __syncthreads();
 
     const int nthr = g.T / 2;            // point pairs: a multiple of 32, so a warp has one part
