@@ -219,3 +219,25 @@ def test_unknown_integrator_is_rejected(pd):
     rd.reserved = 1
     with pytest.raises(pd.PdError):
         pd.pd_create(gd, md, rd)
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_verlet_with_a_changed_time_step_matches_oracle(pd, precision):
+    # pd_set_dt completes the pending half kick first, as the oracle's runs do
+    g, mat, u0, v0 = _free_case("pmb3d")
+    sim = gpu_sim(pd, g, mat, _prec(pd, precision))
+    dt1 = pd.pd_get_dt(sim)
+    dt2 = 0.6 * dt1
+    pd.pd_set_state(sim, u=u0, v=v0)
+    pd.pd_step_explicit(sim, 25)
+    pd.pd_set_dt(sim, dt2)
+    assert pd.pd_get_dt(sim) == dt2
+    pd.pd_step_explicit(sim, 30)
+    u_g, v_g = pd.pd_get_state(sim)
+    st = O.ExplicitState(g, mat, O.neighbors(g), u0, v0)
+    st.run(dt1, 25)
+    st.run(dt2, 30)
+    assert pd.pd_get_step(sim) == 55
+    assert rel_l2(u_g, st.u) <= (U_TOL if precision == "fp32c" else 1e-10)
+    assert rel_l2(v_g, st.v) <= (V_TOL if precision == "fp32c" else 1e-9)
+    sim.close()
