@@ -403,6 +403,28 @@ def test_full_size_block64_force_and_short_run(pd):
     sim.close()
 
 
+def test_full_size_block64_run_of_100_steps(pd):
+    """The 64^3 benchmark workload over 100 fused steps (the pulse crosses the
+    block's centre region) against the oracle's run: u, v and the bond states."""
+    wl = W.block3d_pulse(nside=64, steps=100)
+    sim, bonds, st, u_g, v_g = _run_both(pd, wl, pd.PD_FP32C, wl.steps)
+    assert rel_l2(u_g, st.u) <= U_TOL
+    assert rel_l2(v_g, st.v) <= 1e-3
+    _, _, order, _ = gpu_csr_in_user_numbering(pd, sim)
+    brk = pd.pd_get_broken(sim)[order].astype(bool)
+    assert int((brk != bonds.broken.astype(bool)).sum()) <= max(2, int(1e-4 * bonds.broken.sum()))
+    sim.close()
+
+
+def test_full_size_block128_lps_run_of_10_steps(pd):
+    """The 128^3 LPS workload over 10 steps (two launches each) against the oracle."""
+    wl = W.block3d_lps(nside=128, steps=10)
+    sim, _, st, u_g, v_g = _run_both(pd, wl, pd.PD_FP32C, wl.steps)
+    assert rel_l2(u_g, st.u) <= U_TOL
+    assert rel_l2(v_g - wl.v0, st.v - wl.v0) <= 1e-3
+    sim.close()
+
+
 def test_full_size_block128_lps_force_sampled(pd):
     """128^3 LPS: the force at the initial state on the whole lattice."""
     wl = W.block3d_lps(nside=128, steps=1)
