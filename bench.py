@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -120,7 +121,10 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        # the raw samples: a scratch file (the JSON line carries their summary);
+        # PD_CLOCKS_DIR keeps them elsewhere
+        self.path = os.path.join(os.environ.get("PD_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 "pd_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
