@@ -101,6 +101,10 @@ def workload(name):
     if name == "block64":
         wl = W.block3d_pulse(nside=64)
         return wl, "block3d_64_pmb_break: 64^3 lattice, h=1/64 m, m=3, PMB s_c=1e-3, pulse + pre-notch"
+    if name == "block256":
+        wl = W.block3d_pulse(nside=256)
+        return wl, ("block3d_256_pmb_break: 256^3 lattice (16.8M points), h=1/256 m, m=3, PMB s_c=1e-3, "
+                    "pulse (w = 8h) + pre-notch; the 64^3 workload at 64x the points")
     if name == "lps128":
         wl = W.block3d_lps(nside=128)
         return wl, "block3d_128_lps: 128^3 lattice, h=1/128 m, m=3, LPS K=40 GPa mu=30 GPa"
@@ -508,7 +512,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="block64",
-                    choices=["block64", "lps128", "plate50", "paper443", "serve", "convergence"])
+                    choices=["block64", "block256", "lps128", "plate50", "paper443", "serve", "convergence"])
     ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
@@ -687,6 +691,18 @@ def main():
                                 "ms_per_step": ms3, "steps": len(d3), "launches_per_step": 1,
                                 "alu_frac": FP32_OPS_PER_BOND["np2"] * nb3 / (ms3 * 1e-3) / 1e12 / peak}
             sim3.close()
+            # the same PMB workload at 64x the points (256^3, 2.0e9 bonds): many
+            # waves of tiles per SM instead of one
+            wl4, desc4 = workload("block256")
+            sim4 = make_sim(pd, wl4, pd.PD_FP32C, stream)
+            d4 = time_steps(pd, torch, sim4, wl4, 10, 3, stream, flush)
+            ms4 = float(np.mean(d4))
+            nb4 = pd.pd_bond_count(sim4)
+            line["block256"] = {"workload": desc4, "value": nb4 / (ms4 * 1e-3), "unit": "bond-updates/s",
+                                "ms_per_step": ms4, "steps": len(d4), "bonds": nb4,
+                                "alu_frac": FP32_OPS_PER_BOND["pmb3"] * nb4 / (ms4 * 1e-3) / 1e12 / peak}
+            sim4.close()
+            del wl4
             line["neighbour_build"] = {"block64": time_build(pd, torch, wl, stream),
                                        "lps128": time_build(pd, torch, wl2, stream)}
             line["jvp200"] = {"fp64": time_jvp(pd, torch, pd.PD_FP64), "fp32c": time_jvp(pd, torch, pd.PD_FP32C)}
