@@ -161,12 +161,18 @@ __device__ __forceinline__ float4 stage_one(const TileArgs &a, const float4 *hl,
     return r;
 }
 
-// Coordinates of the two points of pair-box index b.
+// q = floor(b / d) for 0 <= b < 2^16 and 1 <= d <= 2^10 by a float product: b + 1/2
+// lies at least 1/(2d) from a multiple of d, more than the product's error
+// (b/d relative 2^-23), so truncation gives the exact quotient without an
+// integer division sequence.
+__device__ __forceinline__ int fdiv_small(int b, float inv_d) { return (int)(((float)b + 0.5f) * inv_d); }
+
+// Coordinates of the two points of pair-box index b (b < 2^16).
 __device__ __forceinline__ void pair_coords(const Geom &g, const PairBox &pb, const int4 &org, int b, int cA[3],
                                             int cB[3])
 {
-    const int bxl = b % pb.HX, rest = b / pb.HX;
-    const int byl = rest % pb.HY, bzl = rest / pb.HY;
+    const int rest = fdiv_small(b, __frcp_rn((float)pb.HX)), bxl = b - rest * pb.HX;
+    const int bzl = fdiv_small(rest, __frcp_rn((float)pb.HY)), byl = rest - bzl * pb.HY;
     cA[0] = cB[0] = org.x + bxl - g.m;
     if (g.dim == 3) {
         cA[1] = cB[1] = org.y + byl - g.m;
