@@ -620,7 +620,7 @@ def main():
             (bytes_pt * wl.grid.npoints + csr_b * nbonds) / (ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
         roofline["hbm_peak_gbs"] = peaks["hbm_gbs"]
 
-    line = {"metric": "bond updates/s (explicit step, FP32-compensated)", "value": value,
+    line = {"metric": "bond updates/s (explicit step)", "value": value,
             "unit": "bond-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)", "data": "synthetic",
