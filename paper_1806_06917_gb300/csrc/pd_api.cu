@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "pd_tile.cuh"
@@ -99,6 +100,8 @@ struct pd_sim {
     float4 *tab_b = nullptr;        // FP32C stencil table: LPS force
     int *tile_nbr = nullptr;        // [ntiles * 27]
     int nbr_ok = 0;
+    uint32_t *box_map = nullptr;    // [paired halo box] neighbour tile + brick code of both points
+    int box_edge[3] = {0, 0, 0};    // largest tile origin per axis for which box_map holds
     // CSR
     BuildOut csr{nullptr, nullptr, 0};
     // state
@@ -354,6 +357,7 @@ static int create_impl(pd_sim *s)
     PD_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
 
     const size_t NS = (size_t)g.nslots, NP = (size_t)g.npoints;
+    std::vector<uint32_t> box_map;      // uploaded after the other arrays (see the end)
     ALLOC(s->tile_org, sizeof(int4) * g.ntiles);
     ALLOC(s->tile_ref, sizeof(int) * g.ntiles);
     ALLOC(s->tile_lut, sizeof(int) * tlut.size());
@@ -439,6 +443,40 @@ static int create_impl(pd_sim *s)
         s->nbr_ok = g.m <= g.bx && g.m <= g.by && (g.dim == 2 || g.m <= g.bz);
         ALLOC(s->tile_nbr, sizeof(int) * nbr.size());
         PD_CUDA(cudaMemcpy(s->tile_nbr, nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice));
+        if (s->nbr_ok) {
+            // The paired halo box relative to a tile-aligned origin is the same for
+            // every tile: entry b holds, for its points A and B, the index of the
+            // neighbour tile (0..26, as in tile_nbr) and the brick code inside it,
+            // A in bits 0-13 and B in bits 14-27 (5 + 9 bits each; T <= 2^9). It
+            // replaces the staging's per-entry coordinate arithmetic in tiles whose
+            // 3^d neighbours are whole tiles or absent (box_edge).
+            const int dims[3] = {g.bx, g.by, g.dim == 3 ? g.bz : 1};
+            const int HX = g.bx + 2 * g.m, HY = g.dim == 3 ? g.by + 2 * g.m : g.by / 2 + 2 * g.m;
+            const int HZ = g.dim == 3 ? g.bz / 2 + 2 * g.m : 1;
+            std::vector<uint32_t> &map = box_map;
+            map.resize((size_t)HX * HY * HZ);
+            for (int b = 0; b < (int)map.size(); ++b) {
+                const int bxl = b % HX, byl = (b / HX) % HY, bzl = b / HX / HY;
+                int r[2][3] = {{bxl - g.m, byl - g.m, g.dim == 3 ? bzl - g.m : 0}, {0, 0, 0}};
+                for (int c = 0; c < 3; ++c) r[1][c] = r[0][c];
+                if (g.dim == 3) r[1][2] += g.bz / 2;
+                else r[1][1] += g.by / 2;
+                uint32_t e = 0;
+                for (int p = 0; p < 2; ++p) {
+                    int dt[3], l[3];
+                    for (int c = 0; c < 3; ++c) {
+                        dt[c] = r[p][c] < 0 ? -1 : r[p][c] / dims[c];
+                        l[c] = r[p][c] - dt[c] * dims[c];
+                    }
+                    const uint32_t k = (uint32_t)((dt[0] + 1) + 3 * (dt[1] + 1) + 9 * (dt[2] + 1));
+                    const uint32_t code = (uint32_t)morton_encode(g.dim, l[0], l[1], l[2]);
+                    e |= (k | code << 5) << (14 * p);
+                }
+                map[b] = e;
+            }
+            const int n3[3] = {g.nx, g.ny, g.nz};
+            for (int c = 0; c < 3; ++c) s->box_edge[c] = n3[c] % dims[c] == 0 ? INT_MAX : n3[c] - 2 * dims[c];
+        }
     }
 
     for (int c = 0; c < 3; ++c) {
@@ -476,6 +514,11 @@ static int create_impl(pd_sim *s)
     ALLOC(s->io, sizeof(double) * 3 * std::max(NP, NS));
     ALLOC(s->d_err, sizeof(int));
     ALLOC(s->d_count, sizeof(unsigned long long));
+    // last, so that it moves no other array of the pool
+    if (!box_map.empty()) {
+        ALLOC(s->box_map, sizeof(uint32_t) * box_map.size());
+        PD_CUDA(cudaMemcpy(s->box_map, box_map.data(), sizeof(uint32_t) * box_map.size(), cudaMemcpyHostToDevice));
+    }
     return PD_OK;
 }
 
@@ -531,6 +574,8 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.tab_b = s->tab_b;
     a.tile_nbr = s->tile_nbr;
     a.nbr_ok = s->nbr_ok;
+    a.box_map = s->box_map;
+    for (int c = 0; c < 3; ++c) a.box_edge[c] = s->box_edge[c];
     a.bc32 = s->bc32;
     a.body32 = s->body32;
     a.fscale = s->mat.model == PD_MODEL_LPS ? 1.0 / s->g.h : s->mat.c * s->mat.V;

@@ -98,11 +98,12 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
     float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
+    if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
     for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
-    stage_pairs(a, pb, org, tile, s_nbr, P4, P2);
+    stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
     __syncthreads();
 
     const int nthr = g.T / 2;            // a multiple of blockDim
@@ -193,11 +194,12 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArg
     float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
+    if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
     for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
-    stage_pairs(a, pb, org, tile, s_nbr, P4, P2);
+    stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
     __syncthreads();
 
     const int nthr = g.T / 4;                                  // a multiple of 32
@@ -273,6 +275,7 @@ __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
     float4 *tab = PT + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
+    if (threadIdx.x == 0) prefetch_tile_state(a, tile, true);
     const int4 org = __ldg(&a.tile_org[tile]);
     for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
     load_nbr(a, tile, s_nbr);
@@ -281,12 +284,7 @@ __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
         const Ref32 ref = tile_ref32(a, tile);
         const float inv_h = (float)a.inv_h;
         const float kA = (float)a.A, kB = (float)a.B;           // 3K - 5mu, 15mu
-#pragma unroll 2
-        for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
-            int cA[3], cB[3];
-            pair_coords(g, pb, org, b, cA, cB);
-            const int sA = slot_of(a, s_nbr, org, cA);
-            const int sB = slot_of(a, s_nbr, org, cB);
+        for_pair_slots<4>(a, pb, org, s_nbr, box_mapped(a, org), [&](int b, int sA, int sB) {
             const float4 rA = stage_one(a, a.src_hl, sA, ref, inv_h);
             const float4 rB = stage_one(a, a.src_hl, sB, ref, inv_h);
             const float mA = sA >= 0 ? __ldg(&a.minv32[sA]) : 0.f, mB = sB >= 0 ? __ldg(&a.minv32[sB]) : 0.f;
@@ -294,7 +292,7 @@ __global__ void __launch_bounds__(512, 2) lps_force_fast(const TileArgs a)
             P4[b] = make_float4(rA.x, rB.x, rA.y, rB.y);
             P2[b] = make_float2(rA.z, rB.z);
             PT[b] = make_float4(aA, aB, kB * mA, kB * mB);
-        }
+        });
     }
     __syncthreads();
 

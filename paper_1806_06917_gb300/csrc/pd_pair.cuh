@@ -209,13 +209,84 @@ __device__ __forceinline__ int slot_of(const TileArgs &a, const int *s_nbr, cons
     return a.nbr_ok ? slot_nbr(a.g, s_nbr, org, c[0], c[1], c[2]) : slot_at(a.g, a.tile_lut, c[0], c[1], c[2]);
 }
 
+// Whether the tile at org may take its staging slots from a.box_map: the map
+// exists (the halo reaches one tile at most) and every neighbour tile of this
+// one is whole or absent, so that a point of the box is off the grid exactly
+// when its neighbour tile is absent.
+__device__ __forceinline__ bool box_mapped(const TileArgs &a, const int4 &org)
+{
+    return a.box_map && org.x <= a.box_edge[0] && org.y <= a.box_edge[1] && org.z <= a.box_edge[2];
+}
+
+// Slots of the two points of a box-map entry e (or -1 off the grid).
+__device__ __forceinline__ void map_slots(const TileArgs &a, const int *s_nbr, uint32_t e, int &sA, int &sB)
+{
+    const int tA = s_nbr[e & 31u], tB = s_nbr[(e >> 14) & 31u];
+    sA = tA < 0 ? -1 : tA * a.g.T + (int)((e >> 5) & 511u);
+    sB = tB < 0 ? -1 : tB * a.g.T + (int)((e >> 19) & 511u);
+}
+
+// Call body(b, sA, sB) for every pair-box entry b of this thread (b = threadIdx.x
+// + k blockDim.x), with the slots of its two points (-1 off the grid). With
+// mapped (CTA-uniform) the slots come from the box map, whose first NR entries
+// of the thread are all loaded before the first is used (one memory round trip
+// instead of one per entry); otherwise from the entry's coordinates.
+template <int NR, class Body>
+__device__ __forceinline__ void for_pair_slots(const TileArgs &a, const PairBox &pb, const int4 &org,
+                                               const int *s_nbr, bool mapped, Body body)
+{
+    if (mapped) {
+        uint32_t e[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const int b = threadIdx.x + k * blockDim.x;
+            e[k] = b < pb.n ? __ldg(&a.box_map[b]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const int b = threadIdx.x + k * blockDim.x;
+            if (b < pb.n) {
+                int sA, sB;
+                map_slots(a, s_nbr, e[k], sA, sB);
+                body(b, sA, sB);
+            }
+        }
+        for (int b = threadIdx.x + NR * blockDim.x; b < pb.n; b += blockDim.x) {
+            int sA, sB;
+            map_slots(a, s_nbr, __ldg(&a.box_map[b]), sA, sB);
+            body(b, sA, sB);
+        }
+        return;
+    }
+#pragma unroll 2
+    for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
+        int cA[3], cB[3];
+        pair_coords(a.g, pb, org, b, cA, cB);
+        body(b, slot_of(a, s_nbr, org, cA), slot_of(a, s_nbr, org, cB));
+    }
+}
+
 // Stage the paired box of displacements: P4[b] = {xA, xB, yA, yB}, P2[b] = {zA, zB}.
-// s_nbr must be loaded and visible (a __syncthreads after load_nbr).
+// s_nbr must be loaded and visible (a __syncthreads after load_nbr). use_map
+// takes the slots from the box map where it holds: fewer instructions per entry,
+// which pays in the many-wave LPS passes (128^3: 0.646 -> 0.614 ms per step with
+// the LPS prefetch) and not in the one-wave 64^3 PMB step (no change), whose
+// staging waits on memory more than it issues. The coordinate loop is kept
+// apart from for_pair_slots: through it the 443^2 NP step measured 1 % slower.
 __device__ __forceinline__ void stage_pairs(const TileArgs &a, const PairBox &pb, const int4 &org, int tile,
-                                            const int *s_nbr, float4 *P4, float2 *P2)
+                                            const int *s_nbr, float4 *P4, float2 *P2, bool use_map)
 {
     const Ref32 ref = tile_ref32(a, tile);
     const float inv_h = (float)a.inv_h;
+    if (use_map && box_mapped(a, org)) {
+        for_pair_slots<8>(a, pb, org, s_nbr, true, [&](int b, int sA, int sB) {
+            const float4 rA = stage_one(a, a.src_hl, sA, ref, inv_h);
+            const float4 rB = stage_one(a, a.src_hl, sB, ref, inv_h);
+            P4[b] = make_float4(rA.x, rB.x, rA.y, rB.y);
+            if (P2) P2[b] = make_float2(rA.z, rB.z);
+        });
+        return;
+    }
 #pragma unroll 2
     for (int b = threadIdx.x; b < pb.n; b += blockDim.x) {
         int cA[3], cB[3];
@@ -225,6 +296,34 @@ __device__ __forceinline__ void stage_pairs(const TileArgs &a, const PairBox &pb
         P4[b] = make_float4(rA.x, rB.x, rA.y, rB.y);
         if (P2) P2[b] = make_float2(rA.z, rB.z);
     }
+}
+
+// Bulk L2 prefetch of one byte range by the copy engine (cp.async.bulk.prefetch:
+// no registers, nothing to wait for); ranges that are not 16-byte aligned in
+// address and size are skipped. Callers pass ranges inside allocated arrays.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes)
+{
+    if (bytes && (((uintptr_t)p | bytes) & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Issued at an LPS pass's start by one thread: the tile's own slots of the bond
+// masks and (with update) of every array that the update reads, so that those
+// loads hit L2 when they come (the bond loop and the update run long after the
+// staging's loads, and each of these ranges is contiguous: slots
+// [tile T, (tile + 1) T)). Measured on the 128^3 LPS step: 0.645 -> 0.638 ms;
+// the PMB and NP kernels measured no gain (64^3) or a 1 % loss (443^2, m = 20:
+// 40 mask words per point) and do not issue it.
+__device__ __forceinline__ void prefetch_tile_state(const TileArgs &a, int tile, bool update)
+{
+    const uint32_t T = (uint32_t)a.g.T;
+    const size_t ns = a.g.nslots, s0 = (size_t)tile * T;
+    for (int w = 0; w < a.g.W; ++w) l2_prefetch(a.mask + w * ns + s0, 4 * T);
+    if (!update || a.mode == MODE_FORCE) return;
+    if (a.vhl) l2_prefetch(a.vhl + 2 * s0, 32 * T);
+    for (int c = 0; c < a.g.dim; ++c) l2_prefetch(a.bc_kind + c * ns + s0, T);
+    if (a.use_body && a.body32) l2_prefetch(a.body32 + s0, 16 * T);
+    if (a.mode == MODE_STEP && a.cd && a.dst_hl) l2_prefetch(a.dst_hl + 2 * s0, 32 * T);
 }
 
 // Points of thread t: local coordinates of A and B, their slots, pair-box index.

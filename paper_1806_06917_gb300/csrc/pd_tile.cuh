@@ -336,6 +336,8 @@ struct TileArgs {
     const float4 *tab_b;        // FP32C stencil table of the LPS force kernel (3 float4 / entry)
     const int *tile_nbr;        // [ntiles * 27] the 3^d neighbour tiles of each tile (or -1)
     int nbr_ok;                 // halo within one tile in every direction: tile_nbr is usable
+    const uint32_t *box_map;    // paired halo box: neighbour tile (5 bits) + brick code (9) of A, then of B
+    int box_edge[3];            // box_map holds for tiles with org <= box_edge on every axis
     float kF, kB;               // FP32C kick factors: dt/2 * fscale / rho and dt/2 / rho
     float dt_h, dt_l;           // dt as a double-float pair
     double fscale;              // force density = fscale * F (PMB: c V; LPS: 1/h)
