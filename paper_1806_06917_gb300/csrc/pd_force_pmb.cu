@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     }
     load_nbr(a, tile, s_nbr);
     __syncthreads();
-    stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr, false);
+    stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr, true);
     if (tab2) {
         if (k0 < 4 * S) tab[k0] = t0;
         if (k1 < 4 * S) tab[k1] = t1;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     for (int k = threadIdx.x; k < E * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
-    stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr, false);
+    stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr, true);
     __syncthreads();
 
     const int nthr = g.T / 2;            // point pairs; thread (t, part) as in pmb_fast

@@ -269,10 +269,11 @@ __device__ __forceinline__ void for_pair_slots(const TileArgs &a, const PairBox 
 // Stage the paired box of displacements: P4[b] = {xA, xB, yA, yB}, P2[b] = {zA, zB}.
 // s_nbr must be loaded and visible (a __syncthreads after load_nbr). use_map
 // takes the slots from the box map where it holds: fewer instructions per entry,
-// which pays in the many-wave LPS passes (128^3: 0.646 -> 0.614 ms per step with
-// the LPS prefetch) and not in the one-wave 64^3 PMB step (no change), whose
-// staging waits on memory more than it issues. The coordinate loop is kept
-// apart from for_pair_slots: through it the 443^2 NP step measured 1 % slower.
+// which pays where many waves of tiles keep the SMs issue-bound (128^3 LPS step
+// 0.646 -> 0.614 ms with the LPS prefetch; 256^3 PMB step 2.544 -> 2.420 ms) and
+// changes nothing in the one-wave 64^3 PMB step, whose staging waits on memory
+// more than it issues. The coordinate loop is kept apart from for_pair_slots:
+// through it the 2D NP kernel (443^2, m = 20, no map) measured 1 % slower.
 __device__ __forceinline__ void stage_pairs(const TileArgs &a, const PairBox &pb, const int4 &org, int tile,
                                             const int *s_nbr, float4 *P4, float2 *P2, bool use_map)
 {
