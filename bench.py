@@ -72,13 +72,13 @@ KERNEL_LABEL = {
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
-    "pmb3": {"bytes": 21888000 + 0, "sha": "e752433f88102835",
+    "pmb3": {"bytes": 21903872 + 256, "sha": "7acd910d856365a1",
              "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
              "profile": "profiles/pmb_fast_block3d_64.md"},
-    "lps": {"bytes": (109730816 + 5722880) + (195616768 + 97170688), "sha": "e589f5266eefe42a",
+    "lps": {"bytes": (109782272 + 6379264) + (195880960 + 97121792), "sha": "18a8d285ab88776f",
             "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
             "profile": "profiles/lps_block3d_128.md"},
-    "np2": {"bytes": 45660416 + 97024, "sha": "e752433f88102835",
+    "np2": {"bytes": 45660416 + 80128, "sha": "7acd910d856365a1",
             "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
             "profile": "profiles/np_fast2_paper443.md"},
 }
