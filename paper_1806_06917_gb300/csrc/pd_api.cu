@@ -69,6 +69,9 @@ using namespace pdk;
 constexpr int GRAPH_CHUNK = 16;   // steps per captured graph (even: parity-preserving)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
+// Chunks of a pipelined host transfer of one state field (pd_set_state / pd_get_state).
+constexpr int IO_CHUNKS = 4;
+
 struct pd_sim {
     pd_grid grid;
     pd_material pmat;
@@ -79,6 +82,10 @@ struct pd_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // host transfers of pd_set_state / pd_get_state: chunk copies on copy_stream,
+    // each chunk's scatter or gather on the caller's stream (see xfer_chunks)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_copy[IO_CHUNKS] = {}, ev_done[IO_CHUNKS] = {};
     bool built = false;
     double dt = 0.0, dt_crit = 0.0;
     int64_t step = 0;
@@ -355,6 +362,12 @@ static int create_impl(pd_sim *s)
     PD_CUDA(cudaGetDevice(&s->device));
     PD_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     PD_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+    for (int k = 0; k < IO_CHUNKS; ++k) {
+        PD_CUDA(cudaEventCreateWithFlags(&s->ev_copy[k], cudaEventDisableTiming));
+        PD_CUDA(cudaEventCreateWithFlags(&s->ev_done[k], cudaEventDisableTiming));
+    }
 
     const size_t NS = (size_t)g.nslots, NP = (size_t)g.npoints;
     std::vector<uint32_t> box_map;      // uploaded after the other arrays (see the end)
@@ -871,6 +884,7 @@ int pd_destroy(pd_sim *s)
 {
     if (!s) return PD_OK;
     drop_graphs(s);
+    if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaStream_t fs = s->stream;     // stream-ordered release after the simulation's own work
     for (void *p : s->allocs) lib_free(p, fs);
@@ -881,6 +895,12 @@ int pd_destroy(pd_sim *s)
     if (fs) cudaStreamSynchronize(fs);
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    for (int k = 0; k < IO_CHUNKS; ++k) {
+        if (s->ev_copy[k]) cudaEventDestroy(s->ev_copy[k]);
+        if (s->ev_done[k]) cudaEventDestroy(s->ev_done[k]);
+    }
     delete s;
     return PD_OK;
 }
@@ -1000,6 +1020,65 @@ int pd_break_bonds(pd_sim *s, int axis, double pos, const double lo[3], const do
     return PD_OK;
 }
 
+// Pipelined host transfer of up to two state fields (u: the staging pair of the
+// current step, or the FP64 arrays; v: the velocity pair or array) through the
+// staging buffer s->io, in IO_CHUNKS chunks of user rows. Upload: chunk k is
+// copied in on copy_stream, then scattered on st once its copy event fired, so
+// the copy of chunk k + 1 overlaps the scatter of chunk k; the second field's
+// copy of chunk k waits for the first field's scatter of chunk k to have read the
+// buffer. Download: chunk k is gathered on st, then copied out on copy_stream;
+// the second field's gather of chunk k waits for the first field's copy of chunk
+// k. copy_stream first waits for the work already queued on st. Every wait is an
+// event in stream order: no host synchronisation here.
+static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2], bool upload, cudaStream_t st)
+{
+    const Geom &g = s->g;
+    const bool f32c = s->precision == PD_FP32C;
+    const long long n = g.npoints, d = g.dim;
+    const size_t row_bytes = sizeof(double) * d;
+    // one chunk below 1 MB per field: a pipeline of small copies gains nothing
+    const int nc = n * (long long)row_bytes < (1 << 20) ? 1 : IO_CHUNKS;
+    const long long rows = ((n + nc - 1) / nc + 255) / 256 * 256;
+    cudaStream_t cs = s->copy_stream;
+    PD_CUDA(cudaEventRecord(s->ev_in, st));
+    PD_CUDA(cudaStreamWaitEvent(cs, s->ev_in, 0));
+    bool first = true;
+    for (int f = 0; f < 2; ++f) {
+        if (!host[f]) continue;
+        double *const *slot = f32c ? nullptr : (is_u[f] ? s->u : s->v);
+        float4 *hl = f32c ? (is_u[f] ? s->hl[s->cur] : s->vhl) : nullptr;
+        double4_32a *d4 = !f32c && is_u[f] ? s->d4[s->cur] : nullptr;
+        for (int k = 0; k < nc; ++k) {
+            const long long r0 = std::min(n, k * rows), r1 = std::min(n, r0 + rows);
+            if (r1 <= r0) continue;
+            double *io = s->io + r0 * d;
+            const size_t bytes = (size_t)(r1 - r0) * row_bytes;
+            if (upload) {
+                if (!first) PD_CUDA(cudaStreamWaitEvent(cs, s->ev_done[k], 0));
+                PD_CUDA(cudaMemcpyAsync(io, host[f] + r0 * d, bytes, cudaMemcpyDefault, cs));
+                PD_CUDA(cudaEventRecord(s->ev_copy[k], cs));
+                PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[k], 0));
+                int rc = scatter_rows(g, s->slot_of_user, s->io, r0, r1, slot, hl, d4, st);
+                if (rc != PD_OK) return rc;
+                PD_CUDA(cudaEventRecord(s->ev_done[k], st));
+            } else {
+                if (!first) PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[k], 0));
+                int rc = gather_rows(g, s->slot_of_user, hl, slot, s->io, r0, r1, st);
+                if (rc != PD_OK) return rc;
+                PD_CUDA(cudaEventRecord(s->ev_done[k], st));
+                PD_CUDA(cudaStreamWaitEvent(cs, s->ev_done[k], 0));
+                PD_CUDA(cudaMemcpyAsync(const_cast<double *>(host[f]) + r0 * d, io, bytes, cudaMemcpyDefault, cs));
+                PD_CUDA(cudaEventRecord(s->ev_copy[k], cs));
+            }
+        }
+        first = false;
+    }
+    // the caller's stream finishes after every copy of this call
+    PD_CUDA(cudaEventRecord(s->ev_in, cs));
+    PD_CUDA(cudaStreamWaitEvent(st, s->ev_in, 0));
+    return PD_OK;
+}
+
 int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
 {
     CHECK_BUILT(s);
@@ -1014,13 +1093,21 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     // on demand), FP64 writes its SoA arrays and the double4 staging
     const bool f32c = s->precision == PD_FP32C;
     const double *src = nullptr;
-    if (u) {
+    // host arrays: both fields in chunks through the staging buffer, copies
+    // overlapping the scatters of the chunks before them
+    const bool host_u = u && !direct_ptr(s, u), host_v = v && !direct_ptr(s, v);
+    if (host_u || host_v) {
+        const double *hu[2] = {host_u ? u : nullptr, host_v ? v : nullptr};
+        const bool is_u[2] = {true, false};
+        if ((rc = xfer_chunks(s, hu, is_u, true, st)) != PD_OK) return rc;
+    }
+    if (u && !host_u) {
         if ((rc = user_source(s, u, &src, st)) != PD_OK) return rc;
         rc = scatter_stage(s->g, s->user_of_slot, src, f32c ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
                            f32c ? nullptr : s->d4[s->cur], st);
         if (rc != PD_OK) return rc;
     }
-    if (v) {
+    if (v && !host_v) {
         if ((rc = user_source(s, v, &src, st)) != PD_OK) return rc;
         rc = scatter_stage(s->g, s->user_of_slot, src, f32c ? nullptr : s->v, f32c ? s->vhl : nullptr, nullptr, st);
         if (rc != PD_OK) return rc;
@@ -1048,8 +1135,16 @@ int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
     // one pass per field into user order: from the double-float pairs (FP32C)
     // or the FP64 arrays, then one copy to the caller
     const bool f32c = s->precision == PD_FP32C;
-    if (u && (rc = to_user(s, f32c ? s->hl[s->cur] : nullptr, s->u, u, st)) != PD_OK) return rc;
-    if (v && (rc = to_user(s, f32c ? s->vhl : nullptr, s->v, v, st)) != PD_OK) return rc;
+    const bool host_u = u && !direct_ptr(s, u), host_v = v && !direct_ptr(s, v);
+    if (u && !host_u && (rc = to_user(s, f32c ? s->hl[s->cur] : nullptr, s->u, u, st)) != PD_OK) return rc;
+    if (v && !host_v && (rc = to_user(s, f32c ? s->vhl : nullptr, s->v, v, st)) != PD_OK) return rc;
+    if (host_u || host_v) {
+        // gathers in chunks on st, each chunk's copy out on copy_stream behind it
+        const double *hu[2] = {host_u ? u : nullptr, host_v ? v : nullptr};
+        const bool is_u[2] = {true, false};
+        if ((rc = xfer_chunks(s, hu, is_u, false, st)) != PD_OK) return rc;
+        PD_CUDA(cudaStreamSynchronize(s->copy_stream));
+    }
     PD_CUDA(cudaStreamSynchronize(st));
     return PD_OK;
 }

@@ -670,19 +670,9 @@ __global__ void k_scatter(Geom g, const int *slot_of_user, const double *user, d
 // slot-order writes are coalesced and the user array is read in runs of
 // x-consecutive points (a Morton-ordered warp covers 4 x 4 x 2 points); slots
 // off the lattice get zeros.
-__global__ void k_scatter_stage(Geom g, const int *user_of_slot, const double *user, double *s0, double *s1,
-                                double *s2, float4 *hl, double4_32a *d4)
+__device__ __forceinline__ void stage_slot(long long s, int d, double x, double y, double z, double *s0, double *s1,
+                                           double *s2, float4 *hl, double4_32a *d4)
 {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.nslots) return;
-    const long long i = user_of_slot[s];
-    const int d = g.dim;
-    double x = 0.0, y = 0.0, z = 0.0;
-    if (i >= 0) {
-        x = user[i * d];
-        y = user[i * d + 1];
-        if (d == 3) z = user[i * d + 2];
-    }
     if (s0) {
         s0[s] = x;
         s1[s] = y;
@@ -696,12 +686,41 @@ __global__ void k_scatter_stage(Geom g, const int *user_of_slot, const double *u
     }
 }
 
+__global__ void k_scatter_stage(Geom g, const int *user_of_slot, const double *user, double *s0, double *s1,
+                                double *s2, float4 *hl, double4_32a *d4)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.nslots) return;
+    const long long i = user_of_slot[s];
+    const int d = g.dim;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (i >= 0) {
+        x = user[i * d];
+        y = user[i * d + 1];
+        if (d == 3) z = user[i * d + 2];
+    }
+    stage_slot(s, d, x, y, z, s0, s1, s2, hl, d4);
+}
+
+// The same for the user rows [r0, r1) alone, one thread per row (for a chunk of
+// an upload that is still arriving). Slots off the lattice are not written: they
+// hold zeros from the allocation on, as no kernel writes a slot off the lattice.
+__global__ void k_scatter_rows(Geom g, const int *slot_of_user, const double *user, long long r0, long long r1,
+                               double *s0, double *s1, double *s2, float4 *hl, double4_32a *d4)
+{
+    const long long i = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r1) return;
+    const long long s = slot_of_user[i];
+    const int d = g.dim;
+    stage_slot(s, d, user[i * d], user[i * d + 1], d == 3 ? user[i * d + 2] : 0.0, s0, s1, s2, hl, d4);
+}
+
 // The reverse: user order from the double-float pair (hl) or the FP64 SoA arrays.
 __global__ void k_gather_unstage(Geom g, const int *slot_of_user, const float4 *hl, const double *s0,
-                                 const double *s1, const double *s2, double *user)
+                                 const double *s1, const double *s2, double *user, long long r0, long long r1)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.npoints) return;
+    const long long i = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r1) return;
     const int s = slot_of_user[i];
     const int d = g.dim;
     double x, y, z;
@@ -733,9 +752,27 @@ int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, do
 int gather_unstage(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
                    cudaStream_t st)
 {
-    k_gather_unstage<<<(g.npoints + 255) / 256, 256, 0, st>>>(g, slot_of_user, hl, slot ? slot[0] : nullptr,
-                                                              slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
-                                                              user);
+    return gather_rows(g, slot_of_user, hl, slot, user, 0, g.npoints, st);
+}
+
+int gather_rows(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
+                long long r0, long long r1, cudaStream_t st)
+{
+    if (r1 <= r0) return PD_OK;
+    k_gather_unstage<<<(unsigned)((r1 - r0 + 255) / 256), 256, 0, st>>>(
+        g, slot_of_user, hl, slot ? slot[0] : nullptr, slot ? slot[1] : nullptr, slot ? slot[2] : nullptr, user, r0,
+        r1);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int scatter_rows(const Geom &g, const int *slot_of_user, const double *user, long long r0, long long r1,
+                 double *const slot[3], float4 *hl, double4_32a *d4, cudaStream_t st)
+{
+    if (r1 <= r0) return PD_OK;
+    k_scatter_rows<<<(unsigned)((r1 - r0 + 255) / 256), 256, 0, st>>>(
+        g, slot_of_user, user, r0, r1, slot ? slot[0] : nullptr, slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
+        hl, d4);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

@@ -171,6 +171,11 @@ int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, do
                   double4_32a *d4, cudaStream_t st);
 int gather_unstage(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
                    cudaStream_t st);
+// The same for the user rows [r0, r1) only (chunks of a pipelined host transfer).
+int scatter_rows(const Geom &g, const int *slot_of_user, const double *user, long long r0, long long r1,
+                 double *const slot[3], float4 *hl, double4_32a *d4, cudaStream_t st);
+int gather_rows(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
+                long long r0, long long r1, cudaStream_t st);
 
 // Permutations between user order (AoS n x dim) and slot order (SoA).
 int scatter_user_to_slots(const Geom &g, const Tables &t, const double *user, double *const slot[3],
