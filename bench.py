@@ -72,13 +72,13 @@ KERNEL_LABEL = {
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
-    "pmb3": {"bytes": 21903872 + 256, "sha": "7acd910d856365a1",
+    "pmb3": {"bytes": 21903872 + 256, "sha": "e119e3c51498932f",
              "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
              "profile": "profiles/pmb_fast_block3d_64.md"},
-    "lps": {"bytes": (109782272 + 6379264) + (195880960 + 97121792), "sha": "18a8d285ab88776f",
+    "lps": {"bytes": (109782272 + 6379264) + (195880960 + 97121792), "sha": "b78cd3fbc35a53e2",
             "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
             "profile": "profiles/lps_block3d_128.md"},
-    "np2": {"bytes": 45660416 + 80128, "sha": "7acd910d856365a1",
+    "np2": {"bytes": 45660416 + 80128, "sha": "e119e3c51498932f",
             "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
             "profile": "profiles/np_fast2_paper443.md"},
 }
