@@ -72,22 +72,27 @@ KERNEL_LABEL = {
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
-    "pmb3": {"bytes": 21903872 + 256, "sha": "e119e3c51498932f",
-             "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
-             "profile": "profiles/pmb_fast_block3d_64.md"},
-    "lps": {"bytes": (109782272 + 6379264) + (195880960 + 97121792), "sha": "b78cd3fbc35a53e2",
-            "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
-            "profile": "profiles/lps_block3d_128.md"},
-    "np2": {"bytes": 45660416 + 80128, "sha": "e119e3c51498932f",
-            "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
-            "profile": "profiles/np_fast2_paper443.md"},
+    # (kernel key, tile_log2): the capture of that kernel at that tile size
+    ("pmb3", 9): {"bytes": 21903872 + 256, "sha": "e119e3c51498932f",
+                  "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
+                  "profile": "profiles/pmb_fast_block3d_64.md"},
+    ("pmb3", 8): {"bytes": 21968640 + 2560, "sha": "e119e3c51498932f",
+                  "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
+                  "profile": "profiles/pmb_fast_block3d_64.md"},
+    ("lps", 9): {"bytes": (109782272 + 6379264) + (195880960 + 97121792), "sha": "b78cd3fbc35a53e2",
+                 "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
+                 "profile": "profiles/lps_block3d_128.md"},
+    ("np2", 9): {"bytes": 45660416 + 80128, "sha": "e119e3c51498932f",
+                 "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
+                 "profile": "profiles/np_fast2_paper443.md"},
 }
 
 
-def ncu_traffic(key):
-    """Bytes per step from the recorded ncu capture, or None if the kernel changed since."""
+def ncu_traffic(key, tile_log2):
+    """Bytes per step from the recorded ncu capture of this kernel at this tile
+    size, or None if there is none or the kernel changed since."""
     import hashlib
-    rec = NCU_TRAFFIC.get(key)
+    rec = NCU_TRAFFIC.get((key, tile_log2))
     if rec is None:
         return None
     h = hashlib.sha256()
@@ -200,9 +205,16 @@ def measured_peaks():
     return None
 
 
-def make_sim(pd, wl, precision, stream, integrator=0):
-    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator)
+def make_sim(pd, wl, precision, stream, integrator=0, tile_log2=None):
+    """The workload's simulation; tile_log2 None picks the tile with pd_tune_tile
+    (best of 3 x 10 back-to-back steps per admissible tile), 0 the library default."""
+    if tile_log2 is None:
+        g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator)
+        tile_log2 = pd.pd_tune_tile(g, m, r, steps=10, stream=stream)
+    g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator,
+                          tile_log2=tile_log2)
     sim = pd.pd_create(g, m, r)
+    sim.tile_log2 = tile_log2 if tile_log2 else None
     pd.pd_build_neighbors(sim, stream)
     if wl.notch is not None:
         pd.pd_break_bonds(sim, wl.notch.axis, wl.notch.pos, np.asarray(wl.notch.lo), np.asarray(wl.notch.hi),
@@ -519,6 +531,9 @@ def main():
     ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")
     ap.add_argument("--serial-sample", type=int, default=24, help="serve: requests timed one at a time")
     ap.add_argument("--quantum", type=int, default=64, help="serve: steps per scheduling quantum")
+    ap.add_argument("--tile-log2", type=int, default=None,
+                    help="tile size 2^N of the timed simulation (6..9; 0 = library default); "
+                         "by default pd_tune_tile measures and picks it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path and LPS side measurements")
     args = ap.parse_args()
@@ -550,7 +565,7 @@ def main():
     wl, desc = workload(args.workload)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    sim = make_sim(pd, wl, pd.PD_FP32C, stream)
+    sim = make_sim(pd, wl, pd.PD_FP32C, stream, tile_log2=args.tile_log2)
     nbonds = pd.pd_bond_count(sim)
     key = {W.LPS: "lps", W.NP: "np2"}.get(wl.mat.model, "pmb3" if wl.grid.dim == 3 else "pmb2")
     launches_per_step = 2 if key == "lps" else 1
@@ -600,7 +615,7 @@ def main():
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     achieved = ops * nbonds / (ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP32 ops)",
-                "frac": achieved / peak, "traffic": ncu_traffic(key),
+                "frac": achieved / peak, "traffic": ncu_traffic(key, sim.tile_log2),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz, one op per lane per clock",
                 "ops_per_bond": ops, "kernel": KERNEL_LABEL[key](wl),
                 "launch_ms": ms / launches_per_step if key != "lps" else ms,
@@ -626,7 +641,10 @@ def main():
             "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)", "data": "synthetic",
             "config": {"workload": desc, "bonds": nbonds, "points": wl.grid.npoints,
                        "l2": "flushed before every timed step (512 MB write, then a 256 MB read that writes the dirty lines back)", "parallelism": "replicas",
-                       "launches_per_step": launches_per_step},
+                       "launches_per_step": launches_per_step,
+                       "tile_log2": sim.tile_log2,
+                       "tile_choice": "pd_tune_tile (best of 3 x 10 back-to-back steps per tile)" if args.tile_log2 is None
+                       else "--tile-log2"},
             "gpu_launches": args.steps * launches_per_step,
             "roofline": roofline, "e2e": e2e}
 
@@ -636,6 +654,7 @@ def main():
         d64 = time_steps(pd, torch, sim64, wl, max(3, min(args.steps, 10)), 3, stream, flush)
         ms64 = float(np.mean(d64))
         line["fp64_path"] = {"value": nbonds / (ms64 * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms64,
+                             "tile_log2": sim64.tile_log2,
                              "steps": len(d64), "ratio_fp32c_over_fp64": ms64 / ms,
                              "fp64_ops_per_bond": FP64_OPS_PER_BOND,
                              "fp64_tflops": FP64_OPS_PER_BOND * nbonds / (ms64 * 1e-3) / 1e12,
@@ -648,7 +667,7 @@ def main():
         acc_steps = 200
         acc = []
         for prec in (pd.PD_FP32C, pd.PD_FP64):
-            sa = make_sim(pd, wl, prec, stream)
+            sa = make_sim(pd, wl, prec, stream, tile_log2=0)
             pd.pd_set_state(sa, u=wl.u0, v=wl.v0, stream=stream)
             if wl.bc_kind is not None and wl.bc_kind.any():
                 pd.pd_set_bc(sa, wl.bc_kind, wl.bc_val, stream)
@@ -664,7 +683,7 @@ def main():
             "broken_fp32c": int(k32.sum()), "broken_fp64": int(k64.sum()),
             "broken_differ": int((k32 != k64).sum())}
         # the same step with the central-difference drift (Eq. (10))
-        simcd = make_sim(pd, wl, pd.PD_FP32C, stream, integrator=pd.PD_INTEGRATOR_CD)
+        simcd = make_sim(pd, wl, pd.PD_FP32C, stream, integrator=pd.PD_INTEGRATOR_CD, tile_log2=sim.tile_log2)
         dcd = time_steps(pd, torch, simcd, wl, max(3, min(args.steps, 10)), 3, stream, flush)
         mscd = float(np.mean(dcd))
         line["central_difference"] = {"value": nbonds / (mscd * 1e-3), "unit": "bond-updates/s",
@@ -678,7 +697,7 @@ def main():
             nb2 = pd.pd_bond_count(sim2)
             ops2 = FP32_OPS_PER_BOND["lps_dil"] + FP32_OPS_PER_BOND["lps_force"]
             line["lps128"] = {"workload": desc2, "value": nb2 / (ms2 * 1e-3), "unit": "bond-updates/s",
-                              "ms_per_step": ms2, "steps": len(d2), "launches_per_step": 2,
+                              "ms_per_step": ms2, "steps": len(d2), "launches_per_step": 2, "tile_log2": sim2.tile_log2,
                               "alu_frac": ops2 * nb2 / (ms2 * 1e-3) / 1e12 / peak}
             sim2.close()
             # the explicit benchmark shape of Sec. 6.2 (443^2 nodes, m = 20, NP law)
@@ -688,7 +707,7 @@ def main():
             ms3 = float(np.mean(d3))
             nb3 = pd.pd_bond_count(sim3)
             line["paper443"] = {"workload": desc3, "value": nb3 / (ms3 * 1e-3), "unit": "bond-updates/s",
-                                "ms_per_step": ms3, "steps": len(d3), "launches_per_step": 1,
+                                "ms_per_step": ms3, "steps": len(d3), "launches_per_step": 1, "tile_log2": sim3.tile_log2,
                                 "alu_frac": FP32_OPS_PER_BOND["np2"] * nb3 / (ms3 * 1e-3) / 1e12 / peak}
             sim3.close()
             # the same PMB workload at 64x the points (256^3, 2.0e9 bonds): many
@@ -699,7 +718,7 @@ def main():
             ms4 = float(np.mean(d4))
             nb4 = pd.pd_bond_count(sim4)
             line["block256"] = {"workload": desc4, "value": nb4 / (ms4 * 1e-3), "unit": "bond-updates/s",
-                                "ms_per_step": ms4, "steps": len(d4), "bonds": nb4,
+                                "ms_per_step": ms4, "steps": len(d4), "bonds": nb4, "tile_log2": sim4.tile_log2,
                                 "alu_frac": FP32_OPS_PER_BOND["pmb3"] * nb4 / (ms4 * 1e-3) / 1e12 / peak}
             sim4.close()
             del wl4

@@ -248,6 +248,23 @@ int pd_dilatation(pd_sim *sim, const double *u, double *theta_out, void *stream)
  * Stream-ordered. */
 int pd_step_explicit(pd_sim *sim, int64_t nsteps, void *stream);
 
+/* Measured tile choice. For each tile size 2^9, 2^8, 2^7, 2^6 that the
+ * description admits (the halo box of each kernel fits in shared memory),
+ * create the simulation with run->tile_log2 set to it, build its neighbours,
+ * take two untimed explicit steps from rest (u = v = 0, every DOF free, no
+ * breaking reached), then time `steps` more three times with CUDA events on
+ * `stream` (0 = each simulation's own stream) and keep the best; *tile_log2
+ * receives the fastest, a smaller tile
+ * only when it is at least 1 % faster than the best larger one. The trial
+ * simulations are destroyed before return. The tile size changes the
+ * per-tile reference of the FP32C staging, so results at different tiles agree
+ * to the FP32C tolerance, not bit for bit. grid, mat, run: as for pd_create
+ * (run->tile_log2 is ignored); steps >= 1. Errors: PD_EINVAL for a null
+ * pointer or steps < 1, else the error of the last tile tried when none could
+ * be built. Synchronous. */
+int pd_tune_tile(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps,
+                 int32_t *tile_log2, void *stream);
+
 /* ------------------------------------------------------------------- tangent */
 
 /* Tangent Jacobian-vector product out = K w with K = df/du at u_lin (npoints x

@@ -905,6 +905,65 @@ int pd_destroy(pd_sim *s)
     return PD_OK;
 }
 
+int pd_tune_tile(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps,
+                 int32_t *tile_log2, void *stream)
+{
+    if (!grid || !mat || !run || !tile_log2 || steps < 1) {
+        set_error("pd_tune_tile: null argument or steps < 1");
+        return PD_EINVAL;
+    }
+    {   // the description is checked once, before any device call
+        pd_run r = *run;
+        r.tile_log2 = 0;
+        const int rc = validate(grid, mat, &r);
+        if (rc != PD_OK) return rc;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PD_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    int best = 0, last_rc = PD_OK;
+    float best_ms = 0.f;
+    for (int L = 9; L >= 6; --L) {
+        pd_run r = *run;
+        r.tile_log2 = L;
+        pd_sim *s = nullptr;
+        int rc = pd_create(&s, grid, mat, &r);
+        if (rc == PD_OK) rc = pd_build_neighbors(s, stream);
+        if (rc == PD_OK) rc = pd_step_explicit(s, 2, stream);
+        // the best of three timed runs of `steps` steps
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && rc == PD_OK; ++rep) {
+            cudaStream_t st = pick(s, stream);
+            float t = 0.f;
+            cudaError_t e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) rc = pd_step_explicit(s, steps, stream);
+            if (e == cudaSuccess && rc == PD_OK) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess && rc == PD_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && rc == PD_OK) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess && rc == PD_OK) rc = cuda_fail(e, "pd_tune_tile timing");
+            if (rc == PD_OK && (rep == 0 || t < ms)) ms = t;
+        }
+        pd_destroy(s);
+        if (rc != PD_OK) {
+            last_rc = rc;
+            continue;
+        }
+        if (!best || ms < 0.99f * best_ms) {
+            best = L;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best) return last_rc != PD_OK ? last_rc : PD_EINVAL;
+    *tile_log2 = best;
+    return PD_OK;
+}
+
 int pd_build_neighbors(pd_sim *s, void *stream)
 {
     CHECK_SIM(s);

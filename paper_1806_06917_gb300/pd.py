@@ -109,6 +109,8 @@ _SIGS = {
     "pd_force": [_P, _P, _P, ctypes.c_uint, _P],
     "pd_dilatation": [_P, _P, _P, _P],
     "pd_step_explicit": [_P, ctypes.c_int64, _P],
+    "pd_tune_tile": [ctypes.POINTER(pd_grid), ctypes.POINTER(pd_material), ctypes.POINTER(pd_run), ctypes.c_int32,
+                     ctypes.POINTER(ctypes.c_int32), _P],
     "pd_jvp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_vjp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_energy": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
@@ -299,6 +301,14 @@ def pd_dilatation(sim: Sim, u=None, theta_out=None, stream=None):
     _check(_lib.pd_dilatation(sim.h, _buf(u, np.float64, sim.nvec, "u"),
                               _buf(theta_out, np.float64, sim.npoints, "theta", True), _stream(stream)))
     return theta_out
+
+
+def pd_tune_tile(grid: pd_grid, mat: pd_material, run: pd_run, steps: int = 10, stream=None) -> int:
+    """The fastest tile_log2 for this description, measured (the C call of the same name)."""
+    out = ctypes.c_int32()
+    _check(_lib.pd_tune_tile(ctypes.byref(grid), ctypes.byref(mat), ctypes.byref(run), int(steps),
+                             ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def pd_step_explicit(sim: Sim, nsteps: int, stream=None) -> None:

@@ -88,3 +88,16 @@ def test_model_specific_rules(pd, case):
     with pytest.raises(pd.PdError) as e:
         pd.pd_create(g, m, r)
     assert e.value.code == pd.PD_EINVAL
+
+
+def test_tune_tile_refuses_bad_arguments(pd):
+    g, m, r = _good(pd)
+    for steps in (0, -3):
+        with pytest.raises(pd.PdError) as e:
+            pd.pd_tune_tile(g, m, r, steps=steps)
+        assert e.value.code == pd.PD_EINVAL
+    # a malformed description fails the same way for every tile size
+    g.m = 0
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_tune_tile(g, m, r, steps=2)
+    assert e.value.code == pd.PD_EINVAL
