@@ -489,6 +489,56 @@ def cpu_baseline(wl, target_s=12.0, max_steps=50):
     return out, bonds.nbonds
 
 
+def oracle_step_rate(wl, sample, target_s=3.0, max_steps=20):
+    """The oracle's explicit-step rate (as it stands, OpenMP over points) on a
+    bounded sample workload of the same model and horizon as a side measurement."""
+    from oracle import oracle as O
+    bonds = O.neighbors(wl.grid)
+    if wl.notch is not None:
+        O.break_notch(wl.grid, bonds, wl.notch)
+    dt = wl.dt if wl.dt > 0 else wl.dt_factor * O.stable_dt(wl.grid, wl.mat, bonds)
+    st = O.ExplicitState(wl.grid, wl.mat, bonds, wl.u0, wl.v0, wl.bc_kind, wl.bc_val)
+    st.run(dt, 1)
+    t1 = time.time()
+    st.run(dt, 1)
+    one = max(time.time() - t1, 1e-6)
+    n = int(max(1, min(max_steps, target_s / one)))
+    t2 = time.time()
+    st.run(dt, n)
+    el = time.time() - t2
+    return {"value": bonds.nbonds * n / el, "unit": "bond-updates/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d explicit steps of %s (%d bonds)" % (n, sample, bonds.nbonds)}
+
+
+def oracle_build_rate(grid, sample):
+    """The oracle's cell-list neighbour build on the host cores."""
+    from oracle import oracle as O
+    t = time.time()
+    b = O.neighbors(grid)
+    el = time.time() - t
+    return {"value": b.nbonds / el, "unit": "bonds/s", "seconds": el, "cores": O.num_threads(), "kind": "oracle",
+            "sample": sample}
+
+
+def oracle_jvp_rate(nx=200, reps=5):
+    """The oracle's tangent product on the 200^2 plate: its central directional
+    difference of the FP64 force (two force passes per product)."""
+    from oracle import oracle as O
+    L = W.plate_static(nx=nx, variant="clamped")
+    bonds = O.neighbors(L.grid)
+    rng = np.random.default_rng(4)
+    u = rng.normal(0.0, 1e-4 * L.grid.h, (L.grid.npoints, 2))
+    w = rng.normal(size=(L.grid.npoints, 2))
+    O.jvp_fd(L.grid, L.mat, bonds, u, w, 1e-6 * L.grid.h)
+    t = time.time()
+    for _ in range(reps):
+        O.jvp_fd(L.grid, L.mat, bonds, u, w, 1e-6 * L.grid.h)
+    el = (time.time() - t) / reps
+    return {"value": bonds.nbonds / el, "unit": "bond-applications/s", "ms": el * 1e3, "cores": O.num_threads(),
+            "kind": "oracle", "sample": "%d products on the full %d^2 plate (central difference of two FP64 force "
+                                        "passes)" % (reps, nx)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -742,6 +792,16 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(wl)
         line["cpu_baseline"] = cb
+        if "lps128" in line:
+            # the oracle beside the side measurements, each on a bounded sample
+            line["lps128"]["cpu_baseline"] = oracle_step_rate(
+                W.block3d_lps(nside=40), "a 40^3 LPS block (the 128^3 workload's model, moduli and horizon)")
+            line["paper443"]["cpu_baseline"] = oracle_step_rate(
+                W.np_square(k=20, delta=0.2), "a 141^2 NP square at m = 20 (the 443^2 step's law and horizon, "
+                                              "h = 0.01 m)")
+            line["neighbour_build"]["block64"]["cpu_baseline"] = oracle_build_rate(
+                wl.grid, "cell-list build of the full 64^3 lattice")
+            line["jvp200"]["cpu_baseline"] = oracle_jvp_rate()
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
