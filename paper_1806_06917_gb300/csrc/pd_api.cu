@@ -430,12 +430,9 @@ static int create_impl(pd_sim *s)
                 ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)d2, (float)d2);
                 ta[4 * k + 2] = make_float4((float)(rr / vij), (float)(rr / vij), (float)(d2 / vij), (float)(d2 / vij));
                 ta[4 * k + 3] = make_float4(offf, (float)(mt.s_c * vij), 0.f, 0.f);
-            } else {
-                // dilatation: {dz,dz,|d|,|d|} {|d|V_ij x2, |d|^2 x2} {offset,-,-,-}
-                ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
-                ta[4 * k + 2] = make_float4((float)(rr * vij), (float)(rr * vij), (float)d2, (float)d2);
-                ta[4 * k + 3] = make_float4(offf, 0.f, 0.f, 0.f);
             }
+            // LPS: both passes read tb (the dilatation's bond weight |d| V_ij from
+            // its {dz,dz,|d|,|d|} and V_ij entries)
         }
         ALLOC(s->tab_a, sizeof(float4) * ta.size());
         ALLOC(s->tab_b, sizeof(float4) * tb.size());

@@ -22,29 +22,31 @@ namespace pdk {
 // rolled loop over a shared-memory table of pre-splatted stencil constants.
 // One 32-bond word of the dilatation sum (MASKED = false: every bond of the
 // warp's points exists and is intact, no per-bond mask operation).
-template <bool MASKED>
+// The table is the force pass's: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|^2,|d|^2,offset,V_ij};
+// the bond weight |d| V_ij is |d| itself without the partial volume (VOLCORR = false).
+template <bool MASKED, bool VOLCORR>
 __device__ __forceinline__ float2 lps_dil_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
                                                float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1,
                                                float2 acc)
 {
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        // table entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|V_ij,|d|V_ij,|d|^2,|d|^2} {offset,-,-,-}
-        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
-        const int off = __float_as_int(tw[4 * b + 3].x);
+        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
+        const int off = __float_as_int(tc.z);
         const float4 r4 = P4[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
         const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
         float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
         num = f2fma(ey, f2add(yy, f2hi(ta)), num);
         num = f2fma(ez, f2add(yz, f2lo(tb)), num);
-        const float2 qq = f2add(num, f2hi(tc));            // |y|^2 = |d|^2 + 2 d.e + e.e
+        const float2 qq = f2add(num, f2lo(tc));            // |y|^2 = |d|^2 + 2 d.e + e.e
         float2 e = f2mul(num, f2rcp(f2add(f2sqrt(qq), f2hi(tb))));
         if (MASKED) {
             e.x = ((c0 >> b) & 1u) ? e.x : 0.f;
             e.y = ((c1 >> b) & 1u) ? e.y : 0.f;
         }
-        acc = f2fma(e, f2lo(tc), acc);
+        if (VOLCORR) e = f2mul(e, make_float2(tc.w, tc.w));
+        acc = f2fma(e, f2hi(tb), acc);
     }
     return acc;
 }
@@ -87,6 +89,7 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
     }
 }
 
+template <bool VOLCORR>
 __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs a)
 {
     const Geom &g = a.g;
@@ -95,12 +98,12 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
     extern __shared__ float4 smem4[];
     float4 *P4 = smem4;
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
-    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
+    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
@@ -123,11 +126,11 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
             }
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
-            const float4 *tw = tab + 4 * 32 * w;
+            const float4 *tw = tab + 3 * 32 * w;
             if (__all_sync(0xffffffffu, m0 == full && m1 == full))
-                acc = lps_dil_word<false>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
+                acc = lps_dil_word<false, VOLCORR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
             else
-                acc = lps_dil_word<true>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
+                acc = lps_dil_word<true, VOLCORR>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, acc);
         }
         for (int p = 0; p < 2; ++p)
             if (q.act[p]) a.theta32[q.slot[p]] = 3.f * __ldg(&a.minv32[q.slot[p]]) * (p ? acc.y : acc.x);
@@ -140,8 +143,9 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
 // halves of the stencil words, added in a fixed order (half 0 + half 1). The
 // one-pair kernel is bound by the L1 / shared-memory pipe (ncu: 92 % of its
 // throughput, 14 wavefronts per 64 bonds, 7 of them table broadcasts); this
-// form moves 19 per 128.
-template <bool MASKED>
+// form moves 19 per 128. Both dilatation kernels read the force pass's table of 3
+// float4 per entry (from 4: the 128^3 LPS step 0.614 -> 0.611 ms).
+template <bool MASKED, bool VOLCORR>
 __device__ __forceinline__ void lps_dil_word2(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
                                               int dbi, float2 nux0, float2 nuy0, float2 nuz0, float2 nux1,
                                               float2 nuy1, float2 nuz1, uint32_t c0, uint32_t c1, uint32_t c2,
@@ -149,8 +153,8 @@ __device__ __forceinline__ void lps_dil_word2(const float4 *tw, int nb, const fl
 {
 PD_PRAGMA_UNROLL(PD_UNROLL)
     for (int b = 0; b < nb; ++b) {
-        const float4 ta = tw[4 * b], tb = tw[4 * b + 1], tc = tw[4 * b + 2];
-        const int off = __float_as_int(tw[4 * b + 3].x);
+        const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
+        const int off = __float_as_int(tc.z);
         const float4 r0 = P4[bi + off], r1 = P4[bi + dbi + off];
         const float2 z0 = P2[bi + off], z1 = P2[bi + dbi + off];
         float2 e0, e1;
@@ -160,7 +164,7 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
             float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
             num = f2fma(ey, f2add(yy, f2hi(ta)), num);
             num = f2fma(ez, f2add(yz, f2lo(tb)), num);
-            e0 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2hi(tc))), f2hi(tb))));
+            e0 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2lo(tc))), f2hi(tb))));
         }
         {
             const float2 ex = f2add(f2lo(r1), nux1), ey = f2add(f2hi(r1), nuy1), ez = f2add(z1, nuz1);
@@ -168,7 +172,7 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
             float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
             num = f2fma(ey, f2add(yy, f2hi(ta)), num);
             num = f2fma(ez, f2add(yz, f2lo(tb)), num);
-            e1 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2hi(tc))), f2hi(tb))));
+            e1 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2lo(tc))), f2hi(tb))));
         }
         if (MASKED) {
             e0.x = ((c0 >> b) & 1u) ? e0.x : 0.f;
@@ -176,13 +180,18 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
             e1.x = ((c2 >> b) & 1u) ? e1.x : 0.f;
             e1.y = ((c3 >> b) & 1u) ? e1.y : 0.f;
         }
-        acc0 = f2fma(e0, f2lo(tc), acc0);
-        acc1 = f2fma(e1, f2lo(tc), acc1);
+        if (VOLCORR) {
+            e0 = f2mul(e0, make_float2(tc.w, tc.w));
+            e1 = f2mul(e1, make_float2(tc.w, tc.w));
+        }
+        acc0 = f2fma(e0, f2hi(tb), acc0);
+        acc1 = f2fma(e1, f2hi(tb), acc1);
     }
 }
 
 // Launch: one CTA per tile, T/2 threads (tiles of at least 2^7 points and two
 // stencil words).
+template <bool VOLCORR>
 __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArgs a)
 {
     const Geom &g = a.g;
@@ -191,12 +200,12 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArg
     extern __shared__ float4 smem4[];
     float4 *P4 = smem4;
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
-    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 4 float4 per entry
+    float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
     const int tile = blockIdx.x;
     if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
-    for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
+    for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
@@ -229,13 +238,13 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArg
             }
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
-            const float4 *tw = tab + 4 * 32 * w;
+            const float4 *tw = tab + 3 * 32 * w;
             if (__all_sync(0xffffffffu, m0 == full && m1 == full && m2 == full && m3 == full))
-                lps_dil_word2<false>(tw, nb, P4, P2, q0.bi, dbi, nux0, nuy0, nuz0, nux1, nuy1, nuz1, m0, m1, m2,
-                                     m3, acc0, acc1);
+                lps_dil_word2<false, VOLCORR>(tw, nb, P4, P2, q0.bi, dbi, nux0, nuy0, nuz0, nux1, nuy1, nuz1, m0,
+                                              m1, m2, m3, acc0, acc1);
             else
-                lps_dil_word2<true>(tw, nb, P4, P2, q0.bi, dbi, nux0, nuy0, nuz0, nux1, nuy1, nuz1, m0, m1, m2,
-                                    m3, acc0, acc1);
+                lps_dil_word2<true, VOLCORR>(tw, nb, P4, P2, q0.bi, dbi, nux0, nuy0, nuz0, nux1, nuy1, nuz1, m0,
+                                             m1, m2, m3, acc0, acc1);
         }
     }
     // combine the halves: half 1 publishes, half 0 adds and writes theta
@@ -348,7 +357,7 @@ size_t lps_fast_smem(const Geom &g, bool dil)
 {
     const size_t n = (size_t)(g.bx + 2 * g.m) * (g.by + 2 * g.m) * (g.bz / 2 + 2 * g.m);
     const size_t p2 = ((n + 1) / 2) * sizeof(float4);
-    if (dil) return n * sizeof(float4) + p2 + (size_t)g.S * 4 * sizeof(float4);
+    if (dil) return n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
     return 2 * n * sizeof(float4) + p2 + (size_t)g.S * 3 * sizeof(float4);
 }
 
@@ -490,7 +499,9 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
     if (precision == PD_FP32C) {
         // dilatation: two pairs per thread from 2^7-point tiles and two stencil words on
         const bool dil2 = dil && g.T >= 128 && g.W >= 2;
-        auto k = dil ? (dil2 ? lps_dil_fast2 : lps_dil_fast) : (a.vol_corr ? lps_force_fast<true> : lps_force_fast<false>);
+        auto k = dil ? (dil2 ? (a.vol_corr ? lps_dil_fast2<true> : lps_dil_fast2<false>)
+                             : (a.vol_corr ? lps_dil_fast<true> : lps_dil_fast<false>))
+                     : (a.vol_corr ? lps_force_fast<true> : lps_force_fast<false>);
         PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int threads = dil ? (g.T / 2 < 256 ? g.T / 2 : 256) : g.T;
         k<<<g.ntiles, threads, smem, st>>>(a);
