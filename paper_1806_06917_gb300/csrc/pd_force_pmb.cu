@@ -136,6 +136,22 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     } else {
         for (int k = threadIdx.x; k < 4 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     }
+    const int nthr = g.T / 2;            // point pairs: a multiple of 32, so a warp has one part
+    const int part = SPLIT ? threadIdx.x / nthr : 0;
+    const int w0 = SPLIT ? part * g.W / a.split : 0, w1 = SPLIT ? (part + 1) * g.W / a.split : g.W;
+    // With the split (one pair per thread), the pair's first mask words are loaded
+    // before the staging, so that their latency overlaps the staging's (64^3 at
+    // 2^8 tiles: 62.6 -> 61.5 us). The one-thread-per-pair kernel loads them after
+    // it: held across the staging they cost it registers in the bond loop (256^3
+    // at 2^9 tiles: 2.42 -> 2.47 ms).
+    PairPts q_pre;
+    uint32_t n0_pre = 0u, n1_pre = 0u;
+    if constexpr (SPLIT) {
+        q_pre = pair_points(g, pb, org, tile, threadIdx.x % nthr);
+        const size_t mo0 = (size_t)w0 * g.nslots;
+        n0_pre = q_pre.act[0] && w0 < w1 ? a.mask[mo0 + q_pre.slot[0]] : 0u;
+        n1_pre = q_pre.act[1] && w0 < w1 ? a.mask[mo0 + q_pre.slot[1]] : 0u;
+    }
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, DIM == 3 ? P2 : nullptr, true);
@@ -145,19 +161,16 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
     }
     __syncthreads();
 
-    const int nthr = g.T / 2;            // point pairs: a multiple of 32, so a warp has one part
-    const int part = SPLIT ? threadIdx.x / nthr : 0;
-    const int w0 = SPLIT ? part * g.W / a.split : 0, w1 = SPLIT ? (part + 1) * g.W / a.split : g.W;
     // one iteration per thread (T / 2 <= 256 = blockDim without the split)
     for (int t = SPLIT ? threadIdx.x % nthr : threadIdx.x; t < nthr; t += SPLIT ? nthr : blockDim.x) {
-        const PairPts q = pair_points(g, pb, org, tile, t);
+        const PairPts q = SPLIT ? q_pre : pair_points(g, pb, org, tile, t);
         const float4 ui4 = P4[q.bi];
         const float2 nux = f2neg(f2lo(ui4)), nuy = f2neg(f2hi(ui4));
         const float2 nuz = DIM == 3 ? f2neg(P2[q.bi]) : make_float2(0.f, 0.f);
         float2 Fx = make_float2(0.f, 0.f), Fy = Fx, Fz = Fx;
         const size_t mo0 = (size_t)w0 * g.nslots;
-        uint32_t n0 = q.act[0] && (!SPLIT || w0 < w1) ? a.mask[mo0 + q.slot[0]] : 0u;
-        uint32_t n1 = q.act[1] && (!SPLIT || w0 < w1) ? a.mask[mo0 + q.slot[1]] : 0u;
+        uint32_t n0 = SPLIT ? n0_pre : (q.act[0] ? a.mask[mo0 + q.slot[0]] : 0u);
+        uint32_t n1 = SPLIT ? n1_pre : (q.act[1] ? a.mask[mo0 + q.slot[1]] : 0u);
         for (int w = w0; w < w1; ++w) {
             const uint32_t m0 = n0, m1 = n1;
             if (w + 1 < w1) {
