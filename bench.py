@@ -73,16 +73,16 @@ _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_069
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
     # (kernel key, tile_log2): the capture of that kernel at that tile size
-    ("pmb3", 9): {"bytes": 21903616 + 0, "sha": "956795b792a8d119",
+    ("pmb3", 9): {"bytes": 21903616 + 11264, "sha": "fd63c70de79fc282",
                   "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
                   "profile": "profiles/pmb_fast_block3d_64.md"},
-    ("pmb3", 8): {"bytes": 21968640 + 0, "sha": "956795b792a8d119",
+    ("pmb3", 8): {"bytes": 21968640 + 1280, "sha": "fd63c70de79fc282",
                   "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
                   "profile": "profiles/pmb_fast_block3d_64.md"},
     ("lps", 9): {"bytes": (109791488 + 5980928) + (195891200 + 97487872), "sha": "19443b34cf7d882b",
                  "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
                  "profile": "profiles/lps_block3d_128.md"},
-    ("np2", 9): {"bytes": 45660416 + 83200, "sha": "956795b792a8d119",
+    ("np2", 9): {"bytes": 45662464 + 73728, "sha": "fd63c70de79fc282",
                  "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
                  "profile": "profiles/np_fast2_paper443.md"},
 }
