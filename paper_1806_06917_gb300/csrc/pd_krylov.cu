@@ -159,15 +159,24 @@ size_t krylov_dsc_doubles(int krylov_gmres_restart)
     return std::max(g, KRYLOV_DSC_MIN);
 }
 
-// H[0:j+1, j] = dsc[0:j+1] (first Gram-Schmidt pass) or += (second pass)
-__global__ void k_gm_hcol(double *d, int m, int j, int add)
+// The block sums of k_partial_sum for dot i (block i, the same fixed order), and
+// with them column j of the Hessenberg matrix: H[i, j] = dot i (first
+// Gram-Schmidt pass) or += (second pass), unless the cycle is done.
+__global__ void __launch_bounds__(KT) k_partial_sum_hcol(const double *partial, int nb, double *d, int m, int j,
+                                                       int add)
 {
+    __shared__ double red[KT / 32];
     const GmLayout L(m);
+    const double *p = partial + (long long)blockIdx.x * nb;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += KT) acc += p[b];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x != 0) return;
+    const int i = blockIdx.x;
+    d[i] = t;
     if (d[L.sc + GM_DONE] != 0.0) return;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        double *h = d + L.H + i + (m + 1) * j;
-        *h = add ? *h + d[i] : d[i];
-    }
+    double *h = d + L.H + i + (m + 1) * j;
+    *h = add ? *h + t : t;
 }
 
 // After dsc[0] = |w|^2: H[j+1, j] = |w|, the previous rotations and a new one on
@@ -175,11 +184,21 @@ __global__ void k_gm_hcol(double *d, int m, int j, int add)
 // The block stages column j and the rotations in shared memory (3 (m + 1)
 // doubles, dynamic) so that the sequential rotation loop of thread 0 does not
 // wait on global loads.
-__global__ void k_gm_step(double *d, int m, int j)
+// |w|^2 is summed here from the nb block partials of k_mdot, in k_partial_sum's
+// fixed order (KT threads).
+__global__ void __launch_bounds__(KT) k_gm_step(const double *partial, int nb, double *d, int m, int j)
 {
     extern __shared__ double gs[];
+    __shared__ double red[KT / 32];
     const GmLayout L(m);
     double *sc = d + L.sc;
+    {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < nb; b += KT) acc += partial[b];
+        const double t = block_sum(acc, red);
+        if (threadIdx.x == 0) d[0] = t;
+        __syncthreads();
+    }
     if (sc[GM_DONE] != 0.0) {
         if (threadIdx.x == 0) sc[GM_INVH] = 0.0;
         return;
@@ -278,13 +297,14 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
             src = zt;
         }
         if ((e = op.apply(op.ctx, src, vj1, s)) != PD_OK) return e;
+        const int nb = kblocks(n);
         for (int pass = 0; pass < 2; ++pass) {          // CGS2: h = V^T w, w -= V h; twice
-            if ((e = dots(cs, V, n, j + 1, vj1, nullptr)) != PD_OK) return e;
-            k_gm_hcol<<<1, 64, 0, s>>>(cs.dsc, m, j, pass);
+            k_mdot<<<dim3(nb, j + 1), KT, 0, s>>>(V, n, vj1, n, cs.partial);
+            k_partial_sum_hcol<<<j + 1, KT, 0, s>>>(cs.partial, nb, cs.dsc, m, j, pass);
             if ((e = lincomb_dev(cs, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return e;
         }
-        if ((e = dots(cs, vj1, 0, 1, vj1, nullptr)) != PD_OK) return e;
-        k_gm_step<<<1, 64, 3 * (m + 1) * sizeof(double), s>>>(cs.dsc, m, j);
+        k_mdot<<<dim3(nb, 1), KT, 0, s>>>(vj1, 0, vj1, n, cs.partial);
+        k_gm_step<<<1, KT, 3 * (m + 1) * sizeof(double), s>>>(cs.partial, nb, cs.dsc, m, j);
         k_scale_dev<<<nbk, 256, 0, s>>>(cs.dsc, L.sc + GM_INVH, vj1, n);
         PD_CUDA(cudaGetLastError());
         return PD_OK;
