@@ -413,7 +413,7 @@ static_assert(CG_BAD < (int)KRYLOV_DSC_MIN, "CG scalars exceed the device scalar
 constexpr int CG_CHUNK = 32;
 
 // after dsc[0] = p.Ap: alpha = (r.z) / (p.Ap), or a non-positive curvature flag
-__global__ void k_cg_alpha(double *s)
+__device__ __forceinline__ void cg_alpha(double *s)
 {
     if (s[CG_DONE] != 0.0) {
         s[CG_ALPHA] = 0.0;
@@ -429,16 +429,8 @@ __global__ void k_cg_alpha(double *s)
     s[CG_ALPHA] = s[CG_RZ] / pq;
 }
 
-// y = (sign alpha) x + y, alpha from the device
-__global__ void k_cg_axpy(const double *s, double sign, const double *x, double *y, long long n)
-{
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    y[e] = (sign * s[CG_ALPHA]) * x[e] + 1.0 * y[e];
-}
-
 // after dsc[0] = r.r: count the iteration, test ||r|| <= target
-__global__ void k_cg_check(double *s)
+__device__ __forceinline__ void cg_check(double *s)
 {
     if (s[CG_DONE] != 0.0) return;
     const double rr1 = s[0];
@@ -448,7 +440,7 @@ __global__ void k_cg_check(double *s)
 }
 
 // beta = (r.z)_new / (r.z)_old with (r.z)_new in dsc[0] (PCG) or r.r (CG)
-__global__ void k_cg_beta(double *s, int precond)
+__device__ __forceinline__ void cg_beta(double *s, int precond)
 {
     if (s[CG_DONE] != 0.0) return;
     const double rz1 = precond ? s[0] : s[CG_RR];
@@ -456,7 +448,40 @@ __global__ void k_cg_beta(double *s, int precond)
     s[CG_RZ] = rz1;
 }
 
-// p = z + beta p, unless done
+// dsc[0] = the dot product from k_mdot's nb block partials (k_partial_sum's fixed
+// order), then the scalar step `what` of the iteration: CG_STEP_ALPHA; CG_STEP_CHECK
+// (and, without a preconditioner, beta, which needs only r.r); CG_STEP_BETA (PCG,
+// after r.z). One block of KT threads; the scalars run on thread 0.
+enum { CG_STEP_ALPHA = 0, CG_STEP_CHECK, CG_STEP_BETA };
+__global__ void __launch_bounds__(KT) k_cg_sum_step(const double *partial, int nb, double *s, int what,
+                                                  int precond)
+{
+    __shared__ double red[KT / 32];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += KT) acc += partial[b];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x != 0) return;
+    s[0] = t;
+    if (what == CG_STEP_ALPHA) {
+        cg_alpha(s);
+    } else if (what == CG_STEP_CHECK) {
+        cg_check(s);
+        if (!precond) cg_beta(s, 0);
+    } else {
+        cg_beta(s, 1);
+    }
+}
+
+// x += alpha p and r -= alpha q, alpha from the device
+__global__ void k_cg_update(const double *s, const double *p, double *x, const double *q, double *r, long long n)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double alpha = s[CG_ALPHA];
+    x[e] = (1.0 * alpha) * p[e] + 1.0 * x[e];
+    r[e] = (-1.0 * alpha) * q[e] + 1.0 * r[e];
+}
+
 __global__ void k_cg_p(const double *s, const double *z, double *p, long long n)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -497,19 +522,19 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
     // one iteration, enqueued on stream s (no host synchronisation)
     auto iteration = [&](cudaStream_t s) -> int {
         KrylovCtx cs{n, s, wk.partial, wk.dsc, {}};
+        const int nb = kblocks(n), pre = op.precond ? 1 : 0;
         int e = op.apply(op.ctx, p, q, s);
-        if (e == PD_OK) e = dots(cs, p, 0, 1, q, nullptr);
         if (e != PD_OK) return e;
-        k_cg_alpha<<<1, 1, 0, s>>>(cs.dsc);
-        k_cg_axpy<<<nbk, 256, 0, s>>>(cs.dsc, 1.0, p, x, n);
-        k_cg_axpy<<<nbk, 256, 0, s>>>(cs.dsc, -1.0, q, r, n);
-        if ((e = dots(cs, r, 0, 1, r, nullptr)) != PD_OK) return e;
-        k_cg_check<<<1, 1, 0, s>>>(cs.dsc);
+        k_mdot<<<dim3(nb, 1), KT, 0, s>>>(p, 0, q, n, cs.partial);
+        k_cg_sum_step<<<1, KT, 0, s>>>(cs.partial, nb, cs.dsc, CG_STEP_ALPHA, pre);
+        k_cg_update<<<nbk, 256, 0, s>>>(cs.dsc, p, x, q, r, n);
+        k_mdot<<<dim3(nb, 1), KT, 0, s>>>(r, 0, r, n, cs.partial);
+        k_cg_sum_step<<<1, KT, 0, s>>>(cs.partial, nb, cs.dsc, CG_STEP_CHECK, pre);
         if (op.precond) {
             if ((e = op.precond(op.ctx, r, z, s)) != PD_OK) return e;
-            if ((e = dots(cs, r, 0, 1, z, nullptr)) != PD_OK) return e;
+            k_mdot<<<dim3(nb, 1), KT, 0, s>>>(r, 0, z, n, cs.partial);
+            k_cg_sum_step<<<1, KT, 0, s>>>(cs.partial, nb, cs.dsc, CG_STEP_BETA, pre);
         }
-        k_cg_beta<<<1, 1, 0, s>>>(cs.dsc, op.precond ? 1 : 0);
         k_cg_p<<<nbk, 256, 0, s>>>(cs.dsc, z, p, n);
         PD_CUDA(cudaGetLastError());
         return PD_OK;
