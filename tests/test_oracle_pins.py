@@ -460,3 +460,96 @@ def test_tangent_structure_and_jvp():
     w = W.random_field(g, 1.0, seed=5)
     jv = O.jvp_fd(g, mat, b, u, w, eps)
     np.testing.assert_allclose(K @ w.ravel(), jv.ravel(), atol=1e-6 * np.abs(jv).max())
+
+
+# ------------------------------------------------------------ partial volume
+
+def _cell_fraction_in_ball(d, m, samples=48):
+    """Fraction of the lattice cell of offset d (a square or cube of side 1 in
+    lattice units, centred on d) that lies inside the ball of radius m about the
+    origin, by brute-force midpoint sampling: the geometric quantity that the
+    partial volume V_ij approximates (the Remark of Sec. 3.1)."""
+    q = (np.arange(samples) + 0.5) / samples - 0.5
+    pts = np.stack(np.meshgrid(*([q] * len(d)), indexing="ij"), -1).reshape(-1, len(d)) + np.asarray(d, float)
+    return float(((pts ** 2).sum(axis=1) <= m * m).mean())
+
+
+def _two_point_vij(dim, d, m, h=0.01):
+    """V_ij of the single bond between the lattice corners 0 and d, read off the
+    oracle's PMB force: with only the far point displaced, every other bond of
+    point 0 has eta = 0 and carries nothing, so f_0 = c s V V_ij (xi+eta)/|xi+eta|."""
+    n = tuple(abs(int(x)) + 1 for x in d) + (1,) * (3 - dim)
+    g = _grid(dim, n, m, h=h)
+    mat = W.Material(model=W.PMB, E=72e9, vol_corr=1)
+    b = O.neighbors(g)
+    i0 = int(np.flatnonzero(np.all(g.coords()[:, :dim] == [0 if x >= 0 else abs(x) for x in d], axis=1))[0])
+    j = int(np.flatnonzero(np.all(g.coords()[:, :dim] == [abs(x) if x >= 0 else 0 for x in d], axis=1))[0])
+    xi = h * np.asarray(d, float)
+    eta = 1e-4 * xi                                     # pure stretch along the bond: s = 1e-4
+    u = np.zeros((g.npoints, dim))
+    u[j] = eta
+    f = O.pmb_force(g, mat, b, u)
+    s = (np.linalg.norm(xi + eta) - np.linalg.norm(xi)) / np.linalg.norm(xi)
+    V = h ** dim * (mat.thickness if dim == 2 else 1.0)
+    return float(np.linalg.norm(f[i0]) / (O.micromodulus(g, mat) * s * V))
+
+
+def test_partial_volume_of_a_bond_at_the_horizon_is_one_half():
+    """A neighbour at exactly |xi| = delta: the horizon sphere cuts its cell
+    through the centre, so half of V_j lies inside (flat-boundary value,
+    hand-computed). A neighbour well inside keeps its full volume."""
+    for dim, m in ((2, 3), (3, 3), (2, 5)):
+        d = (m,) + (0,) * (dim - 1)
+        assert abs(_two_point_vij(dim, d, m) - 0.5) < 1e-9
+        d_in = (1,) + (0,) * (dim - 1)
+        assert abs(_two_point_vij(dim, d_in, m) - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("dim,m", [(2, 3), (2, 4), (2, 6), (3, 3), (3, 4)])
+def test_partial_volume_matches_cell_ball_geometry(dim, m):
+    """For every bond of the horizon's outer shell (|xi| > delta - h/2), the
+    oracle's V_ij is within 0.06 of the fraction of the neighbour's cell inside
+    the ball, computed by brute-force sampling; neither leaving the volume
+    whole (error ~0.5) nor dropping the h/2 of the cell that reaches past the
+    node (V_ij = (delta - |xi|)/h, error ~0.5) passes."""
+    offs = set()
+    rr = range(0, m + 1)
+    for d in (np.array(t) for t in np.stack(np.meshgrid(*([rr] * dim), indexing="ij"), -1).reshape(-1, dim)):
+        r = math.sqrt(float((d ** 2).sum()))
+        if m - 0.5 < r <= m:
+            offs.add(tuple(int(x) for x in sorted(d, reverse=True)))
+    assert offs
+    for d in sorted(offs):
+        got = _two_point_vij(dim, d, m)
+        want = _cell_fraction_in_ball(d, m)
+        assert abs(got - want) < 0.06, (d, got, want)
+
+
+# --------------------------------------------------------------- body force
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_body_force_gives_uniform_acceleration(dim):
+    """Eq. (3) with a uniform body force b on a free lattice at rest: every point
+    moves together, so eta = 0 and the internal force vanishes, and the motion is
+    the closed form u = (b/rho) t^2 / 2, v = (b/rho) t at every step (velocity-
+    Verlet and central difference are exact for constant acceleration). Fixes
+    the sign of b and its 1/rho."""
+    g = _grid(dim, (6, 5, 4), 2, h=0.02)
+    mat = W.Material(model=W.PMB, E=72e9, rho=2440.0)
+    b = O.neighbors(g)
+    bvec = np.array([3.0e5, -1.25e5, 0.5e5])[:dim]
+    body = np.tile(bvec, (g.npoints, 1))
+    a = bvec / mat.rho
+    dt = 1e-4
+    z = np.zeros((g.npoints, dim))
+    st = O.ExplicitState(g, mat, b, z, z, b=body)
+    done = 0
+    for k in (1, 7, 20):                                # cumulative step counts
+        st.run(dt, k - done)
+        done = k
+        t = k * dt
+        np.testing.assert_allclose(st.u, np.tile(0.5 * a * t * t, (g.npoints, 1)), rtol=1e-12)
+        np.testing.assert_allclose(st.v, np.tile(a * t, (g.npoints, 1)), rtol=1e-12)
+        assert np.all(st.f == 0.0)
+    ucd = O.run_central_difference(g, mat, b, z, z, dt, 20, b=body)
+    np.testing.assert_allclose(ucd, np.tile(0.5 * a * (20 * dt) ** 2, (g.npoints, 1)), rtol=1e-12)
