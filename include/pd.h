@@ -440,7 +440,10 @@ int pd_energy(pd_sim *sim, double *kinetic, double *strain, void *stream);
  *   n: 0 <= n <= PD_SUM_NOALLOC_MAX_VALUES, else PD_EINVAL with a message.
  *   stream: cudaStream_t or NULL for the legacy default stream; stream-ordered.
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress); make that first call before any stream capture. The
+ * (cudaGetSymbolAddress) and keeps it for the rest of the process; make that
+ * first call before any stream capture. The kept address belongs to the
+ * device's current context: after cudaDeviceReset on that device, do not call
+ * this entry point again in the same process. The
  * array (8 KiB per device, held until the process exits) is shared by every
  * call: each call overwrites every partial it reads, so nothing needs
  * clearing, but calls that overlap on the GPU (different streams, no ordering)

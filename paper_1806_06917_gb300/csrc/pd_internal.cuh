@@ -143,7 +143,7 @@ struct KrylovOp {
     int (*precond)(void *ctx, const double *r, double *z, cudaStream_t st); // z = M^-1 r, or null
 };
 // Device scalars a Krylov solve needs at least (dot results and CG's state).
-constexpr size_t KRYLOV_DSC_MIN = 16;
+constexpr size_t KRYLOV_DSC_MIN = 24;
 struct KrylovWork {
     double *basis;      // GMRES: (restart + 1) * n; CG: 3 * n
     double *tmp;        // n

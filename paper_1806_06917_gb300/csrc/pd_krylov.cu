@@ -5,9 +5,13 @@
 // Vectors are FP64, component-major over slots: v[c * nslots + s], c < dim;
 // slots without a point hold 0 and every operation keeps them 0. All sums are
 // deterministic: a fixed block partition, a fixed in-block tree, and a fixed
-// final tree over the block partials. GMRES's few scalars per iteration (the
-// Hessenberg column, the Givens rotations) are FP64 host arithmetic on values
-// read back from the device; CG keeps alpha and beta on the device.
+// final tree over the block partials. The scalar steps run on the device too
+// (one-thread kernels): GMRES's Hessenberg column is formed from the
+// Gram-Schmidt dot products' final sums, and its Givens rotations and the
+// residual estimate from the Arnoldi vector's norm; CG's alpha and beta are
+// formed from p.Ap and r.r. The host reads the scalars back once per chunk of
+// iterations (GM_CHUNK Arnoldi steps, CG_CHUNK CG iterations), each chunk
+// replayed as a captured CUDA graph.
 #include <math.h>
 
 #include <algorithm>
@@ -408,8 +412,10 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
 // residual below the target sets DONE; the later iterations of the chunk then
 // change neither x nor r (alpha = 0, p kept), so x is the iterate at which the
 // host loop would have stopped.
-enum { CG_RZ = 8, CG_ALPHA, CG_BETA, CG_RR, CG_TARGET, CG_DONE, CG_ITERS, CG_BAD };
-static_assert(CG_BAD < (int)KRYLOV_DSC_MIN, "CG scalars exceed the device scalar block");
+// CG_BAD holds the offending p.Ap and CG_BADFLAG marks that one was met (a p.Ap
+// of exactly 0 would not show in CG_BAD alone).
+enum { CG_RZ = 8, CG_ALPHA, CG_BETA, CG_RR, CG_TARGET, CG_DONE, CG_ITERS, CG_BAD, CG_BADFLAG };
+static_assert(CG_BADFLAG < (int)KRYLOV_DSC_MIN, "CG scalars exceed the device scalar block");
 constexpr int CG_CHUNK = 32;
 
 // after dsc[0] = p.Ap: alpha = (r.z) / (p.Ap), or a non-positive curvature flag
@@ -422,6 +428,7 @@ __device__ __forceinline__ void cg_alpha(double *s)
     const double pq = s[0];
     if (!(pq > 0.0)) {
         s[CG_BAD] = pq == pq ? pq : -1.0;     // the offending p.Ap (NaN reported as -1)
+        s[CG_BADFLAG] = 1.0;
         s[CG_DONE] = 1.0;
         s[CG_ALPHA] = 0.0;
         return;
@@ -514,7 +521,7 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
     stats->iters = 0;
     stats->converged = rr == 0.0;
     if (stats->converged) return PD_OK;
-    double init[CG_BAD + 1] = {0.0};
+    double init[CG_BADFLAG + 1] = {0.0};
     init[CG_RZ] = rz;
     init[CG_RR] = rr;
     init[CG_TARGET] = rtol * stats->res0;
@@ -555,7 +562,7 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
         cudaGetLastError();
     }
     int launched = 0;
-    double back[CG_BAD + 1];
+    double back[CG_BADFLAG + 1];
     while (launched < maxit) {
         const int chunk = std::min(CG_CHUNK, maxit - launched);
         if (exec && chunk == CG_CHUNK) {
@@ -580,7 +587,7 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
         }
         stats->iters = (int)back[CG_ITERS];
         stats->res = sqrt(back[CG_RR]);
-        if (back[CG_BAD] != 0.0) {
+        if (back[CG_BADFLAG] != 0.0) {
             if (exec) cudaGraphExecDestroy(exec);
             set_error("CG: the operator is not positive definite (p.Ap = %g)", back[CG_BAD]);
             return PD_EINVAL;

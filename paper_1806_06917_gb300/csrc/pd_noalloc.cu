@@ -26,7 +26,9 @@ static std::mutex g_sum_mu;
 static double *g_sum_addr[256];   // device address of g_sum_partials, per device ordinal
 
 // The address of g_sum_partials on the current device, looked up once per
-// device (the name is only a host-side stand-in for the device array).
+// device (the name is only a host-side stand-in for the device array) and kept
+// for the life of the process: it belongs to the device's context at the time
+// of the lookup, so it is not valid after a cudaDeviceReset of that device.
 static int partials_address(double **out)
 {
     int dev = 0;

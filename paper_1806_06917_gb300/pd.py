@@ -435,7 +435,8 @@ PD_SUM_NOALLOC_MAX_VALUES = 4194304
 
 def pd_sum_noalloc(x, scale=1.0, out=None, stream=None):
     """scale * sum(x) in FP64 and fixed order, with no device allocation in the
-    library. x and out are CUDA tensors (float64); out has one element."""
+    library. x and out are float64 CUDA tensors on the same device; out has one
+    element. stream None means torch's current stream of x's device."""
     import torch
     if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
         raise ValueError("x: need a contiguous float64 CUDA tensor")
@@ -443,8 +444,15 @@ def pd_sum_noalloc(x, scale=1.0, out=None, stream=None):
         out = torch.empty(1, dtype=torch.float64, device=x.device)
     if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
         raise ValueError("out: need a float64 CUDA tensor with one element")
-    _check(_lib.pd_sum_noalloc(_P(x.data_ptr()) if x.numel() else None, int(x.numel()), float(scale),
-                               _P(out.data_ptr()), _stream(stream)))
+    if out.device != x.device:
+        raise ValueError("out must be on x's device (%s), got %s" % (x.device, out.device))
+    # the library looks up its scratch array and launches on the current device;
+    # the default stream is torch's current stream of x's device, so that the sum
+    # is ordered after the work that produced x
+    with torch.cuda.device(x.device):
+        strm = torch.cuda.current_stream(x.device) if stream is None else stream
+        _check(_lib.pd_sum_noalloc(_P(x.data_ptr()) if x.numel() else None, int(x.numel()), float(scale),
+                                   _P(out.data_ptr()), _stream(strm)))
     return out
 
 
