@@ -1,16 +1,23 @@
 """Benchmark of the peridynamic explicit step: bond updates per second.
 
-One step = one fused force + velocity-Verlet kernel of the whole lattice (PMB),
-or the dilatation pass plus the fused force + update kernel (LPS). A bond
-update is one directed bond processed in one step, all passes of that step.
+One step = the dilatation pass plus the fused force + update kernel (LPS), or
+one fused force + velocity-Verlet kernel of the whole lattice (PMB, NP). A
+bond update is one directed bond processed in one step, all passes of that
+step.
 
-Default workload: 3D block 64^3 (h = 1/64 m, m = 3, 30,289,512 directed bonds),
-PMB with breaking at s_c = 1e-3, Gaussian velocity pulse and pre-notch,
-FP32-compensated bond arithmetic with FP64 integrator state. Its per-step
-working set (~45 MB) fits in the 129 MB L2, so L2 is flushed (a 512 MB write,
-then a 256 MB read) before every timed step and each step is timed alone with CUDA events.
+Default workload: 3D block 128^3 (h = 1/128 m, m = 3, 249,027,944 directed
+bonds), state-based LPS (K = 40 GPa, mu = 30 GPa), uniform volumetric strain
+1e-4 plus a seeded perturbation, FP32-compensated bond arithmetic with FP64
+integrator state. L2 is flushed (a 512 MB write, then a 256 MB read) before
+every timed step and each step is timed alone with CUDA events; the two passes
+are timed the same way through pd_step_explicit_timed for the roofline. Side
+measurements: the all-FP64 GPU path, the double-float-state variant, the 64^3
+PMB block with breaking, the 443^2 NP shape of Sec. 6.2, the 256^3 PMB block,
+the neighbour build, the tangent product, the implicit load path and a
+bounded run of the request server.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload block64|lps128|plate50]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload lps128|block64|block256|plate50|paper443]
+  python bench.py --workload serve | convergence
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
 Multi-GPU: independent replicas (the step does not shard across GPUs here), one
@@ -35,56 +42,36 @@ sys.path.insert(0, ROOT)
 
 from paper_1806_06917_gb300 import workloads as W  # noqa: E402
 
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-# FP32 arithmetic of one bond as the kernels evaluate it (hand count; an FMA is
-# one operation; the 2 MUFU ops per bond are not included).
-# NP in 2D (np_fast): eta 2, S = eta.d/|d|^2 3, t S 1, a S^2 2, times exp 1,
-# force 2 (11, plus one MUFU ex2).
-FP32_OPS_PER_BOND = {"pmb3": 24, "pmb2": 18, "lps_dil": 19, "lps_force": 30, "np2": 11}
-# FP64 path (pmb_generic<double>): the arithmetic of one bond as written, flops
-# with an FMA as 2 and rsqrt, divide as one each (their expansion into several
-# FP64 instructions is not counted): eta, y 6; |y|^2 5; numerator 10; rsqrt 1;
-# stretch 6; weight 1; force 6 (plus 2 for the partial-volume factor when on).
-FP64_OPS_PER_BOND = 35
-FP64_NOMINAL_TFLOPS = 1.25
+# Algorithmic bytes of one pass as a CSR-driven kernel would move them: the
+# neighbour index col (4 B per bond per pass that walks bonds; the breaking bit,
+# 1/8 B read and 1/8 B written per bond, for the bond-based step with
+# breaking), and per point X 12 B (FP32), u 24 B read (FP64), the new u 24 B
+# written, v 48 B read and written, and the LPS scalars theta, m (4-8 B).
+#   PMB fused step: 4.25 B/bond + 110 B/point; LPS dilatation: 4 B/bond + 44
+#   B/point; LPS force + update: 4 B/bond + 120 B/point.
+ALG_BYTES = {"pmb3": (4.25, 110.0), "pmb2": (4.25, 76.0), "lps_dil": (4.0, 44.0), "lps_force": (4.0, 120.0),
+             "np2": (4.0, 76.0)}
+# Bytes per point the kernels themselves must move (they read a bond mask of 1
+# bit per bond, not col): PMB 3D u staging pair read 32, FP64 u and v read and
+# written 96, new staging pair 32, 4 mask words 16, BC kinds 3 (179); LPS
+# dilatation u pair 32 + masks 16 + 1/m~ 4 read, theta 4 written (56); LPS
+# force pass u pair 32 + theta, 1/m~ 8 + masks 16 read, u, v 96, new pair 32,
+# kinds 3 (187); 2D PMB: pair 32, u, v 64, new pair 32, mask 4, kinds 2 (134);
+# 2D NP at m = 20: the same with 40 mask words (290).
+PER_POINT_BYTES = {"pmb3": 179.0, "pmb2": 134.0, "lps_dil": 56.0, "lps_force": 187.0, "np2": 290.0}
+PASS_KERNEL = {"pmb3": "pmb_fast<3, *> (fused force + update)", "pmb2": "pmb_fast<2, *> (fused force + update)",
+               "lps_dil": "lps_dil_fast2 (dilatation pass)", "lps_force": "lps_force_fast (force + update pass)",
+               "np2": "np_fast2 (fused force + update, two point pairs per thread)"}
+FALLBACK_HBM_GBS = 6800.0
 
-# Algorithmic bytes per point of one step, in the kernels' layout (u and v as
-# double-float pairs, 2 x float4 = 32 B each): u read 32, v read + written 64,
-# new u written 32, bond-mask words read (4 B x W: W = 4 in 3D, 1 in 2D at m = 3,
-# 40 in 2D at m = 20), BC kinds 1 B per DOF. LPS: dilatation pass u 32 + masks
-# 16 + 1/m~ 4 read, theta 4 written (56); force pass u 32 + theta, 1/m~ 8 +
-# masks 16 read, v 64, new u 32, BC kinds 3 (155).
-BYTES_PER_POINT = {"pmb3": 147.0, "pmb2": 134.0, "lps": 211.0, "np2": 128.0 + 4 * 40 + 2}
-CSR_BYTES_PER_BOND = {"pmb3": 4.25, "pmb2": 4.25, "lps": 8.0, "np2": 4.0}
-KERNEL_LABEL = {
-    "pmb3": lambda wl: "pmb_fast<3, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
-    "pmb2": lambda wl: "pmb_fast<2, %s>" % ("true" if wl.mat.s_c > 0 else "false"),
-    "lps": lambda wl: "lps_dil_fast + lps_force_fast (one step)",
-    "np2": lambda wl: "np_fast2<false> (two point pairs per thread)",
-}
-
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step's
-# launches, from one `ncu --set full` capture of each workload's kernels (the
-# summaries under profiles/). A figure holds only while the kernel's sources and
-# build flags hash to the value recorded with it; otherwise traffic is null.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each pass, from one `ncu --set full` capture of that kernel (the summaries
+# under profiles/). A figure holds only while the kernel's sources and build
+# flags hash to the value recorded with it; otherwise traffic is null.
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
 NCU_TRAFFIC = {
-    # (kernel key, tile_log2): the capture of that kernel at that tile size
-    ("pmb3", 9): {"bytes": 21903616 + 11264, "sha": "fd63c70de79fc282",
-                  "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
-                  "profile": "profiles/pmb_fast_block3d_64.md"},
-    ("pmb3", 8): {"bytes": 21968640 + 1280, "sha": "fd63c70de79fc282",
-                  "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
-                  "profile": "profiles/pmb_fast_block3d_64.md"},
-    ("lps", 9): {"bytes": (109791488 + 5980928) + (195891200 + 97487872), "sha": "19443b34cf7d882b",
-                 "sources": ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + _KERNEL_COMMON,
-                 "profile": "profiles/lps_block3d_128.md"},
-    ("np2", 9): {"bytes": 45662464 + 73728, "sha": "fd63c70de79fc282",
-                 "sources": ["paper_1806_06917_gb300/csrc/pd_force_pmb.cu"] + _KERNEL_COMMON,
-                 "profile": "profiles/np_fast2_paper443.md"},
+    # (pass key, tile_log2): the capture of that kernel at that tile size
 }
 
 
@@ -205,14 +192,14 @@ def measured_peaks():
     return None
 
 
-def make_sim(pd, wl, precision, stream, integrator=0, tile_log2=None):
+def make_sim(pd, wl, precision, stream, integrator=0, tile_log2=None, state=0):
     """The workload's simulation; tile_log2 None picks the tile with pd_tune_tile
     (best of 3 x 10 back-to-back steps per admissible tile), 0 the library default."""
     if tile_log2 is None:
-        g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator)
+        g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator, state=state)
         tile_log2 = pd.pd_tune_tile(g, m, r, steps=10, stream=stream)
     g, m, r = pd.describe(wl.grid, wl.mat, precision=precision, dt=wl.dt, integrator=integrator,
-                          tile_log2=tile_log2)
+                          tile_log2=tile_log2, state=state)
     sim = pd.pd_create(g, m, r)
     sim.tile_log2 = tile_log2 if tile_log2 else None
     pd.pd_build_neighbors(sim, stream)
@@ -327,7 +314,7 @@ def _submit_request(pd, srv, r):
     return pd.pd_submit(srv, g, m, run, r.steps, u0=r.u0)
 
 
-def run_serving(args, pd, torch, rank=0, world=1):
+def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     """The request mix through the server: one-at-a-time capacity on a sample
     (max_active = 1), then the whole mix arriving as a Poisson process at
     args.load x that capacity, max_active concurrent simulations. With N ranks
@@ -372,7 +359,7 @@ def run_serving(args, pd, torch, rank=0, world=1):
             "unit": "bond-updates/s", "n_gpus": world, "steps": len(lat), "warmup": 1,
             "ms_per_step": 1e3 * makespan / len(lat), "higher_is_better": True,
             "scaling": "strong" if world > 1 else "weak",
-            "vs_baseline": None, "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)",
+            "vs_baseline": None, "dtype": "f32 bond arithmetic (compensated), f64 integrator state",
             "data": "synthetic",
             "config": {"workload": "serving_mix: %d requests (2D/3D, PMB/LPS, lognormal sides 20..96, "
                                    "m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
@@ -386,7 +373,9 @@ def run_serving(args, pd, torch, rank=0, world=1):
             "serial": {"requests": k, "value": serial_work / serial_s, "unit": "bond-updates/s",
                        "capacity_requests_per_s": capacity},
             "gpu_launches": None, "roofline": None, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_convergence(args, pd, torch):
@@ -444,7 +433,7 @@ def run_convergence(args, pd, torch):
     line = {"metric": "bond updates/s (2D NP/LP convergence study, 12 runs)", "value": work / sec,
             "unit": "bond-updates/s", "n_gpus": 1, "steps": steps_total, "warmup": 0, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)", "data": "synthetic",
+            "dtype": "f32 bond arithmetic (compensated), f64 integrator state", "data": "synthetic",
             "config": {"workload": "Sec. 5.2.2: [0,1]^2, delta = 0.1, h = delta/2, delta/4, delta/8, "
                                    "collar u = 0, dt = 1e-5, t in [0, %g]" % (steps_total * 1e-5),
                        "l2": "not flushed"},
@@ -567,14 +556,196 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def pass_times(pd, torch, sim, wl, steps, warmup, stream, flush):
+    """Per-pass device times (ms) of single explicit steps, L2 flushed before each:
+    (first launch, second launch) of every step, from pd_step_explicit_timed's
+    CUDA events on the launching stream."""
+    pd.pd_set_state(sim, u=wl.u0, v=wl.v0, stream=stream)
+    if wl.bc_kind is not None and wl.bc_kind.any():
+        pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val, stream)
+    pd.pd_step_explicit(sim, warmup, stream)
+    torch.cuda.synchronize()
+    half = flush.numel() // 2
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        flush[:half].sum()
+        torch.cuda.synchronize()
+        out.append(pd.pd_step_explicit_timed(sim, 1, stream))
+    return out
+
+
+def e2e_rate(pd, torch, sim, wl, nbonds, steps, warmup, stream, world):
+    """End to end through the public API with host buffers every step: the state
+    (u, v) in from pinned host memory, one explicit step, u back out to pinned
+    host memory (pd_get_state is synchronous)."""
+    u_h = torch.from_numpy(wl.u0).pin_memory()
+    v_h = torch.from_numpy(wl.v0).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
+        pd.pd_step_explicit(sim, 1, stream)
+        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
+        pd.pd_step_explicit(sim, 1, stream)
+        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = rank_reduce(torch, e0.elapsed_time(e1), "max", "cuda")
+    return {"value": world * nbonds * steps / (ms * 1e-3), "unit": "bond-updates/s",
+            "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8, "d2h_bytes_per_step": u_o.numel() * 8,
+            "ms_per_step": ms / steps,
+            "note": "per step: pd_set_state(u, v) from pinned host + pd_step_explicit(1) + pd_get_state(u) "
+                    "to pinned host; L2 not flushed"}
+
+
+def roofline_of(key, wl, nbonds, passes_ms, step_ms, tile_log2, peaks):
+    """Roofline of the dominant launch (the LPS force + update pass, or the fused
+    bond-based step) on the algorithmic bytes of a CSR-driven pass, against the
+    measured HBM copy peak; the other pass and the whole step beside it."""
+    npts = wl.grid.npoints
+    hbm = peaks["hbm_gbs"] if peaks else FALLBACK_HBM_GBS
+    src = "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback 6800 GB/s (no measured peak)"
+    names = ["lps_dil", "lps_force"] if key == "lps" else [key]
+    per = {}
+    for i, nm in enumerate(names):
+        b_bond, b_pt = ALG_BYTES[nm]
+        byts = b_bond * nbonds + b_pt * npts
+        gbs = byts / (passes_ms[i] * 1e-3) / 1e9
+        per[nm] = {"kernel": PASS_KERNEL[nm], "launch_ms": passes_ms[i], "bytes_per_launch": byts,
+                   "bytes_model": "%g B/bond + %g B/point" % (b_bond, b_pt), "achieved_gbs": gbs,
+                   "frac": gbs / hbm, "per_point_bytes": PER_POINT_BYTES[nm],
+                   "per_point_frac": PER_POINT_BYTES[nm] * npts / (passes_ms[i] * 1e-3) / 1e9 / hbm,
+                   "traffic": ncu_traffic(nm, tile_log2)}
+    dom = per[names[-1]]
+    step_bytes = sum(ALG_BYTES[nm][0] * nbonds + ALG_BYTES[nm][1] * npts for nm in names)
+    r = {"bound": "hbm", "achieved": dom["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": dom["frac"],
+         "traffic": dom["traffic"], "kernel": dom["kernel"], "launch_ms": dom["launch_ms"],
+         "bytes_per_launch": dom["bytes_per_launch"], "bytes_model": dom["bytes_model"],
+         "peak_source": src, "passes": per,
+         "step": {"bytes": step_bytes, "ms": step_ms, "achieved_gbs": step_bytes / (step_ms * 1e-3) / 1e9,
+                  "frac": step_bytes / (step_ms * 1e-3) / 1e9 / hbm},
+         "note": "algorithmic bytes of a CSR-driven pass (col 4 B per bond per pass; per point u, v in FP64, "
+                 "X, theta and m~); the kernels read a 1-bit-per-bond mask instead of col, so the bytes they "
+                 "must move are the per_point_bytes, and their bound is the L1 / shared-memory pipe "
+                 "(profiles/); traffic = ncu dram bytes of one launch, null when the kernel changed since"}
+    return r
+
+
+def explicit_measurement(pd, torch, wl, key, args, stream, flush, state, world, with_e2e):
+    """Step rate of one workload: every step timed alone (L2 flushed), the passes
+    timed alone the same way, and optionally e2e."""
+    sim = make_sim(pd, wl, pd.PD_FP32C, stream, tile_log2=args.tile_log2, state=state)
+    nbonds = pd.pd_bond_count(sim)
+    durs = time_steps(pd, torch, sim, wl, args.steps, args.warmup, stream, flush)
+    ms = rank_reduce(torch, float(np.mean(durs)), "max", "cuda")
+    pt = pass_times(pd, torch, sim, wl, max(3, min(args.steps, 20)), args.warmup, stream, flush)
+    passes = [float(np.mean([p[0] for p in pt])), float(np.mean([p[1] for p in pt]))]
+    out = {"sim": sim, "nbonds": nbonds, "ms": ms, "passes_ms": passes}
+    if with_e2e:
+        out["e2e"] = e2e_rate(pd, torch, sim, wl, nbonds, args.steps, args.warmup, stream, world)
+    return out
+
+
+def state_variants(pd, torch, wl, stream, flush, tile_log2, steps=100):
+    """The double-float-state variant of the FP32C path beside the FP64-state one:
+    its step time, and its u, v difference from the FP64-state run after `steps`
+    steps of the workload from its initial state."""
+    res = {}
+    for name, state in (("f64", pd.PD_STATE_F64), ("df", pd.PD_STATE_DF)):
+        sim = make_sim(pd, wl, pd.PD_FP32C, stream, tile_log2=tile_log2, state=state)
+        d = time_steps(pd, torch, sim, wl, 10, 3, stream, flush)
+        pd.pd_set_state(sim, u=wl.u0, v=wl.v0, stream=stream)
+        if wl.bc_kind is not None and wl.bc_kind.any():
+            pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val, stream)
+        pd.pd_step_explicit(sim, steps, stream)
+        u, v = pd.pd_get_state(sim, stream=stream)
+        res[name] = (float(np.mean(d)), u, v)
+        sim.close()
+    (m64, u64, v64), (mdf, udf, vdf) = res["f64"], res["df"]
+    return {"ms_per_step_f64_state": m64, "ms_per_step_df_state": mdf, "speedup_df_over_f64": m64 / mdf,
+            "steps_compared": steps,
+            "u_rel_l2_df_vs_f64": float(np.linalg.norm(udf - u64) / max(np.linalg.norm(u64), 1e-300)),
+            "v_rel_l2_df_vs_f64": float(np.linalg.norm(vdf - v64) / max(np.linalg.norm(v64), 1e-300))}
+
+
+def fp64_path(pd, torch, wl, stream, flush, nbonds, ms32, peak_note=True):
+    """The plain all-FP64 GPU path on the same workload."""
+    sim64 = make_sim(pd, wl, pd.PD_FP64, stream)
+    d64 = time_steps(pd, torch, sim64, wl, 5, 3, stream, flush)
+    ms64 = float(np.mean(d64))
+    tile = sim64.tile_log2
+    sim64.close()
+    return {"value": nbonds / (ms64 * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms64, "tile_log2": tile,
+            "steps": len(d64), "ratio_fp64_over_fp32c": ms64 / ms32}
+
+
+def fp32c_vs_fp64(pd, wl, stream, steps=200):
+    """Accuracy of the FP32C path (FP64 state) against the all-FP64 GPU path: the
+    same workload from its initial state, the same number of steps."""
+    acc = []
+    for prec in (pd.PD_FP32C, pd.PD_FP64):
+        sa = make_sim(pd, wl, prec, stream, tile_log2=0)
+        pd.pd_set_state(sa, u=wl.u0, v=wl.v0, stream=stream)
+        if wl.bc_kind is not None and wl.bc_kind.any():
+            pd.pd_set_bc(sa, wl.bc_kind, wl.bc_val, stream)
+        pd.pd_step_explicit(sa, steps, stream)
+        ua, va = pd.pd_get_state(sa, stream=stream)
+        acc.append((ua, va, pd.pd_get_broken(sa, stream=stream)))
+        sa.close()
+    (u32, v32, k32), (u64, v64, k64) = acc
+    return {"steps": steps,
+            "u_rel_l2": float(np.linalg.norm(u32 - u64) / max(np.linalg.norm(u64), 1e-300)),
+            "v_rel_l2": float(np.linalg.norm(v32 - v64) / max(np.linalg.norm(v64), 1e-300)),
+            "broken_fp32c": int(k32.sum()), "broken_fp64": int(k64.sum()), "broken_differ": int((k32 != k64).sum())}
+
+
+def side_step(pd, torch, name, stream, flush, args):
+    """A side workload's FP32C step rate with its roofline (FP64 state)."""
+    wl, desc = workload(name)
+    key = workload_key(wl)
+    sim = make_sim(pd, wl, pd.PD_FP32C, stream)
+    nb = pd.pd_bond_count(sim)
+    d = time_steps(pd, torch, sim, wl, 10, 3, stream, flush)
+    ms = float(np.mean(d))
+    pt = pass_times(pd, torch, sim, wl, 5, 2, stream, flush)
+    passes = [float(np.mean([p[0] for p in pt])), float(np.mean([p[1] for p in pt]))]
+    out = {"workload": desc, "value": nb / (ms * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms,
+           "steps": len(d), "bonds": nb, "tile_log2": sim.tile_log2,
+           "launches_per_step": 2 if key == "lps" else 1,
+           "roofline": roofline_of(key, wl, nb, passes, ms, sim.tile_log2, measured_peaks())}
+    sim.close()
+    return out, wl
+
+
+def serving_side(pd, torch, requests=128, load=2.0, max_active=16, quantum=64):
+    """A bounded run of the request server beside the headline: the first
+    `requests` of the seeded mix arriving as a Poisson process at `load` x the
+    one-at-a-time capacity (measured on 12 requests alone), against those
+    one-at-a-time launches."""
+    class A:
+        pass
+    a = A()
+    a.requests, a.load, a.max_active, a.quantum, a.serial_sample = requests, load, max_active, quantum, 12
+    return run_serving(a, pd, torch, 0, 1, emit=False)
+
+
+def workload_key(wl):
+    return {W.LPS: "lps", W.NP: "np2"}.get(wl.mat.model, "pmb3" if wl.grid.dim == 3 else "pmb2")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="block64",
-                    choices=["block64", "block256", "lps128", "plate50", "paper443", "serve", "convergence"])
+    ap.add_argument("--workload", default="lps128",
+                    choices=["lps128", "block64", "block256", "plate50", "paper443", "serve", "convergence"])
     ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
@@ -584,8 +755,10 @@ def main():
     ap.add_argument("--tile-log2", type=int, default=None,
                     help="tile size 2^N of the timed simulation (6..9; 0 = library default); "
                          "by default pd_tune_tile measures and picks it")
+    ap.add_argument("--state", default="f64", choices=["f64", "df"],
+                    help="integrator state of the timed FP32C simulation: FP64 or double-float")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path and LPS side measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -613,11 +786,10 @@ def main():
         return
 
     wl, desc = workload(args.workload)
+    key = workload_key(wl)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    sim = make_sim(pd, wl, pd.PD_FP32C, stream, tile_log2=args.tile_log2)
-    nbonds = pd.pd_bond_count(sim)
-    key = {W.LPS: "lps", W.NP: "np2"}.get(wl.mat.model, "pmb3" if wl.grid.dim == 3 else "pmb2")
+    state = pd.PD_STATE_F64 if args.state == "f64" else pd.PD_STATE_DF
     launches_per_step = 2 if key == "lps" else 1
 
     def barrier():
@@ -627,182 +799,72 @@ def main():
 
     barrier()
     with Clocks(local) as clk:
-        t_wall = time.time()
-        durs = time_steps(pd, torch, sim, wl, args.steps, args.warmup, stream, flush)
-        t_wall = time.time() - t_wall
+        m = explicit_measurement(pd, torch, wl, key, args, stream, flush, state, world, with_e2e=True)
     barrier()
-    ms = rank_reduce(torch, float(np.mean(durs)), "max", "cuda")
+    sim, nbonds, ms = m["sim"], m["nbonds"], m["ms"]
     value = world * nbonds / (ms * 1e-3)
-
-    # end to end through the public API, host buffers every step: the state
-    # (u, v) in from pinned host memory, one explicit step, u back out to pinned
-    # host memory (pd_get_state is synchronous)
-    u_h = torch.from_numpy(wl.u0).pin_memory()
-    v_h = torch.from_numpy(wl.v0).pin_memory()
-    u_o = torch.empty_like(u_h).pin_memory()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
-        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
-        pd.pd_step_explicit(sim, 1, stream)
-        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
-        pd.pd_step_explicit(sim, 1, stream)
-        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = rank_reduce(torch, e0.elapsed_time(e1), "max", "cuda")
-    e2e = {"value": world * nbonds * args.steps / (e2e_ms * 1e-3), "unit": "bond-updates/s",
-           "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8,
-           "d2h_bytes_per_step": u_o.numel() * 8,
-           "note": "per step: pd_set_state(u, v) from pinned host + pd_step_explicit(1) + pd_get_state(u) "
-                   "to pinned host; L2 not flushed"}
-
-    # roofline of the dominant kernel: FP32 ALU (not HBM) bound
-    ops = FP32_OPS_PER_BOND[key] if key != "lps" else FP32_OPS_PER_BOND["lps_dil"] + FP32_OPS_PER_BOND["lps_force"]
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = ops * nbonds / (ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP32 ops)",
-                "frac": achieved / peak, "traffic": ncu_traffic(key, sim.tile_log2),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz, one op per lane per clock",
-                "ops_per_bond": ops, "kernel": KERNEL_LABEL[key](wl),
-                "launch_ms": ms / launches_per_step if key != "lps" else ms,
-                "traffic_note": "bytes per step (all launches of one step) from one ncu capture, "
-                                "cold L2; null when the kernel changed since"}
-    if roofline["traffic"] is not None:
-        # the captured DRAM bytes per step over this run's step time
-        roofline["traffic_gbs"] = roofline["traffic"] / (ms * 1e-3) / 1e9
     peaks = measured_peaks()
-    if peaks:
-        # per-point bytes the fused step must move (the kernels read no neighbour
-        # list); and, for context, the bytes a CSR kernel would add (4 B of col
-        # per bond per pass plus the breaking bit)
-        bytes_pt, csr_b = BYTES_PER_POINT[key], CSR_BYTES_PER_BOND[key]
-        roofline["hbm_frac_of_measured"] = (bytes_pt * wl.grid.npoints / (ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
-        roofline["hbm_frac_of_measured_csr_equivalent"] = (
-            (bytes_pt * wl.grid.npoints + csr_b * nbonds) / (ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
-        roofline["hbm_peak_gbs"] = peaks["hbm_gbs"]
-
+    roofline = roofline_of(key, wl, nbonds, m["passes_ms"], ms, sim.tile_log2, peaks)
+    state_desc = "f64 integrator state (u, v)" if state == pd.PD_STATE_F64 else \
+        "f32 pairs as double-float integrator state (u, v)"
     line = {"metric": "bond updates/s (explicit step)", "value": value,
             "unit": "bond-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (bond sums), f32 pairs as double-float (integrator state)", "data": "synthetic",
+            "dtype": "f32 bond arithmetic (compensated), " + state_desc, "data": "synthetic",
             "config": {"workload": desc, "bonds": nbonds, "points": wl.grid.npoints,
-                       "l2": "flushed before every timed step (512 MB write, then a 256 MB read that writes the dirty lines back)", "parallelism": "replicas",
-                       "launches_per_step": launches_per_step,
-                       "tile_log2": sim.tile_log2,
-                       "tile_choice": "pd_tune_tile (best of 3 x 10 back-to-back steps per tile)" if args.tile_log2 is None
-                       else "--tile-log2"},
+                       "l2": "flushed before every timed step (512 MB write, then a 256 MB read that writes the "
+                             "dirty lines back)", "parallelism": "replicas",
+                       "launches_per_step": launches_per_step, "tile_log2": sim.tile_log2,
+                       "tile_choice": "pd_tune_tile (best of 3 x 10 back-to-back steps per tile)"
+                       if args.tile_log2 is None else "--tile-log2"},
             "gpu_launches": args.steps * launches_per_step,
-            "roofline": roofline, "e2e": e2e}
+            "roofline": roofline, "e2e": m["e2e"]}
+    sim.close()
 
     if not args.no_extras and rank == 0:
-        # the plain all-FP64 GPU path on the same workload
-        sim64 = make_sim(pd, wl, pd.PD_FP64, stream)
-        d64 = time_steps(pd, torch, sim64, wl, max(3, min(args.steps, 10)), 3, stream, flush)
-        ms64 = float(np.mean(d64))
-        line["fp64_path"] = {"value": nbonds / (ms64 * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms64,
-                             "tile_log2": sim64.tile_log2,
-                             "steps": len(d64), "ratio_fp32c_over_fp64": ms64 / ms,
-                             "fp64_ops_per_bond": FP64_OPS_PER_BOND,
-                             "fp64_tflops": FP64_OPS_PER_BOND * nbonds / (ms64 * 1e-3) / 1e12,
-                             "fp64_frac_of_nominal": FP64_OPS_PER_BOND * nbonds / (ms64 * 1e-3) / 1e12
-                             / FP64_NOMINAL_TFLOPS,
-                             "fp64_peak_source": "nominal GB300 FP64 rate (not measured on this pool)"}
-        sim64.close()
-        # accuracy of the FP32-compensated path against the all-FP64 GPU path: the
-        # same workload from its initial state, the same number of steps
-        acc_steps = 200
-        acc = []
-        for prec in (pd.PD_FP32C, pd.PD_FP64):
-            sa = make_sim(pd, wl, prec, stream, tile_log2=0)
-            pd.pd_set_state(sa, u=wl.u0, v=wl.v0, stream=stream)
-            if wl.bc_kind is not None and wl.bc_kind.any():
-                pd.pd_set_bc(sa, wl.bc_kind, wl.bc_val, stream)
-            pd.pd_step_explicit(sa, acc_steps, stream)
-            ua, va = pd.pd_get_state(sa, stream=stream)
-            acc.append((ua, va, pd.pd_get_broken(sa, stream=stream)))
-            sa.close()
-        (u32, v32, k32), (u64, v64, k64) = acc
-        line["fp32c_vs_fp64"] = {
-            "steps": acc_steps,
-            "u_rel_l2": float(np.linalg.norm(u32 - u64) / max(np.linalg.norm(u64), 1e-300)),
-            "v_rel_l2": float(np.linalg.norm(v32 - v64) / max(np.linalg.norm(v64), 1e-300)),
-            "broken_fp32c": int(k32.sum()), "broken_fp64": int(k64.sum()),
-            "broken_differ": int((k32 != k64).sum())}
-        # the same step with the central-difference drift (Eq. (10))
-        simcd = make_sim(pd, wl, pd.PD_FP32C, stream, integrator=pd.PD_INTEGRATOR_CD, tile_log2=sim.tile_log2)
-        dcd = time_steps(pd, torch, simcd, wl, max(3, min(args.steps, 10)), 3, stream, flush)
-        mscd = float(np.mean(dcd))
-        line["central_difference"] = {"value": nbonds / (mscd * 1e-3), "unit": "bond-updates/s",
-                                      "ms_per_step": mscd, "steps": len(dcd), "ratio_over_verlet": mscd / ms}
-        simcd.close()
-        if args.workload == "block64":
-            wl2, desc2 = workload("lps128")
-            sim2 = make_sim(pd, wl2, pd.PD_FP32C, stream)
-            d2 = time_steps(pd, torch, sim2, wl2, 10, 3, stream, flush)
-            ms2 = float(np.mean(d2))
-            nb2 = pd.pd_bond_count(sim2)
-            ops2 = FP32_OPS_PER_BOND["lps_dil"] + FP32_OPS_PER_BOND["lps_force"]
-            line["lps128"] = {"workload": desc2, "value": nb2 / (ms2 * 1e-3), "unit": "bond-updates/s",
-                              "ms_per_step": ms2, "steps": len(d2), "launches_per_step": 2, "tile_log2": sim2.tile_log2,
-                              "alu_frac": ops2 * nb2 / (ms2 * 1e-3) / 1e12 / peak}
-            sim2.close()
-            # the explicit benchmark shape of Sec. 6.2 (443^2 nodes, m = 20, NP law)
-            wl3, desc3 = workload("paper443")
-            sim3 = make_sim(pd, wl3, pd.PD_FP32C, stream)
-            d3 = time_steps(pd, torch, sim3, wl3, 10, 3, stream, flush)
-            ms3 = float(np.mean(d3))
-            nb3 = pd.pd_bond_count(sim3)
-            line["paper443"] = {"workload": desc3, "value": nb3 / (ms3 * 1e-3), "unit": "bond-updates/s",
-                                "ms_per_step": ms3, "steps": len(d3), "launches_per_step": 1, "tile_log2": sim3.tile_log2,
-                                "alu_frac": FP32_OPS_PER_BOND["np2"] * nb3 / (ms3 * 1e-3) / 1e12 / peak}
-            sim3.close()
-            # the same PMB workload at 64x the points (256^3, 2.0e9 bonds): many
-            # waves of tiles per SM instead of one
-            wl4, desc4 = workload("block256")
-            sim4 = make_sim(pd, wl4, pd.PD_FP32C, stream)
-            d4 = time_steps(pd, torch, sim4, wl4, 10, 3, stream, flush)
-            ms4 = float(np.mean(d4))
-            nb4 = pd.pd_bond_count(sim4)
-            line["block256"] = {"workload": desc4, "value": nb4 / (ms4 * 1e-3), "unit": "bond-updates/s",
-                                "ms_per_step": ms4, "steps": len(d4), "bonds": nb4, "tile_log2": sim4.tile_log2,
-                                "alu_frac": FP32_OPS_PER_BOND["pmb3"] * nb4 / (ms4 * 1e-3) / 1e12 / peak}
-            sim4.close()
-            del wl4
-            line["neighbour_build"] = {"block64": time_build(pd, torch, wl, stream),
-                                       "lps128": time_build(pd, torch, wl2, stream)}
+        line["fp64_path"] = fp64_path(pd, torch, wl, stream, flush, nbonds, ms)
+        line["state_variants"] = state_variants(pd, torch, wl, stream, flush, args.tile_log2 or 0)
+        line["fp32c_vs_fp64"] = fp32c_vs_fp64(pd, wl, stream, steps=100 if key == "lps" else 200)
+        if args.workload == "lps128":
+            b64, wl64 = side_step(pd, torch, "block64", stream, flush, args)
+            b64["fp64_path"] = fp64_path(pd, torch, wl64, stream, flush, b64["bonds"], b64["ms_per_step"])
+            b64["fp32c_vs_fp64"] = fp32c_vs_fp64(pd, wl64, stream, steps=200)
+            simcd = make_sim(pd, wl64, pd.PD_FP32C, stream, integrator=pd.PD_INTEGRATOR_CD,
+                             tile_log2=b64["tile_log2"])
+            dcd = time_steps(pd, torch, simcd, wl64, 10, 3, stream, flush)
+            simcd.close()
+            b64["central_difference"] = {"ms_per_step": float(np.mean(dcd)),
+                                         "ratio_over_verlet": float(np.mean(dcd)) / b64["ms_per_step"]}
+            line["block64"] = b64
+            line["paper443"], _ = side_step(pd, torch, "paper443", stream, flush, args)
+            line["block256"], _ = side_step(pd, torch, "block256", stream, flush, args)
+            line["neighbour_build"] = {"lps128": time_build(pd, torch, wl, stream),
+                                       "block64": time_build(pd, torch, wl64, stream)}
             line["jvp200"] = {"fp64": time_jvp(pd, torch, pd.PD_FP64), "fp32c": time_jvp(pd, torch, pd.PD_FP32C)}
             line["implicit_plate200"] = {
                 "workload": "200x200 plate, h = 1/200 m, m = 3, PMB, left collar clamped, right collar "
                             "u_x = 1e-4 W in 10 load steps; matrix-free Newton-Krylov",
                 "gmres50_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64),
-                "gmres50_fp64_jvp_tangent": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64,
-                                                          tangent=pd.PD_TANGENT_JVP),
                 "cg_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64),
-                "gmres50_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64,
-                                                           precond=pd.PD_PRECOND_BLOCK_JACOBI),
                 "pcg_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64,
                                                        precond=pd.PD_PRECOND_BLOCK_JACOBI),
                 "cg_fp32c": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP32C)}
+            line["serve"] = serving_side(pd, torch)
 
     line["clocks"] = clk.summary()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(wl)
         line["cpu_baseline"] = cb
-        if "lps128" in line:
+        if "block64" in line:
             # the oracle beside the side measurements, each on a bounded sample
-            line["lps128"]["cpu_baseline"] = oracle_step_rate(
-                W.block3d_lps(nside=40), "a 40^3 LPS block (the 128^3 workload's model, moduli and horizon)")
+            line["block64"]["cpu_baseline"] = oracle_step_rate(
+                workload("block64")[0], "the full 64^3 PMB workload")
             line["paper443"]["cpu_baseline"] = oracle_step_rate(
                 W.np_square(k=20, delta=0.2), "a 141^2 NP square at m = 20 (the 443^2 step's law and horizon, "
                                               "h = 0.01 m)")
             line["neighbour_build"]["block64"]["cpu_baseline"] = oracle_build_rate(
-                wl.grid, "cell-list build of the full 64^3 lattice")
+                workload("block64")[0].grid, "cell-list build of the full 64^3 lattice")
             line["jvp200"]["cpu_baseline"] = oracle_jvp_rate()
-    sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

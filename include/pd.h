@@ -62,9 +62,16 @@ extern "C" {
 #define PD_MODEL_LP 3      /* its linearisation: psi'(0) = C beta in place of psi' */
 
 #define PD_FP32C 0         /* FP32 bond arithmetic on per-tile reference-frame
-                              displacements; integrator state u, v held as
-                              double-float (FP32 hi + lo, ~48-bit) */
+                              displacements; integrator state per pd_run.state */
 #define PD_FP64 1          /* all-FP64 bond arithmetic and state */
+
+/* Integrator state of a PD_FP32C simulation (pd_run.state). */
+#define PD_STATE_F64 0     /* u and v in FP64: the velocity kicks and the drift are
+                              FP64 additions / FMAs; the kernels stage u as an FP32
+                              hi + lo pair (~47 bits) split from the FP64 value */
+#define PD_STATE_DF 1      /* u and v as double-float numbers (FP32 hi + lo, ~48
+                              bits) updated in FP32 arithmetic (two-sum, Dekker
+                              product): no FP64 instruction on the step path */
 
 #define PD_BC_FREE 0
 #define PD_BC_VELOCITY 1       /* prescribed velocity on this DOF */
@@ -136,7 +143,8 @@ typedef struct {
                            0 selects 9, or less when the halo box of a large
                            horizon would not fit in shared memory; 6..9 */
     int32_t integrator; /* PD_INTEGRATOR_VERLET (0) or PD_INTEGRATOR_CD */
-    int32_t reserved;   /* must be 0 */
+    int32_t state;      /* PD_FP32C: PD_STATE_F64 (0) or PD_STATE_DF; must be 0
+                           for PD_FP64 */
 } pd_run;
 
 typedef struct pd_sim pd_sim;
@@ -247,6 +255,16 @@ int pd_dilatation(pd_sim *sim, const double *u, double *theta_out, void *stream)
  * force + update kernel per step (two for LPS), replayed as CUDA graphs.
  * Stream-ordered. */
 int pd_step_explicit(pd_sim *sim, int64_t nsteps, void *stream);
+
+/* The same steps as pd_step_explicit, for measurement: launched one kernel at
+ * a time (no graph) with a CUDA event on `stream` before and after each
+ * launch, the host waiting for every step. pass_ms[0] receives the summed
+ * device time of the first launch of each step (PMB, NP, LP: the fused force +
+ * update kernel; LPS: the dilatation pass), pass_ms[1] that of the LPS force +
+ * update pass (0 for the bond-based laws). The trajectory is the one
+ * pd_step_explicit gives. Synchronous. Errors: PD_EINVAL for nsteps < 0 or a
+ * null pass_ms. */
+int pd_step_explicit_timed(pd_sim *sim, int64_t nsteps, double pass_ms[2], void *stream);
 
 /* Measured tile choice. For each tile size 2^9, 2^8, 2^7, 2^6 that the
  * description admits (the halo box of each kernel fits in shared memory),

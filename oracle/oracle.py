@@ -76,6 +76,9 @@ def _lib_handle():
                 "or_stable_dt": (dbl, [_P, _P, _P, _P]),
                 "or_run_verlet": (i32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                         dbl, i64, _P, i32, _P]),
+                "or_run_verlet_tracked": (i32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                                dbl, i64, _P, i32, _P, _P, _P, i64]),
+                "or_bond_stretch": (None, [_P, _P, _P, _P, _P]),
                 "or_run_central_difference": (i32, [_P, _P, _P, _P, _P, _P, _P, _P, _P,
                                                     dbl, i64, _P]),
                 "or_tangent_fd": (i32, [_P, _P, _P, _P, _P, _P, _P, dbl, _P]),
@@ -230,10 +233,23 @@ def stable_dt(grid, mat, bonds: Bonds) -> float:
                                             _ptr(bonds.row_ptr), _ptr(bonds.col)))
 
 
-class ExplicitState:
-    """u, v, the last force and the bond state of a velocity-Verlet run."""
+def bond_stretch(grid, bonds: Bonds, u) -> np.ndarray:
+    """Stretch (|xi + eta| - |xi|) / |xi| of every directed bond (CSR order) at u."""
+    out = np.zeros(bonds.nbonds)
+    _lib_handle().or_bond_stretch(ctypes.byref(_grid(grid)), _ptr(bonds.row_ptr), _ptr(bonds.col),
+                                  _ptr(_c(u, np.float64)), _ptr(out))
+    return out
 
-    def __init__(self, grid, mat, bonds: Bonds, u0, v0, bc_kind=None, bc_val=None, b=None):
+
+class ExplicitState:
+    """u, v, the last force and the bond state of a velocity-Verlet run.
+
+    With track=True the run also records, per directed bond (CSR order),
+    ``s_max``: the largest stretch at which the bond was evaluated while intact
+    (the evaluation that broke it included), and ``brk_step``: the step whose
+    force evaluation broke it (0 = the initial force, -1 = never)."""
+
+    def __init__(self, grid, mat, bonds: Bonds, u0, v0, bc_kind=None, bc_val=None, b=None, track=False):
         self.grid, self.mat, self.bonds = grid, mat, bonds
         self.u = np.array(u0, dtype=np.float64, order="C", copy=True)
         self.v = np.array(v0, dtype=np.float64, order="C", copy=True)
@@ -244,17 +260,22 @@ class ExplicitState:
         self.f_valid = False
         self.theta = np.zeros(grid.npoints)
         self.mvol = weighted_volume(grid, mat, bonds) if mat.model == 1 else None
+        self.steps = 0
+        self.s_max = np.full(bonds.nbonds, -np.inf) if track else None
+        self.brk_step = np.full(bonds.nbonds, -1, dtype=np.int32) if track else None
 
     def run(self, dt: float, nsteps: int) -> None:
-        rc = _lib_handle().or_run_verlet(
+        rc = _lib_handle().or_run_verlet_tracked(
             ctypes.byref(_grid(self.grid)), ctypes.byref(_mat(self.mat)),
             _ptr(self.bonds.row_ptr), _ptr(self.bonds.col), _ptr(self.bonds.broken),
             _ptr(self.mvol), _ptr(self.u), _ptr(self.v), _ptr(self.b),
             _ptr(self.bc_kind), _ptr(self.bc_val), float(dt), int(nsteps),
-            _ptr(self.f), int(self.f_valid), _ptr(self.theta))
+            _ptr(self.f), int(self.f_valid), _ptr(self.theta),
+            _ptr(self.s_max), _ptr(self.brk_step), int(self.steps))
         if rc != 0:
             raise MemoryError("oracle velocity-Verlet run failed")
         self.f_valid = True
+        self.steps += int(nsteps)
 
 
 def run_central_difference(grid, mat, bonds: Bonds, u0, v0, dt: float, nsteps: int, b=None):

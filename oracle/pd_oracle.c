@@ -337,6 +337,21 @@ static double norm3(const double v[3]) { return sqrt(v[0] * v[0] + v[1] * v[1] +
 
 /* ---------------------------------------------------------------- PMB force */
 
+/* Per-bond record of a run (diagnostics for the tests, no arithmetic of the
+ * method): for every directed bond, the largest stretch it was evaluated at
+ * while intact (including the evaluation that broke it) and the step at which
+ * it broke (-1: never). */
+typedef struct {
+    double *s_max;       /* [nbonds], or NULL */
+    int32_t *brk_step;   /* [nbonds], or NULL */
+    int64_t step;        /* step number of the current force evaluation */
+} or_track;
+
+static void pmb_force_tracked(const or_grid *g, const or_material *mat,
+                              const int64_t *row_ptr, const int32_t *col,
+                              const double *u, uint8_t *broken, int update_breaking, double *f,
+                              const or_track *tr);
+
 /* Internal force density of the bond-based model, Eq. (3) with Algorithm 1's
  * loop structure and the PMB pair force f = c s (xi + eta)/|xi + eta|:
  *   f_i = sum_{j in B(i), intact} c s_ij M_ij V_j V_ij.
@@ -345,6 +360,32 @@ static double norm3(const double v[3]) { return sqrt(v[0] * v[0] + v[1] * v[1] +
 void or_pmb_force(const or_grid *g, const or_material *mat,
                   const int64_t *row_ptr, const int32_t *col,
                   const double *u, uint8_t *broken, int update_breaking, double *f)
+{
+    pmb_force_tracked(g, mat, row_ptr, col, u, broken, update_breaking, f, NULL);
+}
+
+/* Stretch s = (|xi + eta| - |xi|) / |xi| of every directed bond at u (the same
+ * expression as the force), into s_out[nbonds]. */
+void or_bond_stretch(const or_grid *g, const int64_t *row_ptr, const int32_t *col,
+                     const double *u, double *s_out)
+{
+    int64_t n = npoints(g);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            double xi[3], eta[3], y[3];
+            bond_vectors(g, i, col[k], u, xi, eta);
+            for (int a = 0; a < 3; ++a) y[a] = xi[a] + eta[a];
+            double r0 = norm3(xi), r = norm3(y);
+            s_out[k] = (r - r0) / r0;
+        }
+    }
+}
+
+static void pmb_force_tracked(const or_grid *g, const or_material *mat,
+                              const int64_t *row_ptr, const int32_t *col,
+                              const double *u, uint8_t *broken, int update_breaking, double *f,
+                              const or_track *tr)
 {
     int64_t n = npoints(g);
     int d = g->dim;
@@ -360,8 +401,10 @@ void or_pmb_force(const or_grid *g, const or_material *mat,
             for (int a = 0; a < 3; ++a) y[a] = xi[a] + eta[a];
             double r0 = norm3(xi), r = norm3(y);
             double s = (r - r0) / r0;
+            if (tr && tr->s_max && s > tr->s_max[k]) tr->s_max[k] = s;
             if (update_breaking && mat->s_c > 0.0 && s > mat->s_c) {
                 broken[k] = 1;
+                if (tr && tr->brk_step) tr->brk_step[k] = (int32_t)tr->step;
                 continue;
             }
             double w = c * s * V * volume_factor(g, mat, r0) / r;
@@ -530,19 +573,27 @@ void or_lps_force_scatter(const or_grid *g, const or_material *mat,
 
 /* ------------------------------------------------------------ model dispatch */
 
-static void internal_force(const or_grid *g, const or_material *mat,
-                           const int64_t *row_ptr, const int32_t *col, uint8_t *broken,
-                           int update_breaking, const double *mvol, double *theta,
-                           const double *u, double *f)
+static void internal_force_tracked(const or_grid *g, const or_material *mat,
+                                   const int64_t *row_ptr, const int32_t *col, uint8_t *broken,
+                                   int update_breaking, const double *mvol, double *theta,
+                                   const double *u, double *f, const or_track *tr)
 {
     if (mat->model == OR_PMB) {
-        or_pmb_force(g, mat, row_ptr, col, u, broken, update_breaking, f);
+        pmb_force_tracked(g, mat, row_ptr, col, u, broken, update_breaking, f, tr);
     } else if (mat->model == OR_NP || mat->model == OR_LP) {
         or_np_force(g, mat, row_ptr, col, broken, u, f);
     } else {
         or_lps_dilatation(g, mat, row_ptr, col, broken, mvol, u, theta);
         or_lps_force(g, mat, row_ptr, col, broken, mvol, theta, u, f);
     }
+}
+
+static void internal_force(const or_grid *g, const or_material *mat,
+                           const int64_t *row_ptr, const int32_t *col, uint8_t *broken,
+                           int update_breaking, const double *mvol, double *theta,
+                           const double *u, double *f)
+{
+    internal_force_tracked(g, mat, row_ptr, col, broken, update_breaking, mvol, theta, u, f, NULL);
 }
 
 /* Internal force of either model at u (no breaking update). theta may be NULL
@@ -678,33 +729,46 @@ static void hold_bc_velocity(int64_t n, int d, const uint8_t *bc_kind, const dou
  * prescribed-displacement DOFs hold u = value, v = 0. The force f^{k+1} of one
  * step is the f^k of the next. f (n*dim) holds f^0 on entry when f_valid != 0
  * and the last force on exit; theta (n) is work space for LPS. */
-int or_run_verlet(const or_grid *g, const or_material *mat,
-                  const int64_t *row_ptr, const int32_t *col, uint8_t *broken,
-                  const double *mvol, double *u, double *v, const double *b,
-                  const uint8_t *bc_kind, const double *bc_val,
-                  double dt, int64_t nsteps, double *f, int f_valid, double *theta)
+int or_run_verlet_tracked(const or_grid *g, const or_material *mat,
+                          const int64_t *row_ptr, const int32_t *col, uint8_t *broken,
+                          const double *mvol, double *u, double *v, const double *b,
+                          const uint8_t *bc_kind, const double *bc_val,
+                          double dt, int64_t nsteps, double *f, int f_valid, double *theta,
+                          double *s_max, int32_t *brk_step, int64_t step0)
 {
     int64_t n = npoints(g);
     int d = g->dim;
+    or_track tr = {s_max, brk_step, step0};
     double *u_prev = (double *)malloc((size_t)n * d * sizeof(double));
     if (!u_prev) return -1;
     if (!f_valid)
-        internal_force(g, mat, row_ptr, col, broken, 1, mvol, theta, u, f);
+        internal_force_tracked(g, mat, row_ptr, col, broken, 1, mvol, theta, u, f, &tr);
     double kick = 0.5 * dt / mat->rho;
     for (int64_t k = 0; k < nsteps; ++k) {
+        tr.step = step0 + k + 1;
         memcpy(u_prev, u, (size_t)n * d * sizeof(double));
         for (int64_t q = 0; q < n * d; ++q) {
             v[q] = v[q] + kick * ((b ? b[q] : 0.0) + f[q]);
             u[q] = u[q] + dt * v[q];
         }
         apply_bc(n, d, bc_kind, bc_val, u_prev, u, v, dt);
-        internal_force(g, mat, row_ptr, col, broken, 1, mvol, theta, u, f);
+        internal_force_tracked(g, mat, row_ptr, col, broken, 1, mvol, theta, u, f, &tr);
         for (int64_t q = 0; q < n * d; ++q)
             v[q] = v[q] + kick * ((b ? b[q] : 0.0) + f[q]);
         hold_bc_velocity(n, d, bc_kind, bc_val, v);
     }
     free(u_prev);
     return 0;
+}
+
+int or_run_verlet(const or_grid *g, const or_material *mat,
+                  const int64_t *row_ptr, const int32_t *col, uint8_t *broken,
+                  const double *mvol, double *u, double *v, const double *b,
+                  const uint8_t *bc_kind, const double *bc_val,
+                  double dt, int64_t nsteps, double *f, int f_valid, double *theta)
+{
+    return or_run_verlet_tracked(g, mat, row_ptr, col, broken, mvol, u, v, b, bc_kind, bc_val, dt, nsteps,
+                                 f, f_valid, theta, NULL, NULL, 0);
 }
 
 /* Central difference, Eq. (10): u^{k+1} = 2u^k - u^{k-1} + dt^2/rho (b + f^k),

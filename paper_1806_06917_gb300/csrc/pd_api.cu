@@ -79,6 +79,7 @@ struct pd_sim {
     Geom g;
     Material mat;
     int precision = PD_FP32C;
+    bool state64 = true;        // FP32C: u, v in the FP64 arrays (PD_STATE_F64), else double-float pairs
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -117,8 +118,8 @@ struct pd_sim {
     double4_32a *d4[2] = {nullptr, nullptr};
     float4 *lin_hl = nullptr;
     double4_32a *lin_d4 = nullptr;
-    float4 *vhl = nullptr;          // FP32C velocity, double-float pairs
-    float *bc32 = nullptr;          // FP32C boundary values, (hi, lo) per DOF
+    float4 *vhl = nullptr;          // FP32C double-float state: velocity pairs
+    float *bc32 = nullptr;          // FP32C double-float state: boundary values, (hi, lo) per DOF
     float4 *body32 = nullptr;       // FP32C body force
     uint8_t *bc_kind = nullptr;
     double *bc_val = nullptr, *body = nullptr;
@@ -226,7 +227,11 @@ static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
         set_error("unknown integrator");
         return PD_EINVAL;
     }
-    if (rn->reserved != 0) { set_error("pd_run.reserved must be 0"); return PD_EINVAL; }
+    if (rn->state != PD_STATE_F64 && rn->state != PD_STATE_DF) { set_error("unknown state precision"); return PD_EINVAL; }
+    if (rn->precision == PD_FP64 && rn->state != PD_STATE_F64) {
+        set_error("the FP64 path keeps FP64 state (pd_run.state must be 0)");
+        return PD_EINVAL;
+    }
     return PD_OK;
 }
 
@@ -426,10 +431,13 @@ static int create_impl(pd_sim *s)
                     ta[E * k + 1] = make_float4(kk, kk, ak, offf);
                 }
             } else if (mt.model == PD_MODEL_PMB) {
-                // {dz,dz,|d|^2,|d|^2} {|d|/V_ij x2, |d|^2/V_ij x2} {offset, s_c V_ij, -, -}
+                // {dz,dz,|d|^2,|d|^2} {|d|/V_ij x2, |d|^2/V_ij x2} {offset, s_c V_ij, lo, hi}: between
+                // lo = s_c V_ij (1 - 2^-13) and hi = s_c V_ij (1 + 2^-13) the kernel decides a
+                // bond's breaking from both ends' global state (the same decision in both rows)
                 ta[4 * k + 1] = make_float4((float)d.z, (float)d.z, (float)d2, (float)d2);
                 ta[4 * k + 2] = make_float4((float)(rr / vij), (float)(rr / vij), (float)(d2 / vij), (float)(d2 / vij));
-                ta[4 * k + 3] = make_float4(offf, (float)(mt.s_c * vij), 0.f, 0.f);
+                ta[4 * k + 3] = make_float4(offf, (float)(mt.s_c * vij), (float)(mt.s_c * vij * (1.0 - 0x1p-13)),
+                                            (float)(mt.s_c * vij * (1.0 + 0x1p-13)));
             }
             // LPS: both passes read tb (the dilatation's bond weight |d| V_ij from
             // its {dz,dz,|d|,|d|} and V_ij entries)
@@ -505,8 +513,10 @@ static int create_impl(pd_sim *s)
         ALLOC(s->hl[0], 2 * sizeof(float4) * NS);
         ALLOC(s->hl[1], 2 * sizeof(float4) * NS);
         ALLOC(s->lin_hl, 2 * sizeof(float4) * NS);
-        ALLOC(s->vhl, 2 * sizeof(float4) * NS);
-        ALLOC(s->bc32, 2 * 3 * sizeof(float) * NS);
+        if (!s->state64) {
+            ALLOC(s->vhl, 2 * sizeof(float4) * NS);
+            ALLOC(s->bc32, 2 * 3 * sizeof(float) * NS);
+        }
     }
     ALLOC(s->bc_kind, 3 * NS);
     ALLOC(s->bc_val, 3 * sizeof(double) * NS);
@@ -574,6 +584,7 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.model = s->mat.model;
     a.v_is_half = s->v_is_half;
     a.cd = s->run.integrator == PD_INTEGRATOR_CD && s->u_prev_ok ? 1 : 0;
+    a.state64 = s->precision == PD_FP32C && s->state64 ? 1 : 0;
     a.update_breaking = s->mat.s_c > 0.0 ? 1 : 0;
     a.mode = mode;
     a.vol_corr = s->mat.vol_corr;
@@ -868,6 +879,7 @@ int pd_create(pd_sim **out, const pd_grid *grid, const pd_material *mat, const p
     s->pmat = *mat;
     s->run = *run;
     s->precision = run->precision;
+    s->state64 = run->state == PD_STATE_F64;
     rc = create_impl(s);
     if (rc != PD_OK) {
         pd_destroy(s);
@@ -1089,6 +1101,9 @@ int pd_break_bonds(pd_sim *s, int axis, double pos, const double lo[3], const do
 static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2], bool upload, cudaStream_t st)
 {
     const Geom &g = s->g;
+    // double-float state: the pairs alone; FP64 state: the FP64 arrays (and for
+    // u the staging pair); the FP64 path: the FP64 arrays (and for u the double4 staging)
+    const bool pairs = s->precision == PD_FP32C && !s->state64;
     const bool f32c = s->precision == PD_FP32C;
     const long long n = g.npoints, d = g.dim;
     const size_t row_bytes = sizeof(double) * d;
@@ -1101,8 +1116,8 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
     bool first = true;
     for (int f = 0; f < 2; ++f) {
         if (!host[f]) continue;
-        double *const *slot = f32c ? nullptr : (is_u[f] ? s->u : s->v);
-        float4 *hl = f32c ? (is_u[f] ? s->hl[s->cur] : s->vhl) : nullptr;
+        double *const *slot = pairs ? nullptr : (is_u[f] ? s->u : s->v);
+        float4 *hl = pairs ? (is_u[f] ? s->hl[s->cur] : s->vhl) : (f32c && is_u[f] && upload ? s->hl[s->cur] : nullptr);
         double4_32a *d4 = !f32c && is_u[f] ? s->d4[s->cur] : nullptr;
         for (int k = 0; k < nc; ++k) {
             const long long r0 = std::min(n, k * rows), r1 = std::min(n, r0 + rows);
@@ -1147,7 +1162,7 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     // one pass per field from the uploaded user array: FP32C writes the
     // double-float pairs the kernels read (its FP64 arrays are a view refreshed
     // on demand), FP64 writes its SoA arrays and the double4 staging
-    const bool f32c = s->precision == PD_FP32C;
+    const bool f32c = s->precision == PD_FP32C, pairs = f32c && !s->state64;
     const double *src = nullptr;
     // host arrays: both fields in chunks through the staging buffer, copies
     // overlapping the scatters of the chunks before them
@@ -1159,22 +1174,23 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     }
     if (u && !host_u) {
         if ((rc = user_source(s, u, &src, st)) != PD_OK) return rc;
-        rc = scatter_stage(s->g, s->user_of_slot, src, f32c ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
+        rc = scatter_stage(s->g, s->user_of_slot, src, pairs ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
                            f32c ? nullptr : s->d4[s->cur], st);
         if (rc != PD_OK) return rc;
     }
     if (v && !host_v) {
         if ((rc = user_source(s, v, &src, st)) != PD_OK) return rc;
-        rc = scatter_stage(s->g, s->user_of_slot, src, f32c ? nullptr : s->v, f32c ? s->vhl : nullptr, nullptr, st);
+        rc = scatter_stage(s->g, s->user_of_slot, src, pairs ? nullptr : s->v, pairs ? s->vhl : nullptr, nullptr, st);
         if (rc != PD_OK) return rc;
     }
     return PD_OK;
 }
 
-// FP32C keeps u and v as double-float pairs; refresh the FP64 SoA copies.
+// FP32C with double-float state keeps u and v as pairs; refresh the FP64 SoA
+// copies (with FP64 state those arrays are the state itself).
 static int unpack_state(pd_sim *s, cudaStream_t st, bool want_u = true, bool want_v = true)
 {
-    if (s->precision != PD_FP32C) return PD_OK;
+    if (s->precision != PD_FP32C || s->state64) return PD_OK;
     int rc = PD_OK;
     if (want_u && (rc = unpack_pairs(s->g, s->hl[s->cur], s->u, st)) != PD_OK) return rc;
     if (want_v && (rc = unpack_pairs(s->g, s->vhl, s->v, st)) != PD_OK) return rc;
@@ -1190,10 +1206,10 @@ int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
     if (v && (rc = finalize(s, st)) != PD_OK) return rc;
     // one pass per field into user order: from the double-float pairs (FP32C)
     // or the FP64 arrays, then one copy to the caller
-    const bool f32c = s->precision == PD_FP32C;
+    const bool pairs = s->precision == PD_FP32C && !s->state64;
     const bool host_u = u && !direct_ptr(s, u), host_v = v && !direct_ptr(s, v);
-    if (u && !host_u && (rc = to_user(s, f32c ? s->hl[s->cur] : nullptr, s->u, u, st)) != PD_OK) return rc;
-    if (v && !host_v && (rc = to_user(s, f32c ? s->vhl : nullptr, s->v, v, st)) != PD_OK) return rc;
+    if (u && !host_u && (rc = to_user(s, pairs ? s->hl[s->cur] : nullptr, s->u, u, st)) != PD_OK) return rc;
+    if (v && !host_v && (rc = to_user(s, pairs ? s->vhl : nullptr, s->v, v, st)) != PD_OK) return rc;
     if (host_u || host_v) {
         // gathers in chunks on st, each chunk's copy out on copy_stream behind it
         const double *hu[2] = {host_u ? u : nullptr, host_v ? v : nullptr};
@@ -1227,8 +1243,7 @@ int pd_set_bc(pd_sim *s, const uint8_t *kind, const double *value, void *stream)
     double *vals[3] = {s->bc_val, s->bc_val + NS, s->bc_val + 2 * NS};
     rc = user_to_slots(s, value, vals, st);
     if (rc != PD_OK) return rc;
-    if (s->precision == PD_FP32C && (rc = pack_dof_pairs(3 * (long long)NS, s->bc_val, s->bc32, st)) != PD_OK)
-        return rc;
+    if (s->bc32 && (rc = pack_dof_pairs(3 * (long long)NS, s->bc_val, s->bc32, st)) != PD_OK) return rc;
     int herr = 0;
     PD_CUDA(cudaMemcpyAsync(&herr, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PD_CUDA(cudaStreamSynchronize(st));
@@ -1323,6 +1338,55 @@ int pd_dilatation(pd_sim *s, const double *u, double *theta_out, void *stream)
     PD_CUDA(cudaGetLastError());
     PD_CUDA(cudaMemcpyAsync(theta_out, s->io, sizeof(double) * s->g.npoints, cudaMemcpyDefault, st));
     return PD_OK;
+}
+
+int pd_step_explicit_timed(pd_sim *s, int64_t nsteps, double pass_ms[2], void *stream)
+{
+    CHECK_BUILT(s);
+    if (nsteps < 0 || !pass_ms) { set_error("nsteps must be >= 0 and pass_ms non-null"); return PD_EINVAL; }
+    cudaStream_t st = pick(s, stream);
+    pass_ms[0] = pass_ms[1] = 0.0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k)
+        if (cudaEventCreate(&ev[k]) != cudaSuccess) {
+            for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
+            return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+        }
+    const bool lps = s->mat.model == PD_MODEL_LPS;
+    int rc = PD_OK;
+    for (int64_t n = 0; n < nsteps && rc == PD_OK; ++n) {
+        TileArgs a = make_args(s, MODE_STEP, s->hl[s->cur], s->d4[s->cur]);
+        a.update_breaking = s->mat.s_c > 0.0;
+        cudaError_t e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess) {
+            if (lps) {
+                rc = launch_lps_args(a, s->precision, 1, st);
+                if (rc == PD_OK) e = cudaEventRecord(ev[1], st);
+                if (rc == PD_OK && e == cudaSuccess) rc = launch_lps_args(a, s->precision, 0, st);
+            } else {
+                rc = launch_pmb_args(a, s->precision, st);
+            }
+        }
+        if (rc == PD_OK && e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+        if (rc == PD_OK && e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        if (rc == PD_OK && e != cudaSuccess) rc = cuda_fail(e, "step timing events");
+        if (rc != PD_OK) break;
+        float t0 = 0.f, t1 = 0.f;
+        if (lps) {
+            cudaEventElapsedTime(&t0, ev[0], ev[1]);
+            cudaEventElapsedTime(&t1, ev[1], ev[2]);
+        } else {
+            cudaEventElapsedTime(&t0, ev[0], ev[2]);
+        }
+        pass_ms[0] += t0;
+        pass_ms[1] += t1;
+        s->cur ^= 1;
+        s->v_is_half = 1;
+        s->u_prev_ok = true;
+        s->step += 1;
+    }
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    return rc;
 }
 
 int pd_step_explicit(pd_sim *s, int64_t nsteps, void *stream)

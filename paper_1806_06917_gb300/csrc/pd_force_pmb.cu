@@ -20,21 +20,109 @@ namespace pdk {
 // FP32C. Thread t owns the point pair (A, B) of pd_pair.cuh and evaluates both
 // in f32x2 arithmetic; the stencil loop is rolled over a shared-memory copy of a
 // host-built table of pre-splatted constants, per entry
-//   {dx, dx, dy, dy}, {dz, dz, |d|^2, |d|^2}, {R, R, C, C}, {offset, s_c V_ij, -, -}
+//   {dx, dx, dy, dy}, {dz, dz, |d|^2, |d|^2}, {R, R, C, C}, {offset, s_c V_ij, lo, hi}
 // with R = |d| / V_ij and C = |d|^2 / V_ij. Per bond (lattice units, e = eta):
 //   num = e.(e + 2d) = 2 d.e + e.e,   q = |y|^2 = |d|^2 + num,   r = sqrt(q)
 //   w   = s V_ij / r = num / (R q + C r),   F += w y,
 // since s = num / (|d| (r + |d|)) and (R r + C) r = R q + C r.
 //
+// Breaking decision of a bond near the threshold, the same from both of its
+// ends. The bond loop forms s from displacements staged relative to each
+// tile's reference, so the two rows of a bond that crosses a tile boundary
+// round it differently and could decide differently when s is within rounding
+// of s_c. A bond whose staged s V_ij lies within 2^-13 relative of s_c V_ij is
+// therefore decided again here from the global staging pairs of its two
+// points: eta = ((hi_j - hi_i) + (lo_j - lo_i)) / h changes sign exactly under
+// (i, j) -> (j, i), as does d, so every product below keeps its value and s
+// comes out bitwise the same from either end (explicit round-to-nearest
+// operations: no contraction choice of the compiler enters). Rare: only such
+// bonds take this path, with four global loads each.
+__device__ __noinline__ bool canon_break32(const TileArgs *ap, const int *s_nbr, int si, int p, int bj, float dx,
+                                           float dy, float dz)
+{
+    const TileArgs &a = *ap;
+    const int tile = blockIdx.x;
+    const int4 org = __ldg(&a.tile_org[tile]);
+    const PairBox pb = pair_box(a.g);
+    int sj;
+    if (box_mapped(a, org)) {
+        int sA, sB;
+        map_slots(a, s_nbr, __ldg(&a.box_map[bj]), sA, sB);
+        sj = p ? sB : sA;
+    } else {
+        int cA[3], cB[3];
+        pair_coords(a.g, pb, org, bj, cA, cB);
+        sj = slot_of(a, s_nbr, org, p ? cB : cA);
+    }
+    if (sj < 0) return false;
+    const float4 hi = __ldg(&a.src_hl[2 * si]), li = __ldg(&a.src_hl[2 * si + 1]);
+    const float4 hj = __ldg(&a.src_hl[2 * sj]), lj = __ldg(&a.src_hl[2 * sj + 1]);
+    const float ih = (float)a.inv_h;
+    const float ex = __fmul_rn(__fadd_rn(__fsub_rn(hj.x, hi.x), __fsub_rn(lj.x, li.x)), ih);
+    const float ey = __fmul_rn(__fadd_rn(__fsub_rn(hj.y, hi.y), __fsub_rn(lj.y, li.y)), ih);
+    const float ez = __fmul_rn(__fadd_rn(__fsub_rn(hj.z, hi.z), __fsub_rn(lj.z, li.z)), ih);
+    // num = e.(e + 2d), as e.((e + d) + d)
+    float num = __fmul_rn(ex, __fadd_rn(__fadd_rn(ex, dx), dx));
+    num = __fmaf_rn(ey, __fadd_rn(__fadd_rn(ey, dy), dy), num);
+    num = __fmaf_rn(ez, __fadd_rn(__fadd_rn(ez, dz), dz), num);
+    const float d2 = dx * dx + dy * dy + dz * dz;             // exact (small integers)
+    const float r0 = __fsqrt_rn(d2);
+    const float r = __fsqrt_rn(__fadd_rn(num, d2));
+    const float s = __fdiv_rn(num, __fmul_rn(r0, __fadd_rn(r, r0)));
+    return s > (float)a.s_c;
+}
+
+// The force of one bond on one point of the pair (lane p): the arithmetic of
+// pmb_word in scalar form (each f32x2 operation is two IEEE operations, the
+// special-function approximations are the same instructions), for the bonds
+// that pmb_word left to canon_break32 and that stay intact.
+template <int DIM>
+__device__ __forceinline__ void pmb_bond1(const float4 *te, const float4 *P4, const float2 *P2, int bi, int p,
+                                          float2 nux, float2 nuy, float2 nuz, float2 &Fx, float2 &Fy, float2 &Fz)
+{
+    const float4 ta = te[0], tb = te[1], tc = te[2], td = te[3];
+    const int off = __float_as_int(td.x);
+    const float4 r4 = P4[bi + off];
+    const float ex = (p ? r4.y : r4.x) + (p ? nux.y : nux.x), ey = (p ? r4.w : r4.z) + (p ? nuy.y : nuy.x);
+    const float yx = ex + ta.x, yy = ey + ta.z;
+    float num = ex * (yx + ta.x);
+    num = fmaf(ey, yy + ta.z, num);
+    float yz = 0.f;
+    if (DIM == 3) {
+        const float2 z2 = P2[bi + off];
+        const float ez = (p ? z2.y : z2.x) + (p ? nuz.y : nuz.x);
+        yz = ez + tb.x;
+        num = fmaf(ez, yz + tb.x, num);
+    }
+    const float qq = num + tb.z;
+    const float rr = sfu_sqrt(qq);
+    const float den = fmaf(qq, tc.x, rr * tc.z);
+    const float wgt = num * sfu_rcp(den);
+    if (p) {
+        Fx.y = fmaf(wgt, yx, Fx.y);
+        Fy.y = fmaf(wgt, yy, Fy.y);
+        if (DIM == 3) Fz.y = fmaf(wgt, yz, Fz.y);
+    } else {
+        Fx.x = fmaf(wgt, yx, Fx.x);
+        Fy.x = fmaf(wgt, yy, Fy.x);
+        if (DIM == 3) Fz.x = fmaf(wgt, yz, Fz.x);
+    }
+}
+
 // One 32-bond word of the stencil at a time. MASKED = false is the path for
 // words whose bonds all exist and are intact for every point of the warp (the
 // common case: the warp then skips every per-bond mask operation); with
-// breaking on, it only reports whether some bond crossed s_c, and the warp then
+// breaking on, it only reports whether some bond came near s_c, and the warp then
 // redoes the word on the masked path, which breaks the bond before it counts.
+// Table thresholds: td.z = s_c V_ij (1 - 2^-13), td.w = s_c V_ij (1 + 2^-13).
+// The masked path breaks the bonds above td.w and only marks those between
+// the two (near0 / near1, contributing nothing); the caller decides the marked
+// ones with canon_break32 and adds those that stay intact (pmb_bond1).
 template <int DIM, bool MASKED, bool BRK>
 __device__ __forceinline__ bool pmb_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
                                          float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1,
-                                         uint32_t &k0, uint32_t &k1, float2 &Fx, float2 &Fy, float2 &Fz)
+                                         uint32_t &k0, uint32_t &k1, uint32_t &near0, uint32_t &near1,
+                                         float2 &Fx, float2 &Fy, float2 &Fz)
 {
     bool anybrk = false;
 PD_PRAGMA_UNROLL(PD_UNROLL)
@@ -60,19 +148,22 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
             const bool in0 = (c0 >> b) & 1u, in1 = (c1 >> b) & 1u;
             bool ok0 = in0, ok1 = in1;
             if (BRK) {
-                // s > s_c, tested as s V_ij = w |y| > s_c V_ij (td.y)
+                // s > s_c, tested as s V_ij = w |y| > s_c V_ij; near s_c: marked for canon_break32
                 const float2 sv = f2mul(wgt, rr);
-                const bool b0 = in0 && sv.x > td.y, b1 = in1 && sv.y > td.y;
+                const bool b0 = in0 && sv.x > td.w, b1 = in1 && sv.y > td.w;
+                const bool n0 = in0 && !b0 && sv.x > td.z, n1 = in1 && !b1 && sv.y > td.z;
                 if (b0) k0 &= ~(1u << b);
                 if (b1) k1 &= ~(1u << b);
-                ok0 = in0 && !b0;
-                ok1 = in1 && !b1;
+                if (n0) near0 |= 1u << b;
+                if (n1) near1 |= 1u << b;
+                ok0 = in0 && !b0 && !n0;
+                ok1 = in1 && !b1 && !n1;
             }
             wgt.x = ok0 ? wgt.x : 0.f;
             wgt.y = ok1 ? wgt.y : 0.f;
         } else if (BRK) {
             const float2 sv = f2mul(wgt, rr);
-            anybrk = anybrk || sv.x > td.y || sv.y > td.y;
+            anybrk = anybrk || sv.x > td.z || sv.y > td.z;
         }
         Fx = f2fma(wgt, yx, Fx);
         Fy = f2fma(wgt, yy, Fy);
@@ -111,7 +202,8 @@ __device__ __forceinline__ void pair_split_sum(const TileArgs &a, float2 *red, i
 // where one CTA's halo box and table fill the shared memory, so that more warps
 // run per SM; SPLIT = false is the one-thread-per-pair kernel.
 template <int DIM, bool BRK, bool SPLIT>
-__global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) pmb_fast(const TileArgs a)
+__global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS)
+    pmb_fast(const __grid_constant__ TileArgs a)
 {
     const Geom &g = a.g;
     const PairBox pb = pair_box(g);
@@ -181,12 +273,12 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
             const int nb = min(32, S - 32 * w);
             const uint32_t full = nb == 32 ? 0xffffffffu : ((1u << nb) - 1u);
             const float4 *tw = tab + 4 * 32 * w;
-            uint32_t k0 = m0, k1 = m1;
+            uint32_t k0 = m0, k1 = m1, near0 = 0u, near1 = 0u;
             bool masked = !__all_sync(0xffffffffu, m0 == full && m1 == full);
             if (!masked) {
                 const float2 sx = Fx, sy = Fy, sz = Fz;
                 const bool brk = pmb_word<DIM, false, BRK>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, k0, k1,
-                                                           Fx, Fy, Fz);
+                                                           near0, near1, Fx, Fy, Fz);
                 if (BRK && __any_sync(0xffffffffu, brk)) {
                     Fx = sx;
                     Fy = sy;
@@ -195,7 +287,24 @@ __global__ void __launch_bounds__(SPLIT ? 1024 : 256, SPLIT ? 1 : PD_MINBLOCKS) 
                 }
             }
             if (masked) {
-                pmb_word<DIM, true, BRK>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, k0, k1, Fx, Fy, Fz);
+                pmb_word<DIM, true, BRK>(tw, nb, P4, P2, q.bi, nux, nuy, nuz, m0, m1, k0, k1, near0, near1, Fx, Fy,
+                                         Fz);
+                if (BRK && (near0 | near1) != 0u) {
+                    // the marked bonds: decided from both ends' global state; those
+                    // that stay intact are added after the rest of the word
+                    for (int p = 0; p < 2; ++p)
+                        for (uint32_t nm = p ? near1 : near0; nm; nm &= nm - 1u) {
+                            const int b = __ffs(nm) - 1;
+                            const float4 ta = tw[4 * b], tb = tw[4 * b + 1], td = tw[4 * b + 3];
+                            if (canon_break32(&a, s_nbr, q.slot[p], p, q.bi + __float_as_int(td.x), ta.x, ta.z,
+                                              tb.x)) {
+                                if (p) k1 &= ~(1u << b);
+                                else k0 &= ~(1u << b);
+                            } else {
+                                pmb_bond1<DIM>(tw + 4 * b, P4, P2, q.bi, p, nux, nuy, nuz, Fx, Fy, Fz);
+                            }
+                        }
+                }
                 if (BRK) {
                     const size_t mo = (size_t)w * g.nslots;
                     if (q.act[0] && k0 != m0) a.mask[mo + q.slot[0]] = k0;
@@ -442,6 +551,22 @@ __global__ void __launch_bounds__(1024, 1) np_fast2(const TileArgs a)
     }
 }
 
+// The FP64 stretch of bond (si, sj) with lattice offset d from the global FP64
+// staging (the FP64 path's u), bitwise the same from both ends of the bond.
+__device__ __forceinline__ double canon_stretch64(const TileArgs &a, int si, int sj, int4 d)
+{
+    const double4_32a ui = a.src_d4[si], uj = a.src_d4[sj];
+    const double ex = __dmul_rn(__dsub_rn(uj.x, ui.x), a.inv_h);
+    const double ey = __dmul_rn(__dsub_rn(uj.y, ui.y), a.inv_h);
+    const double ez = __dmul_rn(__dsub_rn(uj.z, ui.z), a.inv_h);
+    const double dx = d.x, dy = d.y, dz = d.z, d2 = d.w;
+    double num = __dmul_rn(ex, __dadd_rn(__dadd_rn(ex, dx), dx));
+    num = __fma_rn(ey, __dadd_rn(__dadd_rn(ey, dy), dy), num);
+    num = __fma_rn(ez, __dadd_rn(__dadd_rn(ez, dz), dz), num);
+    const double r0 = __dsqrt_rn(d2), r = __dsqrt_rn(__dadd_rn(num, d2));
+    return __ddiv_rn(num, __dmul_rn(r0, __dadd_rn(r, r0)));
+}
+
 // Runtime stencil (any horizon), one point per thread. R = float (FP32C) or
 // double (FP64). Stencil entries come from a.stencil; box dims from a.g.m.
 template <class R>
@@ -506,7 +631,15 @@ __global__ void __launch_bounds__(256) pmb_generic(const TileArgs a)
                 const R r0 = (R)__ldg(&a.stencil_r0[32 * w + b]);
                 const R rs = prsqrt1(q);
                 const R s = pdiv1(num, r0 * (q * rs + r0));
-                if (brk_on && s > s_c) {
+                bool brk = brk_on && s > s_c;
+                // near s_c (2^-30 relative), decided from both points' global state
+                // in an order that is bitwise symmetric in (i, j), as in canon_break32
+                if (brk_on && fabs((double)s - a.s_c) <= 0x1p-30 * a.s_c) {
+                    const int sj = slot_at(g, a.tile_lut, org.x + lx + d.x, org.y + ly + d.y,
+                                           g.dim == 3 ? org.z + lz + d.z : 0);
+                    brk = sj >= 0 && canon_stretch64(a, slot, sj, d) > a.s_c;
+                }
+                if (brk) {
                     nword &= ~(1u << b);
                     continue;
                 }

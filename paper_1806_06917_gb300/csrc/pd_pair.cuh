@@ -10,12 +10,13 @@
 // bond then loads its two neighbours with one 16-byte and one 8-byte shared
 // load straight into f32x2 register pairs.
 //
-// State. In the FP32C mode the integrator state is held as double-float
-// numbers (hi + lo, two FP32 values, about 48 significant bits): GB300 runs FP64
-// at 1/64 of the FP32 rate, and an FP64 update of u and v costs more than the
-// bond loop of a small tile. The sums are Knuth's two-sum and Dekker's
-// product with an FMA, which keep the accumulated rounding of a 1000-step run
-// near 1e-12 relative, far below the 1e-4 tolerance on u.
+// State. In the FP32C mode the integrator state u, v is FP64 (PD_STATE_F64:
+// two FP64 additions and one FMA per component and step, everything else of the
+// update on the integer and FP32 pipes, since GB300 runs FP64 at 1/64 of the
+// FP32 rate) or double-float numbers (PD_STATE_DF: hi + lo, two FP32 values,
+// about 48 significant bits, Knuth's two-sum and Dekker's product with an FMA,
+// no FP64 instruction at all). Either keeps the accumulated rounding of a
+// 1000-step run near 1e-12 relative, far below the 1e-4 tolerance on u.
 #pragma once
 
 #include "pd_tile.cuh"
@@ -362,6 +363,115 @@ __device__ __forceinline__ PairPts pair_points(const Geom &g, const PairBox &pb,
 
 // ---------------------------------------------------------- update (FP32C)
 
+// FP32 -> FP64 from the bits, on the integer pipes (exact, as the conversion
+// instruction; FP32 denormals, which the FP32 arithmetic flushes, give zero).
+__device__ __forceinline__ double f2d_bits(float x)
+{
+    const unsigned X = __float_as_uint(x);
+    const unsigned e = (X >> 23) & 0xffu;
+    const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned hi = (X & 0x80000000u) | (e ? (ed << 20) | ((X >> 3) & 0xfffffu) : 0u);
+    const unsigned lo = e ? X << 29 : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// u = hi + lo to about 47 bits, from the bits of u on the integer and FP32
+// pipes: hi is u with its 29 low mantissa bits cut off (exactly an FP32
+// value, same sign), lo the cut-off part, rest * 2^(e - 1075), rounded once to
+// FP32 (its two 16-bit halves convert exactly through the 2^23 magic number).
+// |u| < 2^-126 stages as 0; |u| >= 2^116 (never a displacement) takes the
+// conversion instruction.
+__device__ __forceinline__ void split_bits(double u, float &hi, float &lo)
+{
+    const unsigned H = (unsigned)__double2hiint(u), Lw = (unsigned)__double2loint(u);
+    const unsigned sign = H & 0x80000000u;
+    const int e = (int)((H >> 20) & 0x7ffu);
+    const unsigned rest = Lw & 0x1fffffffu;
+    const float r1 = __uint_as_float(0x4b000000u | (rest >> 16)) - 8388608.f;
+    const float r0 = __uint_as_float(0x4b000000u | (rest & 0xffffu)) - 8388608.f;
+    const float fr = fmaf(r1, 65536.f, r0);
+    // 2^(e - 1075) as 2^(e - 1011) * 2^-64, both normal FP32 numbers for 897 <= e <= 1138
+    const float s1 = __uint_as_float((unsigned)(e - 884) << 23);
+    const float l = fr * s1 * 5.42101086242752217e-20f;
+    if (e < 897) {
+        hi = 0.f;
+        lo = 0.f;
+    } else if (e > 1138) {
+        hi = __double2float_rn(u);
+        lo = 0.f;
+    } else {
+        hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((H & 0xfffffu) << 3) | (Lw >> 29));
+        lo = sign ? -l : l;
+    }
+}
+
+// The fused update with FP64 integrator state (PD_STATE_F64): u and v live in
+// the FP64 component arrays a.u[c], a.v[c]. The kick dt/2 (f + b)/rho is formed
+// in FP32 from the FP32 force, as in the double-float form, and added to v in
+// FP64 (two additions for the two half-kicks of Eqs. (9) and (7), so that a
+// half step completed by MODE_FINALIZE rounds as in one kernel); the drift
+// u += dt v is one FP64 FMA; the next staging pair is u split into FP32 hi + lo
+// (split_bits). Central difference (Eq. (10)) reads u^{k-1} from the staging
+// pair it overwrites. One point at a time, its loads issued together (the
+// FP64 values of both points at once would not fit beside the bond loop's
+// registers).
+__device__ __forceinline__ void point_update64(const TileArgs &a, int slot, const float F[3], int dim)
+{
+    const int ns = a.g.nslots;
+    const bool step = a.mode == MODE_STEP, cd = step && a.cd;
+    double v[3], u[3];
+    int kind[3];
+    const float4 bb = a.use_body ? a.body32[slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 uph = make_float4(0.f, 0.f, 0.f, 0.f), upl = uph;
+    if (cd) {
+        uph = a.dst_hl[2 * slot];
+        upl = a.dst_hl[2 * slot + 1];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = c < dim ? a.v[c][slot] : 0.0;
+        u[c] = c < dim && step ? a.u[c][slot] : 0.0;
+        kind[c] = c < dim ? a.bc_kind[c * ns + slot] : 0;
+    }
+    const float bcomp[3] = {bb.x, bb.y, bb.z};
+    const float uphc[3] = {uph.x, uph.y, uph.z}, uplc[3] = {upl.x, upl.y, upl.z};
+    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c >= dim) break;
+        const float kick = fmaf(a.kF, F[c], a.kB * bcomp[c]);
+        const double kd = f2d_bits(kick);
+        double vc = v[c], uc = u[c];
+        if (a.v_is_half) vc += kd;
+        if (step) {
+            vc += kd;
+            if (kind[c] == PD_BC_VELOCITY) {
+                vc = a.bc_val[c * ns + slot];
+                uc = fma(a.dt, vc, uc);
+            } else if (kind[c] == PD_BC_DISPLACEMENT) {
+                vc = 0.0;
+                uc = a.bc_val[c * ns + slot];
+            } else if (cd) {
+                // u + (u - u^{k-1}) + dt^2 a^k, dt^2 a^k = 2 dt kick
+                const double up = f2d_bits(uphc[c]) + f2d_bits(uplc[c]);
+                uc = fma(a.dt, f2d_bits(2.f * kick), uc + (uc - up));
+            } else {
+                uc = fma(a.dt, vc, uc);
+            }
+            a.u[c][slot] = uc;
+            split_bits(uc, hi[c], lo[c]);
+        } else {
+            if (kind[c] == PD_BC_VELOCITY) vc = a.bc_val[c * ns + slot];
+            else if (kind[c] == PD_BC_DISPLACEMENT) vc = 0.0;
+        }
+        a.v[c][slot] = vc;
+    }
+    if (step) {
+        a.dst_hl[2 * slot] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        a.dst_hl[2 * slot + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    }
+}
+
 // Velocity-Verlet update of the thread's two points in double-float arithmetic
 // from their forces F (FP32, in the kernel's units): the kick is kF * F (+ kB * b)
 // with kF = dt/2 * (force scale)/rho and kB = dt/2/rho. MODE_STEP applies the
@@ -384,6 +494,11 @@ __device__ __forceinline__ void pair_epilogue2(const TileArgs &a, const PairPts 
             const float *F = p ? FB : FA;
             for (int c = 0; c < dim; ++c) a.f[c][q.slot[p]] = a.fscale * (double)F[c];
         }
+        return;
+    }
+    if (a.state64) {
+        if (q.act[0]) point_update64(a, q.slot[0], FA, dim);
+        if (q.act[1]) point_update64(a, q.slot[1], FB, dim);
         return;
     }
     float4 vh[2], vl[2], uh[2], ul[2], bb[2];

@@ -349,6 +349,7 @@ struct TileArgs {
     int v_is_half, update_breaking, mode, vol_corr, use_body, adjoint;
     int cd;                     // MODE_STEP: central-difference drift from u^{k-1} at dst
     int split;                  // fused bond kernels: threads per point pair (1, 2 or 4)
+    int state64;                // FP32C fused update: u, v in the FP64 arrays u[], v[] (else double-float pairs)
 };
 
 // --------------------------------------------------------------- staging

@@ -28,6 +28,7 @@ PD_KRYLOV_GMRES, PD_KRYLOV_CG = 0, 1
 PD_TANGENT_CACHED, PD_TANGENT_JVP = 0, 1
 PD_PRECOND_NONE, PD_PRECOND_BLOCK_JACOBI = 0, 1
 PD_INTEGRATOR_VERLET, PD_INTEGRATOR_CD = 0, 1
+PD_STATE_F64, PD_STATE_DF = 0, 1          # pd_run.state of a PD_FP32C simulation
 PD_REQ_QUEUED, PD_REQ_RUNNING, PD_REQ_DONE, PD_REQ_CANCELLED, PD_REQ_FAILED = 0, 1, 2, 3, 4
 
 if not os.path.exists(LIB_PATH):
@@ -50,7 +51,7 @@ class pd_material(ctypes.Structure):
 
 class pd_run(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dt_factor", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("tile_log2", ctypes.c_int32), ("integrator", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_log2", ctypes.c_int32), ("integrator", ctypes.c_int32), ("state", ctypes.c_int32)]
 
 
 class pd_newton_opts(ctypes.Structure):
@@ -109,6 +110,7 @@ _SIGS = {
     "pd_force": [_P, _P, _P, ctypes.c_uint, _P],
     "pd_dilatation": [_P, _P, _P, _P],
     "pd_step_explicit": [_P, ctypes.c_int64, _P],
+    "pd_step_explicit_timed": [_P, ctypes.c_int64, _P, _P],
     "pd_tune_tile": [ctypes.POINTER(pd_grid), ctypes.POINTER(pd_material), ctypes.POINTER(pd_run), ctypes.c_int32,
                      ctypes.POINTER(ctypes.c_int32), _P],
     "pd_jvp": [_P, _P, _P, _P, ctypes.c_uint, _P],
@@ -315,6 +317,14 @@ def pd_step_explicit(sim: Sim, nsteps: int, stream=None) -> None:
     _check(_lib.pd_step_explicit(sim.h, int(nsteps), _stream(stream)))
 
 
+def pd_step_explicit_timed(sim: Sim, nsteps: int, stream=None):
+    """The same steps, one launch at a time with CUDA events around each pass;
+    returns the summed device milliseconds of (pass 0, pass 1)."""
+    ms = (ctypes.c_double * 2)()
+    _check(_lib.pd_step_explicit_timed(sim.h, int(nsteps), ms, _stream(stream)))
+    return float(ms[0]), float(ms[1])
+
+
 def pd_jvp(sim: Sim, w, u_lin=None, out=None, flags: int = 0, stream=None):
     out = np.empty((sim.npoints, sim.dim)) if out is None else out
     _check(_lib.pd_jvp(sim.h, _buf(u_lin, np.float64, sim.nvec, "u_lin"), _buf(w, np.float64, sim.nvec, "w"),
@@ -459,7 +469,7 @@ def pd_sum_noalloc(x, scale=1.0, out=None, stream=None):
 # ------------------------------------------------------------ conveniences
 
 def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=0.5, tile_log2=0,
-             integrator=PD_INTEGRATOR_VERLET):
+             integrator=PD_INTEGRATOR_VERLET, state=0):
     """pd_grid / pd_material / pd_run from the plain workload descriptions."""
     g = pd_grid()
     g.dim = workload_grid.dim
@@ -478,5 +488,5 @@ def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=
     m.psi_beta = getattr(workload_mat, "psi_beta", 1.0)
     r = pd_run()
     r.dt, r.dt_factor, r.precision, r.tile_log2 = dt, dt_factor, precision, tile_log2
-    r.integrator, r.reserved = integrator, 0
+    r.integrator, r.state = integrator, state
     return g, m, r

@@ -9,15 +9,42 @@ import bench  # noqa: E402
 from paper_1806_06917_gb300 import workloads as W  # noqa: E402
 
 
+def _sources_sha(files):
+    import hashlib
+    import os
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(bench.ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def test_traffic_lookup_is_keyed_by_kernel_tile_and_sources(monkeypatch):
-    assert bench.ncu_traffic("pmb3", 7) is None              # no capture at that tile
+    files = ["paper_1806_06917_gb300/csrc/pd_force_lps.cu"] + bench._KERNEL_COMMON
+    rec = {"bytes": 123456, "sha": _sources_sha(files), "sources": files, "profile": "profiles/x.md"}
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("lps_force", 9), rec)
+    assert bench.ncu_traffic("lps_force", 9) == 123456
+    assert bench.ncu_traffic("lps_force", 7) is None           # no capture at that tile
     assert bench.ncu_traffic("no-such-kernel", 9) is None
-    rec = dict(bench.NCU_TRAFFIC[("pmb3", 9)])
-    rec["sha"] = "0" * 16                                      # sources changed since the capture
-    monkeypatch.setitem(bench.NCU_TRAFFIC, ("pmb3", 9), rec)
-    assert bench.ncu_traffic("pmb3", 9) is None
-    for key, rec in bench.NCU_TRAFFIC.items():
-        assert rec["bytes"] > 0 and len(rec["sha"]) == 16 and rec["profile"].startswith("profiles/")
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("lps_force", 9), dict(rec, sha="0" * 16))
+    assert bench.ncu_traffic("lps_force", 9) is None            # sources changed since the capture
+    for key, r in bench.NCU_TRAFFIC.items():
+        assert r["bytes"] > 0 and len(r["sha"]) == 16 and r["profile"].startswith("profiles/")
+
+
+def test_roofline_of_the_lps_step():
+    """The dominant launch is the force pass; its bytes are 4 B/bond + 120
+    B/point, the step's 8 B/bond + 164 B/point; fractions against the peak."""
+    wl = W.block3d_lps(nside=8)
+    nb, npts = 10000, wl.grid.npoints
+    r = bench.roofline_of("lps", wl, nb, [0.001, 0.002], 0.0031, 9, {"hbm_gbs": 5000.0})
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 5000.0
+    want = (4.0 * nb + 120.0 * npts) / 2e-6 / 1e9
+    assert abs(r["achieved"] - want) <= 1e-9 * want and abs(r["frac"] - want / 5000.0) <= 1e-12
+    assert abs(r["step"]["bytes"] - (8.0 * nb + 164.0 * npts)) < 1e-6
+    assert set(r["passes"]) == {"lps_dil", "lps_force"}
+    r2 = bench.roofline_of("pmb3", W.block3d_pulse(nside=8), nb, [0.001, 0.0], 0.001, 9, None)
+    assert r2["peak"] == bench.FALLBACK_HBM_GBS and "fallback" in r2["peak_source"]
 
 
 def test_oracle_side_rates_on_tiny_samples():

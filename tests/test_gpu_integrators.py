@@ -216,7 +216,7 @@ def test_unknown_integrator_is_rejected(pd):
             pd.pd_create(gd, md, rd)
         assert e.value.code == pd.PD_EINVAL
     gd, md, rd = pd.describe(g, mat)
-    rd.reserved = 1
+    rd.state = 2
     with pytest.raises(pd.PdError):
         pd.pd_create(gd, md, rd)
 

@@ -553,3 +553,49 @@ def test_uniform_body_force_gives_uniform_acceleration(dim):
         assert np.all(st.f == 0.0)
     ucd = O.run_central_difference(g, mat, b, z, z, dt, 20, b=body)
     np.testing.assert_allclose(ucd, np.tile(0.5 * a * (20 * dt) ** 2, (g.npoints, 1)), rtol=1e-12)
+
+
+# ------------------------------------------------------ bond-state records
+
+def test_run_records_break_steps_and_peak_stretches():
+    """The per-bond records of a tracked run (the diagnostics that the GPU
+    parity tests use for the near-s_c rule): tracking changes nothing in the
+    run; a bond is broken exactly when its record has a break step, its peak
+    stretch then exceeds s_c and otherwise does not; re-running an untracked
+    state to one step before / at the recorded step finds it intact / broken;
+    and the stretch of a bond is the same from both of its ends."""
+    wl = W.block3d_pulse(nside=12, steps=30, s_c=5e-5)
+    b_t = O.neighbors(wl.grid)
+    O.break_notch(wl.grid, b_t, wl.notch)
+    b_u = O.neighbors(wl.grid)
+    O.break_notch(wl.grid, b_u, wl.notch)
+    dt = wl.dt_factor * O.stable_dt(wl.grid, wl.mat, b_t)
+    notch = b_t.broken.astype(bool).copy()
+    tr = O.ExplicitState(wl.grid, wl.mat, b_t, wl.u0, wl.v0, track=True)
+    un = O.ExplicitState(wl.grid, wl.mat, b_u, wl.u0, wl.v0)
+    tr.run(dt, 10)
+    tr.run(dt, 20)
+    un.run(dt, 30)
+    assert np.array_equal(tr.u, un.u) and np.array_equal(tr.v, un.v)
+    assert np.array_equal(b_t.broken, b_u.broken)
+    brk = b_t.broken.astype(bool) & ~notch
+    assert brk.sum() > 10
+    assert np.array_equal(brk, tr.brk_step >= 0)
+    assert np.all(tr.s_max[brk] > wl.mat.s_c)
+    assert np.all(tr.s_max[~brk & ~notch] <= wl.mat.s_c)
+    assert np.all(tr.brk_step[notch] == -1)            # broken before the run, never evaluated
+    rng = np.random.default_rng(0)
+    for k in rng.choice(np.flatnonzero(brk), size=5, replace=False):
+        step = int(tr.brk_step[k])
+        for n, want in ((step - 1, False), (step, True)):
+            b = O.neighbors(wl.grid)
+            O.break_notch(wl.grid, b, wl.notch)
+            O.ExplicitState(wl.grid, wl.mat, b, wl.u0, wl.v0).run(dt, n)   # n = 0: the initial force alone
+            assert bool(b.broken[k]) == want
+    s = O.bond_stretch(wl.grid, b_t, tr.u)
+    rows = np.repeat(np.arange(wl.grid.npoints), np.diff(b_t.row_ptr))
+    key = rows * wl.grid.npoints + b_t.col
+    rkey = b_t.col.astype(np.int64) * wl.grid.npoints + rows
+    order = np.argsort(key)
+    mate = order[np.searchsorted(key[order], rkey)]
+    assert np.array_equal(s, s[mate])

@@ -43,7 +43,8 @@ BAD = {
     "dt < 0": lambda g, m, r: setattr(r, "dt", -1e-6),
     "dt_factor < 0": lambda g, m, r: setattr(r, "dt_factor", -0.5),
     "unknown integrator": lambda g, m, r: setattr(r, "integrator", 2),
-    "run reserved": lambda g, m, r: setattr(r, "reserved", 1),
+    "unknown state precision": lambda g, m, r: setattr(r, "state", 2),
+    "FP64 path with double-float state": lambda g, m, r: (setattr(r, "precision", 1), setattr(r, "state", 1)),
 }
 
 
