@@ -55,7 +55,7 @@ int launch_tangent_jacobi(const Geom &g, int precision, void *cache, const int *
 int launch_tangent_precond(const Geom &g, int precision, const void *cache, const double *r, double *z,
                            cudaStream_t st);
 size_t energy_smem(const Geom &g, int precision);
-int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st);
+int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st, bool bits = false);
 int dirichlet_mask(const Geom &g, const uint8_t *kind, double *const v[3], const double *const w[3], int copy,
                    cudaStream_t st);
 int unpack_pairs(const Geom &g, const float4 *in, double *const x[3], cudaStream_t st);
@@ -1013,7 +1013,7 @@ int pd_build_neighbors(pd_sim *s, void *stream)
     if (s->run.dt > 0.0) s->dt = s->run.dt;
     else s->dt = (s->run.dt_factor > 0.0 ? s->run.dt_factor : 0.5) * s->dt_crit;
     if (!(s->dt > 0.0)) { set_error("time step could not be determined (no bonds?)"); return PD_EINVAL; }
-    rc = pack_stage(s->g, s->u, s->hl[s->cur], s->d4[s->cur], st);
+    rc = pack_stage(s->g, s->u, s->hl[s->cur], s->d4[s->cur], st, s->state64);
     if (rc != PD_OK) return rc;
     PD_CUDA(cudaStreamSynchronize(st));
     s->u_prev_ok = false;
@@ -1129,7 +1129,7 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
                 PD_CUDA(cudaMemcpyAsync(io, host[f] + r0 * d, bytes, cudaMemcpyDefault, cs));
                 PD_CUDA(cudaEventRecord(s->ev_copy[k], cs));
                 PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[k], 0));
-                int rc = scatter_rows(g, s->slot_of_user, s->io, r0, r1, slot, hl, d4, st);
+                int rc = scatter_rows(g, s->slot_of_user, s->io, r0, r1, slot, hl, d4, st, f32c && s->state64);
                 if (rc != PD_OK) return rc;
                 PD_CUDA(cudaEventRecord(s->ev_done[k], st));
             } else {
@@ -1175,7 +1175,7 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     if (u && !host_u) {
         if ((rc = user_source(s, u, &src, st)) != PD_OK) return rc;
         rc = scatter_stage(s->g, s->user_of_slot, src, pairs ? nullptr : s->u, f32c ? s->hl[s->cur] : nullptr,
-                           f32c ? nullptr : s->d4[s->cur], st);
+                           f32c ? nullptr : s->d4[s->cur], st, f32c && s->state64);
         if (rc != PD_OK) return rc;
     }
     if (v && !host_v) {
@@ -1522,7 +1522,7 @@ int pd_solve_static(pd_sim *s, const pd_newton_opts *opts, pd_newton_stats *stat
     PD_CUDA(cudaGetLastError());
     pd_newton_stats ns = {0, 0, 0, 0, 0.0, 0.0};
     for (int it = 0;; ++it) {
-        if ((rc = pack_stage(g, s->u, s->hl[s->cur], s->d4[s->cur], st)) != PD_OK) return rc;
+        if ((rc = pack_stage(g, s->u, s->hl[s->cur], s->d4[s->cur], st, s->state64)) != PD_OK) return rc;
         if ((rc = run_force(s, MODE_FORCE, s->hl[s->cur], s->d4[s->cur], 0, st)) != PD_OK) return rc;
         k_nk_residual<<<nbs, 256, 0, st>>>(g, s->user_of_slot, s->bc_kind, s->f[0], s->f[1], s->f[2],
                                            s->use_body ? s->body : nullptr, s->nk_r);

@@ -670,8 +670,22 @@ __global__ void k_scatter(Geom g, const int *slot_of_user, const double *user, d
 // slot-order writes are coalesced and the user array is read in runs of
 // x-consecutive points (a Morton-ordered warp covers 4 x 4 x 2 points); slots
 // off the lattice get zeros.
+// The FP32 staging pair of an FP64 value: round-to-nearest high word (the
+// double-float state's own representation) or, with bits, split_bits (the
+// split the fused update writes for FP64 state, so that a staging pair made
+// here equals the one a step would make from the same u).
+__device__ __forceinline__ void split_pair(double x, bool bits, float &h, float &l)
+{
+    if (bits) {
+        split_bits(x, h, l);
+    } else {
+        h = (float)x;
+        l = (float)(x - (double)h);
+    }
+}
+
 __device__ __forceinline__ void stage_slot(long long s, int d, double x, double y, double z, double *s0, double *s1,
-                                           double *s2, float4 *hl, double4_32a *d4)
+                                           double *s2, float4 *hl, double4_32a *d4, bool bits)
 {
     if (s0) {
         s0[s] = x;
@@ -680,14 +694,17 @@ __device__ __forceinline__ void stage_slot(long long s, int d, double x, double 
     }
     if (d4) d4[s] = make_double4_32a(x, y, z, 0.0);
     if (hl) {
-        const float hx = (float)x, hy = (float)y, hz = (float)z;
+        float hx, hy, hz, lx, ly, lz;
+        split_pair(x, bits, hx, lx);
+        split_pair(y, bits, hy, ly);
+        split_pair(z, bits, hz, lz);
         hl[2 * s] = make_float4(hx, hy, hz, 0.f);
-        hl[2 * s + 1] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
+        hl[2 * s + 1] = make_float4(lx, ly, lz, 0.f);
     }
 }
 
 __global__ void k_scatter_stage(Geom g, const int *user_of_slot, const double *user, double *s0, double *s1,
-                                double *s2, float4 *hl, double4_32a *d4)
+                                double *s2, float4 *hl, double4_32a *d4, bool bits)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.nslots) return;
@@ -699,20 +716,20 @@ __global__ void k_scatter_stage(Geom g, const int *user_of_slot, const double *u
         y = user[i * d + 1];
         if (d == 3) z = user[i * d + 2];
     }
-    stage_slot(s, d, x, y, z, s0, s1, s2, hl, d4);
+    stage_slot(s, d, x, y, z, s0, s1, s2, hl, d4, bits);
 }
 
 // The same for the user rows [r0, r1) alone, one thread per row (for a chunk of
 // an upload that is still arriving). Slots off the lattice are not written: they
 // hold zeros from the allocation on, as no kernel writes a slot off the lattice.
 __global__ void k_scatter_rows(Geom g, const int *slot_of_user, const double *user, long long r0, long long r1,
-                               double *s0, double *s1, double *s2, float4 *hl, double4_32a *d4)
+                               double *s0, double *s1, double *s2, float4 *hl, double4_32a *d4, bool bits)
 {
     const long long i = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r1) return;
     const long long s = slot_of_user[i];
     const int d = g.dim;
-    stage_slot(s, d, user[i * d], user[i * d + 1], d == 3 ? user[i * d + 2] : 0.0, s0, s1, s2, hl, d4);
+    stage_slot(s, d, user[i * d], user[i * d + 1], d == 3 ? user[i * d + 2] : 0.0, s0, s1, s2, hl, d4, bits);
 }
 
 // The reverse: user order from the double-float pair (hl) or the FP64 SoA arrays.
@@ -740,11 +757,11 @@ __global__ void k_gather_unstage(Geom g, const int *slot_of_user, const float4 *
 }
 
 int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, double *const slot[3], float4 *hl,
-                  double4_32a *d4, cudaStream_t st)
+                  double4_32a *d4, cudaStream_t st, bool bits)
 {
     k_scatter_stage<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, user_of_slot, user, slot ? slot[0] : nullptr,
                                                              slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
-                                                             hl, d4);
+                                                             hl, d4, bits);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -767,12 +784,12 @@ int gather_rows(const Geom &g, const int *slot_of_user, const float4 *hl, double
 }
 
 int scatter_rows(const Geom &g, const int *slot_of_user, const double *user, long long r0, long long r1,
-                 double *const slot[3], float4 *hl, double4_32a *d4, cudaStream_t st)
+                 double *const slot[3], float4 *hl, double4_32a *d4, cudaStream_t st, bool bits)
 {
     if (r1 <= r0) return PD_OK;
     k_scatter_rows<<<(unsigned)((r1 - r0 + 255) / 256), 256, 0, st>>>(
         g, slot_of_user, user, r0, r1, slot ? slot[0] : nullptr, slot ? slot[1] : nullptr, slot ? slot[2] : nullptr,
-        hl, d4);
+        hl, d4, bits);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -806,23 +823,19 @@ int scatter_kinds(const Geom &g, const Tables &t, const uint8_t *user, uint8_t *
 }
 
 // Staging buffer from FP64 SoA displacements (FP32 hi/lo pairs or double4_32a).
-__global__ void k_pack_stage(Geom g, const double *u0, const double *u1, const double *u2, float4 *hl, double4_32a *d4)
+__global__ void k_pack_stage(Geom g, const double *u0, const double *u1, const double *u2, float4 *hl, double4_32a *d4,
+                             bool bits)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.nslots) return;
     const double x = u0[s], y = u1[s], z = g.dim == 3 ? u2[s] : 0.0;
-    if (d4) {
-        d4[s] = make_double4_32a(x, y, z, 0.0);
-    } else {
-        const float hx = (float)x, hy = (float)y, hz = (float)z;
-        hl[2 * s] = make_float4(hx, hy, hz, 0.f);
-        hl[2 * s + 1] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
-    }
+    if (d4) d4[s] = make_double4_32a(x, y, z, 0.0);
+    else stage_slot(s, g.dim, x, y, z, nullptr, nullptr, nullptr, hl, nullptr, bits);
 }
 
-int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st)
+int pack_stage(const Geom &g, double *const u[3], float4 *hl, double4_32a *d4, cudaStream_t st, bool bits)
 {
-    k_pack_stage<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, u[0], u[1], u[2], hl, d4);
+    k_pack_stage<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, u[0], u[1], u[2], hl, d4, bits);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

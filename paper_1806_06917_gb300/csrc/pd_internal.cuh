@@ -167,13 +167,15 @@ size_t krylov_dsc_doubles(int krylov_gmres_restart);
 int krylov_norm(const double *x, long long n, KrylovWork &wk, double *out, cudaStream_t st);
 
 // User order to slots with the staging form in one pass, and back (pd_build.cu).
+// bits: the FP32 staging pair by split_bits (FP64 integrator state) instead of
+// the round-to-nearest double-float split.
 int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, double *const slot[3], float4 *hl,
-                  double4_32a *d4, cudaStream_t st);
+                  double4_32a *d4, cudaStream_t st, bool bits = false);
 int gather_unstage(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
                    cudaStream_t st);
 // The same for the user rows [r0, r1) only (chunks of a pipelined host transfer).
 int scatter_rows(const Geom &g, const int *slot_of_user, const double *user, long long r0, long long r1,
-                 double *const slot[3], float4 *hl, double4_32a *d4, cudaStream_t st);
+                 double *const slot[3], float4 *hl, double4_32a *d4, cudaStream_t st, bool bits = false);
 int gather_rows(const Geom &g, const int *slot_of_user, const float4 *hl, double *const slot[3], double *user,
                 long long r0, long long r1, cudaStream_t st);
 

@@ -300,6 +300,50 @@ __device__ __forceinline__ int slot_at(const Geom &g, const int *tile_lut, int x
     return t * g.T + brick_code(g.dim, x & (g.bx - 1), y & (g.by - 1), z & (g.bz - 1));
 }
 
+// ------------------------------------------------------- FP64 <-> FP32 pairs
+
+// FP32 -> FP64 from the bits, on the integer pipes (exact, as the conversion
+// instruction; FP32 denormals, which the FP32 arithmetic flushes, give zero).
+__device__ __forceinline__ double f2d_bits(float x)
+{
+    const unsigned X = __float_as_uint(x);
+    const unsigned e = (X >> 23) & 0xffu;
+    const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned hi = (X & 0x80000000u) | (e ? (ed << 20) | ((X >> 3) & 0xfffffu) : 0u);
+    const unsigned lo = e ? X << 29 : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// u = hi + lo to about 47 bits, from the bits of u on the integer and FP32
+// pipes: hi is u with its 29 low mantissa bits cut off (exactly an FP32
+// value, same sign), lo the cut-off part, rest * 2^(e - 1075), rounded once to
+// FP32 (its two 16-bit halves convert exactly through the 2^23 magic number).
+// |u| < 2^-126 stages as 0; |u| >= 2^116 (never a displacement) takes the
+// conversion instruction.
+__device__ __forceinline__ void split_bits(double u, float &hi, float &lo)
+{
+    const unsigned H = (unsigned)__double2hiint(u), Lw = (unsigned)__double2loint(u);
+    const unsigned sign = H & 0x80000000u;
+    const int e = (int)((H >> 20) & 0x7ffu);
+    const unsigned rest = Lw & 0x1fffffffu;
+    const float r1 = __uint_as_float(0x4b000000u | (rest >> 16)) - 8388608.f;
+    const float r0 = __uint_as_float(0x4b000000u | (rest & 0xffffu)) - 8388608.f;
+    const float fr = fmaf(r1, 65536.f, r0);
+    // 2^(e - 1075) as 2^(e - 1011) * 2^-64, both normal FP32 numbers for 897 <= e <= 1138
+    const float s1 = __uint_as_float((unsigned)(e - 884) << 23);
+    const float l = fr * s1 * 5.42101086242752217e-20f;
+    if (e < 897) {
+        hi = 0.f;
+        lo = 0.f;
+    } else if (e > 1138) {
+        hi = __double2float_rn(u);
+        lo = 0.f;
+    } else {
+        hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((H & 0xfffffu) << 3) | (Lw >> 29));
+        lo = sign ? -l : l;
+    }
+}
+
 // ------------------------------------------------------------ kernel args
 
 // One POD argument block for every tile kernel.
