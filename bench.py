@@ -378,14 +378,37 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     return line
 
 
+def coarse_nodes(wl, k, k0):
+    """Row indices of the coarse mesh's nodes (k = k0) in [0, 1]^2 on the mesh of
+    refinement k: the coarse node i is the fine node k / k0 * i (the lattices are
+    aligned at -delta)."""
+    n = wl.grid.n[0]
+    step = k // k0
+    idx = np.arange(n * n).reshape(n, n)[::step, ::step].reshape(-1)
+    X = wl.grid.positions()[idx]
+    inside = np.all((X > -1e-9) & (X < 1.0 + 1e-9), axis=1)
+    return idx[inside]
+
+
+def convergence_rate(us, wls, ks):
+    """Sec. 5.2.2's rate from three meshes h1 > h2 > h3 (h = delta / k):
+      alpha = (log ||u_1 - u_2|| - log ||u_2 - u_3||) / log 2,
+    ||f||^2 = sum over the coarse nodes in [0, 1]^2 of |f|^2 h_1^2."""
+    h1 = wls[0].grid.h
+    cs = [u[coarse_nodes(wl, k, ks[0])] for u, wl, k in zip(us, wls, ks)]
+    e12 = math.sqrt(float(((cs[0] - cs[1]) ** 2).sum()) * h1 * h1)
+    e23 = math.sqrt(float(((cs[1] - cs[2]) ** 2).sum()) * h1 * h1)
+    return (math.log(e12) - math.log(e23)) / math.log(2.0) if e12 > 0 and e23 > 0 else None
+
+
 def run_convergence(args, pd, torch):
-    """Sec. 5.2.2's 2D study: NP and LP, IC 1 and IC 2, meshes h = delta/2,
-    delta/4, delta/8 on [-delta, 1 + delta]^2 with the collar held at 0, dt =
-    1e-5 to t = 2. Every 0.1 time units the rate
-      alpha = (log ||u_1 - u_2|| - log ||u_2 - u_3||) / log 2
-    with ||f||^2 = sum over the coarse nodes in [0, 1]^2 of |f|^2 h_1^2 (the
-    coarse nodes are nodes of the finer meshes: index 2i and 4i)."""
-    ks = (2, 4, 8)
+    """Sec. 5.2.2's 2D study: NP and LP, IC 1 and IC 2, meshes h = delta/k on
+    [-delta, 1 + delta]^2 with the collar held at 0, dt = 1e-5 to t = 2. Every
+    0.1 time units the rate alpha of every three consecutive meshes of
+    --conv-meshes (default 2, 4, 8: the paper's three; a fourth, 16, shows how
+    the rate depends on the coarsest mesh)."""
+    ks = tuple(int(k) for k in args.conv_meshes.split(","))
+    prec = pd.PD_FP64 if args.conv_precision == "fp64" else pd.PD_FP32C
     steps_total = args.conv_steps
     chunk = max(1, steps_total // 20)
     out = {}
@@ -396,46 +419,38 @@ def run_convergence(args, pd, torch):
             wls = [W.np_square(k=k, model=model, ic=ic) for k in ks]
             sims = []
             for wl in wls:
-                g, m, r = pd.describe(wl.grid, wl.mat, precision=pd.PD_FP32C, dt=wl.dt)
+                g, m, r = pd.describe(wl.grid, wl.mat, precision=prec, dt=wl.dt)
                 sim = pd.pd_create(g, m, r)
                 pd.pd_build_neighbors(sim)
                 pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
                 pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
                 sims.append(sim)
-            n1 = wls[0].grid.n[0]
-            X1 = wls[0].grid.positions()
-            inside = np.all((X1 > -1e-9) & (X1 < 1.0 + 1e-9), axis=1)
-            h1 = wls[0].grid.h
-            rates, times = [], []
+            rates = {"%s" % (ks[i:i + 3],): [] for i in range(len(ks) - 2)}
+            times = []
             done = 0
             while done < steps_total:
                 q = min(chunk, steps_total - done)
                 for sim in sims:
                     pd.pd_step_explicit(sim, q)
                 done += q
-                us = []
-                for wl, sim, k in zip(wls, sims, ks):
-                    u, _ = pd.pd_get_state(sim, want_v=False)
-                    n = wl.grid.n[0]
-                    step = k // ks[0]
-                    U = u.reshape(n, n, 2)[::step, ::step].reshape(-1, 2)      # the coarse nodes
-                    us.append(U[inside])
-                e12 = math.sqrt(float(((us[0] - us[1]) ** 2).sum()) * h1 * h1)
-                e23 = math.sqrt(float(((us[1] - us[2]) ** 2).sum()) * h1 * h1)
+                us = [pd.pd_get_state(sim, want_v=False)[0] for sim in sims]
                 times.append(done * wls[0].dt)
-                rates.append((math.log(e12) - math.log(e23)) / math.log(2.0) if e12 > 0 and e23 > 0 else None)
-            for sim, wl in zip(sims, wls):
+                for i in range(len(ks) - 2):
+                    a = convergence_rate(us[i:i + 3], wls[i:i + 3], ks[i:i + 3])
+                    rates["%s" % (ks[i:i + 3],)].append(None if a is None else round(a, 4))
+            for sim in sims:
                 work += pd.pd_bond_count(sim) * steps_total
                 sim.close()
-            out["%s_ic%d" % ("np" if model == W.NP else "lp", ic)] = {
-                "t": [round(t, 4) for t in times], "alpha": [None if a is None else round(a, 4) for a in rates]}
+            out["%s_ic%d" % ("np" if model == W.NP else "lp", ic)] = {"t": [round(t, 4) for t in times],
+                                                                       "alpha": rates}
     sec = time.perf_counter() - t_all
-    line = {"metric": "bond updates/s (2D NP/LP convergence study, 12 runs)", "value": work / sec,
+    line = {"metric": "bond updates/s (2D NP/LP convergence study)", "value": work / sec,
             "unit": "bond-updates/s", "n_gpus": 1, "steps": steps_total, "warmup": 0, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 bond arithmetic (compensated), f64 integrator state", "data": "synthetic",
-            "config": {"workload": "Sec. 5.2.2: [0,1]^2, delta = 0.1, h = delta/2, delta/4, delta/8, "
-                                   "collar u = 0, dt = 1e-5, t in [0, %g]" % (steps_total * 1e-5),
+            "dtype": "f32 bond arithmetic (compensated), f64 integrator state" if prec == pd.PD_FP32C else "f64",
+            "data": "synthetic",
+            "config": {"workload": "Sec. 5.2.2: [0,1]^2, delta = 0.1, h = delta/k for k in %s, "
+                                   "collar u = 0, dt = 1e-5, t in [0, %g]" % (list(ks), steps_total * 1e-5),
                        "l2": "not flushed"},
             "seconds": sec, "alpha": out, "gpu_launches": None, "roofline": None}
     print(json.dumps(line), flush=True)
@@ -747,6 +762,8 @@ def main():
     ap.add_argument("--workload", default="lps128",
                     choices=["lps128", "block64", "block256", "plate50", "paper443", "serve", "convergence"])
     ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
+    ap.add_argument("--conv-meshes", default="2,4,8", help="convergence: refinements k (h = delta / k)")
+    ap.add_argument("--conv-precision", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
     ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")

@@ -145,6 +145,12 @@ typedef struct {
     int32_t integrator; /* PD_INTEGRATOR_VERLET (0) or PD_INTEGRATOR_CD */
     int32_t state;      /* PD_FP32C: PD_STATE_F64 (0) or PD_STATE_DF; must be 0
                            for PD_FP64 */
+    int32_t pair_threads; /* PD_FP32C PMB: threads that share a point pair's
+                           stencil words (1, 2 or 4, at most the stencil's
+                           32-bond words; their partial sums are added in a fixed
+                           order); 0 lets the library choose (the most resident
+                           threads per SM) */
+    int32_t reserved;   /* must be 0 */
 } pd_run;
 
 typedef struct pd_sim pd_sim;
@@ -283,6 +289,16 @@ int pd_step_explicit_timed(pd_sim *sim, int64_t nsteps, double pass_ms[2], void 
 int pd_tune_tile(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps,
                  int32_t *tile_log2, void *stream);
 
+/* Measured tile and threads-per-pair choice: as pd_tune_tile, over every
+ * admissible tile size and, for the FP32C PMB kernel, every pd_run.pair_threads
+ * of 1, 2 and 4 up to the stencil's 32-bond words (a larger count, like a
+ * smaller tile, only when at least 1 % faster). *pair_threads receives the
+ * choice (0 where the kernel has no such choice: other models and
+ * precisions); pair_threads == NULL measures tiles only (pd_tune_tile).
+ * Synchronous. */
+int pd_tune(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps, int32_t *tile_log2,
+            int32_t *pair_threads, void *stream);
+
 /* ------------------------------------------------------------------- tangent */
 
 /* Tangent Jacobian-vector product out = K w with K = df/du at u_lin (npoints x
@@ -369,18 +385,42 @@ int pd_solve_static(pd_sim *sim, const pd_newton_opts *opts, pd_newton_stats *st
  * the library admits queued requests in submission order while their device
  * memory (bond list, bond mask and per-point state, estimated before creation)
  * fits the budget and fewer than max_active run; each admitted request gets its
- * own simulation and stream and advances in quanta of quantum_steps explicit
- * steps (graph-replayed), and a finished request frees its memory for the next
- * in the queue between quanta (continuous batching). A request's result does
- * not depend on what else runs: it equals the same simulation run alone with
- * the tile size reported in pd_result. */
+ * own simulation and advances in quanta of up to quantum_steps explicit steps,
+ * and a finished request frees its memory for the next in the queue between
+ * quanta (continuous batching).
+ *
+ * PD_SERVE_PACKED (default): FP32C PMB requests without breaking and FP32C LPS
+ * requests without partial volume (on 2^9-point tiles, with the pair_threads
+ * the server sets: 2 where the stencil has two or more 32-bond words, else 1)
+ * are stepped together by one packed kernel: per explicit step one launch of a
+ * persistent grid whose CTAs take (request, pass, tile) work items of every
+ * such request from a device-side list (the LPS force items after the
+ * dilatation items they need, with a bounded wait on completion flags), the
+ * steps of a quantum replayed from a captured CUDA graph. Other requests run
+ * on their own streams, as every request does under PD_SERVE_STREAMS.
+ *
+ * A request's result does not depend on what else runs: it equals the same
+ * simulation run alone with the tile_log2 and pair_threads reported in
+ * pd_result. */
 
 typedef struct pd_server pd_server;
+
+#define PD_SERVE_PACKED 0
+#define PD_SERVE_STREAMS 1
 
 typedef struct {
     int64_t device_bytes;     /* admission budget; 0 = half the free device memory */
     int32_t max_active;       /* simulations stepping at once, 1..256 (16) */
-    int32_t quantum_steps;    /* steps per scheduling quantum, >= 1 (64) */
+    int32_t quantum_steps;    /* steps per scheduling quantum, 1..4096 (64) */
+    int32_t mode;             /* PD_SERVE_PACKED (0) or PD_SERVE_STREAMS */
+    int32_t wait_limit_ms;    /* limit of one device-side wait of the packed kernel;
+                                 0 = 2000 ms. A wait that runs out ends the quantum's
+                                 launch, and every request of that quantum fails
+                                 with PD_ETIMEOUT */
+    int32_t test_stall;       /* tests only, else 0: in the server's first packed
+                                 quantum the first LPS force item waits for a flag
+                                 that nothing sets, so that its wait runs out */
+    int32_t reserved;         /* must be 0 */
 } pd_server_opts;
 
 typedef struct {
@@ -406,7 +446,7 @@ typedef struct {
     int32_t state;            /* PD_REQ_* */
     int32_t error;            /* PD_OK, or the status that failed the request */
     int32_t tile_log2;        /* tile size the request runs with (0 before admission) */
-    int32_t reserved;
+    int32_t pair_threads;     /* pd_run.pair_threads it runs with (0: the library's choice) */
     int64_t steps_done;
     int64_t bonds;            /* directed bonds (0 before admission) */
     double submit_s, start_s, end_s;   /* server clock (s since pd_server_create); 0 if not yet */

@@ -10,7 +10,7 @@
 #include <climits>
 #include <vector>
 
-#include "pd_tile.cuh"
+#include "pd_packed.cuh"
 
 namespace pdk {
 
@@ -106,6 +106,7 @@ struct pd_sim {
     int *stencil_lut = nullptr;
     float4 *tab_a = nullptr;        // FP32C stencil table: PMB, or LPS dilatation
     float4 *tab_b = nullptr;        // FP32C stencil table: LPS force
+    std::vector<float4> htab_a, htab_b;   // host copies (passed as kernel parameters when small)
     int *tile_nbr = nullptr;        // [ntiles * 27]
     int nbr_ok = 0;
     uint32_t *box_map = nullptr;    // [paired halo box] neighbour tile + brick code of both points
@@ -228,6 +229,11 @@ static int validate(const pd_grid *gr, const pd_material *mt, const pd_run *rn)
         return PD_EINVAL;
     }
     if (rn->state != PD_STATE_F64 && rn->state != PD_STATE_DF) { set_error("unknown state precision"); return PD_EINVAL; }
+    if (rn->pair_threads != 0 && rn->pair_threads != 1 && rn->pair_threads != 2 && rn->pair_threads != 4) {
+        set_error("pair_threads must be 0, 1, 2 or 4");
+        return PD_EINVAL;
+    }
+    if (rn->reserved != 0) { set_error("pd_run.reserved must be 0"); return PD_EINVAL; }
     if (rn->precision == PD_FP64 && rn->state != PD_STATE_F64) {
         set_error("the FP64 path keeps FP64 state (pd_run.state must be 0)");
         return PD_EINVAL;
@@ -446,6 +452,10 @@ static int create_impl(pd_sim *s)
         ALLOC(s->tab_b, sizeof(float4) * tb.size());
         PD_CUDA(cudaMemcpy(s->tab_a, ta.data(), sizeof(float4) * ta.size(), cudaMemcpyHostToDevice));
         PD_CUDA(cudaMemcpy(s->tab_b, tb.data(), sizeof(float4) * tb.size(), cudaMemcpyHostToDevice));
+        // the entries the kernels read: PMB 4 float4 each (NP / LP keep theirs in
+        // shared memory), LPS 3
+        if (mt.model == PD_MODEL_PMB) s->htab_a.assign(ta.begin(), ta.begin() + 4 * (size_t)g.S);
+        if (mt.model == PD_MODEL_LPS) s->htab_b = tb;
         // neighbour tiles (index (dx+1) + 3 (dy+1) + 9 (dz+1)); usable when the halo
         // reaches at most one tile in every direction
         std::vector<int> nbr(27 * (size_t)g.ntiles, -1);
@@ -585,6 +595,7 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.v_is_half = s->v_is_half;
     a.cd = s->run.integrator == PD_INTEGRATOR_CD && s->u_prev_ok ? 1 : 0;
     a.state64 = s->precision == PD_FP32C && s->state64 ? 1 : 0;
+    a.split = s->run.pair_threads;   // 0: the launcher's choice
     a.update_breaking = s->mat.s_c > 0.0 ? 1 : 0;
     a.mode = mode;
     a.vol_corr = s->mat.vol_corr;
@@ -593,6 +604,10 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.vhl = s->vhl;
     a.tab_a = s->tab_a;
     a.tab_b = s->tab_b;
+    a.htab_a = s->htab_a.empty() ? nullptr : s->htab_a.data();
+    a.htab_b = s->htab_b.empty() ? nullptr : s->htab_b.data();
+    a.ntab_a = (int)s->htab_a.size();
+    a.ntab_b = (int)s->htab_b.size();
     a.tile_nbr = s->tile_nbr;
     a.nbr_ok = s->nbr_ok;
     a.box_map = s->box_map;
@@ -606,6 +621,54 @@ static TileArgs make_args(pd_sim *s, int mode, const float4 *src_hl, const doubl
     a.dt_h = (float)s->dt;
     a.dt_l = (float)(s->dt - (double)a.dt_h);
     return a;
+}
+
+// ------------------------------------------------- the server's packed kernel
+
+int pdk::sim_pack_info(pd_sim *s, PackInfo *pi)
+{
+    memset(pi, 0, sizeof(*pi));
+    if (!s->built) { set_error("neighbours not built"); return PD_ESTATE; }
+    const Geom &g = s->g;
+    const int model = s->mat.model;
+    const int split = pack_split_for(g.W);
+    int kind = -1;
+    if (model == PD_MODEL_PMB && s->mat.s_c == 0.0) kind = g.dim == 3 ? PK_PMB3 : PK_PMB2;
+    if (model == PD_MODEL_LPS && !s->mat.vol_corr) kind = PK_LPS;
+    pi->eligible = s->precision == PD_FP32C && kind >= 0 && g.L == 9 && s->nbr_ok &&
+                   (kind == PK_LPS || s->run.pair_threads == split);
+    if (!pi->eligible) return PD_OK;
+    pi->kind = kind;
+    pi->split = kind == PK_LPS ? 2 : split;
+    pi->ntiles = g.ntiles;
+    pi->smem = pack_smem(g, kind, split);
+    for (int p = 0; p < 2; ++p) {
+        TileArgs a = make_args(s, MODE_STEP, s->hl[p], s->d4[p]);
+        a.dst_hl = s->hl[p ^ 1];
+        a.dst_d4 = s->d4[p ^ 1];
+        a.v_is_half = 1;
+        a.cd = s->run.integrator == PD_INTEGRATOR_CD ? 1 : 0;
+        a.update_breaking = 0;
+        a.split = pi->split;
+        a.htab_a = a.htab_b = nullptr;      // the packed bodies read the device tables
+        a.ntab_a = a.ntab_b = 0;
+        pi->a[p] = a;
+    }
+    pi->cur = s->cur;
+    pi->vhalf = s->v_is_half;
+    pi->cd0 = s->run.integrator == PD_INTEGRATOR_CD && s->u_prev_ok ? 1 : 0;
+    pi->cd = s->run.integrator == PD_INTEGRATOR_CD ? 1 : 0;
+    pi->step = s->step;
+    return PD_OK;
+}
+
+void pdk::sim_pack_advance(pd_sim *s, long long n)
+{
+    if (n <= 0) return;
+    s->cur ^= (int)(n & 1);
+    s->step += n;
+    s->v_is_half = 1;
+    s->u_prev_ok = true;
 }
 
 // Internal force at the staging buffer src (+ update per mode).
@@ -733,7 +796,9 @@ static int stage_lin(pd_sim *s, const double *u, const float4 **hl, const double
     }
     int rc = user_to_slots(s, u, s->ulin, st);
     if (rc != PD_OK) return rc;
-    rc = pack_stage(s->g, s->ulin, s->lin_hl, s->lin_d4, st);
+    // the same split as the state's staging, so that a force at a passed u equals
+    // the force at the same u set as the state
+    rc = pack_stage(s->g, s->ulin, s->lin_hl, s->lin_d4, st, s->precision == PD_FP32C && s->state64);
     *hl = s->lin_hl;
     *d4 = s->lin_d4;
     return rc;
@@ -914,16 +979,17 @@ int pd_destroy(pd_sim *s)
     return PD_OK;
 }
 
-int pd_tune_tile(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps,
-                 int32_t *tile_log2, void *stream)
+int pd_tune(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps, int32_t *tile_log2,
+            int32_t *pair_threads, void *stream)
 {
     if (!grid || !mat || !run || !tile_log2 || steps < 1) {
-        set_error("pd_tune_tile: null argument or steps < 1");
+        set_error("pd_tune: null argument or steps < 1");
         return PD_EINVAL;
     }
     {   // the description is checked once, before any device call
         pd_run r = *run;
         r.tile_log2 = 0;
+        r.pair_threads = 0;
         const int rc = validate(grid, mat, &r);
         if (rc != PD_OK) return rc;
     }
@@ -934,43 +1000,59 @@ int pd_tune_tile(const pd_grid *grid, const pd_material *mat, const pd_run *run,
         cudaEventDestroy(e0);
         return cuda_fail(ce, "cudaEventCreate");
     }
-    int best = 0, last_rc = PD_OK;
+    // threads per point pair are a choice of the FP32C PMB kernel only; 1, 2, 4
+    // up to the stencil's 32-bond words
+    const int W = (stencil_size(grid->dim, grid->m) + 31) / 32;
+    const bool splits = pair_threads && run->precision == PD_FP32C && mat->model == PD_MODEL_PMB;
+    int best = 0, best_pt = 0, last_rc = PD_OK;
     float best_ms = 0.f;
     for (int L = 9; L >= 6; --L) {
-        pd_run r = *run;
-        r.tile_log2 = L;
-        pd_sim *s = nullptr;
-        int rc = pd_create(&s, grid, mat, &r);
-        if (rc == PD_OK) rc = pd_build_neighbors(s, stream);
-        if (rc == PD_OK) rc = pd_step_explicit(s, 2, stream);
-        // the best of three timed runs of `steps` steps
-        float ms = 0.f;
-        for (int rep = 0; rep < 3 && rc == PD_OK; ++rep) {
-            cudaStream_t st = pick(s, stream);
-            float t = 0.f;
-            cudaError_t e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) rc = pd_step_explicit(s, steps, stream);
-            if (e == cudaSuccess && rc == PD_OK) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess && rc == PD_OK) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess && rc == PD_OK) e = cudaEventElapsedTime(&t, e0, e1);
-            if (e != cudaSuccess && rc == PD_OK) rc = cuda_fail(e, "pd_tune_tile timing");
-            if (rc == PD_OK && (rep == 0 || t < ms)) ms = t;
-        }
-        pd_destroy(s);
-        if (rc != PD_OK) {
-            last_rc = rc;
-            continue;
-        }
-        if (!best || ms < 0.99f * best_ms) {
-            best = L;
-            best_ms = ms;
+        for (int pt = splits ? 1 : 0; pt <= (splits ? std::min(4, W) : 0); pt = pt ? 2 * pt : 1) {
+            pd_run r = *run;
+            r.tile_log2 = L;
+            r.pair_threads = pt;
+            pd_sim *s = nullptr;
+            int rc = pd_create(&s, grid, mat, &r);
+            if (rc == PD_OK) rc = pd_build_neighbors(s, stream);
+            if (rc == PD_OK) rc = pd_step_explicit(s, 2, stream);
+            // the best of three timed runs of `steps` steps
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && rc == PD_OK; ++rep) {
+                cudaStream_t st = pick(s, stream);
+                float t = 0.f;
+                cudaError_t e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) rc = pd_step_explicit(s, steps, stream);
+                if (e == cudaSuccess && rc == PD_OK) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess && rc == PD_OK) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess && rc == PD_OK) e = cudaEventElapsedTime(&t, e0, e1);
+                if (e != cudaSuccess && rc == PD_OK) rc = cuda_fail(e, "pd_tune timing");
+                if (rc == PD_OK && (rep == 0 || t < ms)) ms = t;
+            }
+            pd_destroy(s);
+            if (rc != PD_OK) {
+                last_rc = rc;
+                continue;
+            }
+            // a smaller tile or more threads per pair only when at least 1 % faster
+            if (!best || ms < 0.99f * best_ms) {
+                best = L;
+                best_pt = pt;
+                best_ms = ms;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!best) return last_rc != PD_OK ? last_rc : PD_EINVAL;
     *tile_log2 = best;
+    if (pair_threads) *pair_threads = best_pt;
     return PD_OK;
+}
+
+int pd_tune_tile(const pd_grid *grid, const pd_material *mat, const pd_run *run, int32_t steps,
+                 int32_t *tile_log2, void *stream)
+{
+    return pd_tune(grid, mat, run, steps, tile_log2, nullptr, stream);
 }
 
 int pd_build_neighbors(pd_sim *s, void *stream)

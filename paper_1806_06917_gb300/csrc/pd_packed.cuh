@@ -1,0 +1,82 @@
+// pd_packed.cuh -- the request server's packed kernel: every active request of
+// the server advanced by one explicit step in one launch ("round"), its CTAs
+// taking (request, pass, tile) work items from a device-side list.
+//
+// Work items of round s (the s-th step of the quantum): for every request with
+// more than s steps left in the quantum, group A holds one item per tile for
+// its first pass (the fused PMB force + update, or the LPS dilatation) and
+// group B one per tile for the LPS force + update pass; A comes first. An LPS
+// force item needs the dilatation of its 27 neighbour tiles (theta of the halo),
+// which items of group A of the same launch compute: its CTA waits for their
+// completion flags, a bounded wait that ends the launch with an error status
+// after a time limit instead of hanging. Items are claimed in list order and a
+// claimed item's CTA stays resident until it is done, so every item waited on
+// is already held by a running CTA: the waits end.
+#pragma once
+
+#include "pd_tile.cuh"
+
+struct pd_sim;
+
+namespace pdk {
+
+enum PackKind { PK_PMB3 = 0, PK_PMB2 = 1, PK_LPS = 2 };
+
+constexpr int PACK_THREADS = 512;         // CTA size: the LPS force pass of a 2^9-point tile
+
+// One request of a quantum (device table entry, built by the server).
+struct PackReq {
+    TileArgs a[2];          // MODE_STEP arguments by staging parity (src = hl[p], dst = hl[p ^ 1]),
+                            // with the flags of every step after the quantum's first
+    int kind;               // PackKind
+    int split;              // PMB: threads per point pair of its body (1 or 2)
+    int ntiles;
+    int nsteps;             // rounds this request takes part in
+    int cur0;               // staging parity at the quantum's start
+    int vhalf0, cd0;        // v_is_half and the central-difference flag of the quantum's first step
+    int pad_;
+    unsigned *dil_done;     // LPS: per tile, 1 + the step of its last dilatation (monotonic)
+    long long step0;        // the simulation's step count at the quantum's start
+};
+
+// Status word of a quantum (device): code, request, tile, round of the first failure.
+enum { PACK_OK = 0, PACK_TIMEOUT = 1 };
+
+// Kernel parameters of a quantum's rounds.
+struct PackTable {
+    const PackReq *req;     // sorted by nsteps, descending
+    const int *offA;        // [nreq + 1] prefix sums of the requests' group-A items
+    const int *offB;        // [nreq + 1] the same for group B
+    const int *nsteps;      // [nreq] req[r].nsteps (descending)
+    unsigned *counters;     // [rounds] item counters, zero at the quantum's start
+    unsigned *status;       // [4]
+    long long wait_ns;      // limit of one wait
+    int nreq;
+    int stall;              // tests only: the first group-B item of round 0 waits on a flag nothing sets
+};
+
+// What the server needs of a simulation to pack it (pd_api.cu).
+struct PackInfo {
+    int eligible;           // the packed kernel can step it (FP32C, PMB without breaking or LPS without
+                            // partial volume, 2^9-point tiles, pair_threads as the packed body's)
+    int kind, split, ntiles;
+    size_t smem;
+    TileArgs a[2];          // MODE_STEP by staging parity, flags of a step after the first
+    int cur, vhalf, cd0, cd;
+    long long step;
+};
+int sim_pack_info(pd_sim *s, PackInfo *pi);
+// Bookkeeping after n packed steps (staging parity, step count, half-step velocity).
+void sim_pack_advance(pd_sim *s, long long n);
+// The packed body's threads per point pair for a lattice: 2 where the stencil
+// has at least two 32-bond words (all PACK_THREADS threads busy), else 1.
+inline int pack_split_for(int W) { return W >= 2 ? 2 : 1; }
+
+// Host side (pd_packed.cu). Dynamic shared memory of a request's items, and the
+// resident CTAs per SM of the kernel at that size.
+size_t pack_smem(const Geom &g, int kind, int split);
+int pack_occupancy(size_t smem, int *ctas_per_sm);
+// Enqueue `rounds` rounds (round indices 0 .. rounds - 1) on st with `grid` CTAs.
+int pack_launch_rounds(const PackTable &t, int rounds, int grid, size_t smem, cudaStream_t st);
+
+}  // namespace pdk

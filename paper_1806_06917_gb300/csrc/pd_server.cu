@@ -11,6 +11,7 @@
 // running ones; from then on the worker owns the simulation, its stream and
 // event. Every wait of either thread is bounded (event queries with short
 // sleeps, timed condition-variable waits).
+#include <stdio.h>
 #include <string.h>
 
 #include <chrono>
@@ -22,7 +23,11 @@
 #include <unordered_map>
 #include <vector>
 
-#include "pd_tile.cuh"
+#include <algorithm>
+#include <map>
+#include <tuple>
+
+#include "pd_packed.cuh"
 
 using namespace pdk;
 
@@ -48,6 +53,10 @@ struct Req {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     int64_t inflight = 0;
+    bool packed = false;            // stepped by the packed kernel (else on its own stream)
+    bool tune = false;              // tile and threads per pair from the server's measured choices
+    unsigned *dil_done = nullptr;   // LPS in the packed kernel: per-tile dilatation flags
+    int pack_kind = 0;
 };
 
 bool ended(int state) { return state == PD_REQ_DONE || state == PD_REQ_CANCELLED || state == PD_REQ_FAILED; }
@@ -105,6 +114,29 @@ struct pd_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker, setup_worker;
+    // the packed kernel: device request table for max_active requests, its
+    // pinned host staging, counters and status; graphs of the rounds by
+    // (rounds, grid, shared memory)
+    int mode = PD_SERVE_PACKED;
+    long long wait_ns = 2000000000LL;
+    int stall = 0;
+    cudaStream_t pk_stream = nullptr;
+    cudaEvent_t pk_ev = nullptr;
+    PackReq *d_req = nullptr, *h_req = nullptr;
+    int *d_idx = nullptr, *h_idx = nullptr;      // offA, offB (max_active + 1 each), nsteps (max_active)
+    unsigned *d_counters = nullptr, *d_status = nullptr, *h_status = nullptr;
+    int pk_rounds_max = 0;
+    std::map<std::tuple<int, int, size_t>, cudaGraphExec_t> graphs;
+    std::vector<std::pair<Req *, int>> pk_inflight;   // requests of the quantum in flight, their steps
+    // measured (tile_log2, pair_threads) of the requests on their own streams, by
+    // dimension, horizon, model, precision, state, integrator and size class
+    // (log2 of the points), measured once per class with pd_tune
+    std::mutex tune_mu;
+    std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> tuned;
+    int pk_init();
+    void pk_free();
+    int pk_issue(std::vector<Req *> &active);
+    void pk_collect();
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void run();
@@ -131,6 +163,40 @@ int pd_server::setup(Req *r)
     cudaError_t e = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "server stream/event");
+    if (r->tune) {
+        const long long np = (long long)r->grid.n[0] * r->grid.n[1] * (r->grid.dim == 3 ? r->grid.n[2] : 1);
+        int cls = 0;
+        while ((1LL << (cls + 1)) <= np) ++cls;
+        const auto key = std::make_tuple(r->grid.dim, r->grid.m, r->mat.model, r->run.precision, r->run.state,
+                                         r->run.integrator, cls);
+        std::pair<int, int> choice{0, 0};
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(tune_mu);
+            auto it = tuned.find(key);
+            if (it != tuned.end()) {
+                choice = it->second;
+                have = true;
+            }
+        }
+        if (!have) {
+            int32_t tl = 0, pt = 0;
+            pd_run rr = r->run;
+            rr.tile_log2 = 0;
+            rr.pair_threads = 0;
+            if (pd_tune(&r->grid, &r->mat, &rr, 5, &tl, &pt, nullptr) == PD_OK) {
+                choice = {tl, pt};
+                std::lock_guard<std::mutex> lk(tune_mu);
+                tuned[key] = choice;
+            }
+        }
+        if (choice.first) {
+            r->run.tile_log2 = choice.first;
+            r->run.pair_threads = choice.second;
+            std::lock_guard<std::mutex> lk(mu);
+            r->res.tile_log2 = choice.first;
+        }
+    }
     int rc = pd_create(&r->sim, &r->grid, &r->mat, &r->run);
     if (rc != PD_OK) return rc;
     if ((rc = pd_build_neighbors(r->sim, r->stream)) != PD_OK) return rc;
@@ -141,13 +207,34 @@ int pd_server::setup(Req *r)
         return rc;
     int64_t nb = 0;
     if ((rc = pd_bond_count(r->sim, &nb)) != PD_OK) return rc;
+    if (mode == PD_SERVE_PACKED) {
+        PackInfo pi;
+        if ((rc = sim_pack_info(r->sim, &pi)) != PD_OK) return rc;
+        if (pi.eligible) {
+            r->packed = true;
+            r->pack_kind = pi.kind;
+            if (pi.kind == PK_LPS) {
+                cudaError_t e = lib_malloc(reinterpret_cast<void **>(&r->dil_done), sizeof(unsigned) * pi.ntiles,
+                                           r->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemsetAsync(r->dil_done, 0, sizeof(unsigned) * pi.ntiles, r->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "server dilatation flags");
+            }
+        }
+    }
+    // everything above is in place before the worker (another stream) steps it
+    e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "server setup");
     std::lock_guard<std::mutex> lk(mu);
     r->res.bonds = nb;
+    r->res.pair_threads = r->run.pair_threads;
     return PD_OK;
 }
 
 void pd_server::teardown(Req *r)
 {
+    if (r->dil_done) lib_free(r->dil_done, r->stream);
+    r->dil_done = nullptr;
     if (r->stream) cudaStreamSynchronize(r->stream);
     if (r->sim) pd_destroy(r->sim);
     if (r->ev) cudaEventDestroy(r->ev);
@@ -237,9 +324,21 @@ void pd_server::run()
                 continue;
             }
         }
-        // issue the next quantum of every idle simulation
+        // the packed requests: collect a finished quantum, issue the next
+        pk_collect();
+        if (pk_issue(active) != PD_OK) {
+            char msg[160];
+            pd_last_error(msg, sizeof(msg));
+            std::lock_guard<std::mutex> lk(mu);
+            for (Req *r : active)
+                if (r->packed && !r->res.error) {
+                    r->res.error = PD_ECUDA;
+                    strncpy(r->res.message, msg, sizeof(r->res.message) - 1);
+                }
+        }
+        // issue the next quantum of every idle simulation on its own stream
         for (Req *r : active) {
-            if (r->inflight) continue;
+            if (r->inflight || r->packed) continue;
             bool cancel;
             int64_t done;
             {
@@ -267,6 +366,12 @@ void pd_server::run()
         bool progressed = false;
         for (size_t i = 0; i < active.size();) {
             Req *r = active[i];
+            if (std::any_of(pk_inflight.begin(), pk_inflight.end(), [r](const std::pair<Req *, int> &x) {
+                    return x.first == r;
+                })) {
+                ++i;                                        // in the packed quantum in flight
+                continue;
+            }
             if (r->inflight) {
                 const cudaError_t q = cudaEventQuery(r->ev);
                 if (q == cudaErrorNotReady) {
@@ -311,17 +416,185 @@ void pd_server::run()
     }
 }
 
+int pd_server::pk_init()
+{
+    const int n = max_active;
+    PD_CUDA(cudaStreamCreateWithFlags(&pk_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaEventCreateWithFlags(&pk_ev, cudaEventDisableTiming));
+    PD_CUDA(cudaMalloc(&d_req, sizeof(PackReq) * n));
+    PD_CUDA(cudaMallocHost(&h_req, sizeof(PackReq) * n));
+    PD_CUDA(cudaMalloc(&d_idx, sizeof(int) * (3 * n + 2)));
+    PD_CUDA(cudaMallocHost(&h_idx, sizeof(int) * (3 * n + 2)));
+    pk_rounds_max = quantum;
+    PD_CUDA(cudaMalloc(&d_counters, sizeof(unsigned) * pk_rounds_max));
+    PD_CUDA(cudaMalloc(&d_status, sizeof(unsigned) * 4));
+    PD_CUDA(cudaMallocHost(&h_status, sizeof(unsigned) * 4));
+    memset(h_status, 0, sizeof(unsigned) * 4);
+    return PD_OK;
+}
+
+void pd_server::pk_free()
+{
+    if (pk_stream) cudaStreamSynchronize(pk_stream);
+    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    graphs.clear();
+    cudaFree(d_req);
+    cudaFreeHost(h_req);
+    cudaFree(d_idx);
+    cudaFreeHost(h_idx);
+    cudaFree(d_counters);
+    cudaFree(d_status);
+    cudaFreeHost(h_status);
+    if (pk_ev) cudaEventDestroy(pk_ev);
+    if (pk_stream) cudaStreamDestroy(pk_stream);
+}
+
+// The next packed quantum: every packed request that is not cancelled, failed or
+// done takes part with min(quantum, steps left) steps. Requests are sorted by
+// their step count (descending), so that those still stepping in round s are a
+// prefix of the table; entries past the last request have no steps. The rounds
+// are replayed from a captured graph (memsets of the counters and status, the
+// round launches, the status read-back), cached by (rounds, grid, shared memory).
+int pd_server::pk_issue(std::vector<Req *> &active)
+{
+    if (!pk_inflight.empty()) return PD_OK;
+    std::vector<std::pair<Req *, int>> list;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (Req *r : active)
+            if (r->packed && !r->cancel && r->res.error == PD_OK && r->res.steps_done < r->nsteps)
+                list.emplace_back(r, (int)std::min<int64_t>(quantum, r->nsteps - r->res.steps_done));
+    }
+    if (list.empty()) return PD_OK;
+    std::stable_sort(list.begin(), list.end(), [](const std::pair<Req *, int> &x, const std::pair<Req *, int> &y) {
+        return x.second > y.second;
+    });
+    const int n = max_active;
+    int *offA = h_idx, *offB = h_idx + (n + 1), *nst = h_idx + 2 * (n + 1);
+    offA[0] = offB[0] = 0;
+    size_t smem = 0;
+    memset(h_req, 0, sizeof(PackReq) * n);
+    for (int i = 0; i < n; ++i) {
+        int na = 0, nb = 0;
+        nst[i] = 0;
+        if (i < (int)list.size()) {
+            PackInfo pi;
+            int rc = sim_pack_info(list[i].first->sim, &pi);
+            if (rc != PD_OK) return rc;
+            if (!pi.eligible) { set_error("a packed request is no longer eligible"); return PD_ESTATE; }
+            PackReq &q = h_req[i];
+            q.a[0] = pi.a[0];
+            q.a[1] = pi.a[1];
+            q.kind = pi.kind;
+            q.split = pi.split;
+            q.ntiles = pi.ntiles;
+            q.nsteps = list[i].second;
+            q.cur0 = pi.cur;
+            q.vhalf0 = pi.vhalf;
+            q.cd0 = pi.cd0;
+            q.dil_done = list[i].first->dil_done;
+            q.step0 = pi.step;
+            nst[i] = q.nsteps;
+            na = pi.ntiles;
+            nb = pi.kind == PK_LPS ? pi.ntiles : 0;
+            smem = std::max(smem, pi.smem);
+        }
+        offA[i + 1] = offA[i] + na;
+        offB[i + 1] = offB[i] + nb;
+    }
+    const int rounds = list[0].second;
+    int ctas = 0;
+    int rc = pack_occupancy(smem, &ctas);
+    if (rc != PD_OK) return rc;
+    if (ctas < 1) { set_error("the packed kernel does not fit an SM with %zu bytes of shared memory", smem); return PD_EINVAL; }
+    const int grid = ctas * sms;
+    PD_CUDA(cudaMemcpyAsync(d_req, h_req, sizeof(PackReq) * n, cudaMemcpyHostToDevice, pk_stream));
+    PD_CUDA(cudaMemcpyAsync(d_idx, h_idx, sizeof(int) * (3 * n + 2), cudaMemcpyHostToDevice, pk_stream));
+    const auto key = std::make_tuple(rounds, grid, smem);
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+        PackTable t;
+        t.req = d_req;
+        t.offA = d_idx;
+        t.offB = d_idx + (n + 1);
+        t.nsteps = d_idx + 2 * (n + 1);
+        t.counters = d_counters;
+        t.status = d_status;
+        t.wait_ns = wait_ns;
+        t.nreq = n;
+        t.stall = stall;
+        PD_CUDA(cudaStreamBeginCapture(pk_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * rounds, pk_stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned) * 4, pk_stream);
+        int lrc = e == cudaSuccess ? pack_launch_rounds(t, rounds, grid, smem, pk_stream) : PD_OK;
+        if (e == cudaSuccess && lrc == PD_OK)
+            e = cudaMemcpyAsync(h_status, d_status, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, pk_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(pk_stream, &graph);
+        if (e == cudaSuccess) e = ee;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && lrc == PD_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (lrc != PD_OK) return lrc;
+        if (e != cudaSuccess) return cuda_fail(e, "packed quantum graph");
+        it = graphs.emplace(key, exec).first;
+    }
+    PD_CUDA(cudaGraphLaunch(it->second, pk_stream));
+    PD_CUDA(cudaEventRecord(pk_ev, pk_stream));
+    pk_inflight = list;
+    return PD_OK;
+}
+
+// A finished packed quantum: the steps count, or, if a device-side wait ran out,
+// every request of the quantum fails with PD_ETIMEOUT (their states are partly
+// stepped). A test stall applies to the first quantum only.
+void pd_server::pk_collect()
+{
+    if (pk_inflight.empty()) return;
+    const cudaError_t q = cudaEventQuery(pk_ev);
+    if (q == cudaErrorNotReady) return;
+    const unsigned code = q == cudaSuccess ? h_status[0] : (unsigned)PACK_OK;
+    char msg[160] = {0};
+    if (q != cudaSuccess) {
+        cuda_fail(q, "packed quantum");
+        pd_last_error(msg, sizeof(msg));
+    } else if (code != PACK_OK) {
+        snprintf(msg, sizeof(msg), "packed kernel: a dilatation wait ran out after %lld ns (table entry %u, tile %u, "
+                 "round %u)", wait_ns, h_status[1], h_status[2], h_status[3]);
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &x : pk_inflight) {
+        Req *r = x.first;
+        if (q == cudaSuccess && code == PACK_OK) {
+            sim_pack_advance(r->sim, x.second);
+            r->res.steps_done += x.second;
+        } else {
+            r->res.error = q != cudaSuccess ? PD_ECUDA : PD_ETIMEOUT;
+            strncpy(r->res.message, msg, sizeof(r->res.message) - 1);
+        }
+    }
+    pk_inflight.clear();
+    if (stall) {
+        stall = 0;
+        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        graphs.clear();
+    }
+}
+
 extern "C" {
 
 int pd_server_create(pd_server **out, const pd_server_opts *opts)
 {
     if (!out) { set_error("null output"); return PD_EINVAL; }
     *out = nullptr;
-    pd_server_opts o = {0, 16, 64};
+    pd_server_opts o = {0, 16, 64, PD_SERVE_PACKED, 0, 0, 0};
     if (opts) o = *opts;
     if (o.max_active < 1 || o.max_active > 256) { set_error("max_active must be in [1, 256]"); return PD_EINVAL; }
-    if (o.quantum_steps < 1) { set_error("quantum_steps must be >= 1"); return PD_EINVAL; }
+    if (o.quantum_steps < 1 || o.quantum_steps > 4096) { set_error("quantum_steps must be in [1, 4096]"); return PD_EINVAL; }
     if (o.device_bytes < 0) { set_error("device_bytes must be >= 0"); return PD_EINVAL; }
+    if (o.mode != PD_SERVE_PACKED && o.mode != PD_SERVE_STREAMS) { set_error("unknown server mode"); return PD_EINVAL; }
+    if (o.wait_limit_ms < 0) { set_error("wait_limit_ms must be >= 0"); return PD_EINVAL; }
+    if (o.reserved != 0) { set_error("pd_server_opts.reserved must be 0"); return PD_EINVAL; }
     std::unique_ptr<pd_server> s(new pd_server());
     PD_CUDA(cudaGetDevice(&s->device));
     PD_CUDA(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device));
@@ -330,6 +603,16 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
     s->budget = o.device_bytes > 0 ? (size_t)o.device_bytes : fr / 2;
     s->max_active = o.max_active;
     s->quantum = o.quantum_steps;
+    s->mode = o.mode;
+    s->wait_ns = 1000000LL * (o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000);
+    s->stall = o.test_stall ? 1 : 0;
+    if (s->mode == PD_SERVE_PACKED) {
+        const int rc = s->pk_init();
+        if (rc != PD_OK) {
+            s->pk_free();
+            return rc;
+        }
+    }
     s->t0 = Clock::now();
     pd_server *raw = s.get();
     s->setup_worker = std::thread([raw] { raw->run_setup(); });
@@ -349,6 +632,7 @@ int pd_server_destroy(pd_server *s)
     s->cv_setup.notify_all();
     if (s->worker.joinable()) s->worker.join();
     if (s->setup_worker.joinable()) s->setup_worker.join();
+    s->pk_free();
     delete s;
     return PD_OK;
 }
@@ -365,8 +649,29 @@ int pd_submit(pd_server *s, const pd_request *rq, uint64_t *ticket)
     r->mat = rq->material;
     r->run = rq->run;
     r->nsteps = rq->nsteps;
-    if (r->run.tile_log2 == 0) r->run.tile_log2 = choose_tile_log2(r->grid, s->max_active, s->sms);
-    r->est_bytes = estimate_bytes(r->grid, r->mat, r->run.tile_log2);
+    // FP32C PMB without breaking and LPS without partial volume go to the packed
+    // kernel, which runs 2^9-point tiles and its own threads per point pair
+    const bool packable = s->mode == PD_SERVE_PACKED && r->run.precision == PD_FP32C &&
+                          ((r->mat.model == PD_MODEL_PMB && r->mat.s_c == 0.0) ||
+                           (r->mat.model == PD_MODEL_LPS && !r->mat.vol_corr)) &&
+                          (r->run.tile_log2 == 0 || r->run.tile_log2 == 9);
+    if (packable) {
+        const int W = (stencil_size(r->grid.dim, r->grid.m) + 31) / 32;
+        const int split = r->mat.model == PD_MODEL_PMB ? pack_split_for(W) : 0;
+        if (r->run.pair_threads == 0 || r->run.pair_threads == split) {
+            r->run.tile_log2 = 9;
+            r->run.pair_threads = split;
+        }
+    }
+    if (r->run.tile_log2 == 0) {
+        // measured at setup (once per class of request); the estimate takes the
+        // largest footprint over the tile sizes the measurement may pick
+        r->tune = true;
+        r->run.tile_log2 = choose_tile_log2(r->grid, s->max_active, s->sms);
+        for (int L = 6; L <= 9; ++L) r->est_bytes = std::max(r->est_bytes, estimate_bytes(r->grid, r->mat, L));
+    } else {
+        r->est_bytes = estimate_bytes(r->grid, r->mat, r->run.tile_log2);
+    }
     if (r->est_bytes > s->budget) {
         set_error("request needs about %zu device bytes, more than the server budget of %zu", r->est_bytes,
                   s->budget);

@@ -29,6 +29,7 @@ PD_TANGENT_CACHED, PD_TANGENT_JVP = 0, 1
 PD_PRECOND_NONE, PD_PRECOND_BLOCK_JACOBI = 0, 1
 PD_INTEGRATOR_VERLET, PD_INTEGRATOR_CD = 0, 1
 PD_STATE_F64, PD_STATE_DF = 0, 1          # pd_run.state of a PD_FP32C simulation
+PD_SERVE_PACKED, PD_SERVE_STREAMS = 0, 1   # pd_server_opts.mode
 PD_REQ_QUEUED, PD_REQ_RUNNING, PD_REQ_DONE, PD_REQ_CANCELLED, PD_REQ_FAILED = 0, 1, 2, 3, 4
 
 if not os.path.exists(LIB_PATH):
@@ -51,7 +52,8 @@ class pd_material(ctypes.Structure):
 
 class pd_run(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dt_factor", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("tile_log2", ctypes.c_int32), ("integrator", ctypes.c_int32), ("state", ctypes.c_int32)]
+                ("tile_log2", ctypes.c_int32), ("integrator", ctypes.c_int32), ("state", ctypes.c_int32),
+                ("pair_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pd_newton_opts(ctypes.Structure):
@@ -68,7 +70,8 @@ class pd_newton_stats(ctypes.Structure):
 
 class pd_server_opts(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
-                ("quantum_steps", ctypes.c_int32)]
+                ("quantum_steps", ctypes.c_int32), ("mode", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
+                ("test_stall", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pd_request(ctypes.Structure):
@@ -79,7 +82,7 @@ class pd_request(ctypes.Structure):
 
 class pd_result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("tile_log2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("steps_done", ctypes.c_int64), ("bonds", ctypes.c_int64),
+                ("pair_threads", ctypes.c_int32), ("steps_done", ctypes.c_int64), ("bonds", ctypes.c_int64),
                 ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("end_s", ctypes.c_double),
                 ("message", ctypes.c_char * 160)]
 
@@ -113,6 +116,8 @@ _SIGS = {
     "pd_step_explicit_timed": [_P, ctypes.c_int64, _P, _P],
     "pd_tune_tile": [ctypes.POINTER(pd_grid), ctypes.POINTER(pd_material), ctypes.POINTER(pd_run), ctypes.c_int32,
                      ctypes.POINTER(ctypes.c_int32), _P],
+    "pd_tune": [ctypes.POINTER(pd_grid), ctypes.POINTER(pd_material), ctypes.POINTER(pd_run), ctypes.c_int32,
+                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _P],
     "pd_jvp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_vjp": [_P, _P, _P, _P, ctypes.c_uint, _P],
     "pd_energy": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
@@ -313,6 +318,14 @@ def pd_tune_tile(grid: pd_grid, mat: pd_material, run: pd_run, steps: int = 10, 
     return out.value
 
 
+def pd_tune(grid: pd_grid, mat: pd_material, run: pd_run, steps: int = 10, stream=None):
+    """The fastest (tile_log2, pair_threads) for this description, measured."""
+    tl, pt = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.pd_tune(ctypes.byref(grid), ctypes.byref(mat), ctypes.byref(run), int(steps), ctypes.byref(tl),
+                        ctypes.byref(pt), _stream(stream)))
+    return tl.value, pt.value
+
+
 def pd_step_explicit(sim: Sim, nsteps: int, stream=None) -> None:
     _check(_lib.pd_step_explicit(sim.h, int(nsteps), _stream(stream)))
 
@@ -357,7 +370,7 @@ def pd_solve_static(sim: Sim, opts: pd_newton_opts | None = None, stream=None) -
 
 
 def _result(r: pd_result) -> dict:
-    d = {k: getattr(r, k) for k, _ in pd_result._fields_ if k not in ("reserved", "message")}
+    d = {k: getattr(r, k) for k, _ in pd_result._fields_ if k != "message"}
     d["message"] = r.message.decode(errors="replace")
     return d
 
@@ -367,10 +380,11 @@ class Server:
     until the ticket has ended (the library copies the inputs at submit and
     writes the outputs at completion)."""
 
-    def __init__(self, device_bytes: int = 0, max_active: int = 16, quantum_steps: int = 64):
+    def __init__(self, device_bytes: int = 0, max_active: int = 16, quantum_steps: int = 64,
+                 mode: int = 0, wait_limit_ms: int = 0, test_stall: int = 0):
         h = _P()
-        _check(_lib.pd_server_create(ctypes.byref(h), ctypes.byref(pd_server_opts(device_bytes, max_active,
-                                                                                  quantum_steps))))
+        opts = pd_server_opts(device_bytes, max_active, quantum_steps, mode, wait_limit_ms, test_stall, 0)
+        _check(_lib.pd_server_create(ctypes.byref(h), ctypes.byref(opts)))
         self.h = h
         self._keep = {}
 
@@ -469,7 +483,7 @@ def pd_sum_noalloc(x, scale=1.0, out=None, stream=None):
 # ------------------------------------------------------------ conveniences
 
 def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=0.5, tile_log2=0,
-             integrator=PD_INTEGRATOR_VERLET, state=0):
+             integrator=PD_INTEGRATOR_VERLET, state=0, pair_threads=0):
     """pd_grid / pd_material / pd_run from the plain workload descriptions."""
     g = pd_grid()
     g.dim = workload_grid.dim
@@ -488,5 +502,5 @@ def describe(workload_grid, workload_mat, precision=PD_FP32C, dt=0.0, dt_factor=
     m.psi_beta = getattr(workload_mat, "psi_beta", 1.0)
     r = pd_run()
     r.dt, r.dt_factor, r.precision, r.tile_log2 = dt, dt_factor, precision, tile_log2
-    r.integrator, r.state = integrator, state
+    r.integrator, r.state, r.pair_threads, r.reserved = integrator, state, pair_threads, 0
     return g, m, r

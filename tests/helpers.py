@@ -17,12 +17,12 @@ def rel_l2(a, b):
 PRECISIONS = {"fp32c": (0, 0), "fp32c_df": (0, 1), "fp64": (1, 0)}
 
 
-def gpu_sim(pd, grid, mat, precision, dt=0.0, notch=None, tile_log2=0, integrator=0, state=0):
+def gpu_sim(pd, grid, mat, precision, dt=0.0, notch=None, tile_log2=0, integrator=0, state=0, pair_threads=0):
     """A built simulation; precision is a PD_* value or a name of PRECISIONS."""
     if isinstance(precision, str):
         precision, state = PRECISIONS[precision]
     g, m, r = pd.describe(grid, mat, precision=precision, dt=dt, tile_log2=tile_log2, integrator=integrator,
-                          state=state)
+                          state=state, pair_threads=pair_threads)
     sim = pd.pd_create(g, m, r)
     pd.pd_build_neighbors(sim)
     if notch is not None:

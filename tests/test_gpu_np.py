@@ -99,3 +99,37 @@ def test_np_lp_refuse_breaking_and_the_tangent(pd):
         pd.pd_jvp(sim, np.zeros((g.npoints, 2)))
     assert e.value.code == pd.PD_EINVAL
     sim.close()
+
+
+def test_convergence_rate_to_t02_matches_oracle(pd):
+    """The study of Sec. 5.2.2 (NP, IC 1) on its three meshes (h = delta / 2,
+    delta / 4, delta / 8) to t = 0.2: each mesh's u against the oracle's run,
+    and the rate alpha at t = 0.1 and 0.2 from the GPU's u against the rate
+    from the oracle's u (about 80 s of oracle time on 16 host cores)."""
+    import bench
+    ks = (2, 4, 8)
+    wls = [W.np_square(k=k, model=W.NP, ic=1) for k in ks]
+    sims = []
+    states = []
+    for wl in wls:
+        sim = gpu_sim(pd, wl.grid, wl.mat, "fp32c", dt=wl.dt)
+        pd.pd_set_state(sim, u=wl.u0, v=wl.v0)
+        pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
+        sims.append(sim)
+        states.append(O.ExplicitState(wl.grid, wl.mat, O.neighbors(wl.grid), wl.u0, wl.v0, wl.bc_kind, wl.bc_val))
+    for _ in range(2):                               # t = 0.1, then t = 0.2
+        ug, uo = [], []
+        for sim, st, wl in zip(sims, states, wls):
+            pd.pd_step_explicit(sim, 10000)
+            st.run(wl.dt, 10000)
+            u, _ = pd.pd_get_state(sim, want_v=False)
+            assert rel_l2(u, st.u) <= 1e-4
+            ug.append(u)
+            uo.append(st.u.copy())
+        a_g = bench.convergence_rate(ug, wls, ks)
+        a_o = bench.convergence_rate(uo, wls, ks)
+        assert a_g is not None and a_o is not None
+        assert abs(a_g - a_o) <= 1e-3, (a_g, a_o)
+        assert a_o > 1.0                             # the paper's regime at early times
+    for sim in sims:
+        sim.close()

@@ -1,8 +1,10 @@
 """GPU: the request server (pd_server_* / pd_submit / pd_poll / pd_wait /
 pd_cancel). A served request's result must equal, bit for bit, the same
-simulation run alone through the ordinary entry points with the tile size the
-server reports; admission must respect the memory budget; cancellation and
-bounded waits must work without touching the GPU's state."""
+simulation run alone through the ordinary entry points with the tile size and
+threads per point pair the server reports, whether it ran in the packed kernel
+(with whatever else was packed with it) or on its own stream; admission must
+respect the memory budget; cancellation and bounded waits (host-side, and the
+packed kernel's device-side wait) must work without touching the GPU's state."""
 import numpy as np
 import pytest
 
@@ -27,9 +29,9 @@ def _submit(pd, srv, r, u_out=None, v_out=None, precision=None, tile_log2=0, int
     return pd.pd_submit(srv, g, m, run, r.steps, u0=r.u0, v0=np.zeros_like(r.u0), u_out=u_out, v_out=v_out)
 
 
-def _alone(pd, r, tile_log2, precision=None, integrator=0):
+def _alone(pd, r, tile_log2, precision=None, integrator=0, pair_threads=0):
     sim = gpu_sim(pd, r.grid, r.mat, pd.PD_FP32C if precision is None else precision, tile_log2=tile_log2,
-                  integrator=integrator)
+                  integrator=integrator, pair_threads=pair_threads)
     pd.pd_set_state(sim, u=r.u0, v=np.zeros_like(r.u0))
     pd.pd_step_explicit(sim, r.steps)
     u, v = pd.pd_get_state(sim)
@@ -42,20 +44,64 @@ def _small_mix(count, seed):
                          steps_lo=5, steps_hi=70, m_choices=(2, 3))
 
 
-def test_served_results_equal_the_same_runs_alone(pd):
+@pytest.mark.parametrize("mode", ["packed", "streams"])
+def test_served_results_equal_the_same_runs_alone(pd, mode):
     mix = _small_mix(10, 21)
     assert {r.grid.dim for r in mix} == {2, 3} and {r.mat.model for r in mix} == {W.PMB, W.LPS}
-    srv = pd.Server(max_active=3, quantum_steps=7)        # quanta that do not divide the step counts
+    srv = pd.Server(max_active=3, quantum_steps=7,        # quanta that do not divide the step counts
+                    mode=pd.PD_SERVE_PACKED if mode == "packed" else pd.PD_SERVE_STREAMS)
     outs = [(np.full(r.u0.shape, np.nan), np.full(r.u0.shape, np.nan)) for r in mix]
     tickets = [_submit(pd, srv, r, u_out=o[0], v_out=o[1]) for r, o in zip(mix, outs)]
     results = [pd.pd_wait(srv, t, timeout_s=120.0) for t in tickets]
     srv.close()
     for r, res, (u, v) in zip(mix, results, outs):
-        assert res["state"] == pd.PD_REQ_DONE and res["error"] == pd.PD_OK, res
+        assert res["state"] == pd.PD_REQ_DONE and res["error"] == pd.PD_OK, res["message"]
         assert res["steps_done"] == r.steps and res["bonds"] > 0
         assert 0.0 < res["submit_s"] <= res["start_s"] <= res["end_s"]
-        ua, va = _alone(pd, r, res["tile_log2"])
+        if mode == "packed":
+            assert res["tile_log2"] == 9 and res["pair_threads"] in (1, 2) or r.mat.model == W.LPS
+        ua, va = _alone(pd, r, res["tile_log2"], pair_threads=res["pair_threads"])
         assert np.array_equal(u, ua) and np.array_equal(v, va)
+
+
+def test_a_request_is_the_same_alone_and_in_a_packed_mix(pd):
+    """The same request served alone and among others in the packed kernel:
+    bit-identical results (its work items run the same arithmetic whatever is
+    packed beside them)."""
+    mix = _small_mix(8, 31)
+    probe = [r for r in mix if r.mat.model == W.LPS][0]
+    res = []
+    for others in (False, True):
+        srv = pd.Server(max_active=8, quantum_steps=5)
+        u = np.full(probe.u0.shape, np.nan)
+        t = _submit(pd, srv, probe, u_out=u)
+        ts = [_submit(pd, srv, r) for r in mix if r is not probe] if others else []
+        rp = pd.pd_wait(srv, t, timeout_s=120.0)
+        for x in ts:
+            assert pd.pd_wait(srv, x, timeout_s=120.0)["state"] == pd.PD_REQ_DONE
+        srv.close()
+        assert rp["state"] == pd.PD_REQ_DONE, rp
+        res.append(u)
+    assert np.array_equal(res[0], res[1])
+
+
+def test_packed_kernel_wait_runs_out_and_the_server_goes_on(pd):
+    """test_stall: the first packed quantum's first LPS force item waits for a
+    flag that nothing sets; its bounded wait (200 ms) runs out, the launch ends,
+    the quantum's request fails with PD_ETIMEOUT, and the next request is served
+    normally (the GPU context is intact)."""
+    mix = _small_mix(12, 41)
+    lps = [r for r in mix if r.mat.model == W.LPS][:2]
+    srv = pd.Server(max_active=1, quantum_steps=4, wait_limit_ms=200, test_stall=1)
+    first = pd.pd_wait(srv, _submit(pd, srv, lps[0]), timeout_s=60.0)
+    assert first["state"] == pd.PD_REQ_FAILED and first["error"] == pd.PD_ETIMEOUT, first
+    assert "wait ran out" in first["message"]
+    u = np.full(lps[1].u0.shape, np.nan)
+    second = pd.pd_wait(srv, _submit(pd, srv, lps[1], u_out=u), timeout_s=60.0)
+    srv.close()
+    assert second["state"] == pd.PD_REQ_DONE, second
+    ua, _ = _alone(pd, lps[1], second["tile_log2"], pair_threads=second["pair_threads"])
+    assert np.array_equal(u, ua)
 
 
 def test_central_difference_requests_equal_the_same_runs_alone(pd):
@@ -68,7 +114,7 @@ def test_central_difference_requests_equal_the_same_runs_alone(pd):
     srv.close()
     for r, res, u in zip(mix, results, outs):
         assert res["state"] == pd.PD_REQ_DONE, res
-        ua, _ = _alone(pd, r, res["tile_log2"], integrator=pd.PD_INTEGRATOR_CD)
+        ua, _ = _alone(pd, r, res["tile_log2"], integrator=pd.PD_INTEGRATOR_CD, pair_threads=res["pair_threads"])
         assert np.array_equal(u, ua)
 
 
@@ -80,7 +126,7 @@ def test_fp64_requests_are_served_too(pd):
     res = pd.pd_wait(srv, t, timeout_s=120.0)
     srv.close()
     assert res["state"] == pd.PD_REQ_DONE
-    ua, _ = _alone(pd, r, res["tile_log2"], precision=pd.PD_FP64)
+    ua, _ = _alone(pd, r, res["tile_log2"], precision=pd.PD_FP64, pair_threads=res["pair_threads"])
     assert np.array_equal(u, ua)
 
 

@@ -44,6 +44,8 @@ BAD = {
     "dt_factor < 0": lambda g, m, r: setattr(r, "dt_factor", -0.5),
     "unknown integrator": lambda g, m, r: setattr(r, "integrator", 2),
     "unknown state precision": lambda g, m, r: setattr(r, "state", 2),
+    "pair_threads = 3": lambda g, m, r: setattr(r, "pair_threads", 3),
+    "run reserved": lambda g, m, r: setattr(r, "reserved", 1),
     "FP64 path with double-float state": lambda g, m, r: (setattr(r, "precision", 1), setattr(r, "state", 1)),
 }
 
