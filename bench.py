@@ -70,8 +70,13 @@ FALLBACK_HBM_GBS = 6800.0
 # flags hash to the value recorded with it; otherwise traffic is null.
 _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_06917_gb300/csrc/pd_tile.cuh",
                   "paper_1806_06917_gb300/csrc/pd_pair.cuh", "paper_1806_06917_gb300/build.py"]
+_LPS_SOURCES = ["paper_1806_06917_gb300/csrc/pd_force_lps.cu", "paper_1806_06917_gb300/csrc/pd_lps_fast.cuh"]
 NCU_TRAFFIC = {
     # (pass key, tile_log2): the capture of that kernel at that tile size
+    ("lps_dil", 9): {"bytes": 109863424 + 6181376, "sha": "38c4d4e24b339496",
+                     "sources": _LPS_SOURCES + _KERNEL_COMMON, "profile": "profiles/lps_block3d_128.md"},
+    ("lps_force", 9): {"bytes": 229948416 + 123038208, "sha": "38c4d4e24b339496",
+                       "sources": _LPS_SOURCES + _KERNEL_COMMON, "profile": "profiles/lps_block3d_128.md"},
 }
 
 
@@ -322,7 +327,9 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     one rank's share), with no collective until the totals are combined."""
     mix = shard(W.serving_mix(count=args.requests), rank, world)
     k = min(args.serial_sample, len(mix))
-    srv = pd.Server(max_active=1, quantum_steps=64)
+    mode = pd.PD_SERVE_STREAMS if getattr(args, "serve_mode", "packed") == "streams" else pd.PD_SERVE_PACKED
+    # one at a time: every request alone, with the simulation's own kernels
+    srv = pd.Server(max_active=1, quantum_steps=64, mode=pd.PD_SERVE_STREAMS)
     _submit_request(pd, srv, mix[0])                       # warm-up (module load, first graph)
     t0 = time.perf_counter()
     sres = [pd.pd_wait(srv, _submit_request(pd, srv, r), timeout_s=600.0) for r in mix[:k]]
@@ -333,7 +340,7 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     # the shard holds every world-th arrival of the global process, so the global
     # rate world x load x capacity offers each rank load x its own capacity
     rate = world * args.load * capacity
-    srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum)
+    srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum, mode=mode)
     with Clocks(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         tickets = []
@@ -365,8 +372,9 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
                                    "m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
                                    "one-at-a-time capacity" % (args.requests, args.load),
                        "parallelism": "requests sharded round robin over %d rank(s)" % world,
-                       "max_active": args.max_active, "quantum_steps": args.quantum, "l2": "not flushed (independent "
-                       "simulations stream through it)"},
+                       "max_active": args.max_active, "quantum_steps": args.quantum,
+                       "mode": getattr(args, "serve_mode", "packed"),
+                       "l2": "not flushed (independent simulations stream through it)"},
             "all_done": ok, "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
             "offered_rate_per_s": rate, "bond_updates": work,
@@ -741,12 +749,22 @@ def serving_side(pd, torch, requests=128, load=2.0, max_active=16, quantum=64):
     """A bounded run of the request server beside the headline: the first
     `requests` of the seeded mix arriving as a Poisson process at `load` x the
     one-at-a-time capacity (measured on 12 requests alone), against those
-    one-at-a-time launches."""
+    one-at-a-time launches; the packed kernel, and every request on its own
+    stream beside it."""
     class A:
         pass
-    a = A()
-    a.requests, a.load, a.max_active, a.quantum, a.serial_sample = requests, load, max_active, quantum, 12
-    return run_serving(a, pd, torch, 0, 1, emit=False)
+    out = None
+    for mode in ("packed", "streams"):
+        a = A()
+        a.requests, a.load, a.max_active, a.quantum, a.serial_sample = requests, load, max_active, quantum, 12
+        a.serve_mode = mode
+        r = run_serving(a, pd, torch, 0, 1, emit=False)
+        if out is None:
+            out = r
+        else:
+            out["streams_mode"] = {k: r[k] for k in ("value", "latency_p50_s", "latency_p99_s", "makespan_s",
+                                                     "all_done", "serial")}
+    return out
 
 
 def workload_key(wl):
@@ -769,6 +787,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")
     ap.add_argument("--serial-sample", type=int, default=24, help="serve: requests timed one at a time")
     ap.add_argument("--quantum", type=int, default=64, help="serve: steps per scheduling quantum")
+    ap.add_argument("--serve-mode", default="packed", choices=["packed", "streams"],
+                    help="serve: the packed kernel, or every request on its own stream")
     ap.add_argument("--tile-log2", type=int, default=None,
                     help="tile size 2^N of the timed simulation (6..9; 0 = library default); "
                          "by default pd_tune_tile measures and picks it")

@@ -642,6 +642,15 @@ int pdk::sim_pack_info(pd_sim *s, PackInfo *pi)
     pi->split = kind == PK_LPS ? 2 : split;
     pi->ntiles = g.ntiles;
     pi->smem = pack_smem(g, kind, split);
+    // items that would leave the packed kernel fewer than two CTAs per SM stay on
+    // their own stream
+    int ctas = 0;
+    const int rc = pack_occupancy(pi->smem, &ctas);
+    if (rc != PD_OK && rc != PD_EINVAL) return rc;
+    if (rc == PD_EINVAL || ctas < 2) {
+        pi->eligible = 0;
+        return PD_OK;
+    }
     for (int p = 0; p < 2; ++p) {
         TileArgs a = make_args(s, MODE_STEP, s->hl[p], s->d4[p]);
         a.dst_hl = s->hl[p ^ 1];

@@ -254,74 +254,6 @@ __global__ void k_gm_solve(double *d, int m)
     }
 }
 
-// One pass of classical Gram-Schmidt in one launch, for k <= CGS_MAXK basis
-// vectors: every block sums the pass's k dot products from the nbin block
-// partials of the launch before (warp i takes products i, i + 8, ...: lanes
-// stride the partials, then a fixed shuffle tree, the same in every block),
-// block 0 records them (d[i], and column j of the Hessenberg matrix unless the
-// cycle is done: = for the first pass, += for the second), y -= sum_i h_i V_i
-// on the block's CGS_CHUNK elements (the order of k_lincomb), and then, with
-// the new y, the block partials of the next products: the k products V_i . y
-// (DOTS, for the second pass) or |y|^2 (for the norm). It replaces k_partial_sum_hcol,
-// k_lincomb and the k_mdot that followed them.
-constexpr int CGS_MAXK = 64;
-constexpr int CGS_CHUNK = KT;   // one element per thread: enough blocks to fill the GPU at n ~ 1e5
-
-template <bool DOTS>
-__global__ void __launch_bounds__(KT) k_cgs_pass(double *y, const double *V, long long ldv, int k, const double *pin,
-                                                 int nbin, double *d, int m, int j, int add, long long n,
-                                                 double *pout)
-{
-    __shared__ double coef[CGS_MAXK];
-    __shared__ double red[(KT / 32) * CGS_MAXK];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int i = warp; i < k; i += KT / 32) {
-        double s = 0.0;
-        for (int b = lane; b < nbin; b += 32) s += pin[(long long)i * nbin + b];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) coef[i] = s;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0) {
-        const GmLayout L(m);
-        const bool done = d[L.sc + GM_DONE] != 0.0;
-        for (int i = threadIdx.x; i < k; i += KT) {
-            d[i] = coef[i];
-            if (!done) {
-                double *h = d + L.H + i + (m + 1) * j;
-                *h = add ? *h + coef[i] : coef[i];
-            }
-        }
-    }
-    const long long e = (long long)blockIdx.x * CGS_CHUNK + threadIdx.x;
-    double yn = 0.0;
-    // unrolled so that the loads of several basis vectors are in flight at once
-    if (e < n) {
-        double acc = y[e];
-#pragma unroll 8
-        for (int i = 0; i < k; ++i) acc = fma(-coef[i], V[(long long)i * ldv + e], acc);
-        y[e] = acc;
-        yn = acc;
-    }
-    if (DOTS) {
-#pragma unroll 8
-        for (int i = 0; i < k; ++i) {
-            double p = e < n ? V[(long long)i * ldv + e] * yn : 0.0;
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == 0) red[warp * CGS_MAXK + i] = p;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < k; i += KT) {
-            double t = 0.0;
-            for (int w = 0; w < KT / 32; ++w) t += red[w * CGS_MAXK + i];
-            pout[(long long)i * gridDim.x + blockIdx.x] = t;
-        }
-    } else {
-        const double t = block_sum(yn * yn, red);
-        if (threadIdx.x == 0) pout[blockIdx.x] = t;
-    }
-}
-
 // y *= d[idx]
 __global__ void k_scale_dev(const double *d, int idx, double *y, long long n)
 {
@@ -370,24 +302,18 @@ int krylov_gmres(const KrylovOp &op, const double *b, double *x, long long n, in
         }
         if ((e = op.apply(op.ctx, src, vj1, s)) != PD_OK) return e;
         const int nb = kblocks(n);
-        if (j + 1 <= CGS_MAXK) {
-            // CGS2 in three launches: the products of pass 1; pass 1's update with
-            // pass 2's products; pass 2's update with |w|^2 (cgs_blocks partials each)
-            const int nc = (int)((n + CGS_CHUNK - 1) / CGS_CHUNK);
-            double *pa = cs.partial, *pb = cs.partial + (size_t)nb * (m + 1);
-            k_mdot<<<dim3(nb, j + 1), KT, 0, s>>>(V, n, vj1, n, pa);
-            k_cgs_pass<true><<<nc, KT, 0, s>>>(vj1, V, n, j + 1, pa, nb, cs.dsc, m, j, 0, n, pb);
-            k_cgs_pass<false><<<nc, KT, 0, s>>>(vj1, V, n, j + 1, pb, nc, cs.dsc, m, j, 1, n, pa);
-            k_gm_step<<<1, KT, 3 * (m + 1) * sizeof(double), s>>>(pa, nc, cs.dsc, m, j);
-        } else {
-            for (int pass = 0; pass < 2; ++pass) {      // CGS2: h = V^T w, w -= V h; twice
-                k_mdot<<<dim3(nb, j + 1), KT, 0, s>>>(V, n, vj1, n, cs.partial);
-                k_partial_sum_hcol<<<j + 1, KT, 0, s>>>(cs.partial, nb, cs.dsc, m, j, pass);
-                if ((e = lincomb_dev(cs, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return e;
-            }
-            k_mdot<<<dim3(nb, 1), KT, 0, s>>>(vj1, 0, vj1, n, cs.partial);
-            k_gm_step<<<1, KT, 3 * (m + 1) * sizeof(double), s>>>(cs.partial, nb, cs.dsc, m, j);
+        // CGS2: h = V^T w, w -= V h; twice. (Fusing each pass's update with the
+        // next products into one launch, every block summing the previous
+        // products itself, measured slower on the 200^2 plate: 0.0975 -> 0.122 ms
+        // per Arnoldi step; the per-thread loops over the basis vectors have far
+        // less parallelism than k_mdot's (chunk, vector) grid.)
+        for (int pass = 0; pass < 2; ++pass) {
+            k_mdot<<<dim3(nb, j + 1), KT, 0, s>>>(V, n, vj1, n, cs.partial);
+            k_partial_sum_hcol<<<j + 1, KT, 0, s>>>(cs.partial, nb, cs.dsc, m, j, pass);
+            if ((e = lincomb_dev(cs, vj1, 1.0, V, n, j + 1, -1.0)) != PD_OK) return e;
         }
+        k_mdot<<<dim3(nb, 1), KT, 0, s>>>(vj1, 0, vj1, n, cs.partial);
+        k_gm_step<<<1, KT, 3 * (m + 1) * sizeof(double), s>>>(cs.partial, nb, cs.dsc, m, j);
         k_scale_dev<<<nbk, 256, 0, s>>>(cs.dsc, L.sc + GM_INVH, vj1, n);
         PD_CUDA(cudaGetLastError());
         return PD_OK;
@@ -680,12 +606,7 @@ int krylov_cg(const KrylovOp &op, const double *b, double *x, long long n, int m
     return PD_OK;
 }
 
-// k_mdot's partials (kblocks(n) per product) and, for the fused Gram-Schmidt
-// passes, theirs (one block per CGS_CHUNK elements) after them.
-size_t krylov_partial_doubles(long long n, int kmax)
-{
-    return (size_t)kblocks(n) * (kmax + 1) + (size_t)((n + CGS_CHUNK - 1) / CGS_CHUNK) * (kmax + 1);
-}
+size_t krylov_partial_doubles(long long n, int kmax) { return (size_t)kblocks(n) * (kmax + 1); }
 
 int krylov_norm(const double *x, long long n, KrylovWork &wk, double *out, cudaStream_t st)
 {

@@ -54,6 +54,7 @@ struct Req {
     cudaEvent_t ev = nullptr;
     int64_t inflight = 0;
     bool packed = false;            // stepped by the packed kernel (else on its own stream)
+    int64_t pk_pending = 0;         // steps in packed quanta still in flight
     bool tune = false;              // tile and threads per pair from the server's measured choices
     unsigned *dil_done = nullptr;   // LPS in the packed kernel: per-tile dilatation flags
     int pack_kind = 0;
@@ -120,14 +121,19 @@ struct pd_server {
     int mode = PD_SERVE_PACKED;
     long long wait_ns = 2000000000LL;
     int stall = 0;
+    // two of each, so that the next quantum is issued while the last one runs
     cudaStream_t pk_stream = nullptr;
-    cudaEvent_t pk_ev = nullptr;
-    PackReq *d_req = nullptr, *h_req = nullptr;
-    int *d_idx = nullptr, *h_idx = nullptr;      // offA, offB (max_active + 1 each), nsteps (max_active)
-    unsigned *d_counters = nullptr, *d_status = nullptr, *h_status = nullptr;
-    int pk_rounds_max = 0;
-    std::map<std::tuple<int, int, size_t>, cudaGraphExec_t> graphs;
-    std::vector<std::pair<Req *, int>> pk_inflight;   // requests of the quantum in flight, their steps
+    cudaEvent_t pk_ev[2] = {nullptr, nullptr};
+    PackReq *d_req[2] = {nullptr, nullptr}, *h_req[2] = {nullptr, nullptr};
+    int *d_idx[2] = {nullptr, nullptr}, *h_idx[2] = {nullptr, nullptr};   // offA, offB, nsteps
+    unsigned *d_counters[2] = {nullptr, nullptr}, *d_status[2] = {nullptr, nullptr};
+    unsigned *h_status[2] = {nullptr, nullptr};
+    std::map<std::tuple<int, int, size_t, int>, cudaGraphExec_t> graphs;   // (rounds, grid, smem, buffer)
+    struct PkQuantum {
+        int buf;
+        std::vector<std::pair<Req *, int>> list;   // requests and their steps
+    };
+    std::deque<PkQuantum> pk_q;                    // in flight, oldest first (at most 2)
     // measured (tile_log2, pair_threads) of the requests on their own streams, by
     // dimension, horizon, model, precision, state, integrator and size class
     // (log2 of the points), measured once per class with pd_tune
@@ -366,10 +372,8 @@ void pd_server::run()
         bool progressed = false;
         for (size_t i = 0; i < active.size();) {
             Req *r = active[i];
-            if (std::any_of(pk_inflight.begin(), pk_inflight.end(), [r](const std::pair<Req *, int> &x) {
-                    return x.first == r;
-                })) {
-                ++i;                                        // in the packed quantum in flight
+            if (r->pk_pending > 0) {
+                ++i;                                        // in a packed quantum in flight
                 continue;
             }
             if (r->inflight) {
@@ -420,16 +424,17 @@ int pd_server::pk_init()
 {
     const int n = max_active;
     PD_CUDA(cudaStreamCreateWithFlags(&pk_stream, cudaStreamNonBlocking));
-    PD_CUDA(cudaEventCreateWithFlags(&pk_ev, cudaEventDisableTiming));
-    PD_CUDA(cudaMalloc(&d_req, sizeof(PackReq) * n));
-    PD_CUDA(cudaMallocHost(&h_req, sizeof(PackReq) * n));
-    PD_CUDA(cudaMalloc(&d_idx, sizeof(int) * (3 * n + 2)));
-    PD_CUDA(cudaMallocHost(&h_idx, sizeof(int) * (3 * n + 2)));
-    pk_rounds_max = quantum;
-    PD_CUDA(cudaMalloc(&d_counters, sizeof(unsigned) * pk_rounds_max));
-    PD_CUDA(cudaMalloc(&d_status, sizeof(unsigned) * 4));
-    PD_CUDA(cudaMallocHost(&h_status, sizeof(unsigned) * 4));
-    memset(h_status, 0, sizeof(unsigned) * 4);
+    for (int k = 0; k < 2; ++k) {
+        PD_CUDA(cudaEventCreateWithFlags(&pk_ev[k], cudaEventDisableTiming));
+        PD_CUDA(cudaMalloc(&d_req[k], sizeof(PackReq) * n));
+        PD_CUDA(cudaMallocHost(&h_req[k], sizeof(PackReq) * n));
+        PD_CUDA(cudaMalloc(&d_idx[k], sizeof(int) * (3 * n + 2)));
+        PD_CUDA(cudaMallocHost(&h_idx[k], sizeof(int) * (3 * n + 2)));
+        PD_CUDA(cudaMalloc(&d_counters[k], sizeof(unsigned) * quantum));
+        PD_CUDA(cudaMalloc(&d_status[k], sizeof(unsigned) * 4));
+        PD_CUDA(cudaMallocHost(&h_status[k], sizeof(unsigned) * 4));
+        memset(h_status[k], 0, sizeof(unsigned) * 4);
+    }
     return PD_OK;
 }
 
@@ -438,42 +443,51 @@ void pd_server::pk_free()
     if (pk_stream) cudaStreamSynchronize(pk_stream);
     for (auto &g : graphs) cudaGraphExecDestroy(g.second);
     graphs.clear();
-    cudaFree(d_req);
-    cudaFreeHost(h_req);
-    cudaFree(d_idx);
-    cudaFreeHost(h_idx);
-    cudaFree(d_counters);
-    cudaFree(d_status);
-    cudaFreeHost(h_status);
-    if (pk_ev) cudaEventDestroy(pk_ev);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(d_req[k]);
+        cudaFreeHost(h_req[k]);
+        cudaFree(d_idx[k]);
+        cudaFreeHost(h_idx[k]);
+        cudaFree(d_counters[k]);
+        cudaFree(d_status[k]);
+        cudaFreeHost(h_status[k]);
+        if (pk_ev[k]) cudaEventDestroy(pk_ev[k]);
+    }
     if (pk_stream) cudaStreamDestroy(pk_stream);
 }
 
-// The next packed quantum: every packed request that is not cancelled, failed or
-// done takes part with min(quantum, steps left) steps. Requests are sorted by
-// their step count (descending), so that those still stepping in round s are a
-// prefix of the table; entries past the last request have no steps. The rounds
-// are replayed from a captured graph (memsets of the counters and status, the
-// round launches, the status read-back), cached by (rounds, grid, shared memory).
+// The next packed quantum, issued while the one before it may still run (two
+// in flight at most, in two sets of buffers): every packed request that is not
+// cancelled, failed or done takes part with min(quantum, steps left after the
+// quantum in flight) steps, and its simulation's bookkeeping (staging parity,
+// step count) advances now, at issue. Requests are sorted by their step count
+// (descending), so that those still stepping in round s are a prefix of the
+// table; entries past the last request have no steps. The rounds are replayed
+// from a captured graph (memsets of the counters and status, the round
+// launches, the status read-back), cached by (rounds, grid, shared memory,
+// buffer set).
 int pd_server::pk_issue(std::vector<Req *> &active)
 {
-    if (!pk_inflight.empty()) return PD_OK;
+    if (pk_q.size() >= 2) return PD_OK;
+    const int buf = pk_q.empty() ? 0 : 1 - pk_q.back().buf;
     std::vector<std::pair<Req *, int>> list;
     {
         std::lock_guard<std::mutex> lk(mu);
-        for (Req *r : active)
-            if (r->packed && !r->cancel && r->res.error == PD_OK && r->res.steps_done < r->nsteps)
-                list.emplace_back(r, (int)std::min<int64_t>(quantum, r->nsteps - r->res.steps_done));
+        for (Req *r : active) {
+            const int64_t left = r->nsteps - r->res.steps_done - r->pk_pending;
+            if (r->packed && !r->cancel && r->res.error == PD_OK && left > 0)
+                list.emplace_back(r, (int)std::min<int64_t>(quantum, left));
+        }
     }
     if (list.empty()) return PD_OK;
     std::stable_sort(list.begin(), list.end(), [](const std::pair<Req *, int> &x, const std::pair<Req *, int> &y) {
         return x.second > y.second;
     });
     const int n = max_active;
-    int *offA = h_idx, *offB = h_idx + (n + 1), *nst = h_idx + 2 * (n + 1);
+    int *offA = h_idx[buf], *offB = h_idx[buf] + (n + 1), *nst = h_idx[buf] + 2 * (n + 1);
     offA[0] = offB[0] = 0;
     size_t smem = 0;
-    memset(h_req, 0, sizeof(PackReq) * n);
+    memset(h_req[buf], 0, sizeof(PackReq) * n);
     for (int i = 0; i < n; ++i) {
         int na = 0, nb = 0;
         nst[i] = 0;
@@ -482,7 +496,7 @@ int pd_server::pk_issue(std::vector<Req *> &active)
             int rc = sim_pack_info(list[i].first->sim, &pi);
             if (rc != PD_OK) return rc;
             if (!pi.eligible) { set_error("a packed request is no longer eligible"); return PD_ESTATE; }
-            PackReq &q = h_req[i];
+            PackReq &q = h_req[buf][i];
             q.a[0] = pi.a[0];
             q.a[1] = pi.a[1];
             q.kind = pi.kind;
@@ -508,27 +522,28 @@ int pd_server::pk_issue(std::vector<Req *> &active)
     if (rc != PD_OK) return rc;
     if (ctas < 1) { set_error("the packed kernel does not fit an SM with %zu bytes of shared memory", smem); return PD_EINVAL; }
     const int grid = ctas * sms;
-    PD_CUDA(cudaMemcpyAsync(d_req, h_req, sizeof(PackReq) * n, cudaMemcpyHostToDevice, pk_stream));
-    PD_CUDA(cudaMemcpyAsync(d_idx, h_idx, sizeof(int) * (3 * n + 2), cudaMemcpyHostToDevice, pk_stream));
-    const auto key = std::make_tuple(rounds, grid, smem);
+    PD_CUDA(cudaMemcpyAsync(d_req[buf], h_req[buf], sizeof(PackReq) * n, cudaMemcpyHostToDevice, pk_stream));
+    PD_CUDA(cudaMemcpyAsync(d_idx[buf], h_idx[buf], sizeof(int) * (3 * n + 2), cudaMemcpyHostToDevice, pk_stream));
+    const auto key = std::make_tuple(rounds, grid, smem, buf);
     auto it = graphs.find(key);
     if (it == graphs.end()) {
         PackTable t;
-        t.req = d_req;
-        t.offA = d_idx;
-        t.offB = d_idx + (n + 1);
-        t.nsteps = d_idx + 2 * (n + 1);
-        t.counters = d_counters;
-        t.status = d_status;
+        t.req = d_req[buf];
+        t.offA = d_idx[buf];
+        t.offB = d_idx[buf] + (n + 1);
+        t.nsteps = d_idx[buf] + 2 * (n + 1);
+        t.counters = d_counters[buf];
+        t.status = d_status[buf];
         t.wait_ns = wait_ns;
         t.nreq = n;
         t.stall = stall;
         PD_CUDA(cudaStreamBeginCapture(pk_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * rounds, pk_stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned) * 4, pk_stream);
+        cudaError_t e = cudaMemsetAsync(d_counters[buf], 0, sizeof(unsigned) * rounds, pk_stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_status[buf], 0, sizeof(unsigned) * 4, pk_stream);
         int lrc = e == cudaSuccess ? pack_launch_rounds(t, rounds, grid, smem, pk_stream) : PD_OK;
         if (e == cudaSuccess && lrc == PD_OK)
-            e = cudaMemcpyAsync(h_status, d_status, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, pk_stream);
+            e = cudaMemcpyAsync(h_status[buf], d_status[buf], sizeof(unsigned) * 4, cudaMemcpyDeviceToHost,
+                                pk_stream);
         cudaGraph_t graph = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(pk_stream, &graph);
         if (e == cudaSuccess) e = ee;
@@ -540,44 +555,54 @@ int pd_server::pk_issue(std::vector<Req *> &active)
         it = graphs.emplace(key, exec).first;
     }
     PD_CUDA(cudaGraphLaunch(it->second, pk_stream));
-    PD_CUDA(cudaEventRecord(pk_ev, pk_stream));
-    pk_inflight = list;
+    PD_CUDA(cudaEventRecord(pk_ev[buf], pk_stream));
+    for (auto &x : list) {
+        sim_pack_advance(x.first->sim, x.second);
+        x.first->pk_pending += x.second;
+    }
+    pk_q.push_back(PkQuantum{buf, list});
     return PD_OK;
 }
 
-// A finished packed quantum: the steps count, or, if a device-side wait ran out,
-// every request of the quantum fails with PD_ETIMEOUT (their states are partly
-// stepped). A test stall applies to the first quantum only.
+// The oldest packed quantum, once finished: its steps count, or, if a
+// device-side wait ran out, every request of the quantum fails with
+// PD_ETIMEOUT (their states are partly stepped). A test stall applies to the
+// first quantum only.
 void pd_server::pk_collect()
 {
-    if (pk_inflight.empty()) return;
-    const cudaError_t q = cudaEventQuery(pk_ev);
-    if (q == cudaErrorNotReady) return;
-    const unsigned code = q == cudaSuccess ? h_status[0] : (unsigned)PACK_OK;
-    char msg[160] = {0};
-    if (q != cudaSuccess) {
-        cuda_fail(q, "packed quantum");
-        pd_last_error(msg, sizeof(msg));
-    } else if (code != PACK_OK) {
-        snprintf(msg, sizeof(msg), "packed kernel: a dilatation wait ran out after %lld ns (table entry %u, tile %u, "
-                 "round %u)", wait_ns, h_status[1], h_status[2], h_status[3]);
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    for (auto &x : pk_inflight) {
-        Req *r = x.first;
-        if (q == cudaSuccess && code == PACK_OK) {
-            sim_pack_advance(r->sim, x.second);
-            r->res.steps_done += x.second;
-        } else {
-            r->res.error = q != cudaSuccess ? PD_ECUDA : PD_ETIMEOUT;
-            strncpy(r->res.message, msg, sizeof(r->res.message) - 1);
+    while (!pk_q.empty()) {
+        PkQuantum &pq = pk_q.front();
+        const cudaError_t q = cudaEventQuery(pk_ev[pq.buf]);
+        if (q == cudaErrorNotReady) return;
+        const unsigned code = q == cudaSuccess ? h_status[pq.buf][0] : (unsigned)PACK_OK;
+        char msg[160] = {0};
+        if (q != cudaSuccess) {
+            cuda_fail(q, "packed quantum");
+            pd_last_error(msg, sizeof(msg));
+        } else if (code != PACK_OK) {
+            const unsigned *st = h_status[pq.buf];
+            snprintf(msg, sizeof(msg), "packed kernel: a dilatation wait ran out after %lld ns (table entry %u, tile "
+                     "%u, round %u)", wait_ns, st[1], st[2], st[3]);
         }
-    }
-    pk_inflight.clear();
-    if (stall) {
-        stall = 0;
-        for (auto &g : graphs) cudaGraphExecDestroy(g.second);
-        graphs.clear();
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto &x : pq.list) {
+                Req *r = x.first;
+                r->pk_pending -= x.second;
+                if (q == cudaSuccess && code == PACK_OK) {
+                    r->res.steps_done += x.second;
+                } else if (r->res.error == PD_OK) {
+                    r->res.error = q != cudaSuccess ? PD_ECUDA : PD_ETIMEOUT;
+                    strncpy(r->res.message, msg, sizeof(r->res.message) - 1);
+                }
+            }
+        }
+        pk_q.pop_front();
+        if (stall) {
+            stall = 0;
+            for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+            graphs.clear();
+        }
     }
 }
 
@@ -651,9 +676,11 @@ int pd_submit(pd_server *s, const pd_request *rq, uint64_t *ticket)
     r->nsteps = rq->nsteps;
     // FP32C PMB without breaking and LPS without partial volume go to the packed
     // kernel, which runs 2^9-point tiles and its own threads per point pair
+    // (LPS up to m = 3: the force pass of a wider horizon would leave the packed
+    // kernel one CTA per SM for every request of the quantum)
     const bool packable = s->mode == PD_SERVE_PACKED && r->run.precision == PD_FP32C &&
                           ((r->mat.model == PD_MODEL_PMB && r->mat.s_c == 0.0) ||
-                           (r->mat.model == PD_MODEL_LPS && !r->mat.vol_corr)) &&
+                           (r->mat.model == PD_MODEL_LPS && !r->mat.vol_corr && r->grid.m <= 3)) &&
                           (r->run.tile_log2 == 0 || r->run.tile_log2 == 9);
     if (packable) {
         const int W = (stencil_size(r->grid.dim, r->grid.m) + 31) / 32;
