@@ -255,14 +255,20 @@ def time_build(pd, torch, wl, stream, reps=3):
     return {"ms": best * 1e3, "bonds": nb, "bonds_per_s": nb / best}
 
 
-def time_implicit(pd, torch, krylov, precision, nx=200, tangent=None, precond=0):
+def time_implicit(pd, torch, krylov, precision, nx=200, tangent=None, precond=0, notch=False):
     """The 200 x 200 clamped plate (left collar u = 0, right collar u_x = 1e-4 W)
     in 10 load steps, one pd_solve_static per step (matrix-free Newton-Krylov,
-    linear rtol 1e-8). Wall time of the whole load path and the iteration counts."""
+    linear rtol 1e-8). Wall time of the whole load path and the iteration counts.
+    notch: the bonds crossing x = (nx/2 - 1/2) h for y in [0, ny/2] h are broken
+    first (a crack across half the plate, normal to the load), so that the
+    points on its faces keep about half their bonds."""
     L = W.plate_static(nx=nx, variant="clamped")
     g, m, r = pd.describe(L.grid, L.mat, precision=precision)
     sim = pd.pd_create(g, m, r)
     pd.pd_build_neighbors(sim)
+    if notch:
+        ny = L.grid.n[1]
+        pd.pd_break_bonds(sim, 0, nx / 2 - 0.5, [0.0, -1.0, -1.0], [0.0, ny / 2, 1.0])
     z = np.zeros((L.grid.npoints, 2))
     pd.pd_set_state(sim, u=z, v=z)
     fp64 = precision == pd.PD_FP64
@@ -398,14 +404,21 @@ def coarse_nodes(wl, k, k0):
     return idx[inside]
 
 
-def convergence_rate(us, wls, ks):
-    """Sec. 5.2.2's rate from three meshes h1 > h2 > h3 (h = delta / k):
-      alpha = (log ||u_1 - u_2|| - log ||u_2 - u_3||) / log 2,
-    ||f||^2 = sum over the coarse nodes in [0, 1]^2 of |f|^2 h_1^2."""
+def convergence_norms(us, wls, ks):
+    """||u_1 - u_2||, ||u_2 - u_3|| and ||u_3|| of three meshes h1 > h2 > h3
+    (h = delta / k), ||f||^2 = sum over the coarse nodes in [0, 1]^2 of |f|^2 h_1^2."""
     h1 = wls[0].grid.h
     cs = [u[coarse_nodes(wl, k, ks[0])] for u, wl, k in zip(us, wls, ks)]
     e12 = math.sqrt(float(((cs[0] - cs[1]) ** 2).sum()) * h1 * h1)
     e23 = math.sqrt(float(((cs[1] - cs[2]) ** 2).sum()) * h1 * h1)
+    n3 = math.sqrt(float((cs[2] ** 2).sum()) * h1 * h1)
+    return e12, e23, n3
+
+
+def convergence_rate(us, wls, ks):
+    """Sec. 5.2.2's rate from three meshes h1 > h2 > h3 (h = delta / k):
+      alpha = (log ||u_1 - u_2|| - log ||u_2 - u_3||) / log 2."""
+    e12, e23, _ = convergence_norms(us, wls, ks)
     return (math.log(e12) - math.log(e23)) / math.log(2.0) if e12 > 0 and e23 > 0 else None
 
 
@@ -422,8 +435,11 @@ def run_convergence(args, pd, torch):
     out = {}
     work = 0
     t_all = time.perf_counter()
+    cases = set(args.conv_cases.split(","))
     for model in (W.NP, W.LP):
         for ic in (1, 2):
+            if "%s_ic%d" % ("np" if model == W.NP else "lp", ic) not in cases:
+                continue
             wls = [W.np_square(k=k, model=model, ic=ic) for k in ks]
             sims = []
             for wl in wls:
@@ -434,6 +450,7 @@ def run_convergence(args, pd, torch):
                 pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val)
                 sims.append(sim)
             rates = {"%s" % (ks[i:i + 3],): [] for i in range(len(ks) - 2)}
+            norms = {"%s" % (ks[i:i + 3],): [] for i in range(len(ks) - 2)}
             times = []
             done = 0
             while done < steps_total:
@@ -446,11 +463,14 @@ def run_convergence(args, pd, torch):
                 for i in range(len(ks) - 2):
                     a = convergence_rate(us[i:i + 3], wls[i:i + 3], ks[i:i + 3])
                     rates["%s" % (ks[i:i + 3],)].append(None if a is None else round(a, 4))
+                    norms["%s" % (ks[i:i + 3],)].append(
+                        ["%.4e" % x for x in convergence_norms(us[i:i + 3], wls[i:i + 3], ks[i:i + 3])])
             for sim in sims:
                 work += pd.pd_bond_count(sim) * steps_total
                 sim.close()
             out["%s_ic%d" % ("np" if model == W.NP else "lp", ic)] = {"t": [round(t, 4) for t in times],
-                                                                       "alpha": rates}
+                                                                       "alpha": rates,
+                                                                       "e12_e23_u3": norms}
     sec = time.perf_counter() - t_all
     line = {"metric": "bond updates/s (2D NP/LP convergence study)", "value": work / sec,
             "unit": "bond-updates/s", "n_gpus": 1, "steps": steps_total, "warmup": 0, "ms_per_step": None,
@@ -782,6 +802,8 @@ def main():
     ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
     ap.add_argument("--conv-meshes", default="2,4,8", help="convergence: refinements k (h = delta / k)")
     ap.add_argument("--conv-precision", default="fp32c", choices=["fp32c", "fp64"])
+    ap.add_argument("--conv-cases", default="np_ic1,np_ic2,lp_ic1,lp_ic2",
+                    help="convergence: the (law, initial condition) cases to run")
     ap.add_argument("--requests", type=int, default=512, help="serve: requests in the mix")
     ap.add_argument("--load", type=float, default=2.0, help="serve: offered load / one-at-a-time capacity")
     ap.add_argument("--max-active", type=int, default=16, help="serve: concurrent simulations")
@@ -885,7 +907,15 @@ def main():
                 "cg_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64),
                 "pcg_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64,
                                                        precond=pd.PD_PRECOND_BLOCK_JACOBI),
-                "cg_fp32c": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP32C)}
+                "cg_fp32c": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP32C),
+                "notched": {
+                    "workload": "the same plate with a crack across half its height at mid-span",
+                    "gmres50_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64, notch=True),
+                    "gmres50_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_GMRES, pd.PD_FP64,
+                                                               precond=pd.PD_PRECOND_BLOCK_JACOBI, notch=True),
+                    "cg_fp64": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64, notch=True),
+                    "pcg_fp64_block_jacobi": time_implicit(pd, torch, pd.PD_KRYLOV_CG, pd.PD_FP64,
+                                                           precond=pd.PD_PRECOND_BLOCK_JACOBI, notch=True)}}
             line["serve"] = serving_side(pd, torch)
 
     line["clocks"] = clk.summary()

@@ -89,6 +89,16 @@ __device__ bool wait_dil(const PackTable &t, const PackReq &q, int r, int tile, 
     return true;
 }
 
+// The bodies as separate functions: each gets its own register allocation
+// within the kernel's 64 registers (inlined into one kernel, the six bodies
+// and the item loop spilled 216 bytes per thread; apart, at most 40).
+static __device__ __noinline__ void pk_lps_dil(const TileArgs &a, int tile) { lps_dil_h2_body<false, false>(a, tile, nullptr); }
+static __device__ __noinline__ void pk_lps_force(const TileArgs &a, int tile) { lps_force_fast_body<false, false>(a, tile, nullptr); }
+static __device__ __noinline__ void pk_pmb3s(const TileArgs &a, int tile) { pmb_fast_body<3, false, true, false>(a, tile, nullptr); }
+static __device__ __noinline__ void pk_pmb3(const TileArgs &a, int tile) { pmb_fast_body<3, false, false, false>(a, tile, nullptr); }
+static __device__ __noinline__ void pk_pmb2s(const TileArgs &a, int tile) { pmb_fast_body<2, false, true, false>(a, tile, nullptr); }
+static __device__ __noinline__ void pk_pmb2(const TileArgs &a, int tile) { pmb_fast_body<2, false, false, false>(a, tile, nullptr); }
+
 __global__ void __launch_bounds__(PACK_THREADS, 2) pd_packed_round(const __grid_constant__ PackTable t, int round)
 {
     __shared__ TileArgs s_a;
@@ -139,14 +149,14 @@ __global__ void __launch_bounds__(PACK_THREADS, 2) pd_packed_round(const __grid_
         __syncthreads();
         const int kind = q.kind, split = q.split;
         if (kind == PK_LPS) {
-            if (grp == 0) lps_dil_h2_body<false, false>(s_a, tile, nullptr);
-            else lps_force_fast_body<false, false>(s_a, tile, nullptr);
+            if (grp == 0) pk_lps_dil(s_a, tile);
+            else pk_lps_force(s_a, tile);
         } else if (kind == PK_PMB3) {
-            if (split == 2) pmb_fast_body<3, false, true, false>(s_a, tile, nullptr);
-            else pmb_fast_body<3, false, false, false>(s_a, tile, nullptr);
+            if (split == 2) pk_pmb3s(s_a, tile);
+            else pk_pmb3(s_a, tile);
         } else {
-            if (split == 2) pmb_fast_body<2, false, true, false>(s_a, tile, nullptr);
-            else pmb_fast_body<2, false, false, false>(s_a, tile, nullptr);
+            if (split == 2) pk_pmb2s(s_a, tile);
+            else pk_pmb2(s_a, tile);
         }
         __syncthreads();
         if (kind == PK_LPS && grp == 0 && threadIdx.x == 0) {
