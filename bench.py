@@ -358,7 +358,11 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
         res = [pd.pd_wait(srv, t, timeout_s=3600.0) for t in tickets]
     srv.close()
     ok = all(x["state"] == pd.PD_REQ_DONE for x in res)
-    work = rank_reduce(torch, float(sum(x["bonds"] * r.steps for x, r in zip(res, mix))), "sum", "cuda")
+    failed = [{"request": i, "state": x["state"], "error": x["error"], "message": x["message"],
+               "steps_done": x["steps_done"]} for i, x in enumerate(res) if x["state"] != pd.PD_REQ_DONE]
+    # the work done: requests that did not finish count with the steps they took
+    work = rank_reduce(torch, float(sum(x["bonds"] * (r.steps if x["state"] == pd.PD_REQ_DONE else x["steps_done"])
+                                        for x, r in zip(res, mix))), "sum", "cuda")
     makespan = rank_reduce(torch, max(x["end_s"] for x in res) - min(x["submit_s"] for x in res), "max", "cuda")
     lat = np.array([x["end_s"] - x["submit_s"] for x in res])
     if world > 1:
@@ -381,7 +385,7 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
                        "max_active": args.max_active, "quantum_steps": args.quantum,
                        "mode": getattr(args, "serve_mode", "packed"),
                        "l2": "not flushed (independent simulations stream through it)"},
-            "all_done": ok, "latency_p50_s": float(np.percentile(lat, 50)),
+            "all_done": ok, "failed": failed[:8], "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
             "offered_rate_per_s": rate, "bond_updates": work,
             "serial": {"requests": k, "value": serial_work / serial_s, "unit": "bond-updates/s",
@@ -783,7 +787,7 @@ def serving_side(pd, torch, requests=128, load=2.0, max_active=16, quantum=64):
             out = r
         else:
             out["streams_mode"] = {k: r[k] for k in ("value", "latency_p50_s", "latency_p99_s", "makespan_s",
-                                                     "all_done", "serial")}
+                                                     "all_done", "failed", "serial")}
     return out
 
 

@@ -61,92 +61,116 @@ __device__ __forceinline__ int find_req(const int *off, int n, int i)
     return lo;
 }
 
-// Wait (thread 0 of the CTA) until the 27 neighbour tiles of `tile` have
-// finished this round's dilatation. Bounded: after t.wait_ns (or once another
-// CTA has reported a failure) it records the failure in t.status and returns
-// false. With stall, it waits for a flag value that nothing writes (tests).
+// Wait (warp 0 of the CTA, lane k polling neighbour k) until the 27 neighbour
+// tiles of `tile` have finished this round's dilatation: one round trip per
+// poll instead of 27 in a row. Bounded: after t.wait_ns (or once another CTA has
+// reported a failure) lane 0 records the failure in t.status and the warp
+// returns false. With stall, it waits for a flag value that nothing writes
+// (tests).
 __device__ bool wait_dil(const PackTable &t, const PackReq &q, int r, int tile, int round, bool stall)
 {
+    const unsigned lane = threadIdx.x & 31u;
     const unsigned want = stall ? 0xffffffffu : (unsigned)(q.step0 + round + 1);
-    const int *nbr = q.a[0].tile_nbr + 27 * (size_t)tile;
+    const int n = lane < 27u ? __ldg(&q.a[0].tile_nbr[27 * (size_t)tile + lane]) : -1;
     const long long t0 = globaltimer_ns();
-    for (int k = 0; k < 27; ++k) {
-        const int n = __ldg(&nbr[k]);
-        if (n < 0) continue;
-        while (ld_acquire_u32(q.dil_done + n) < want) {
-            if (*(volatile unsigned *)t.status != PACK_OK) return false;
-            if (globaltimer_ns() - t0 > t.wait_ns) {
+    for (;;) {
+        const bool ok = n < 0 || ld_acquire_u32(q.dil_done + n) >= want;
+        if (__all_sync(0xffffffffu, ok)) return true;
+        int fail = 0;
+        if (lane == 0) {
+            if (*(volatile unsigned *)t.status != PACK_OK) {
+                fail = 1;
+            } else if (globaltimer_ns() - t0 > t.wait_ns) {
                 if (atomicCAS(t.status, (unsigned)PACK_OK, (unsigned)PACK_TIMEOUT) == (unsigned)PACK_OK) {
                     t.status[1] = (unsigned)r;
                     t.status[2] = (unsigned)tile;
                     t.status[3] = (unsigned)round;
                 }
-                return false;
+                fail = 1;
             }
-            __nanosleep(128);
         }
+        if (__shfl_sync(0xffffffffu, fail, 0)) return false;
+        __nanosleep(128);
     }
-    return true;
 }
 
-// The bodies as separate functions: each gets its own register allocation
-// within the kernel's 64 registers (inlined into one kernel, the six bodies
-// and the item loop spilled 216 bytes per thread; apart, at most 40).
-static __device__ __noinline__ void pk_lps_dil(const TileArgs &a, int tile) { lps_dil_h2_body<false, false>(a, tile, nullptr); }
-static __device__ __noinline__ void pk_lps_force(const TileArgs &a, int tile) { lps_force_fast_body<false, false>(a, tile, nullptr); }
-static __device__ __noinline__ void pk_pmb3s(const TileArgs &a, int tile) { pmb_fast_body<3, false, true, false>(a, tile, nullptr); }
-static __device__ __noinline__ void pk_pmb3(const TileArgs &a, int tile) { pmb_fast_body<3, false, false, false>(a, tile, nullptr); }
-static __device__ __noinline__ void pk_pmb2s(const TileArgs &a, int tile) { pmb_fast_body<2, false, true, false>(a, tile, nullptr); }
-static __device__ __noinline__ void pk_pmb2(const TileArgs &a, int tile) { pmb_fast_body<2, false, false, false>(a, tile, nullptr); }
+// The bodies, inlined into the kernel. (As separate functions each would get
+// its own register allocation, 216 bytes of spills per thread down to at most
+// 40, but the request mix measured slower that way: 2.38e11 against 2.47e11
+// bond updates/s.)
+static __device__ __forceinline__ void pk_lps_dil(const TileArgs &a, int tile) { lps_dil_h2_body<false, false>(a, tile, nullptr); }
+static __device__ __forceinline__ void pk_lps_force(const TileArgs &a, int tile) { lps_force_fast_body<false, false>(a, tile, nullptr); }
+static __device__ __forceinline__ void pk_pmb3s(const TileArgs &a, int tile) { pmb_fast_body<3, false, true, false>(a, tile, nullptr); }
+static __device__ __forceinline__ void pk_pmb3(const TileArgs &a, int tile) { pmb_fast_body<3, false, false, false>(a, tile, nullptr); }
+static __device__ __forceinline__ void pk_pmb2s(const TileArgs &a, int tile) { pmb_fast_body<2, false, true, false>(a, tile, nullptr); }
+static __device__ __forceinline__ void pk_pmb2(const TileArgs &a, int tile) { pmb_fast_body<2, false, false, false>(a, tile, nullptr); }
 
 __global__ void __launch_bounds__(PACK_THREADS, 2) pd_packed_round(const __grid_constant__ PackTable t, int round)
 {
     __shared__ TileArgs s_a;
     __shared__ int s_item[4];               // request, tile, group, stop
+    __shared__ int s_have;                  // the request whose arguments s_a holds (-1: none)
+    if (threadIdx.x == 0) s_have = -1;      // published by the claim loop's first barrier
     const int A = active_count(t.nsteps, t.nreq, round);
     const int nA = __ldg(&t.offA[A]), nB = __ldg(&t.offB[A]);
     for (;;) {
-        if (threadIdx.x == 0) {
-            int r = 0, tile = 0, grp = 0, stop = 0;
-            if (*(volatile unsigned *)t.status != PACK_OK) {
-                stop = 1;
-            } else {
-                const int i = (int)atomicAdd(&t.counters[round], 1u);
-                if (i >= nA + nB) {
+        if (threadIdx.x < 32) {
+            // lane 0 claims the next item; warp 0 waits for a force item's inputs
+            int r = 0, tile = 0, grp = 0, stop = 0, stall = 0;
+            if (threadIdx.x == 0) {
+                if (*(volatile unsigned *)t.status != PACK_OK) {
                     stop = 1;
-                } else if (i < nA) {
-                    r = find_req(t.offA, A, i);
-                    tile = i - __ldg(&t.offA[r]);
                 } else {
-                    const int j = i - nA;
-                    r = find_req(t.offB, A, j);
-                    tile = j - __ldg(&t.offB[r]);
-                    grp = 1;
-                    if (!wait_dil(t, t.req[r], r, tile, round, t.stall && round == 0 && j == 0)) stop = 1;
+                    const int i = (int)atomicAdd(&t.counters[round], 1u);
+                    if (i >= nA + nB) {
+                        stop = 1;
+                    } else if (i < nA) {
+                        r = find_req(t.offA, A, i);
+                        tile = i - __ldg(&t.offA[r]);
+                    } else {
+                        const int j = i - nA;
+                        r = find_req(t.offB, A, j);
+                        tile = j - __ldg(&t.offB[r]);
+                        grp = 1;
+                        stall = t.stall && round == 0 && j == 0;
+                    }
                 }
             }
-            s_item[0] = r;
-            s_item[1] = tile;
-            s_item[2] = grp;
-            s_item[3] = stop;
+            r = __shfl_sync(0xffffffffu, r, 0);
+            tile = __shfl_sync(0xffffffffu, tile, 0);
+            grp = __shfl_sync(0xffffffffu, grp, 0);
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            stall = __shfl_sync(0xffffffffu, stall, 0);
+            if (!stop && grp && !wait_dil(t, t.req[r], r, tile, round, stall != 0)) stop = 1;
+            if (threadIdx.x == 0) {
+                s_item[0] = r;
+                s_item[1] = tile;
+                s_item[2] = grp;
+                s_item[3] = stop;
+            }
         }
         __syncthreads();
         if (s_item[3]) break;
         const int r = s_item[0], tile = s_item[1], grp = s_item[2];
         const PackReq &q = t.req[r];
         const int cur = q.cur0 ^ (round & 1);
-        {
+        if (s_have != r) {
+            // the request's arguments of this round (the same for all its items of
+            // the launch: copied once per run of items of one request)
             const int *src = reinterpret_cast<const int *>(&q.a[cur]);
             int *dst = reinterpret_cast<int *>(&s_a);
             for (int k = threadIdx.x; k < (int)(sizeof(TileArgs) / sizeof(int)); k += blockDim.x)
                 dst[k] = __ldg(&src[k]);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (round == 0) {
+                    s_a.v_is_half = q.vhalf0;
+                    s_a.cd = q.cd0;
+                }
+                s_have = r;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && round == 0) {
-            s_a.v_is_half = q.vhalf0;
-            s_a.cd = q.cd0;
-        }
-        __syncthreads();
         const int kind = q.kind, split = q.split;
         if (kind == PK_LPS) {
             if (grp == 0) pk_lps_dil(s_a, tile);
