@@ -331,7 +331,9 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     args.load x that capacity, max_active concurrent simulations. With N ranks
     each serves its round-robin share of the mix (arrivals at N x the rate of
     one rank's share), with no collective until the totals are combined."""
-    mix = shard(W.serving_mix(count=args.requests), rank, world)
+    sides = getattr(args, "serve_sides", "40,20,96").split(",")
+    mix = shard(W.serving_mix(count=args.requests, side_median=float(sides[0]), side_lo=int(sides[1]),
+                              side_hi=int(sides[2])), rank, world)
     k = min(args.serial_sample, len(mix))
     mode = pd.PD_SERVE_STREAMS if getattr(args, "serve_mode", "packed") == "streams" else pd.PD_SERVE_PACKED
     # one at a time: every request alone, with the simulation's own kernels
@@ -346,7 +348,8 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     # the shard holds every world-th arrival of the global process, so the global
     # rate world x load x capacity offers each rank load x its own capacity
     rate = world * args.load * capacity
-    srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum, mode=mode)
+    srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum, mode=mode,
+                    pack_max_tiles=getattr(args, "pack_max_tiles", 0))
     with Clocks(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         tickets = []
@@ -378,12 +381,14 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
             "scaling": "strong" if world > 1 else "weak",
             "vs_baseline": None, "dtype": "f32 bond arithmetic (compensated), f64 integrator state",
             "data": "synthetic",
-            "config": {"workload": "serving_mix: %d requests (2D/3D, PMB/LPS, lognormal sides 20..96, "
-                                   "m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
-                                   "one-at-a-time capacity" % (args.requests, args.load),
+            "config": {"workload": "serving_mix: %d requests (2D/3D, PMB/LPS, lognormal sides of median %s "
+                                   "in %s..%s, m in {2,3,4}, 100..2000 steps), Poisson arrivals at %.2fx the "
+                                   "one-at-a-time capacity" % (args.requests, sides[0], sides[1], sides[2],
+                                                               args.load),
                        "parallelism": "requests sharded round robin over %d rank(s)" % world,
                        "max_active": args.max_active, "quantum_steps": args.quantum,
                        "mode": getattr(args, "serve_mode", "packed"),
+                       "pack_max_tiles": getattr(args, "pack_max_tiles", 0),
                        "l2": "not flushed (independent simulations stream through it)"},
             "all_done": ok, "failed": failed[:8], "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
@@ -394,6 +399,24 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     if emit:
         print(json.dumps(line), flush=True)
     return line
+
+
+def serve_single(pd, mode, steps, quantum, nside=128):
+    """One 128^3 LPS request (the headline workload) alone through the request
+    server in `mode`: the wall time of a request of `quantum` steps and of one of
+    quantum + steps steps, the difference giving the time per step in that mode
+    (admission, setup and the result's copy cancel out)."""
+    wl = W.block3d_lps(nside=nside)
+    secs = []
+    for n in (quantum, quantum + steps):
+        srv = pd.Server(max_active=1, quantum_steps=quantum, mode=mode)
+        g, m, r = pd.describe(wl.grid, wl.mat, precision=pd.PD_FP32C, tile_log2=9)
+        res = pd.pd_wait(srv, pd.pd_submit(srv, g, m, r, n, u0=wl.u0), timeout_s=600.0)
+        srv.close()
+        if res["state"] != pd.PD_REQ_DONE:
+            raise RuntimeError("request failed: %s" % res["message"])
+        secs.append(res["end_s"] - res["start_s"])
+    return {"ms_per_step": 1e3 * (secs[1] - secs[0]) / steps, "steps": steps, "quantum_steps": quantum}
 
 
 def coarse_nodes(wl, k, k0):
@@ -781,13 +804,16 @@ def serving_side(pd, torch, requests=128, load=2.0, max_active=16, quantum=64):
     for mode in ("packed", "streams"):
         a = A()
         a.requests, a.load, a.max_active, a.quantum, a.serial_sample = requests, load, max_active, quantum, 12
-        a.serve_mode = mode
+        a.serve_mode, a.pack_max_tiles, a.serve_sides = mode, 0, "40,20,96"
         r = run_serving(a, pd, torch, 0, 1, emit=False)
         if out is None:
             out = r
         else:
             out["streams_mode"] = {k: r[k] for k in ("value", "latency_p50_s", "latency_p99_s", "makespan_s",
                                                      "all_done", "failed", "serial")}
+    # the 128^3 LPS workload alone through the server, in both modes
+    out["single_lps128"] = {"packed": serve_single(pd, pd.PD_SERVE_PACKED, 384, 64),
+                            "streams": serve_single(pd, pd.PD_SERVE_STREAMS, 384, 64)}
     return out
 
 
@@ -802,7 +828,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lps128",
-                    choices=["lps128", "block64", "block256", "plate50", "paper443", "serve", "convergence"])
+                    choices=["lps128", "block64", "block256", "plate50", "paper443", "serve", "serve1",
+                             "convergence"])
     ap.add_argument("--conv-steps", type=int, default=200000, help="convergence: steps (dt = 1e-5)")
     ap.add_argument("--conv-meshes", default="2,4,8", help="convergence: refinements k (h = delta / k)")
     ap.add_argument("--conv-precision", default="fp32c", choices=["fp32c", "fp64"])
@@ -815,6 +842,11 @@ def main():
     ap.add_argument("--quantum", type=int, default=64, help="serve: steps per scheduling quantum")
     ap.add_argument("--serve-mode", default="packed", choices=["packed", "streams"],
                     help="serve: the packed kernel, or every request on its own stream")
+    ap.add_argument("--pack-max-tiles", type=int, default=0,
+                    help="serve, packed mode: larger requests (in 512-point tiles) run on their own stream; "
+                         "0 = no limit (every eligible request is packed)")
+    ap.add_argument("--serve-sides", default="40,20,96",
+                    help="serve: median, smallest and largest side per axis of the mix's lattices")
     ap.add_argument("--tile-log2", type=int, default=None,
                     help="tile size 2^N of the timed simulation (6..9; 0 = library default); "
                          "by default pd_tune_tile measures and picks it")
@@ -846,6 +878,15 @@ def main():
     if args.workload == "convergence":
         if rank == 0:
             run_convergence(args, pd, torch)
+        return
+    if args.workload == "serve1":
+        # the 128^3 LPS workload alone through the request server (per-step time of
+        # the packed kernel or of the simulation's own kernels on its stream)
+        if rank == 0:
+            mode = pd.PD_SERVE_STREAMS if args.serve_mode == "streams" else pd.PD_SERVE_PACKED
+            r = serve_single(pd, mode, args.steps, args.quantum)
+            print(json.dumps({"workload": "128^3 LPS request alone through the server", "mode": args.serve_mode,
+                              **r}), flush=True)
         return
 
     wl, desc = workload(args.workload)

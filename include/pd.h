@@ -420,7 +420,11 @@ typedef struct {
     int32_t test_stall;       /* tests only, else 0: in the server's first packed
                                  quantum the first LPS force item waits for a flag
                                  that nothing sets, so that its wait runs out */
-    int32_t reserved;         /* must be 0 */
+    int32_t pack_max_tiles;   /* PD_SERVE_PACKED: a request of more than this many
+                                 512-point tiles runs on its own stream with the
+                                 simulation's own kernels, the smaller ones are
+                                 packed; 0 = no limit (every eligible request is
+                                 packed), >= 0 */
 } pd_server_opts;
 
 typedef struct {

@@ -422,8 +422,8 @@ int build_csr(const Geom &g, const Tables &t, BuildOut *out, uint32_t *mask, cud
         cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st);
         cudaMemsetAsync(err, 0, sizeof(int), st);
         cudaMemsetAsync(mask, 0, sizeof(uint32_t) * (size_t)g.W * g.nslots, st);
-        PD_CUDA(cudaFuncSetAttribute(k_cell_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PD_CUDA(cudaFuncSetAttribute(k_cell_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(k_cell_rows<false>, smem));
+        PD_CUDA(smem_limit(k_cell_rows<true>, smem));
         k_rank_coords<<<nb, 256, 0, st>>>(g, t.tile_org, t.slot_of_rank, crd);
         k_cell_count<<<nb, 256, 0, st>>>(g, cg, crd, cell_count);
         rc = exclusive_scan(cell_count, ncell, cell_start, st);

@@ -174,18 +174,18 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
             auto k = dil ? (dil2 ? (a.vol_corr ? lps_dil_fast2_pt<true> : lps_dil_fast2_pt<false>)
                                  : (a.vol_corr ? lps_dil_fast_pt<true> : lps_dil_fast_pt<false>))
                          : (a.vol_corr ? lps_force_fast_pt<true> : lps_force_fast_pt<false>);
-            PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            PD_CUDA(smem_limit(k, smem));
             k<<<g.ntiles, threads, smem, st>>>(a, tp);
         } else {
             auto k = dil ? (dil2 ? (a.vol_corr ? lps_dil_fast2<true> : lps_dil_fast2<false>)
                                  : (a.vol_corr ? lps_dil_fast<true> : lps_dil_fast<false>))
                          : (a.vol_corr ? lps_force_fast<true> : lps_force_fast<false>);
-            PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            PD_CUDA(smem_limit(k, smem));
             k<<<g.ntiles, threads, smem, st>>>(a);
         }
     } else {
         auto k = dil ? lps_dil_generic<double> : lps_force_generic<double>;
-        PD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(k, smem));
         k<<<g.ntiles, 256, smem, st>>>(a);
     }
     PD_CUDA(cudaGetLastError());

@@ -405,12 +405,10 @@ static int launch_fast_split(const TileArgs &a, cudaStream_t st)
     const size_t smem = split_smem(a.g, pmb_fast_smem(a.g), a.split);
     static thread_local ParamTab tp;
     if (param_table(a.htab_a, a.ntab_a, a.g.ntiles, tp)) {
-        PD_CUDA(cudaFuncSetAttribute(pmb_fast_pt<DIM, BRK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+        PD_CUDA(smem_limit(pmb_fast_pt<DIM, BRK, SPLIT>, smem));
         pmb_fast_pt<DIM, BRK, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a, tp);
     } else {
-        PD_CUDA(cudaFuncSetAttribute(pmb_fast<DIM, BRK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+        PD_CUDA(smem_limit(pmb_fast<DIM, BRK, SPLIT>, smem));
         pmb_fast<DIM, BRK, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a);
     }
     PD_CUDA(cudaGetLastError());
@@ -445,8 +443,7 @@ template <int DIM, bool LINEAR, bool SPLIT>
 static int launch_np_split(const TileArgs &a, cudaStream_t st)
 {
     const size_t smem = split_smem(a.g, np_fast_smem(a.g), a.split);
-    PD_CUDA(cudaFuncSetAttribute(np_fast<DIM, LINEAR, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    PD_CUDA(smem_limit(np_fast<DIM, LINEAR, SPLIT>, smem));
     np_fast<DIM, LINEAR, SPLIT><<<a.g.ntiles, a.g.T / 2 * a.split, smem, st>>>(a);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
@@ -456,7 +453,7 @@ template <bool LINEAR>
 static int launch_np_fast2(const TileArgs &a, cudaStream_t st)
 {
     const size_t smem = split_smem(a.g, np_fast_smem(a.g), a.split);
-    PD_CUDA(cudaFuncSetAttribute(np_fast2<LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PD_CUDA(smem_limit(np_fast2<LINEAR>, smem));
     np_fast2<LINEAR><<<a.g.ntiles, a.g.T / 4 * a.split, smem, st>>>(a);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
@@ -490,7 +487,7 @@ int launch_pmb_args(const TileArgs &a, int precision, cudaStream_t st)
         return brk ? launch_fast<2, true>(a, st) : launch_fast<2, false>(a, st);
     }
     const size_t smem = pmb_generic_smem(g, precision);
-    PD_CUDA(cudaFuncSetAttribute(pmb_generic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PD_CUDA(smem_limit(pmb_generic<double>, smem));
     pmb_generic<double><<<g.ntiles, 256, smem, st>>>(a);
     PD_CUDA(cudaGetLastError());
     return PD_OK;

@@ -34,6 +34,19 @@ int cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::pdk::cuda_fail(e_, #call);  \
     } while (0)
 
+// A kernel's dynamic shared-memory limit (cudaFuncAttributeMaxDynamicSharedMemorySize)
+// is one value per kernel and device, shared by every host thread: one thread
+// lowering it between another's setting and launch would fail that launch
+// ("too many resources requested for launch"; the request server's setup and
+// worker threads launch the same kernels with different sizes). So the limit
+// is only ever raised, under a lock (pd_mem.cu), to at least `bytes`.
+cudaError_t raise_smem_limit(const void *func, size_t bytes);
+template <class F>
+inline cudaError_t smem_limit(F *func, size_t bytes)
+{
+    return raise_smem_limit(reinterpret_cast<const void *>(func), bytes);
+}
+
 // ------------------------------------------------------------------- Morton
 
 // Bit b of coordinate a goes to bit DIM*b + a of the code (x least significant).

@@ -108,10 +108,10 @@ int launch_jvp_args(const TileArgs &a, int precision, cudaStream_t st)
 {
     const size_t smem = jvp_smem(a.g, precision);
     if (precision == PD_FP64) {
-        PD_CUDA(cudaFuncSetAttribute(jvp_generic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(jvp_generic<double>, smem));
         jvp_generic<double><<<a.g.ntiles, 256, smem, st>>>(a);
     } else {
-        PD_CUDA(cudaFuncSetAttribute(jvp_generic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(jvp_generic<float>, smem));
         jvp_generic<float><<<a.g.ntiles, 256, smem, st>>>(a);
     }
     PD_CUDA(cudaGetLastError());

@@ -9,7 +9,9 @@
 // only when no work on another stream still uses p.
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "pd_internal.cuh"
 
@@ -53,5 +55,21 @@ cudaError_t lib_malloc(void **p, size_t bytes, cudaStream_t st)
 }
 
 cudaError_t lib_free(void *p, cudaStream_t st) { return p ? cudaFreeAsync(p, st) : cudaSuccess; }
+
+
+cudaError_t raise_smem_limit(const void *func, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[std::make_pair(dev, func)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 }  // namespace pdk

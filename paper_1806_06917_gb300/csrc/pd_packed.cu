@@ -208,7 +208,7 @@ int pack_occupancy(size_t smem, int *ctas_per_sm)
         set_error("packed kernel: %zu bytes of shared memory requested, %d available", smem, dyn_max);
         return PD_EINVAL;
     }
-    PD_CUDA(cudaFuncSetAttribute(pd_packed_round, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    PD_CUDA(smem_limit(pd_packed_round, dyn_max));
     PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, pd_packed_round, PACK_THREADS, smem));
     return PD_OK;
 }

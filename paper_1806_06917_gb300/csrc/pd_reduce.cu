@@ -166,10 +166,10 @@ int launch_energy_points(const TileArgs &a, int precision, double *kin, cudaStre
 {
     const size_t smem = energy_smem(a.g, precision);
     if (precision == PD_FP64) {
-        PD_CUDA(cudaFuncSetAttribute(energy_generic<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(energy_generic<double>, smem));
         energy_generic<double><<<a.g.ntiles, 256, smem, st>>>(a);
     } else {
-        PD_CUDA(cudaFuncSetAttribute(energy_generic<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(energy_generic<float>, smem));
         energy_generic<float><<<a.g.ntiles, 256, smem, st>>>(a);
     }
     PD_CUDA(cudaGetLastError());

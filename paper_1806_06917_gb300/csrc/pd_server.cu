@@ -121,6 +121,7 @@ struct pd_server {
     int mode = PD_SERVE_PACKED;
     long long wait_ns = 2000000000LL;
     int stall = 0;
+    int pack_max_tiles = 0;       // requests of more tiles than this are not packed (0: no limit)
     // two of each, so that the next quantum is issued while the last one runs
     cudaStream_t pk_stream = nullptr;
     cudaEvent_t pk_ev[2] = {nullptr, nullptr};
@@ -619,7 +620,7 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
     if (o.device_bytes < 0) { set_error("device_bytes must be >= 0"); return PD_EINVAL; }
     if (o.mode != PD_SERVE_PACKED && o.mode != PD_SERVE_STREAMS) { set_error("unknown server mode"); return PD_EINVAL; }
     if (o.wait_limit_ms < 0) { set_error("wait_limit_ms must be >= 0"); return PD_EINVAL; }
-    if (o.reserved != 0) { set_error("pd_server_opts.reserved must be 0"); return PD_EINVAL; }
+    if (o.pack_max_tiles < 0) { set_error("pack_max_tiles must be >= 0"); return PD_EINVAL; }
     std::unique_ptr<pd_server> s(new pd_server());
     PD_CUDA(cudaGetDevice(&s->device));
     PD_CUDA(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device));
@@ -631,6 +632,7 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
     s->mode = o.mode;
     s->wait_ns = 1000000LL * (o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000);
     s->stall = o.test_stall ? 1 : 0;
+    s->pack_max_tiles = o.pack_max_tiles;
     if (s->mode == PD_SERVE_PACKED) {
         const int rc = s->pk_init();
         if (rc != PD_OK) {
@@ -678,10 +680,14 @@ int pd_submit(pd_server *s, const pd_request *rq, uint64_t *ticket)
     // kernel, which runs 2^9-point tiles and its own threads per point pair
     // (LPS up to m = 3: the force pass of a wider horizon would leave the packed
     // kernel one CTA per SM for every request of the quantum)
+    // (and only requests below the size limit: a larger one fills the GPU with its
+    // own kernels, which read their stencil table from the constant bank)
+    const long long npts = (long long)r->grid.n[0] * r->grid.n[1] * (r->grid.dim == 3 ? r->grid.n[2] : 1);
     const bool packable = s->mode == PD_SERVE_PACKED && r->run.precision == PD_FP32C &&
                           ((r->mat.model == PD_MODEL_PMB && r->mat.s_c == 0.0) ||
                            (r->mat.model == PD_MODEL_LPS && !r->mat.vol_corr && r->grid.m <= 3)) &&
-                          (r->run.tile_log2 == 0 || r->run.tile_log2 == 9);
+                          (r->run.tile_log2 == 0 || r->run.tile_log2 == 9) &&
+                          (s->pack_max_tiles == 0 || (npts + 511) / 512 <= s->pack_max_tiles);
     if (packable) {
         const int W = (stencil_size(r->grid.dim, r->grid.m) + 31) / 32;
         const int split = r->mat.model == PD_MODEL_PMB ? pack_split_for(W) : 0;

@@ -266,10 +266,10 @@ int launch_tangent_prepare(const TileArgs &a, int precision, void *cache, cudaSt
         return PD_EINVAL;
     }
     if (precision == PD_FP64) {
-        PD_CUDA(cudaFuncSetAttribute(tangent_prepare<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(tangent_prepare<double>, smem));
         tangent_prepare<double><<<g.ntiles, 256, smem, st>>>(a, static_cast<double *>(cache), nbr);
     } else {
-        PD_CUDA(cudaFuncSetAttribute(tangent_prepare<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PD_CUDA(smem_limit(tangent_prepare<float>, smem));
         tangent_prepare<float><<<g.ntiles, 256, smem, st>>>(a, static_cast<float *>(cache), nbr);
     }
     PD_CUDA(cudaGetLastError());

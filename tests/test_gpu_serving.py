@@ -44,12 +44,18 @@ def _small_mix(count, seed):
                          steps_lo=5, steps_hi=70, m_choices=(2, 3))
 
 
-@pytest.mark.parametrize("mode", ["packed", "streams"])
+@pytest.mark.parametrize("mode", ["packed", "streams", "packed_small_only"])
 def test_served_results_equal_the_same_runs_alone(pd, mode):
+    # packed_small_only: requests of more than 4 tiles run on their own streams
+    # beside the packed kernel, which steps the rest
     mix = _small_mix(10, 21)
     assert {r.grid.dim for r in mix} == {2, 3} and {r.mat.model for r in mix} == {W.PMB, W.LPS}
+    if mode == "packed_small_only":
+        tiles = [(r.grid.npoints + 511) // 512 for r in mix]
+        assert min(tiles) <= 4 < max(tiles)
     srv = pd.Server(max_active=3, quantum_steps=7,        # quanta that do not divide the step counts
-                    mode=pd.PD_SERVE_PACKED if mode == "packed" else pd.PD_SERVE_STREAMS)
+                    mode=pd.PD_SERVE_STREAMS if mode == "streams" else pd.PD_SERVE_PACKED,
+                    pack_max_tiles=4 if mode == "packed_small_only" else 0)
     outs = [(np.full(r.u0.shape, np.nan), np.full(r.u0.shape, np.nan)) for r in mix]
     tickets = [_submit(pd, srv, r, u_out=o[0], v_out=o[1]) for r, o in zip(mix, outs)]
     results = [pd.pd_wait(srv, t, timeout_s=120.0) for t in tickets]

@@ -104,3 +104,11 @@ def test_tune_tile_refuses_bad_arguments(pd):
     with pytest.raises(pd.PdError) as e:
         pd.pd_tune_tile(g, m, r, steps=2)
     assert e.value.code == pd.PD_EINVAL
+
+
+@pytest.mark.parametrize("opt", [dict(max_active=0), dict(max_active=257), dict(quantum_steps=0), dict(mode=7),
+                                 dict(wait_limit_ms=-1), dict(pack_max_tiles=-1), dict(device_bytes=-1)])
+def test_server_options_are_refused_before_any_device_call(pd, opt):
+    with pytest.raises(pd.PdError) as e:
+        pd.Server(**opt)
+    assert e.value.code == pd.PD_EINVAL
