@@ -349,7 +349,9 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
     # rate world x load x capacity offers each rank load x its own capacity
     rate = world * args.load * capacity
     srv = pd.Server(max_active=args.max_active, quantum_steps=args.quantum, mode=mode,
-                    pack_max_tiles=getattr(args, "pack_max_tiles", 0))
+                    pack_max_tiles=getattr(args, "pack_max_tiles", 0),
+                    max_queued=getattr(args, "max_queued", 0))
+    rejected = 0
     with Clocks(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         tickets = []
@@ -357,9 +359,15 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
             delay = t0 + r.arrival / rate - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(_submit_request(pd, srv, r))
-        res = [pd.pd_wait(srv, t, timeout_s=3600.0) for t in tickets]
+            try:
+                tickets.append((r, _submit_request(pd, srv, r)))
+            except pd.PdError as e:                        # back-pressure (max_queued): refused
+                if e.code != pd.PD_EBUSY:
+                    raise
+                rejected += 1
+        res = [pd.pd_wait(srv, t, timeout_s=3600.0) for _, t in tickets]
     srv.close()
+    mix = [r for r, _ in tickets]                          # the accepted requests
     ok = all(x["state"] == pd.PD_REQ_DONE for x in res)
     failed = [{"request": i, "state": x["state"], "error": x["error"], "message": x["message"],
                "steps_done": x["steps_done"]} for i, x in enumerate(res) if x["state"] != pd.PD_REQ_DONE]
@@ -373,6 +381,7 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
         torch.distributed.all_gather_object(parts, lat.tolist())
         lat = np.array([x for part in parts for x in part])
         ok = bool(rank_reduce(torch, 1.0 if ok else 0.0, "sum", "cuda") == world)
+        rejected = int(rank_reduce(torch, float(rejected), "sum", "cuda"))
     if rank != 0:
         return
     line = {"metric": "aggregate bond updates/s (served request mix)", "value": work / makespan,
@@ -389,8 +398,10 @@ def run_serving(args, pd, torch, rank=0, world=1, emit=True):
                        "max_active": args.max_active, "quantum_steps": args.quantum,
                        "mode": getattr(args, "serve_mode", "packed"),
                        "pack_max_tiles": getattr(args, "pack_max_tiles", 0),
+                       "max_queued": getattr(args, "max_queued", 0),
                        "l2": "not flushed (independent simulations stream through it)"},
-            "all_done": ok, "failed": failed[:8], "latency_p50_s": float(np.percentile(lat, 50)),
+            "all_done": ok, "failed": failed[:8], "rejected": rejected,
+            "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "makespan_s": makespan,
             "offered_rate_per_s": rate, "bond_updates": work,
             "serial": {"requests": k, "value": serial_work / serial_s, "unit": "bond-updates/s",
@@ -804,7 +815,7 @@ def serving_side(pd, torch, requests=128, load=2.0, max_active=16, quantum=64):
     for mode in ("packed", "streams"):
         a = A()
         a.requests, a.load, a.max_active, a.quantum, a.serial_sample = requests, load, max_active, quantum, 12
-        a.serve_mode, a.pack_max_tiles, a.serve_sides = mode, 0, "40,20,96"
+        a.serve_mode, a.pack_max_tiles, a.serve_sides, a.max_queued = mode, 0, "40,20,96", 0
         r = run_serving(a, pd, torch, 0, 1, emit=False)
         if out is None:
             out = r
@@ -845,6 +856,8 @@ def main():
     ap.add_argument("--pack-max-tiles", type=int, default=0,
                     help="serve, packed mode: larger requests (in 512-point tiles) run on their own stream; "
                          "0 = no limit (every eligible request is packed)")
+    ap.add_argument("--max-queued", type=int, default=0,
+                    help="serve: back-pressure, refuse submits while this many wait (0 = no limit)")
     ap.add_argument("--serve-sides", default="40,20,96",
                     help="serve: median, smallest and largest side per axis of the mix's lattices")
     ap.add_argument("--tile-log2", type=int, default=None,

@@ -425,6 +425,11 @@ typedef struct {
                                  simulation's own kernels, the smaller ones are
                                  packed; 0 = no limit (every eligible request is
                                  packed), >= 0 */
+    int32_t max_queued;       /* back-pressure: while this many requests wait for
+                                 admission, pd_submit refuses the next with PD_EBUSY
+                                 (admitted and running requests do not count);
+                                 0 = no limit, >= 0 */
+    int32_t reserved;         /* must be 0 */
 } pd_server_opts;
 
 typedef struct {
@@ -464,7 +469,7 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts);
 int pd_server_destroy(pd_server *srv);
 /* Validate and copy a request and queue it; *ticket identifies it (> 0).
  * PD_EINVAL for an invalid description or one whose memory estimate exceeds the
- * budget on its own. */
+ * budget on its own; PD_EBUSY (nothing queued) while max_queued requests wait. */
 int pd_submit(pd_server *srv, const pd_request *req, uint64_t *ticket);
 /* Current state of a ticket, without blocking. PD_EINVAL for an unknown ticket. */
 int pd_poll(pd_server *srv, uint64_t ticket, pd_result *out);

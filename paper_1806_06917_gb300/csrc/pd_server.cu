@@ -122,6 +122,7 @@ struct pd_server {
     long long wait_ns = 2000000000LL;
     int stall = 0;
     int pack_max_tiles = 0;       // requests of more tiles than this are not packed (0: no limit)
+    int max_queued = 0;           // pd_submit refuses while this many wait (0: no limit)
     // two of each, so that the next quantum is issued while the last one runs
     cudaStream_t pk_stream = nullptr;
     cudaEvent_t pk_ev[2] = {nullptr, nullptr};
@@ -613,7 +614,7 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
 {
     if (!out) { set_error("null output"); return PD_EINVAL; }
     *out = nullptr;
-    pd_server_opts o = {0, 16, 64, PD_SERVE_PACKED, 0, 0, 0};
+    pd_server_opts o = {0, 16, 64, PD_SERVE_PACKED, 0, 0, 0, 0, 0};
     if (opts) o = *opts;
     if (o.max_active < 1 || o.max_active > 256) { set_error("max_active must be in [1, 256]"); return PD_EINVAL; }
     if (o.quantum_steps < 1 || o.quantum_steps > 4096) { set_error("quantum_steps must be in [1, 4096]"); return PD_EINVAL; }
@@ -621,6 +622,8 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
     if (o.mode != PD_SERVE_PACKED && o.mode != PD_SERVE_STREAMS) { set_error("unknown server mode"); return PD_EINVAL; }
     if (o.wait_limit_ms < 0) { set_error("wait_limit_ms must be >= 0"); return PD_EINVAL; }
     if (o.pack_max_tiles < 0) { set_error("pack_max_tiles must be >= 0"); return PD_EINVAL; }
+    if (o.max_queued < 0) { set_error("max_queued must be >= 0"); return PD_EINVAL; }
+    if (o.reserved != 0) { set_error("pd_server_opts.reserved must be 0"); return PD_EINVAL; }
     std::unique_ptr<pd_server> s(new pd_server());
     PD_CUDA(cudaGetDevice(&s->device));
     PD_CUDA(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device));
@@ -633,6 +636,7 @@ int pd_server_create(pd_server **out, const pd_server_opts *opts)
     s->wait_ns = 1000000LL * (o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000);
     s->stall = o.test_stall ? 1 : 0;
     s->pack_max_tiles = o.pack_max_tiles;
+    s->max_queued = o.max_queued;
     if (s->mode == PD_SERVE_PACKED) {
         const int rc = s->pk_init();
         if (rc != PD_OK) {
@@ -723,6 +727,10 @@ int pd_submit(pd_server *s, const pd_request *rq, uint64_t *ticket)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) { set_error("server is shutting down"); return PD_ESTATE; }
+        if (s->max_queued > 0 && (long long)s->queue.size() >= s->max_queued) {
+            set_error("%d requests wait for admission (max_queued)", s->max_queued);
+            return PD_EBUSY;
+        }
         r->ticket = s->next_ticket++;
         r->res.state = PD_REQ_QUEUED;
         r->res.tile_log2 = r->run.tile_log2;

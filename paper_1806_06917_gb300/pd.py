@@ -71,7 +71,8 @@ class pd_newton_stats(ctypes.Structure):
 class pd_server_opts(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
                 ("quantum_steps", ctypes.c_int32), ("mode", ctypes.c_int32), ("wait_limit_ms", ctypes.c_int32),
-                ("test_stall", ctypes.c_int32), ("pack_max_tiles", ctypes.c_int32)]
+                ("test_stall", ctypes.c_int32), ("pack_max_tiles", ctypes.c_int32),
+                ("max_queued", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pd_request(ctypes.Structure):
@@ -381,10 +382,11 @@ class Server:
     writes the outputs at completion)."""
 
     def __init__(self, device_bytes: int = 0, max_active: int = 16, quantum_steps: int = 64,
-                 mode: int = 0, wait_limit_ms: int = 0, test_stall: int = 0, pack_max_tiles: int = 0):
+                 mode: int = 0, wait_limit_ms: int = 0, test_stall: int = 0, pack_max_tiles: int = 0,
+                 max_queued: int = 0):
         h = _P()
         opts = pd_server_opts(device_bytes, max_active, quantum_steps, mode, wait_limit_ms, test_stall,
-                              pack_max_tiles)
+                              pack_max_tiles, max_queued, 0)
         _check(_lib.pd_server_create(ctypes.byref(h), ctypes.byref(opts)))
         self.h = h
         self._keep = {}

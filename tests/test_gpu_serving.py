@@ -5,6 +5,8 @@ threads per point pair the server reports, whether it ran in the packed kernel
 (with whatever else was packed with it) or on its own stream; admission must
 respect the memory budget; cancellation and bounded waits (host-side, and the
 packed kernel's device-side wait) must work without touching the GPU's state."""
+import time
+
 import numpy as np
 import pytest
 
@@ -108,6 +110,34 @@ def test_packed_kernel_wait_runs_out_and_the_server_goes_on(pd):
     assert second["state"] == pd.PD_REQ_DONE, second
     ua, _ = _alone(pd, lps[1], second["tile_log2"], pair_threads=second["pair_threads"])
     assert np.array_equal(u, ua)
+
+
+def test_a_full_queue_refuses_new_requests(pd):
+    """max_queued: with the one active slot held by a long request and two more
+    waiting, the next submit is refused with PD_EBUSY and nothing is queued; once
+    the queue has drained, submits are accepted again."""
+    g3 = W.Grid(dim=3, n=(20, 20, 20), h=0.05, m=3)
+    held = W.Request(grid=g3, mat=W.Material(model=W.PMB), steps=10 ** 7, arrival=0.0,
+                     u0=np.zeros((g3.npoints, 3)), seed=0)
+    short = _small_mix(3, 51)
+    srv = pd.Server(max_active=1, quantum_steps=16, max_queued=2)
+    t0 = _submit(pd, srv, held)
+    for _ in range(4000):                                  # admission is asynchronous
+        if pd.pd_poll(srv, t0)["state"] == pd.PD_REQ_RUNNING:
+            break
+        time.sleep(0.005)
+    assert pd.pd_poll(srv, t0)["state"] == pd.PD_REQ_RUNNING
+    waiting = [_submit(pd, srv, short[0]), _submit(pd, srv, short[1])]
+    with pytest.raises(pd.PdError) as e:
+        _submit(pd, srv, short[2])
+    assert e.value.code == pd.PD_EBUSY
+    pd.pd_cancel(srv, t0)
+    assert pd.pd_wait(srv, t0, timeout_s=120.0)["state"] == pd.PD_REQ_CANCELLED
+    for t in waiting:
+        assert pd.pd_wait(srv, t, timeout_s=120.0)["state"] == pd.PD_REQ_DONE
+    again = pd.pd_wait(srv, _submit(pd, srv, short[2]), timeout_s=120.0)
+    srv.close()
+    assert again["state"] == pd.PD_REQ_DONE
 
 
 def test_central_difference_requests_equal_the_same_runs_alone(pd):

@@ -107,7 +107,8 @@ def test_tune_tile_refuses_bad_arguments(pd):
 
 
 @pytest.mark.parametrize("opt", [dict(max_active=0), dict(max_active=257), dict(quantum_steps=0), dict(mode=7),
-                                 dict(wait_limit_ms=-1), dict(pack_max_tiles=-1), dict(device_bytes=-1)])
+                                 dict(wait_limit_ms=-1), dict(pack_max_tiles=-1), dict(device_bytes=-1),
+                                 dict(max_queued=-1)])
 def test_server_options_are_refused_before_any_device_call(pd, opt):
     with pytest.raises(pd.PdError) as e:
         pd.Server(**opt)
