@@ -403,7 +403,7 @@ static int create_impl(pd_sim *s)
     // paired halo box (x extent bx + 2m; y extent by + 2m in 3D, by/2 + 2m in 2D)
     {
         const int PHX = g.bx + 2 * g.m, PHY = g.dim == 3 ? g.by + 2 * g.m : g.by / 2 + 2 * g.m;
-        std::vector<float4> ta(4 * (size_t)g.S), tb(3 * (size_t)g.S);
+        std::vector<float4> ta(4 * (size_t)g.S), tb(3 * (size_t)g.S), tc(3 * (size_t)g.S);
         for (int k = 0; k < g.S; ++k) {
             const int4 d = st[k];
             const double rr = r0[k], d2 = d.w;
@@ -418,6 +418,11 @@ static int create_impl(pd_sim *s)
             tb[3 * k] = dxy;
             tb[3 * k + 1] = make_float4((float)d.z, (float)d.z, (float)rr, (float)rr);
             tb[3 * k + 2] = make_float4((float)d2, (float)d2, offf, (float)vij);
+            // LPS dilatation, 3 float4 per entry: {2dx,2dx,2dy,2dy} {2dz,2dz,|d|,|d|}
+            // {|d|^2,|d|^2,offset,V_ij} (its extension needs e.(e + 2d), not y)
+            tc[3 * k] = make_float4(2.f * d.x, 2.f * d.x, 2.f * d.y, 2.f * d.y);
+            tc[3 * k + 1] = make_float4(2.f * d.z, 2.f * d.z, (float)rr, (float)rr);
+            tc[3 * k + 2] = tb[3 * k + 2];
             if (mt.model == PD_MODEL_NP || mt.model == PD_MODEL_LP) {
                 // compact entries (NP_TAB_WORDS float4 each, written over the first
                 // entries of the table): the bond weight t = J V_ij / |d| and the
@@ -445,8 +450,12 @@ static int create_impl(pd_sim *s)
                 ta[4 * k + 3] = make_float4(offf, (float)(mt.s_c * vij), (float)(mt.s_c * vij * (1.0 - 0x1p-13)),
                                             (float)(mt.s_c * vij * (1.0 + 0x1p-13)));
             }
-            // LPS: both passes read tb (the dilatation's bond weight |d| V_ij from
-            // its {dz,dz,|d|,|d|} and V_ij entries)
+        }
+        // LPS: the force pass reads tb, the dilatation tc (held in tab_a, which no
+        // LPS kernel reads otherwise)
+        if (mt.model == PD_MODEL_LPS) {
+            std::fill(ta.begin(), ta.end(), make_float4(0.f, 0.f, 0.f, 0.f));
+            std::copy(tc.begin(), tc.end(), ta.begin());
         }
         ALLOC(s->tab_a, sizeof(float4) * ta.size());
         ALLOC(s->tab_b, sizeof(float4) * tb.size());
@@ -455,7 +464,10 @@ static int create_impl(pd_sim *s)
         // the entries the kernels read: PMB 4 float4 each (NP / LP keep theirs in
         // shared memory), LPS 3
         if (mt.model == PD_MODEL_PMB) s->htab_a.assign(ta.begin(), ta.begin() + 4 * (size_t)g.S);
-        if (mt.model == PD_MODEL_LPS) s->htab_b = tb;
+        if (mt.model == PD_MODEL_LPS) {
+            s->htab_a = tc;
+            s->htab_b = tb;
+        }
         // neighbour tiles (index (dx+1) + 3 (dy+1) + 9 (dz+1)); usable when the halo
         // reaches at most one tile in every direction
         std::vector<int> nbr(27 * (size_t)g.ntiles, -1);

@@ -168,9 +168,12 @@ int launch_lps_args(const TileArgs &a, int precision, int dil, cudaStream_t st)
         static thread_local ParamTab tp;
         // the table as a kernel parameter on grids of several waves (as for PMB,
         // pd_force_pmb.cu): 128^3 force pass 0.392 -> 0.361 ms
-        const bool pt = a.htab_b && a.ntab_b > 0 && a.ntab_b <= PTAB_N && g.ntiles >= 2048;
+        // (the dilatation's table is tab_a, the force pass's tab_b)
+        const float4 *ht = dil ? a.htab_a : a.htab_b;
+        const int nt = dil ? a.ntab_a : a.ntab_b;
+        const bool pt = ht && nt > 0 && nt <= PTAB_N && g.ntiles >= 2048;
         if (pt) {
-            memcpy(tp.e, a.htab_b, sizeof(float4) * (size_t)a.ntab_b);
+            memcpy(tp.e, ht, sizeof(float4) * (size_t)nt);
             auto k = dil ? (dil2 ? (a.vol_corr ? lps_dil_fast2_pt<true> : lps_dil_fast2_pt<false>)
                                  : (a.vol_corr ? lps_dil_fast_pt<true> : lps_dil_fast_pt<false>))
                          : (a.vol_corr ? lps_force_fast_pt<true> : lps_force_fast_pt<false>);

@@ -22,8 +22,9 @@ namespace pdk {
 // rolled loop over a shared-memory table of pre-splatted stencil constants.
 // One 32-bond word of the dilatation sum (MASKED = false: every bond of the
 // warp's points exists and is intact, no per-bond mask operation).
-// The table is the force pass's: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|^2,|d|^2,offset,V_ij};
-// the bond weight |d| V_ij is |d| itself without the partial volume (VOLCORR = false).
+// The table is the dilatation's: {2dx,2dx,2dy,2dy} {2dz,2dz,|d|,|d|} {|d|^2,|d|^2,offset,V_ij}:
+// the extension needs 2 d.e + e.e = e.(e + 2d) and |y|, not y itself; the bond
+// weight |d| V_ij is |d| itself without the partial volume (VOLCORR = false).
 template <bool MASKED, bool VOLCORR>
 __device__ __forceinline__ float2 lps_dil_word(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
                                                float2 nux, float2 nuy, float2 nuz, uint32_t c0, uint32_t c1,
@@ -35,10 +36,9 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
         const int off = __float_as_int(tc.z);
         const float4 r4 = P4[bi + off];
         const float2 ex = f2add(f2lo(r4), nux), ey = f2add(f2hi(r4), nuy), ez = f2add(P2[bi + off], nuz);
-        const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
-        float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
-        num = f2fma(ey, f2add(yy, f2hi(ta)), num);
-        num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+        float2 num = f2mul(ex, f2add(ex, f2lo(ta)));
+        num = f2fma(ey, f2add(ey, f2hi(ta)), num);
+        num = f2fma(ez, f2add(ez, f2lo(tb)), num);
         const float2 qq = f2add(num, f2lo(tc));            // |y|^2 = |d|^2 + 2 d.e + e.e
         float2 e = f2mul(num, f2rcp(f2add(f2sqrt(qq), f2hi(tb))));
         if (MASKED) {
@@ -103,7 +103,7 @@ __device__ __forceinline__ void lps_dil_fast_body(const TileArgs &a, int tile, c
     if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
-        for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
+        for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
@@ -143,15 +143,26 @@ __device__ __forceinline__ void lps_dil_fast_body(const TileArgs &a, int tile, c
 // halves of the stencil words, added in a fixed order (half 0 + half 1). The
 // one-pair kernel is bound by the L1 / shared-memory pipe (ncu: 92 % of its
 // throughput, 14 wavefronts per 64 bonds, 7 of them table broadcasts); this
-// form moves 19 per 128. Both dilatation kernels read the force pass's table of 3
-// float4 per entry (from 4: the 128^3 LPS step 0.614 -> 0.611 ms).
+// form moves 19 per 128. The dilatation table has 3 float4 per entry (from 4:
+// the 128^3 LPS step 0.614 -> 0.611 ms).
+// Unroll depth of the two-pair dilatation's bond loop and its CTAs per SM:
+// built for 3 CTAs per SM (80 registers, no spills) it measured 0.2176 ms per
+// 128^3 pass against 0.2215 ms for 4 (64 registers, 36 bytes of spills);
+// unrolled by 2 or 8 at 4 CTAs, 0.2179 and 0.2193 ms.
+#ifndef PD_DIL2_UNROLL
+#define PD_DIL2_UNROLL 4
+#endif
+#ifndef PD_DIL2_MINBLOCKS
+#define PD_DIL2_MINBLOCKS 3
+#endif
+
 template <bool MASKED, bool VOLCORR>
 __device__ __forceinline__ void lps_dil_word2(const float4 *tw, int nb, const float4 *P4, const float2 *P2, int bi,
                                               int dbi, float2 nux0, float2 nuy0, float2 nuz0, float2 nux1,
                                               float2 nuy1, float2 nuz1, uint32_t c0, uint32_t c1, uint32_t c2,
                                               uint32_t c3, float2 &acc0, float2 &acc1)
 {
-PD_PRAGMA_UNROLL(PD_UNROLL)
+PD_PRAGMA_UNROLL(PD_DIL2_UNROLL)
     for (int b = 0; b < nb; ++b) {
         const float4 ta = tw[3 * b], tb = tw[3 * b + 1], tc = tw[3 * b + 2];
         const int off = __float_as_int(tc.z);
@@ -160,18 +171,16 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
         float2 e0, e1;
         {
             const float2 ex = f2add(f2lo(r0), nux0), ey = f2add(f2hi(r0), nuy0), ez = f2add(z0, nuz0);
-            const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
-            float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
-            num = f2fma(ey, f2add(yy, f2hi(ta)), num);
-            num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+            float2 num = f2mul(ex, f2add(ex, f2lo(ta)));
+            num = f2fma(ey, f2add(ey, f2hi(ta)), num);
+            num = f2fma(ez, f2add(ez, f2lo(tb)), num);
             e0 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2lo(tc))), f2hi(tb))));
         }
         {
             const float2 ex = f2add(f2lo(r1), nux1), ey = f2add(f2hi(r1), nuy1), ez = f2add(z1, nuz1);
-            const float2 yx = f2add(ex, f2lo(ta)), yy = f2add(ey, f2hi(ta)), yz = f2add(ez, f2lo(tb));
-            float2 num = f2mul(ex, f2add(yx, f2lo(ta)));
-            num = f2fma(ey, f2add(yy, f2hi(ta)), num);
-            num = f2fma(ez, f2add(yz, f2lo(tb)), num);
+            float2 num = f2mul(ex, f2add(ex, f2lo(ta)));
+            num = f2fma(ey, f2add(ey, f2hi(ta)), num);
+            num = f2fma(ez, f2add(ez, f2lo(tb)), num);
             e1 = f2mul(num, f2rcp(f2add(f2sqrt(f2add(num, f2lo(tc))), f2hi(tb))));
         }
         if (MASKED) {
@@ -205,7 +214,7 @@ __device__ __forceinline__ void lps_dil_fast2_body(const TileArgs &a, int tile, 
     if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
-        for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
+        for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
@@ -375,7 +384,7 @@ __device__ __forceinline__ void lps_dil_h2_body(const TileArgs &a, int tile, con
     if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
-        for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
+        for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
     load_nbr(a, tile, s_nbr);
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast(const TileArgs
 }
 
 template <bool VOLCORR>
-__global__ void __launch_bounds__(256, PD_MINBLOCKS) lps_dil_fast2(const TileArgs a)
+__global__ void __launch_bounds__(256, PD_DIL2_MINBLOCKS) lps_dil_fast2(const TileArgs a)
 {
     lps_dil_fast2_body<VOLCORR, false>(a, blockIdx.x, nullptr);
 }
@@ -447,7 +456,7 @@ __global__ void __launch_bounds__(256, PD_MINBLOCKS)
 }
 
 template <bool VOLCORR>
-__global__ void __launch_bounds__(256, PD_MINBLOCKS)
+__global__ void __launch_bounds__(256, PD_DIL2_MINBLOCKS)
     lps_dil_fast2_pt(const __grid_constant__ TileArgs a, const __grid_constant__ ParamTab tp)
 {
     lps_dil_fast2_body<VOLCORR, true>(a, blockIdx.x, tp.e);

@@ -400,9 +400,12 @@ __device__ __forceinline__ void point_update64(const TileArgs &a, int slot, cons
         const float kick = fmaf(a.kF, F[c], a.kB * bcomp[c]);
         const double kd = f2d_bits(kick);
         double vc = v[c], uc = u[c];
-        if (a.v_is_half) vc += kd;
+        // the previous step's second half-kick and this step's first are the same
+        // kick: one add of 2 kick (exact) from the half-step velocity, the leapfrog
+        // form of Eq. (9), one rounding instead of two
+        if (step && a.v_is_half) vc += 2.0 * kd;
+        else if (a.v_is_half || step) vc += kd;
         if (step) {
-            vc += kd;
             if (kind[c] == PD_BC_VELOCITY) {
                 vc = a.bc_val[c * ns + slot];
                 uc = fma(a.dt, vc, uc);

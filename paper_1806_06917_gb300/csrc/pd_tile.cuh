@@ -376,8 +376,9 @@ struct TileArgs {
     float4 *vhl;                // FP32C velocity as double-float pairs (2 float4 per slot)
     const float *bc32;          // FP32C boundary values as (hi, lo) per DOF, component-major
     const float4 *body32;       // FP32C body force per slot
-    const float4 *tab_a;        // FP32C stencil table of the PMB and NP kernels (4 or NP_TAB_WORDS float4 / entry)
-    const float4 *tab_b;        // FP32C stencil table of both LPS passes (3 float4 / entry)
+    const float4 *tab_a;        // FP32C stencil table of the PMB and NP kernels (4 or NP_TAB_WORDS float4 / entry),
+                                // or of the LPS dilatation (3 float4 / entry)
+    const float4 *tab_b;        // FP32C stencil table of the LPS force pass (3 float4 / entry)
     const int *tile_nbr;        // [ntiles * 27] the 3^d neighbour tiles of each tile (or -1)
     int nbr_ok;                 // halo within one tile in every direction: tile_nbr is usable
     const uint32_t *box_map;    // paired halo box: neighbour tile (5 bits) + brick code (9) of A, then of B
