@@ -51,6 +51,12 @@ PD_PRAGMA_UNROLL(PD_UNROLL)
     return acc;
 }
 
+// Unroll depth of the force pass's bond loop: 8 measured 0.3569 ms per 128^3
+// pass against 0.3598-0.3600 ms for 4 and 0.3680 ms for 2.
+#ifndef PD_FORCE_UNROLL
+#define PD_FORCE_UNROLL 8
+#endif
+
 // One 32-bond word of the LPS force sum. The staged a = (3K - 5mu) theta / m~ and
 // b = 15 mu / m~ carry the moduli, so the bond weight is
 //   (t_i + t_j) V_ij / |y| = (|d| (a_i + a_j) + e (b_i + b_j)) V_ij / |y|
@@ -61,7 +67,7 @@ __device__ __forceinline__ void lps_force_word(const float4 *tw, int nb, const f
                                                float2 ai, float2 bi_, uint32_t c0, uint32_t c1, float2 &Fx,
                                                float2 &Fy, float2 &Fz)
 {
-PD_PRAGMA_UNROLL(PD_UNROLL)
+PD_PRAGMA_UNROLL(PD_FORCE_UNROLL)
     for (int b = 0; b < nb; ++b) {
         // table entry: {dx,dx,dy,dy} {dz,dz,|d|,|d|} {|d|^2,|d|^2,offset,V_ij}
         const float4 ta = tw[3 * b], tb = tw[3 * b + 1], td = tw[3 * b + 2];
