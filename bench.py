@@ -659,29 +659,48 @@ def pass_times(pd, torch, sim, wl, steps, warmup, stream, flush):
 def e2e_rate(pd, torch, sim, wl, nbonds, steps, warmup, stream, world):
     """End to end through the public API with host buffers every step: the state
     (u, v) in from pinned host memory, one explicit step, u back out to pinned
-    host memory (pd_get_state is synchronous)."""
+    host memory. Pipelined (the value): pd_set_state_async, pd_step_explicit and
+    pd_get_state_async per step and one pd_io_sync at the end, so the next
+    step's upload overlaps this step's compute and download; every step still
+    moves its own input and result across the host link. Beside it the
+    synchronous loop (pd_set_state, pd_step_explicit, pd_get_state, which
+    returns with the result in host memory)."""
     u_h = torch.from_numpy(wl.u0).pin_memory()
     v_h = torch.from_numpy(wl.v0).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(warmup):
-        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
-        pd.pd_step_explicit(sim, 1, stream)
-        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
-        pd.pd_step_explicit(sim, 1, stream)
-        pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = rank_reduce(torch, e0.elapsed_time(e1), "max", "cuda")
+
+    def loop(n, pipelined):
+        for _ in range(n):
+            if pipelined:
+                pd.pd_set_state_async(sim, u=u_h, v=v_h, stream=stream)
+                pd.pd_step_explicit(sim, 1, stream)
+                pd.pd_get_state_async(sim, u=u_o, stream=stream)
+            else:
+                pd.pd_set_state(sim, u=u_h, v=v_h, stream=stream)
+                pd.pd_step_explicit(sim, 1, stream)
+                pd.pd_get_state(sim, u=u_o, stream=stream, want_v=False)
+        if pipelined:
+            pd.pd_io_sync(sim)
+
+    res = {}
+    for pipelined in (True, False):
+        loop(warmup, pipelined)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        loop(steps, pipelined)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[pipelined] = rank_reduce(torch, e0.elapsed_time(e1), "max", "cuda")
+    ms = res[True]
     return {"value": world * nbonds * steps / (ms * 1e-3), "unit": "bond-updates/s",
             "h2d_bytes_per_step": (u_h.numel() + v_h.numel()) * 8, "d2h_bytes_per_step": u_o.numel() * 8,
             "ms_per_step": ms / steps,
-            "note": "per step: pd_set_state(u, v) from pinned host + pd_step_explicit(1) + pd_get_state(u) "
-                    "to pinned host; L2 not flushed"}
+            "note": "per step: pd_set_state_async(u, v) from pinned host + pd_step_explicit(1) + "
+                    "pd_get_state_async(u) to pinned host, pd_io_sync after the last step (the event that "
+                    "ends the timed region is recorded after it); L2 not flushed",
+            "sync": {"value": world * nbonds * steps / (res[False] * 1e-3), "ms_per_step": res[False] / steps,
+                     "note": "pd_set_state + pd_step_explicit(1) + pd_get_state (synchronous) per step"}}
 
 
 def roofline_of(key, wl, nbonds, passes_ms, step_ms, tile_log2, peaks):

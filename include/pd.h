@@ -221,6 +221,25 @@ int pd_set_state(pd_sim *sim, const double *u, const double *v, void *stream);
  * to complete it (Eq. (9)); the trajectory is unchanged. Synchronous. */
 int pd_get_state(pd_sim *sim, double *u, double *v, void *stream);
 
+/* Pipelined forms for host arrays (device arrays behave as in pd_set_state and
+ * pd_get_state, stream-ordered). pd_set_state_async copies the host arrays
+ * without first waiting for the work already queued on `stream` (only for the
+ * library's staging buffer), so the upload of the next state can run while the
+ * current step computes: the caller guarantees that the arrays hold their values
+ * when the call is made and keeps them unchanged until pd_io_sync returns.
+ * pd_get_state_async queues the read on `stream` and the copies to the caller's
+ * arrays, and returns at once: the arrays hold the result after pd_io_sync has
+ * returned; until then the caller neither reads nor writes them nor passes them
+ * to pd_set_state(_async) (a later pd_get_state_async into the same arrays is
+ * ordered after this one). Uploads and
+ * downloads use separate staging buffers and copy streams, so one step's
+ * download, the next step's upload and the compute between them overlap. */
+int pd_set_state_async(pd_sim *sim, const double *u, const double *v, void *stream);
+int pd_get_state_async(pd_sim *sim, double *u, double *v, void *stream);
+/* Block until every host-array copy of pd_set_state(_async) and
+ * pd_get_state(_async) issued so far has completed. */
+int pd_io_sync(pd_sim *sim);
+
 /* Boundary conditions on a collar Omega_c (Sec. 3; Sec. 5.2.2): kind and value
  * per DOF (npoints x dim; uint8 PD_BC_*, FP64). PD_BC_VELOCITY holds v = value
  * and advances u by dt*value; PD_BC_DISPLACEMENT holds u = value, v = 0.

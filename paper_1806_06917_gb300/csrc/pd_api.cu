@@ -83,10 +83,14 @@ struct pd_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    // host transfers of pd_set_state / pd_get_state: chunk copies on copy_stream,
-    // each chunk's scatter or gather on the caller's stream (see xfer_chunks)
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_copy[IO_CHUNKS] = {}, ev_done[IO_CHUNKS] = {};
+    // host transfers of pd_set_state / pd_get_state (see xfer_chunks): uploads copy
+    // into io_up on copy_stream, downloads copy out of io_dn on copy_out (room for
+    // both fields each), each chunk's scatter or gather on the caller's stream;
+    // events per field and chunk
+    cudaStream_t copy_stream = nullptr, copy_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_copy[2][IO_CHUNKS] = {}, ev_done[2][IO_CHUNKS] = {};
+    cudaEvent_t ev_out = nullptr, ev_dgath[2][IO_CHUNKS] = {}, ev_dcopy[2][IO_CHUNKS] = {};
+    double *io_up = nullptr, *io_dn = nullptr;
     bool built = false;
     double dt = 0.0, dt_crit = 0.0;
     int64_t step = 0;
@@ -374,11 +378,16 @@ static int create_impl(pd_sim *s)
     PD_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     PD_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     PD_CUDA(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaStreamCreateWithFlags(&s->copy_out, cudaStreamNonBlocking));
     PD_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
-    for (int k = 0; k < IO_CHUNKS; ++k) {
-        PD_CUDA(cudaEventCreateWithFlags(&s->ev_copy[k], cudaEventDisableTiming));
-        PD_CUDA(cudaEventCreateWithFlags(&s->ev_done[k], cudaEventDisableTiming));
-    }
+    PD_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < IO_CHUNKS; ++k) {
+            PD_CUDA(cudaEventCreateWithFlags(&s->ev_copy[f][k], cudaEventDisableTiming));
+            PD_CUDA(cudaEventCreateWithFlags(&s->ev_done[f][k], cudaEventDisableTiming));
+            PD_CUDA(cudaEventCreateWithFlags(&s->ev_dgath[f][k], cudaEventDisableTiming));
+            PD_CUDA(cudaEventCreateWithFlags(&s->ev_dcopy[f][k], cudaEventDisableTiming));
+        }
 
     const size_t NS = (size_t)g.nslots, NP = (size_t)g.npoints;
     std::vector<uint32_t> box_map;      // uploaded after the other arrays (see the end)
@@ -554,6 +563,8 @@ static int create_impl(pd_sim *s)
     ALLOC(s->red, sizeof(double) * reduce_blocks_for(NS));
     ALLOC(s->dout, sizeof(double) * 8);
     ALLOC(s->io, sizeof(double) * 3 * std::max(NP, NS));
+    ALLOC(s->io_up, sizeof(double) * 2 * 3 * NP);
+    ALLOC(s->io_dn, sizeof(double) * 2 * 3 * NP);
     ALLOC(s->d_err, sizeof(int));
     ALLOC(s->d_count, sizeof(unsigned long long));
     // last, so that it moves no other array of the pool
@@ -980,6 +991,7 @@ int pd_destroy(pd_sim *s)
     if (!s) return PD_OK;
     drop_graphs(s);
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+    if (s->copy_out) cudaStreamSynchronize(s->copy_out);
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaStream_t fs = s->stream;     // stream-ordered release after the simulation's own work
     for (void *p : s->allocs) lib_free(p, fs);
@@ -991,11 +1003,16 @@ int pd_destroy(pd_sim *s)
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->copy_out) cudaStreamDestroy(s->copy_out);
     if (s->ev_in) cudaEventDestroy(s->ev_in);
-    for (int k = 0; k < IO_CHUNKS; ++k) {
-        if (s->ev_copy[k]) cudaEventDestroy(s->ev_copy[k]);
-        if (s->ev_done[k]) cudaEventDestroy(s->ev_done[k]);
-    }
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < IO_CHUNKS; ++k) {
+            if (s->ev_copy[f][k]) cudaEventDestroy(s->ev_copy[f][k]);
+            if (s->ev_done[f][k]) cudaEventDestroy(s->ev_done[f][k]);
+            if (s->ev_dgath[f][k]) cudaEventDestroy(s->ev_dgath[f][k]);
+            if (s->ev_dcopy[f][k]) cudaEventDestroy(s->ev_dcopy[f][k]);
+        }
     delete s;
     return PD_OK;
 }
@@ -1192,16 +1209,22 @@ int pd_break_bonds(pd_sim *s, int axis, double pos, const double lo[3], const do
 }
 
 // Pipelined host transfer of up to two state fields (u: the staging pair of the
-// current step, or the FP64 arrays; v: the velocity pair or array) through the
-// staging buffer s->io, in IO_CHUNKS chunks of user rows. Upload: chunk k is
-// copied in on copy_stream, then scattered on st once its copy event fired, so
-// the copy of chunk k + 1 overlaps the scatter of chunk k; the second field's
-// copy of chunk k waits for the first field's scatter of chunk k to have read the
-// buffer. Download: chunk k is gathered on st, then copied out on copy_stream;
-// the second field's gather of chunk k waits for the first field's copy of chunk
-// k. copy_stream first waits for the work already queued on st. Every wait is an
-// event in stream order: no host synchronisation here.
-static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2], bool upload, cudaStream_t st)
+// current step, or the FP64 arrays; v: the velocity pair or array), in IO_CHUNKS
+// chunks of user rows, each field in its own half of the staging buffer.
+// Upload: chunk k of a field is copied into io_up on copy_stream, then scattered
+// on st once its copy event fired, so the copy of chunk k + 1 overlaps the
+// scatter of chunk k; a copy into a chunk first waits for the last scatter of
+// that chunk (of an earlier upload) to have read it. Download: chunk k is
+// gathered on st into io_dn, then copied out on copy_out; a gather into a chunk
+// first waits for the last copy out of that chunk. Uploads and downloads have
+// their own buffers and copy streams, so an upload may run while an earlier
+// download is still copying out, in the other direction of the link, and both
+// fields of an upload may cross the link while st still computes.
+// Unless async, the copies also wait for the work already queued on st (the
+// caller's arrays may be written by it) and st waits for them at the end. Every
+// wait is an event in stream order: no host synchronisation here.
+static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2], bool upload, cudaStream_t st,
+                       bool async)
 {
     const Geom &g = s->g;
     // double-float state: the pairs alone; FP64 state: the FP64 arrays (and for
@@ -1213,10 +1236,12 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
     // one chunk below 1 MB per field: a pipeline of small copies gains nothing
     const int nc = n * (long long)row_bytes < (1 << 20) ? 1 : IO_CHUNKS;
     const long long rows = ((n + nc - 1) / nc + 255) / 256 * 256;
-    cudaStream_t cs = s->copy_stream;
-    PD_CUDA(cudaEventRecord(s->ev_in, st));
-    PD_CUDA(cudaStreamWaitEvent(cs, s->ev_in, 0));
-    bool first = true;
+    cudaStream_t cs = upload ? s->copy_stream : s->copy_out;
+    cudaEvent_t ev_join = upload ? s->ev_in : s->ev_out;
+    if (!async) {
+        PD_CUDA(cudaEventRecord(ev_join, st));
+        PD_CUDA(cudaStreamWaitEvent(cs, ev_join, 0));
+    }
     for (int f = 0; f < 2; ++f) {
         if (!host[f]) continue;
         double *const *slot = pairs ? nullptr : (is_u[f] ? s->u : s->v);
@@ -1225,35 +1250,38 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
         for (int k = 0; k < nc; ++k) {
             const long long r0 = std::min(n, k * rows), r1 = std::min(n, r0 + rows);
             if (r1 <= r0) continue;
-            double *io = s->io + r0 * d;
             const size_t bytes = (size_t)(r1 - r0) * row_bytes;
             if (upload) {
-                if (!first) PD_CUDA(cudaStreamWaitEvent(cs, s->ev_done[k], 0));
-                PD_CUDA(cudaMemcpyAsync(io, host[f] + r0 * d, bytes, cudaMemcpyDefault, cs));
-                PD_CUDA(cudaEventRecord(s->ev_copy[k], cs));
-                PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[k], 0));
-                int rc = scatter_rows(g, s->slot_of_user, s->io, r0, r1, slot, hl, d4, st, f32c && s->state64);
+                double *base = s->io_up + (size_t)f * n * d;
+                PD_CUDA(cudaStreamWaitEvent(cs, s->ev_done[f][k], 0));
+                PD_CUDA(cudaMemcpyAsync(base + r0 * d, host[f] + r0 * d, bytes, cudaMemcpyDefault, cs));
+                PD_CUDA(cudaEventRecord(s->ev_copy[f][k], cs));
+                PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[f][k], 0));
+                int rc = scatter_rows(g, s->slot_of_user, base, r0, r1, slot, hl, d4, st, f32c && s->state64);
                 if (rc != PD_OK) return rc;
-                PD_CUDA(cudaEventRecord(s->ev_done[k], st));
+                PD_CUDA(cudaEventRecord(s->ev_done[f][k], st));
             } else {
-                if (!first) PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[k], 0));
-                int rc = gather_rows(g, s->slot_of_user, hl, slot, s->io, r0, r1, st);
+                double *base = s->io_dn + (size_t)f * n * d;
+                PD_CUDA(cudaStreamWaitEvent(st, s->ev_dcopy[f][k], 0));
+                int rc = gather_rows(g, s->slot_of_user, hl, slot, base, r0, r1, st);
                 if (rc != PD_OK) return rc;
-                PD_CUDA(cudaEventRecord(s->ev_done[k], st));
-                PD_CUDA(cudaStreamWaitEvent(cs, s->ev_done[k], 0));
-                PD_CUDA(cudaMemcpyAsync(const_cast<double *>(host[f]) + r0 * d, io, bytes, cudaMemcpyDefault, cs));
-                PD_CUDA(cudaEventRecord(s->ev_copy[k], cs));
+                PD_CUDA(cudaEventRecord(s->ev_dgath[f][k], st));
+                PD_CUDA(cudaStreamWaitEvent(cs, s->ev_dgath[f][k], 0));
+                PD_CUDA(cudaMemcpyAsync(const_cast<double *>(host[f]) + r0 * d, base + r0 * d, bytes,
+                                        cudaMemcpyDefault, cs));
+                PD_CUDA(cudaEventRecord(s->ev_dcopy[f][k], cs));
             }
         }
-        first = false;
     }
-    // the caller's stream finishes after every copy of this call
-    PD_CUDA(cudaEventRecord(s->ev_in, cs));
-    PD_CUDA(cudaStreamWaitEvent(st, s->ev_in, 0));
+    if (!async) {
+        // the caller's stream finishes after every copy of this call
+        PD_CUDA(cudaEventRecord(ev_join, cs));
+        PD_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
+    }
     return PD_OK;
 }
 
-int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
+static int set_state_impl(pd_sim *s, const double *u, const double *v, void *stream, bool async)
 {
     CHECK_BUILT(s);
     cudaStream_t st = pick(s, stream);
@@ -1273,7 +1301,7 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     if (host_u || host_v) {
         const double *hu[2] = {host_u ? u : nullptr, host_v ? v : nullptr};
         const bool is_u[2] = {true, false};
-        if ((rc = xfer_chunks(s, hu, is_u, true, st)) != PD_OK) return rc;
+        if ((rc = xfer_chunks(s, hu, is_u, true, st, async)) != PD_OK) return rc;
     }
     if (u && !host_u) {
         if ((rc = user_source(s, u, &src, st)) != PD_OK) return rc;
@@ -1289,6 +1317,16 @@ int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
     return PD_OK;
 }
 
+int pd_set_state(pd_sim *s, const double *u, const double *v, void *stream)
+{
+    return set_state_impl(s, u, v, stream, false);
+}
+
+int pd_set_state_async(pd_sim *s, const double *u, const double *v, void *stream)
+{
+    return set_state_impl(s, u, v, stream, true);
+}
+
 // FP32C with double-float state keeps u and v as pairs; refresh the FP64 SoA
 // copies (with FP64 state those arrays are the state itself).
 static int unpack_state(pd_sim *s, cudaStream_t st, bool want_u = true, bool want_v = true)
@@ -1300,7 +1338,7 @@ static int unpack_state(pd_sim *s, cudaStream_t st, bool want_u = true, bool wan
     return PD_OK;
 }
 
-int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
+static int get_state_impl(pd_sim *s, double *u, double *v, void *stream, bool async)
 {
     CHECK_BUILT(s);
     cudaStream_t st = pick(s, stream);
@@ -1317,10 +1355,28 @@ int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
         // gathers in chunks on st, each chunk's copy out on copy_stream behind it
         const double *hu[2] = {host_u ? u : nullptr, host_v ? v : nullptr};
         const bool is_u[2] = {true, false};
-        if ((rc = xfer_chunks(s, hu, is_u, false, st)) != PD_OK) return rc;
-        PD_CUDA(cudaStreamSynchronize(s->copy_stream));
+        if ((rc = xfer_chunks(s, hu, is_u, false, st, async)) != PD_OK) return rc;
+        if (!async) PD_CUDA(cudaStreamSynchronize(s->copy_out));
     }
-    PD_CUDA(cudaStreamSynchronize(st));
+    if (!async) PD_CUDA(cudaStreamSynchronize(st));
+    return PD_OK;
+}
+
+int pd_get_state(pd_sim *s, double *u, double *v, void *stream)
+{
+    return get_state_impl(s, u, v, stream, false);
+}
+
+int pd_get_state_async(pd_sim *s, double *u, double *v, void *stream)
+{
+    return get_state_impl(s, u, v, stream, true);
+}
+
+int pd_io_sync(pd_sim *s)
+{
+    CHECK_BUILT(s);
+    PD_CUDA(cudaStreamSynchronize(s->copy_stream));
+    PD_CUDA(cudaStreamSynchronize(s->copy_out));
     return PD_OK;
 }
 

@@ -64,7 +64,8 @@ bool ended(int state) { return state == PD_REQ_DONE || state == PD_REQ_CANCELLED
 
 // Points of the lattice, slots of its tile grid, and an upper bound of the
 // device bytes a simulation of it allocates (per-slot state and tables, the
-// bond mask, the CSR with every stencil offset counted).
+// bond mask, the CSR with every stencil offset counted, the host-transfer
+// staging of two fields each way).
 size_t estimate_bytes(const pd_grid &g, const pd_material &mt, int L)
 {
     int b[3];
@@ -77,7 +78,7 @@ size_t estimate_bytes(const pd_grid &g, const pd_material &mt, int L)
     const int S = stencil_size(g.dim, g.m);
     const int W = (S + 31) / 32;
     const long long per_slot = 400 + 4LL * W + (mt.model == PD_MODEL_LPS ? 24 : 0);
-    return (size_t)(slots * per_slot + np * (8 + 4LL * S) + (1 << 20));
+    return (size_t)(slots * per_slot + np * (8 + 96 + 4LL * S) + (1 << 20));
 }
 
 // Tile size: the largest 2^L (L = 9..6) that still gives the simulation its

@@ -106,6 +106,9 @@ _SIGS = {
     "pd_break_bonds": [_P, ctypes.c_int, ctypes.c_double, _P, _P, ctypes.POINTER(ctypes.c_int64), _P],
     "pd_set_state": [_P, _P, _P, _P],
     "pd_get_state": [_P, _P, _P, _P],
+    "pd_set_state_async": [_P, _P, _P, _P],
+    "pd_get_state_async": [_P, _P, _P, _P],
+    "pd_io_sync": [_P],
     "pd_set_bc": [_P, _P, _P, _P],
     "pd_set_body_force": [_P, _P, _P],
     "pd_get_dt": [_P, ctypes.POINTER(ctypes.c_double)],
@@ -270,6 +273,31 @@ def pd_get_state(sim: Sim, u=None, v=None, stream=None, want_v: bool = True):
     _check(_lib.pd_get_state(sim.h, _buf(u, np.float64, sim.nvec, "u", True),
                              _buf(v, np.float64, sim.nvec, "v", True), _stream(stream)))
     return u, v
+
+
+def pd_set_state_async(sim: Sim, u=None, v=None, stream=None) -> None:
+    """pd_set_state without waiting for the work queued on the stream: u and v
+    (pinned host arrays or device tensors) stay unchanged until pd_io_sync; the
+    simulation keeps references to them until then."""
+    _check(_lib.pd_set_state_async(sim.h, _buf(u, np.float64, sim.nvec, "u"), _buf(v, np.float64, sim.nvec, "v"),
+                                   _stream(stream)))
+    sim._io_keep = getattr(sim, "_io_keep", []) + [x for x in (u, v) if x is not None]
+
+
+def pd_get_state_async(sim: Sim, u=None, v=None, stream=None) -> None:
+    """Queue the read of u and/or v into the given arrays and return; they hold
+    the result once pd_io_sync has returned."""
+    if u is None and v is None:
+        raise ValueError("pd_get_state_async needs u or v")
+    _check(_lib.pd_get_state_async(sim.h, _buf(u, np.float64, sim.nvec, "u", True),
+                                   _buf(v, np.float64, sim.nvec, "v", True), _stream(stream)))
+    sim._io_keep = getattr(sim, "_io_keep", []) + [x for x in (u, v) if x is not None]
+
+
+def pd_io_sync(sim: Sim) -> None:
+    """Wait for every host-array copy of the simulation issued so far."""
+    _check(_lib.pd_io_sync(sim.h))
+    sim._io_keep = []
 
 
 def pd_set_bc(sim: Sim, kind=None, value=None, stream=None) -> None:

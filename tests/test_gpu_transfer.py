@@ -115,3 +115,43 @@ def test_repeated_host_transfers_in_a_loop(env):
         assert np.array_equal(uo.numpy(), want)
     sim.close()
     ref.close()
+
+
+@pytest.mark.parametrize("dim,n", [GRIDS[0], GRIDS[2]])
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_pipelined_transfers_equal_the_synchronous_ones(env, dim, n, prec):
+    """pd_set_state_async / pd_step_explicit / pd_get_state_async per step, one
+    pd_io_sync at the end (the next step's upload overlapping this step's
+    compute and download), with a different state every step and a result array
+    per step: every result equals the synchronous loop's, bit for bit."""
+    pd, torch = env
+    precision = pd.PD_FP32C if prec == "fp32c" else pd.PD_FP64
+    steps = 5
+    ins = [_fields(W.Grid(dim=dim, n=n, h=0.01, m=3), 11 + k) for k in range(steps)]
+    want = []
+    sim, grid = _sim(pd, dim, n, precision)
+    for u, v in ins:
+        pd.pd_set_state(sim, u=u, v=v)
+        pd.pd_step_explicit(sim, 1)
+        want.append(pd.pd_get_state(sim, want_v=True))
+    sim.close()
+    sim, grid = _sim(pd, dim, n, precision)
+    pin = [(torch.from_numpy(u).pin_memory(), torch.from_numpy(v).pin_memory()) for u, v in ins]
+    outs = [(torch.empty(u.shape, dtype=torch.float64).pin_memory(),
+             torch.empty(v.shape, dtype=torch.float64).pin_memory()) for u, v in ins]
+    for (u, v), (uo, vo) in zip(pin, outs):
+        pd.pd_set_state_async(sim, u=u, v=v)
+        pd.pd_step_explicit(sim, 1)
+        pd.pd_get_state_async(sim, u=uo, v=vo)
+    pd.pd_io_sync(sim)
+    # the last result again into one array written by every step (ordered copies)
+    same = torch.empty(ins[0][0].shape, dtype=torch.float64).pin_memory()
+    for u, v in pin:
+        pd.pd_set_state_async(sim, u=u, v=v)
+        pd.pd_step_explicit(sim, 1)
+        pd.pd_get_state_async(sim, u=same)
+    pd.pd_io_sync(sim)
+    sim.close()
+    for (uw, vw), (uo, vo) in zip(want, outs):
+        assert np.array_equal(uo.numpy(), uw) and np.array_equal(vo.numpy(), vw)
+    assert np.array_equal(same.numpy(), want[-1][0])
