@@ -748,7 +748,29 @@ def explicit_measurement(pd, torch, wl, key, args, stream, flush, state, world, 
     out = {"sim": sim, "nbonds": nbonds, "ms": ms, "passes_ms": passes}
     if with_e2e:
         out["e2e"] = e2e_rate(pd, torch, sim, wl, nbonds, args.steps, args.warmup, stream, world)
+        out["back_to_back"] = back_to_back(pd, torch, sim, wl, nbonds, stream, world)
     return out
+
+
+def back_to_back(pd, torch, sim, wl, nbonds, stream, world, steps=64):
+    """Steps run back to back as a long run does (pd_step_explicit(steps): CUDA
+    graphs of 16 steps replayed), L2 not flushed between them. The step's state,
+    staging pairs, bond masks and tables are read (and the state written) every
+    step: for the 128^3 LPS block about 290 MB per step, more than the 129 MB
+    L2; the 64^3 block's fit in it."""
+    pd.pd_set_state(sim, u=wl.u0, v=wl.v0, stream=stream)
+    if wl.bc_kind is not None and wl.bc_kind.any():
+        pd.pd_set_bc(sim, wl.bc_kind, wl.bc_val, stream)
+    pd.pd_step_explicit(sim, 33, stream)                  # the first (restart) step and both graph parities
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pd.pd_step_explicit(sim, steps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = rank_reduce(torch, e0.elapsed_time(e1), "max", "cuda") / steps
+    return {"value": world * nbonds / (ms * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms, "steps": steps,
+            "note": "pd_step_explicit(%d) timed as one call (graph replays), L2 not flushed between steps" % steps}
 
 
 def state_variants(pd, torch, wl, stream, flush, tile_log2, steps=100):
@@ -817,7 +839,8 @@ def side_step(pd, torch, name, stream, flush, args):
     out = {"workload": desc, "value": nb / (ms * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms,
            "steps": len(d), "bonds": nb, "tile_log2": sim.tile_log2,
            "launches_per_step": 2 if key == "lps" else 1,
-           "roofline": roofline_of(key, wl, nb, passes, ms, sim.tile_log2, measured_peaks())}
+           "roofline": roofline_of(key, wl, nb, passes, ms, sim.tile_log2, measured_peaks()),
+           "back_to_back": back_to_back(pd, torch, sim, wl, nb, stream, 1)}
     sim.close()
     return out, wl
 
@@ -954,7 +977,7 @@ def main():
                        "tile_choice": "pd_tune_tile (best of 3 x 10 back-to-back steps per tile)"
                        if args.tile_log2 is None else "--tile-log2"},
             "gpu_launches": args.steps * launches_per_step,
-            "roofline": roofline, "e2e": m["e2e"]}
+            "roofline": roofline, "e2e": m["e2e"], "back_to_back": m["back_to_back"]}
     sim.close()
 
     if not args.no_extras and rank == 0:
