@@ -522,6 +522,20 @@ def run_convergence(args, pd, torch):
     print(json.dumps(line), flush=True)
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(wl, target_s=12.0, max_steps=50):
     """The FP64 oracle (as it stands) on the host cores: a bounded number of explicit
     steps of the same workload."""
@@ -542,6 +556,7 @@ def cpu_baseline(wl, target_s=12.0, max_steps=50):
     st.run(dt, n)
     el = time.time() - t2
     out = {"value": bonds.nbonds * n / el, "unit": "bond-updates/s", "cores": O.num_threads(),
+           "cpu": cpu_model(),
            "kind": "oracle",
            "sample": "%d explicit steps of the full workload (FP64 C oracle, OpenMP over points); "
                      "setup %.1f s not timed" % (n, setup)}
@@ -630,7 +645,7 @@ def run_reference(args):
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "bonds": bonds.nbonds},
-            "cpu_baseline": {"value": val, "unit": "bond-updates/s", "cores": O.num_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "bond-updates/s", "cores": O.num_threads(), "cpu": cpu_model(), "kind": "oracle",
                              "sample": "%d explicit steps of the full workload after %d warm-up steps"
                                        % (args.steps, max(args.warmup, 1))},
             "e2e": {"value": val, "unit": "bond-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -721,10 +736,13 @@ def roofline_of(key, wl, nbonds, passes_ms, step_ms, tile_log2, peaks):
                    "frac": gbs / hbm, "per_point_bytes": PER_POINT_BYTES[nm],
                    "per_point_frac": PER_POINT_BYTES[nm] * npts / (passes_ms[i] * 1e-3) / 1e9 / hbm,
                    "traffic": ncu_traffic(nm, tile_log2)}
+        per[nm]["traffic_gbs"] = (per[nm]["traffic"] / (passes_ms[i] * 1e-3) / 1e9
+                                  if per[nm]["traffic"] else None)
     dom = per[names[-1]]
     step_bytes = sum(ALG_BYTES[nm][0] * nbonds + ALG_BYTES[nm][1] * npts for nm in names)
     r = {"bound": "hbm", "achieved": dom["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": dom["frac"],
-         "traffic": dom["traffic"], "kernel": dom["kernel"], "launch_ms": dom["launch_ms"],
+         "traffic": dom["traffic"], "traffic_gbs": dom["traffic_gbs"], "kernel": dom["kernel"],
+         "launch_ms": dom["launch_ms"],
          "bytes_per_launch": dom["bytes_per_launch"], "bytes_model": dom["bytes_model"],
          "peak_source": src, "passes": per,
          "step": {"bytes": step_bytes, "ms": step_ms, "achieved_gbs": step_bytes / (step_ms * 1e-3) / 1e9,
@@ -795,15 +813,27 @@ def state_variants(pd, torch, wl, stream, flush, tile_log2, steps=100):
             "v_rel_l2_df_vs_f64": float(np.linalg.norm(vdf - v64) / max(np.linalg.norm(v64), 1e-300))}
 
 
+# FP64 operations per bond and step of the all-FP64 path, estimated from the bond
+# arithmetic of each pass (square root and division counted as one each): the
+# bond-based step about 30, the LPS dilatation about 20 and its force pass 35.
+FP64_FLOPS_PER_BOND = {"pmb3": 30.0, "pmb2": 30.0, "lps": 55.0, "np2": 30.0}
+FP64_NOMINAL_TFLOPS = 1.25
+
+
 def fp64_path(pd, torch, wl, stream, flush, nbonds, ms32, peak_note=True):
-    """The plain all-FP64 GPU path on the same workload."""
+    """The plain all-FP64 GPU path on the same workload, with its FP64 rate
+    against GB300's nominal FP64 rate (no measured FP64 peak is available)."""
     sim64 = make_sim(pd, wl, pd.PD_FP64, stream)
     d64 = time_steps(pd, torch, sim64, wl, 5, 3, stream, flush)
     ms64 = float(np.mean(d64))
     tile = sim64.tile_log2
     sim64.close()
+    fpb = FP64_FLOPS_PER_BOND[workload_key(wl)]
+    tf = fpb * nbonds / (ms64 * 1e-3) / 1e12
     return {"value": nbonds / (ms64 * 1e-3), "unit": "bond-updates/s", "ms_per_step": ms64, "tile_log2": tile,
-            "steps": len(d64), "ratio_fp64_over_fp32c": ms64 / ms32}
+            "steps": len(d64), "ratio_fp64_over_fp32c": ms64 / ms32,
+            "fp64": {"flops_per_bond": fpb, "achieved_tflops": tf, "peak_tflops": FP64_NOMINAL_TFLOPS,
+                     "frac": tf / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 FP64 rate"}}
 
 
 def fp32c_vs_fp64(pd, wl, stream, steps=200):
