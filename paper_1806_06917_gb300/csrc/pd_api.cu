@@ -659,9 +659,17 @@ int pdk::sim_pack_info(pd_sim *s, PackInfo *pi)
     if (model == PD_MODEL_PMB && s->mat.s_c == 0.0) kind = g.dim == 3 ? PK_PMB3 : PK_PMB2;
     if (model == PD_MODEL_LPS && !s->mat.vol_corr) kind = PK_LPS;
     pi->eligible = s->precision == PD_FP32C && kind >= 0 && g.L == 9 && s->nbr_ok &&
-                   (kind == PK_LPS || s->run.pair_threads == split);
+                   (kind == PK_LPS || s->run.pair_threads == split) &&
+                   (kind != PK_LPS || (g.dim == 3 && g.m <= PACK_LPS_MMAX &&
+                                       s->htab_a.size() == 3 * (size_t)pack_lps_stencil(g.m) &&
+                                       s->htab_b.size() == 3 * (size_t)pack_lps_stencil(g.m)));
     if (!pi->eligible) return PD_OK;
     pi->kind = kind;
+    pi->m = g.m;
+    if (kind == PK_LPS) {
+        pi->htab_dil = s->htab_a.data();
+        pi->htab_force = s->htab_b.data();
+    }
     pi->split = kind == PK_LPS ? 2 : split;
     pi->ntiles = g.ntiles;
     pi->smem = pack_smem(g, kind, split);

@@ -98,8 +98,14 @@ __device__ bool wait_dil(const PackTable &t, const PackReq &q, int r, int tile, 
 // its own register allocation, 216 bytes of spills per thread down to at most
 // 40, but the request mix measured slower that way: 2.38e11 against 2.47e11
 // bond updates/s.)
-static __device__ __forceinline__ void pk_lps_dil(const TileArgs &a, int tile) { lps_dil_h2_body<false, false>(a, tile, nullptr); }
-static __device__ __forceinline__ void pk_lps_force(const TileArgs &a, int tile) { lps_force_fast_body<false, false>(a, tile, nullptr); }
+static __device__ __forceinline__ void pk_lps_dil(const TileArgs &a, int tile, const float4 *tab)
+{
+    lps_dil_h2_body<false, true>(a, tile, tab);
+}
+static __device__ __forceinline__ void pk_lps_force(const TileArgs &a, int tile, const float4 *tab)
+{
+    lps_force_fast_body<false, true>(a, tile, tab);
+}
 static __device__ __forceinline__ void pk_pmb3s(const TileArgs &a, int tile) { pmb_fast_body<3, false, true, false>(a, tile, nullptr); }
 static __device__ __forceinline__ void pk_pmb3(const TileArgs &a, int tile) { pmb_fast_body<3, false, false, false>(a, tile, nullptr); }
 static __device__ __forceinline__ void pk_pmb2s(const TileArgs &a, int tile) { pmb_fast_body<2, false, true, false>(a, tile, nullptr); }
@@ -173,8 +179,10 @@ __global__ void __launch_bounds__(PACK_THREADS, 2) pd_packed_round(const __grid_
         }
         const int kind = q.kind, split = q.split;
         if (kind == PK_LPS) {
-            if (grp == 0) pk_lps_dil(s_a, tile);
-            else pk_lps_force(s_a, tile);
+            // the tables from the parameter bank (the host packs LPS requests of
+            // m <= 3 only, whose tables it has placed there)
+            if (grp == 0) pk_lps_dil(s_a, tile, t.tabs + q.tab_dil);
+            else pk_lps_force(s_a, tile, t.tabs + q.tab_force);
         } else if (kind == PK_PMB3) {
             if (split == 2) pk_pmb3s(s_a, tile);
             else pk_pmb3(s_a, tile);

@@ -24,6 +24,22 @@ enum PackKind { PK_PMB3 = 0, PK_PMB2 = 1, PK_LPS = 2 };
 
 constexpr int PACK_THREADS = 512;         // CTA size: the LPS force pass of a 2^9-point tile
 
+// The LPS passes' stencil tables (3 float4 per stencil entry, the dilatation's
+// then the force pass's) for horizons m = 1, 2, 3 on 2^9-point (8 x 8 x 8)
+// tiles, carried in the kernel's parameter bank (read as constant-bank loads,
+// as the simulations' own kernels read theirs) instead of shared memory: they
+// depend on m alone. Stencil sizes 6, 32 and 122.
+constexpr int PACK_LPS_MMAX = 3;
+constexpr int PACK_TAB_N = 2 * 3 * (6 + 32 + 122);
+inline int pack_lps_stencil(int m) { return m == 1 ? 6 : m == 2 ? 32 : m == 3 ? 122 : 0; }
+// Offset of horizon m's dilatation table (which = 0) or force table (which = 1).
+inline int pack_tab_offset(int m, int which)
+{
+    int off = 0;
+    for (int k = 1; k < m; ++k) off += 2 * 3 * pack_lps_stencil(k);
+    return off + which * 3 * pack_lps_stencil(m);
+}
+
 // One request of a quantum (device table entry, built by the server).
 struct PackReq {
     TileArgs a[2];          // MODE_STEP arguments by staging parity (src = hl[p], dst = hl[p ^ 1]),
@@ -34,6 +50,7 @@ struct PackReq {
     int nsteps;             // rounds this request takes part in
     int cur0;               // staging parity at the quantum's start
     int vhalf0, cd0;        // v_is_half and the central-difference flag of the quantum's first step
+    int tab_dil, tab_force; // LPS: offsets of its tables in PackTable.tabs
     int pad_;
     unsigned *dil_done;     // LPS: per tile, 1 + the step of its last dilatation (monotonic)
     long long step0;        // the simulation's step count at the quantum's start
@@ -53,13 +70,16 @@ struct PackTable {
     long long wait_ns;      // limit of one wait
     int nreq;
     int stall;              // tests only: the first group-B item of round 0 waits on a flag nothing sets
+    float4 tabs[PACK_TAB_N];  // the LPS tables (pack_tab_offset)
 };
 
 // What the server needs of a simulation to pack it (pd_api.cu).
 struct PackInfo {
     int eligible;           // the packed kernel can step it (FP32C, PMB without breaking or LPS without
-                            // partial volume, 2^9-point tiles, pair_threads as the packed body's)
+                            // partial volume and m <= 3, 2^9-point tiles, pair_threads as the packed body's)
     int kind, split, ntiles;
+    int m;                  // horizon in lattice spacings
+    const float4 *htab_dil, *htab_force;   // LPS: the simulation's host tables (3 pack_lps_stencil(m) float4 each)
     size_t smem;
     TileArgs a[2];          // MODE_STEP by staging parity, flags of a step after the first
     int cur, vhalf, cd0, cd;

@@ -131,7 +131,16 @@ struct pd_server {
     int *d_idx[2] = {nullptr, nullptr}, *h_idx[2] = {nullptr, nullptr};   // offA, offB, nsteps
     unsigned *d_counters[2] = {nullptr, nullptr}, *d_status[2] = {nullptr, nullptr};
     unsigned *h_status[2] = {nullptr, nullptr};
-    std::map<std::tuple<int, int, size_t, int>, cudaGraphExec_t> graphs;   // (rounds, grid, smem, buffer)
+    std::map<std::tuple<int, int, size_t, int, int>, cudaGraphExec_t> graphs;   // (rounds, grid, smem, buffer,
+                                                                                // table version)
+    // the packed kernel's LPS tables (PackTable.tabs), each horizon's taken from
+    // the first simulation of that horizon set up; a later one whose tables differ
+    // is not packed. tab_version counts the fills (graphs hold the tables they
+    // were captured with).
+    std::mutex tab_mu;
+    std::vector<float4> pk_tabs = std::vector<float4>(PACK_TAB_N, make_float4(0.f, 0.f, 0.f, 0.f));
+    bool tab_filled[PACK_LPS_MMAX + 1] = {};
+    int tab_version = 0;
     struct PkQuantum {
         int buf;
         std::vector<std::pair<Req *, int>> list;   // requests and their steps
@@ -219,6 +228,21 @@ int pd_server::setup(Req *r)
     if (mode == PD_SERVE_PACKED) {
         PackInfo pi;
         if ((rc = sim_pack_info(r->sim, &pi)) != PD_OK) return rc;
+        if (pi.eligible && pi.kind == PK_LPS) {
+            // its tables into the packed kernel's parameter bank (or the same already there)
+            const size_t n = 3 * (size_t)pack_lps_stencil(pi.m);
+            const int o0 = pack_tab_offset(pi.m, 0), o1 = pack_tab_offset(pi.m, 1);
+            std::lock_guard<std::mutex> lk(tab_mu);
+            if (!tab_filled[pi.m]) {
+                std::copy(pi.htab_dil, pi.htab_dil + n, pk_tabs.begin() + o0);
+                std::copy(pi.htab_force, pi.htab_force + n, pk_tabs.begin() + o1);
+                tab_filled[pi.m] = true;
+                ++tab_version;
+            } else if (memcmp(pi.htab_dil, pk_tabs.data() + o0, n * sizeof(float4)) != 0 ||
+                       memcmp(pi.htab_force, pk_tabs.data() + o1, n * sizeof(float4)) != 0) {
+                pi.eligible = 0;
+            }
+        }
         if (pi.eligible) {
             r->packed = true;
             r->pack_kind = pi.kind;
@@ -511,6 +535,10 @@ int pd_server::pk_issue(std::vector<Req *> &active)
             q.cd0 = pi.cd0;
             q.dil_done = list[i].first->dil_done;
             q.step0 = pi.step;
+            if (pi.kind == PK_LPS) {
+                q.tab_dil = pack_tab_offset(pi.m, 0);
+                q.tab_force = pack_tab_offset(pi.m, 1);
+            }
             nst[i] = q.nsteps;
             na = pi.ntiles;
             nb = pi.kind == PK_LPS ? pi.ntiles : 0;
@@ -527,10 +555,21 @@ int pd_server::pk_issue(std::vector<Req *> &active)
     const int grid = ctas * sms;
     PD_CUDA(cudaMemcpyAsync(d_req[buf], h_req[buf], sizeof(PackReq) * n, cudaMemcpyHostToDevice, pk_stream));
     PD_CUDA(cudaMemcpyAsync(d_idx[buf], h_idx[buf], sizeof(int) * (3 * n + 2), cudaMemcpyHostToDevice, pk_stream));
-    const auto key = std::make_tuple(rounds, grid, smem, buf);
+    int version;
+    {
+        std::lock_guard<std::mutex> lk(tab_mu);
+        version = tab_version;
+    }
+    const auto key = std::make_tuple(rounds, grid, smem, buf, version);
     auto it = graphs.find(key);
     if (it == graphs.end()) {
-        PackTable t;
+        // (about 15 KB of parameters: on the heap, copied into the launches)
+        std::unique_ptr<PackTable> tp(new PackTable());
+        PackTable &t = *tp;
+        {
+            std::lock_guard<std::mutex> lk(tab_mu);
+            std::copy(pk_tabs.begin(), pk_tabs.end(), t.tabs);
+        }
         t.req = d_req[buf];
         t.offA = d_idx[buf];
         t.offB = d_idx[buf] + (n + 1);
