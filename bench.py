@@ -1010,7 +1010,9 @@ def main():
             "roofline": roofline, "e2e": m["e2e"], "back_to_back": m["back_to_back"]}
     sim.close()
 
-    if not args.no_extras and rank == 0:
+    # single-GPU side measurements (their own reductions would wait for the other
+    # ranks of a multi-GPU run, which do not take part)
+    if not args.no_extras and world == 1:
         line["fp64_path"] = fp64_path(pd, torch, wl, stream, flush, nbonds, ms)
         line["state_variants"] = state_variants(pd, torch, wl, stream, flush, args.tile_log2 or 0)
         line["fp32c_vs_fp64"] = fp32c_vs_fp64(pd, wl, stream, steps=100 if key == "lps" else 200)
