@@ -1,16 +1,23 @@
 // pd_server.cu -- the request server of include/pd.h: independent simulations
-// submitted at any time, admitted by device-memory budget, stepped concurrently
-// on their own streams in quanta of graph-replayed explicit steps, and
-// collected through tickets. This is the paper's task model (Sec. 2: work
-// expressed as futures that a runtime schedules as resources allow) applied to
-// whole simulations on one GPU.
+// submitted at any time (refused with PD_EBUSY while max_queued wait), admitted
+// by device-memory budget, stepped concurrently in quanta and collected through
+// tickets. Packed mode (the default): the FP32C PMB requests without breaking
+// and the LPS requests without partial volume (m <= 3) advance together, one
+// launch of the packed kernel (pd_packed.cu) per step of a quantum, the
+// quantum's launches replayed from a captured graph, two quanta in flight; the
+// other requests, and all of them in streams mode, step on their own streams in
+// quanta of graph-replayed explicit steps, with a measured (tile, threads per
+// pair) choice cached per request class. This is the paper's task model (Sec. 2:
+// work expressed as futures that a runtime schedules as resources allow) applied
+// to whole simulations on one GPU.
 //
 // Threads: the caller's threads only touch the queue and the ticket records
 // (under one mutex). A setup thread builds each admitted simulation (tables,
-// neighbour build, initial state) while the worker thread keeps stepping the
-// running ones; from then on the worker owns the simulation, its stream and
-// event. Every wait of either thread is bounded (event queries with short
-// sleeps, timed condition-variable waits).
+// neighbour build, initial state, the packed kernel's LPS tables) while the
+// worker thread keeps stepping the running ones; from then on the worker owns
+// the simulation, its stream and event. Every wait of either thread is bounded
+// (event queries with short sleeps, timed condition-variable waits), and so is
+// every device-side wait of the packed kernel (PD_ETIMEOUT).
 #include <stdio.h>
 #include <string.h>
 
