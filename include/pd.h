@@ -409,9 +409,10 @@ int pd_solve_static(pd_sim *sim, const pd_newton_opts *opts, pd_newton_stats *st
  * quanta (continuous batching).
  *
  * PD_SERVE_PACKED (default): FP32C PMB requests without breaking and FP32C LPS
- * requests without partial volume (on 2^9-point tiles, with the pair_threads
- * the server sets: 2 where the stencil has two or more 32-bond words, else 1)
- * are stepped together by one packed kernel: per explicit step one launch of a
+ * requests without partial volume and of horizon m <= 3 (on 2^9-point tiles,
+ * with the pair_threads the server sets: 2 where the stencil has two or more
+ * 32-bond words, else 1; up to pack_max_tiles tiles when that is set) are
+ * stepped together by one packed kernel: per explicit step one launch of a
  * persistent grid whose CTAs take (request, pass, tile) work items of every
  * such request from a device-side list (the LPS force items after the
  * dilatation items they need, with a bounded wait on completion flags), the
