@@ -155,3 +155,43 @@ def test_pipelined_transfers_equal_the_synchronous_ones(env, dim, n, prec):
     for (uw, vw), (uo, vo) in zip(want, outs):
         assert np.array_equal(uo.numpy(), uw) and np.array_equal(vo.numpy(), vw)
     assert np.array_equal(same.numpy(), want[-1][0])
+
+
+def test_async_calls_mix_with_synchronous_ones_and_device_arrays(env):
+    """pd_get_state_async with v (the half-step velocity completed first), its
+    result read after pd_io_sync; a synchronous pd_set_state / pd_get_state
+    between asynchronous ones; device tensors through the async calls (used in
+    place, stream-ordered): every read equals the synchronous reference."""
+    pd, torch = env
+    dim, n = GRIDS[0]
+    grid = W.Grid(dim=dim, n=n, h=0.01, m=3)
+    u0, v0 = _fields(grid, 21)
+    u1, v1 = _fields(grid, 22)
+    ref, _ = _sim(pd, dim, n, pd.PD_FP32C)
+    pd.pd_set_state(ref, u=u0, v=v0)
+    pd.pd_step_explicit(ref, 3)
+    want0 = pd.pd_get_state(ref)
+    pd.pd_set_state(ref, u=u1, v=v1)
+    pd.pd_step_explicit(ref, 2)
+    want1 = pd.pd_get_state(ref)
+    ref.close()
+    sim, _ = _sim(pd, dim, n, pd.PD_FP32C)
+    pd.pd_set_state_async(sim, u=torch.from_numpy(u0).pin_memory(), v=torch.from_numpy(v0).pin_memory())
+    pd.pd_step_explicit(sim, 3)
+    uo, vo = (torch.empty(u0.shape, dtype=torch.float64).pin_memory() for _ in range(2))
+    pd.pd_get_state_async(sim, u=uo, v=vo)
+    pd.pd_io_sync(sim)
+    assert np.array_equal(uo.numpy(), want0[0]) and np.array_equal(vo.numpy(), want0[1])
+    # synchronous calls in between, then device tensors through the async ones
+    pd.pd_set_state(sim, u=u1, v=v1)
+    ud, vd = torch.from_numpy(u1).cuda(), torch.from_numpy(v1).cuda()
+    pd.pd_set_state_async(sim, u=ud, v=vd, stream=torch.cuda.current_stream())
+    pd.pd_step_explicit(sim, 2, torch.cuda.current_stream())
+    uo2, vo2 = torch.empty_like(ud), torch.empty_like(vd)
+    pd.pd_get_state_async(sim, u=uo2, v=vo2, stream=torch.cuda.current_stream())
+    pd.pd_io_sync(sim)
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(uo2.cpu().numpy(), want1[0]) and np.array_equal(vo2.cpu().numpy(), want1[1])
+    u_s, v_s = pd.pd_get_state(sim)
+    assert np.array_equal(u_s, want1[0]) and np.array_equal(v_s, want1[1])
+    sim.close()
