@@ -1228,9 +1228,11 @@ int pd_break_bonds(pd_sim *s, int axis, double pos, const double lo[3], const do
 // their own buffers and copy streams, so an upload may run while an earlier
 // download is still copying out, in the other direction of the link, and both
 // fields of an upload may cross the link while st still computes.
-// Unless async, the copies also wait for the work already queued on st (the
-// caller's arrays may be written by it) and st waits for them at the end. Every
-// wait is an event in stream order: no host synchronisation here.
+// Synchronous calls: the copies also wait for the work already queued on st (the
+// caller's arrays may be written by it) and st waits for them at the end.
+// Pipelined (async) calls move each field in one copy and one conversion pass,
+// waiting only for the staging buffer. Every wait is an event in stream order:
+// no host synchronisation here.
 static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2], bool upload, cudaStream_t st,
                        bool async)
 {
@@ -1246,10 +1248,42 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
     const long long rows = ((n + nc - 1) / nc + 255) / 256 * 256;
     cudaStream_t cs = upload ? s->copy_stream : s->copy_out;
     cudaEvent_t ev_join = upload ? s->ev_in : s->ev_out;
-    if (!async) {
-        PD_CUDA(cudaEventRecord(ev_join, st));
-        PD_CUDA(cudaStreamWaitEvent(cs, ev_join, 0));
+    if (async) {
+        // pipelined calls: each field in one copy and one conversion pass (its
+        // copy overlaps the previous step, so chunks would only add launches on
+        // st); every chunk's event is recorded, so that a later chunked call
+        // waits for the whole pass
+        for (int f = 0; f < 2; ++f) {
+            if (!host[f]) continue;
+            double *const *slot = pairs ? nullptr : (is_u[f] ? s->u : s->v);
+            float4 *hl = pairs ? (is_u[f] ? s->hl[s->cur] : s->vhl)
+                               : (f32c && is_u[f] && upload ? s->hl[s->cur] : nullptr);
+            double4_32a *d4 = !f32c && is_u[f] ? s->d4[s->cur] : nullptr;
+            const size_t bytes = (size_t)n * row_bytes;
+            if (upload) {
+                double *base = s->io_up + (size_t)f * n * d;
+                for (int k = 0; k < IO_CHUNKS; ++k) PD_CUDA(cudaStreamWaitEvent(cs, s->ev_done[f][k], 0));
+                PD_CUDA(cudaMemcpyAsync(base, host[f], bytes, cudaMemcpyDefault, cs));
+                PD_CUDA(cudaEventRecord(s->ev_copy[f][0], cs));
+                PD_CUDA(cudaStreamWaitEvent(st, s->ev_copy[f][0], 0));
+                int rc = scatter_rows(g, s->slot_of_user, base, 0, n, slot, hl, d4, st, f32c && s->state64);
+                if (rc != PD_OK) return rc;
+                for (int k = 0; k < IO_CHUNKS; ++k) PD_CUDA(cudaEventRecord(s->ev_done[f][k], st));
+            } else {
+                double *base = s->io_dn + (size_t)f * n * d;
+                for (int k = 0; k < IO_CHUNKS; ++k) PD_CUDA(cudaStreamWaitEvent(st, s->ev_dcopy[f][k], 0));
+                int rc = gather_rows(g, s->slot_of_user, hl, slot, base, 0, n, st);
+                if (rc != PD_OK) return rc;
+                PD_CUDA(cudaEventRecord(s->ev_dgath[f][0], st));
+                PD_CUDA(cudaStreamWaitEvent(cs, s->ev_dgath[f][0], 0));
+                PD_CUDA(cudaMemcpyAsync(const_cast<double *>(host[f]), base, bytes, cudaMemcpyDefault, cs));
+                for (int k = 0; k < IO_CHUNKS; ++k) PD_CUDA(cudaEventRecord(s->ev_dcopy[f][k], cs));
+            }
+        }
+        return PD_OK;
     }
+    PD_CUDA(cudaEventRecord(ev_join, st));
+    PD_CUDA(cudaStreamWaitEvent(cs, ev_join, 0));
     for (int f = 0; f < 2; ++f) {
         if (!host[f]) continue;
         double *const *slot = pairs ? nullptr : (is_u[f] ? s->u : s->v);
@@ -1281,11 +1315,9 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
             }
         }
     }
-    if (!async) {
-        // the caller's stream finishes after every copy of this call
-        PD_CUDA(cudaEventRecord(ev_join, cs));
-        PD_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
-    }
+    // the caller's stream finishes after every copy of this call
+    PD_CUDA(cudaEventRecord(ev_join, cs));
+    PD_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
     return PD_OK;
 }
 
