@@ -106,7 +106,7 @@ __device__ __forceinline__ void lps_dil_fast_body(const TileArgs &a, int tile, c
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
     float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
-    if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
+    if (threadIdx.x == 0) prefetch_tile_masks(a, tile);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
         for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
@@ -217,7 +217,7 @@ __device__ __forceinline__ void lps_dil_fast2_body(const TileArgs &a, int tile, 
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
     float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
-    if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
+    if (threadIdx.x == 0) prefetch_tile_masks(a, tile);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
         for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);
@@ -225,6 +225,8 @@ __device__ __forceinline__ void lps_dil_fast2_body(const TileArgs &a, int tile, 
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
     __syncthreads();
+    // 1/m~ of the tile's points, read by the epilogue (128^3 LPS pass 0.2167 -> 0.2151 ms)
+    if (threadIdx.x == 0) l2_prefetch(a.minv32 + (size_t)tile * g.T, 4 * g.T);
 
     const int nthr = g.T / 4;                                  // a multiple of 32
     const int half = threadIdx.x >= nthr, t = threadIdx.x - half * nthr;
@@ -298,7 +300,7 @@ __device__ __forceinline__ void lps_force_fast_body(const TileArgs &a, int tile,
     float2 *P2 = reinterpret_cast<float2 *>(PT + pb.n);        // {zA, zB}
     float4 *tab = PT + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
-    if (threadIdx.x == 0) prefetch_tile_state(a, tile, true);
+    if (threadIdx.x == 0) prefetch_tile_masks(a, tile);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
         for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_b[k]);
@@ -322,6 +324,7 @@ __device__ __forceinline__ void lps_force_fast_body(const TileArgs &a, int tile,
         });
     }
     __syncthreads();
+    if (threadIdx.x == 0) prefetch_tile_update(a, tile);
 
     const int np = g.T / 2;                                    // point pairs of the tile
     const int half = threadIdx.x >= np;
@@ -387,7 +390,7 @@ __device__ __forceinline__ void lps_dil_h2_body(const TileArgs &a, int tile, con
     float2 *P2 = reinterpret_cast<float2 *>(P4 + pb.n);
     float4 *tab = P4 + pb.n + (pb.n + 1) / 2;                  // 3 float4 per entry
     __shared__ int s_nbr[27];
-    if (threadIdx.x == 0) prefetch_tile_state(a, tile, false);
+    if (threadIdx.x == 0) prefetch_tile_masks(a, tile);
     const int4 org = __ldg(&a.tile_org[tile]);
     if (!PTAB)
         for (int k = threadIdx.x; k < 3 * S; k += blockDim.x) tab[k] = __ldg(&a.tab_a[k]);

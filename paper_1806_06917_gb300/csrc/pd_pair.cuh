@@ -309,19 +309,33 @@ __device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Issued at an LPS pass's start by one thread: the tile's own slots of the bond
-// masks and (with update) of every array that the update reads, so that those
-// loads hit L2 when they come (the bond loop and the update run long after the
-// staging's loads, and each of these ranges is contiguous: slots
-// [tile T, (tile + 1) T)). Measured on the 128^3 LPS step: 0.645 -> 0.638 ms;
-// the PMB and NP kernels measured no gain (64^3) or a 1 % loss (443^2, m = 20:
-// 40 mask words per point) and do not issue it.
-__device__ __forceinline__ void prefetch_tile_state(const TileArgs &a, int tile, bool update)
+// Bulk L2 prefetches of one tile's own slots [tile T, (tile + 1) T) of arrays
+// that an LPS pass reads long after its staging loads (each range contiguous),
+// issued by one thread so that those loads hit L2 when they come. The bond masks
+// at the pass's start (the bond loop follows the staging); the update's state
+// (FP64 u and v, or the double-float velocity, the boundary kinds, the body
+// force, u^{k-1}) once the staging is done: issued at the start, beside the
+// staging's own loads, the FP64 u and v measured slower (128^3 LPS step 0.596
+// against 0.588 ms); after the staging, 0.568 -> 0.559 ms. The PMB and NP
+// kernels measured no gain from the mask prefetch (64^3) or a 1 % loss (443^2,
+// m = 20: 40 mask words per point) and do not issue it.
+__device__ __forceinline__ void prefetch_tile_masks(const TileArgs &a, int tile)
 {
     const uint32_t T = (uint32_t)a.g.T;
     const size_t ns = a.g.nslots, s0 = (size_t)tile * T;
     for (int w = 0; w < a.g.W; ++w) l2_prefetch(a.mask + w * ns + s0, 4 * T);
-    if (!update || a.mode == MODE_FORCE) return;
+}
+
+__device__ __forceinline__ void prefetch_tile_update(const TileArgs &a, int tile)
+{
+    if (a.mode == MODE_FORCE) return;
+    const uint32_t T = (uint32_t)a.g.T;
+    const size_t ns = a.g.nslots, s0 = (size_t)tile * T;
+    if (a.state64)
+        for (int c = 0; c < a.g.dim; ++c) {
+            if (a.mode == MODE_STEP) l2_prefetch(a.u[c] + s0, 8 * T);
+            l2_prefetch(a.v[c] + s0, 8 * T);
+        }
     if (a.vhl) l2_prefetch(a.vhl + 2 * s0, 32 * T);
     for (int c = 0; c < a.g.dim; ++c) l2_prefetch(a.bc_kind + c * ns + s0, T);
     if (a.use_body && a.body32) l2_prefetch(a.body32 + s0, 16 * T);
