@@ -398,6 +398,7 @@ __device__ __forceinline__ void lps_dil_h2_body(const TileArgs &a, int tile, con
     __syncthreads();
     stage_pairs(a, pb, org, tile, s_nbr, P4, P2, true);
     __syncthreads();
+    if (threadIdx.x == 0) l2_prefetch(a.minv32 + (size_t)tile * g.T, 4 * g.T);
 
     const int np = g.T / 2;                                    // point pairs; blockDim == 2 np
     const int half = threadIdx.x >= np, t = threadIdx.x - half * np;
