@@ -44,9 +44,6 @@ size_t pmb_fast_smem(const Geom &g);
 size_t np_fast_smem(const Geom &g);
 size_t lps_generic_smem(const Geom &g, int precision, bool dil);
 size_t jvp_smem(const Geom &g, int precision);
-// Slot order to user order with one thread per slot (pd_build.cu).
-int gather_slots(const Geom &g, const int *user_of_slot, const float4 *hl, double *const slot[3], double *user,
-                 cudaStream_t st);
 // Per-bond tangent cache (pd_tangent.cu): prepare at a linearisation point,
 // then y = A w (A = -K on free DOFs, identity on prescribed ones) from the cache.
 size_t tangent_cache_bytes(const Geom &g, int precision);
@@ -1254,10 +1251,11 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
     if (async) {
         // pipelined calls: each field in one copy and one conversion pass (its
         // copy overlaps the previous step, so chunks would only add launches on
-        // st), one thread per slot, so that the slot-order side is coalesced
-        // (128^3 LPS e2e step 0.694 -> 0.685 ms against one thread per user row);
-        // every chunk's event is recorded, so that a later chunked call waits
-        // for the whole pass
+        // st); the upload with one thread per slot, so that its slot-order writes
+        // (u, v and the staging pair) are coalesced, the download with one per
+        // user row (coalesced user-order writes): both measured faster than the
+        // other way round. Every chunk's event is recorded, so that a later
+        // chunked call waits for the whole pass
         for (int f = 0; f < 2; ++f) {
             if (!host[f]) continue;
             double *const *slot = pairs ? nullptr : (is_u[f] ? s->u : s->v);
@@ -1277,7 +1275,7 @@ static int xfer_chunks(pd_sim *s, const double *const host[2], const bool is_u[2
             } else {
                 double *base = s->io_dn + (size_t)f * n * d;
                 for (int k = 0; k < IO_CHUNKS; ++k) PD_CUDA(cudaStreamWaitEvent(st, s->ev_dcopy[f][k], 0));
-                int rc = gather_slots(g, s->user_of_slot, hl, slot, base, st);
+                int rc = gather_rows(g, s->slot_of_user, hl, slot, base, 0, n, st);
                 if (rc != PD_OK) return rc;
                 PD_CUDA(cudaEventRecord(s->ev_dgath[f][0], st));
                 PD_CUDA(cudaStreamWaitEvent(cs, s->ev_dgath[f][0], 0));

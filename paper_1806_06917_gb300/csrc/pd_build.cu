@@ -756,41 +756,6 @@ __global__ void k_gather_unstage(Geom g, const int *slot_of_user, const float4 *
     if (d == 3) user[i * d + 2] = z;
 }
 
-// The same gather with one thread per slot: slot-order reads coalesced, the
-// user rows written in runs of x-consecutive points.
-__global__ void k_gather_slots(Geom g, const int *user_of_slot, const float4 *hl, const double *s0, const double *s1,
-                               const double *s2, double *user)
-{
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.nslots) return;
-    const long long i = user_of_slot[s];
-    if (i < 0) return;
-    const int d = g.dim;
-    double x, y, z;
-    if (hl) {
-        const float4 hi = hl[2 * s], lo = hl[2 * s + 1];
-        x = (double)hi.x + (double)lo.x;
-        y = (double)hi.y + (double)lo.y;
-        z = (double)hi.z + (double)lo.z;
-    } else {
-        x = s0[s];
-        y = s1[s];
-        z = d == 3 ? s2[s] : 0.0;
-    }
-    user[i * d] = x;
-    user[i * d + 1] = y;
-    if (d == 3) user[i * d + 2] = z;
-}
-
-int gather_slots(const Geom &g, const int *user_of_slot, const float4 *hl, double *const slot[3], double *user,
-                 cudaStream_t st)
-{
-    k_gather_slots<<<(g.nslots + 255) / 256, 256, 0, st>>>(g, user_of_slot, hl, slot ? slot[0] : nullptr,
-                                                            slot ? slot[1] : nullptr, slot ? slot[2] : nullptr, user);
-    PD_CUDA(cudaGetLastError());
-    return PD_OK;
-}
-
 int scatter_stage(const Geom &g, const int *user_of_slot, const double *user, double *const slot[3], float4 *hl,
                   double4_32a *d4, cudaStream_t st, bool bits)
 {
