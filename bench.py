@@ -73,9 +73,9 @@ _KERNEL_COMMON = ["paper_1806_06917_gb300/csrc/pd_internal.cuh", "paper_1806_069
 _LPS_SOURCES = ["paper_1806_06917_gb300/csrc/pd_force_lps.cu", "paper_1806_06917_gb300/csrc/pd_lps_fast.cuh"]
 NCU_TRAFFIC = {
     # (pass key, tile_log2): the capture of that kernel at that tile size
-    ("lps_dil", 9): {"bytes": 109745408 + 6098176, "sha": "a04a9b831e87453c",
+    ("lps_dil", 9): {"bytes": 109745408 + 6098176, "sha": "e7864e5b1918a9c7",
                      "sources": _LPS_SOURCES + _KERNEL_COMMON, "profile": "profiles/lps_block3d_128.md"},
-    ("lps_force", 9): {"bytes": 230127872 + 123059968, "sha": "a04a9b831e87453c",
+    ("lps_force", 9): {"bytes": 230127872 + 123059968, "sha": "e7864e5b1918a9c7",
                        "sources": _LPS_SOURCES + _KERNEL_COMMON, "profile": "profiles/lps_block3d_128.md"},
 }
 

@@ -380,8 +380,10 @@ __device__ __forceinline__ PairPts pair_points(const Geom &g, const PairBox &pb,
 // The fused update with FP64 integrator state (PD_STATE_F64): u and v live in
 // the FP64 component arrays a.u[c], a.v[c]. The kick dt/2 (f + b)/rho is formed
 // in FP32 from the FP32 force, as in the double-float form, and added to v in
-// FP64 (two additions for the two half-kicks of Eqs. (9) and (7), so that a
-// half step completed by MODE_FINALIZE rounds as in one kernel); the drift
+// FP64: from a half-step velocity, the previous step's second half-kick and this
+// step's first (the same kick) as one add of 2 kick, the leapfrog form of Eq.
+// (9); from a full-step velocity (a first step, or after MODE_FINALIZE) one
+// kick; MODE_FINALIZE adds the pending half-kick alone. The drift
 // u += dt v is one FP64 FMA; the next staging pair is u split into FP32 hi + lo
 // (split_bits). Central difference (Eq. (10)) reads u^{k-1} from the staging
 // pair it overwrites. One point at a time, its loads issued together (the
