@@ -438,6 +438,104 @@ def test_stable_dt_bound_separates_stable_from_unstable():
     assert not (np.isfinite(bad.u).all() and np.abs(bad.u).max() < 1e-3)
 
 
+@pytest.mark.parametrize("case", ["pmb3", "pmb2", "np2", "lp2"])
+def test_stable_dt_is_the_leapfrog_limit_of_a_two_point_body(case):
+    """Two points joined by one bond: the relative displacement along the bond is
+    one harmonic oscillator, rho w'' = -2 k w with k the bond's linear stiffness
+    per unit volume (c V / |xi|), and velocity-Verlet (leapfrog) keeps it bounded
+    exactly for omega dt < 2, omega^2 = 2 k / rho. The Silling-Askari sum has the
+    one term k here, so the bound sqrt(2 rho / k) is that limit 2 / omega: a run
+    at 0.98 dt_crit stays bounded, one at 1.02 dt_crit grows without bound."""
+    if case == "pmb3":
+        g, mat = _grid(3, (2, 1, 1), 1, h=0.02), W.Material(model=W.PMB, E=72e9, rho=2440.0)
+    elif case == "pmb2":
+        g, mat = _grid(2, (2, 1, 1), 1, h=0.02), W.Material(model=W.PMB, E=72e9, rho=2440.0, thickness=0.1)
+    else:
+        # m = 2: the neighbour at distance h lies inside the open horizon ball (J = 1)
+        g = _grid(2, (2, 1, 1), 2, h=0.0025)
+        mat = W.Material(model=W.NP if case == "np2" else W.LP, rho=1.0, psi_c=1.0, psi_beta=1.0)
+    b = O.neighbors(g)
+    assert b.nbonds == 2
+    dtc = O.stable_dt(g, mat, b)
+    a = 1e-9 * g.h                          # small: the NP law stays linear
+    u0 = np.zeros((2, g.dim))
+    u0[1, 0] = a
+    ok = O.ExplicitState(g, mat, b, u0, np.zeros_like(u0))
+    ok.run(0.98 * dtc, 3000)
+    assert np.isfinite(ok.u).all() and np.abs(ok.u).max() < 20 * a
+    bad = O.ExplicitState(g, mat, b, u0, np.zeros_like(u0))
+    bad.run(1.02 * dtc, 80)
+    assert not (np.isfinite(bad.u).all() and np.abs(bad.u).max() < 1e6 * a)
+
+
+def test_lps_stable_dt_is_the_pmb_bound_of_the_same_young_modulus():
+    """Reading of the LPS step bound: the PMB bound of the material's Young's
+    modulus, here formed from K and mu through the Poisson ratio,
+    E = 2 mu (1 + nu), nu = (3K - 2mu) / (2 (3K + mu))."""
+    g = _grid(3, (9, 8, 7), 3, h=0.01)
+    b = O.neighbors(g)
+    K, mu, rho = 40e9, 30e9, 2440.0
+    nu = (3 * K - 2 * mu) / (2 * (3 * K + mu))
+    E = 2 * mu * (1 + nu)
+    dt_lps = O.stable_dt(g, W.Material(model=W.LPS, K=K, mu=mu, rho=rho), b)
+    dt_pmb = O.stable_dt(g, W.Material(model=W.PMB, E=E, rho=rho), b)
+    assert abs(dt_lps - dt_pmb) <= 1e-12 * dt_pmb
+
+
+def test_2d_pmb_force_density_does_not_depend_on_the_plate_thickness():
+    """The 2D micromodulus is calibrated per unit thickness (c t is fixed by E and
+    delta), so a plate's force per unit volume is the same for every thickness
+    and its strain energy grows in proportion to the thickness."""
+    g = _grid(2, (9, 8, 1), 3, h=0.01)
+    b = O.neighbors(g)
+    u = W.random_field(g, 1e-6, seed=7)
+    m1 = W.Material(model=W.PMB, E=72e9, thickness=1.0)
+    m2 = W.Material(model=W.PMB, E=72e9, thickness=0.013)
+    f1, f2 = O.pmb_force(g, m1, b, u), O.pmb_force(g, m2, b, u)
+    np.testing.assert_allclose(f2, f1, rtol=1e-12, atol=1e-12 * np.abs(f1).max())
+    e1, e2 = O.strain_energy(g, m1, b, u), O.strain_energy(g, m2, b, u)
+    assert abs(e2 / e1 - 0.013) < 1e-12
+
+
+def test_prescribed_displacement_holds_its_value_with_zero_velocity():
+    """A degree of freedom with a prescribed displacement takes its value at every
+    step with zero velocity, whatever force acts on it, while the free ones move."""
+    g = _grid(2, (12, 10, 1), 3, h=0.01)
+    mat = W.Material(model=W.PMB, E=72e9, rho=2440.0)
+    b = O.neighbors(g)
+    u0 = W.random_field(g, 1e-6, seed=3)
+    v0 = W.random_field(g, 1e-3, seed=4)
+    c = g.coords()
+    kind = np.zeros((g.npoints, 2), dtype=np.uint8)
+    val = np.zeros((g.npoints, 2))
+    sel = c[:, 0] < 3
+    kind[sel] = W.BC_DISPLACEMENT
+    val[sel, 0] = 2e-5 * (c[sel, 1] + 1)
+    val[sel, 1] = -1e-5
+    st = O.ExplicitState(g, mat, b, u0, v0, kind, val)
+    st.run(0.5 * O.stable_dt(g, mat, b), 5)
+    assert np.all(st.u[sel] == val[sel])
+    assert np.all(st.v[sel] == 0.0)
+    assert np.all(st.u[~sel] != u0[~sel])
+
+
+@pytest.mark.parametrize("m,cut", [(1, 0), (2, 2)])
+def test_notch_through_a_lattice_point_cuts_only_strict_crossings(m, cut):
+    """A bond crosses the notch plane when its ends lie strictly on opposite
+    sides of it; an end on the plane is not a crossing. Three points on a line,
+    the plane through the middle one: with m = 1 no bond crosses, with m = 2 only
+    the bond from the first to the third point, in both directions."""
+    g = _grid(2, (3, 1, 1), m, h=0.01)
+    b = O.neighbors(g)
+    notch = W.Notch(axis=0, pos=1.0, lo=(0.0, -1.0, 0.0), hi=(0.0, 1.0, 0.0))
+    assert O.break_notch(g, b, notch) == cut
+    c = g.coords()
+    for i in range(g.npoints):
+        for k in range(b.row_ptr[i], b.row_ptr[i + 1]):
+            j = b.col[k]
+            assert bool(b.broken[k]) == ({int(c[i, 0]), int(c[j, 0])} == {0, 2})
+
+
 # ------------------------------------------------------------------ tangent
 
 def test_tangent_structure_and_jvp():
